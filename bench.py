@@ -1,0 +1,296 @@
+"""Benchmark: spaND factor + PCG to a relative residual of 1e-12 on one GB300.
+
+A step is one pass of the whole hot path over the resident problem: the
+numerical factorization (Algorithm 2 with the chosen scheme) followed by PCG
+with the spaND preconditioner from x0 = 0 to ||r||/||b|| < 1e-12.  The default
+workload is the 3D 7-point Poisson problem on a 64^3 grid (n = 262144,
+12 nested-dissection levels, eps = 1e-2, full second-order scheme, RHS
+N(0, 1) from seed 0).  The symbolic analysis (host) and the upload of A
+happen before the timed region; the factor's working set (panel rows of
+~1 GB) is far larger than the 129 MB L2, so no L2 flush is needed between
+steps.
+
+Printed: one JSON line (rank 0).  ``value`` is the device-timed seconds per
+step (CUDA events on the launch stream, max over ranks), ``e2e`` the same
+solve through the host-buffer C-ABI path (analyze + factor + PCG with the
+H2D copy of A and b and the D2H copy of x inside the timed region),
+``roofline`` the dominant kernel's algorithmic FP64 rate against the FP64
+peak, ``cpu_baseline`` the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle instead (the reference arm of this
+build; there is no other implementation of the paper to run).
+
+Multi-GPU: independent problems, one replica per rank (weak scaling, no data
+exchange; the method's own multi-GPU partitioning is not built).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+PCG time to rel. residual 1e-12, CG its; served solves/s, p99 latency"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (the profiling recipe's figure); no measured FP64 peak is provided
+
+WORKLOADS = {
+    # name: (factory, dim, ell, rhs)
+    "poisson3d_64": ("laplacian_3d(64)", 12, "rhs_normal"),
+    "poisson2d_64": ("laplacian_2d(64)", 6, "rhs_uniform"),
+    "diffusion3d_64": ("diffusion_3d(64, seed=0)", 12, "rhs_normal"),
+    "poisson3d_32": ("laplacian_3d(32)", 9, "rhs_normal"),
+}
+
+
+def make_problem(name):
+    import spand_inputs as si
+    expr, ell, rhs = WORKLOADS[name]
+    prob = eval("si." + expr, {"si": si})
+    b = getattr(si, rhs)(prob.n, seed=0)
+    return prob, ell, b
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+                for i, nm in enumerate(names):
+                    if s[3 + i].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(name="poisson3d_32", scheme=1, eps=1e-2):
+    """Time the CPU oracle (factor + PCG) on a bounded sample, single-threaded BLAS."""
+    code = (
+        "import time,sys,json; sys.path.insert(0, %r)\n"
+        "import bench, oracle.spand as OS\n"
+        "prob, ell, b = bench.make_problem(%r)\n"
+        "A = prob.to_scipy(); t0 = time.perf_counter()\n"
+        "F, res = OS.solve(A, prob.coords, b, ell, %r, %d)\n"
+        "t = time.perf_counter() - t0\n"
+        "print(json.dumps({'s': t, 'iters': res.iters, 'relres': res.relres, 'n': prob.n}))\n"
+    ) % (ROOT, name, eps, scheme)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1200)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle, timed per step on a bounded sample."""
+    if rank != 0:
+        return
+    sample = "poisson3d_32"
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not repeated
+    times, last = [], None
+    for _ in range(args.steps):
+        last = oracle_sample(sample, args.scheme, args.eps)
+        times.append(last["s"])
+    prob, _, _ = make_problem(args.workload)
+    scale = prob.n / last["n"]
+    per = sum(times) / len(times)
+    value = per * scale
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "scheme": args.scheme, "eps": args.eps,
+                   "tol": 1e-12, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"oracle factor+PCG on {sample} (n={last['n']}, same leaf size, eps,"
+                                   f" scheme), {per:.2f} s/solve, scaled by n ratio {scale:.0f}"
+                                   " (linear in n: a lower bound for the O(n log n) factor)"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spand", choices=["spand", "reference"])
+    ap.add_argument("--workload", default="poisson3d_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--scheme", type=int, default=1)
+    ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2007_00789_gb300 import spand
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prob, ell, b = make_problem(args.workload)
+    tol = 1e-12
+    stream = torch.cuda.current_stream()
+    h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    iters = rel = None
+    for _ in range(args.warmup):
+        h.factor(stream)
+        iters, rel = h.pcg(bd, xd, tol, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: K steps of factor + PCG, events on the launch stream
+    h.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.factor(stream)
+            iters, rel = h.pcg(bd, xd, tol, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    kstats = h.kernel_stats()
+    h.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = h.info()
+
+    # ---- end to end through the host-buffer path (analyze + factor + PCG, host A/b/x)
+    e2e = None
+    if not args.no_e2e:
+        times = []
+        for i in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme)
+            he.factor(stream)
+            x_host, it_e, rel_e = he.pcg_host(b, tol, stream)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            he.close()
+        h2d = 4 * (prob.n + 1) + 12 * prob.nnz + 8 * prob.nnz + 8 * prob.n
+        d2h = 8 * prob.n + 12 * sum(1 for _ in range(ell))
+        e2e = {"value": min(times[1:] or times), "unit": "s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the dominant kernel (FP64 ALU bound)
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    dom_launch_ms = dom["total_ms"] / max(dom["launches"], 1)
+    achieved = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["total_ms"] > 0 else 0.0
+    roof = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "fallback (profiling recipe's nominal FP64 1.25 TFLOP/s; FP64 is not in the measured peaks)",
+            "avg_launch_ms": dom_launch_ms, "launches_per_step": dom["launches"] / args.steps}
+    launches = sum(k["launches"] for k in kstats) // args.steps
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": prob.n, "nnz": prob.nnz, "nlevels": ell,
+                   "eps": args.eps, "scheme": args.scheme, "tol": tol, "cg_iters": iters,
+                   "relres": rel, "mu": info["mu"], "skip": info["skip"],
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": {k["name"]: {"ms_per_step": k["total_ms"] / args.steps,
+                                "launches_per_step": k["launches"] / args.steps,
+                                "gflop_per_step": k["flops"] / args.steps / 1e9}
+                    for k in kstats if k["launches"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        try:
+            o = oracle_sample("poisson3d_32", args.scheme, args.eps)
+            scale = prob.n / o["n"]
+            line["cpu_baseline"] = {
+                "value": o["s"] * scale, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle factor+PCG on poisson3d_32 (n={o['n']}, ell=9: same 128-vertex leaves,"
+                          f" eps, scheme), {o['s']:.2f} s measured, scaled by n ratio {scale:.0f}"
+                          " (linear in n: a lower bound for the O(n log n) factor)"}
+        except Exception as exc:  # the baseline must not sink the GPU line
+            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {exc}"[:300]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * spand.h -- C ABI of a single-GPU (sm_103a) Sparsified Nested Dissection
+ * preconditioner with first- and second-order sparsification, and the PCG
+ * solver that uses it.
+ *
+ * Method: Klockiewicz, Cambier, Humble, Tchelepi, Darve, "Second Order
+ * Accurate Hierarchical Approximate Factorization of Sparse SPD Matrices",
+ * arXiv 2007.00789.  Section references below are to that paper.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SPAND_OK (0) on success, a negative SPAND_E* code on
+ *     failure.  spand_strerror() turns a code into text; spand_last_error()
+ *     gives a message about the most recent failure in the calling thread.
+ *   - Floating point is IEEE binary64 everywhere.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device (e.g. torch.Tensor.data_ptr()).
+ *   - stream: a cudaStream_t cast to void* (NULL = the legacy default
+ *     stream).  Every device-side effect is ordered on that stream; calls
+ *     that return results to the host (ranks, iteration counts) synchronise
+ *     it before returning.
+ *   - A handle is not thread safe: use one handle from one thread at a time.
+ */
+#ifndef SPAND_H
+#define SPAND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPAND_OK 0
+#define SPAND_EINVAL (-1)   /* bad argument: CSR, coordinates, eps, levels, scheme, sizes */
+#define SPAND_ENOTSPD (-2)  /* a Cholesky pivot was not positive (A is not SPD) */
+#define SPAND_ENOMEM (-3)   /* a device or host allocation failed */
+#define SPAND_ECUDA (-4)    /* a CUDA runtime call failed */
+#define SPAND_ENOCONV (-5)  /* PCG reached maxit; x holds the last iterate */
+#define SPAND_ESTATE (-6)   /* call out of order (e.g. apply before factor) */
+
+/* Sparsification schemes (Algorithm 1 / §2). */
+#define SPAND_FIRST_ORDER 0            /* eq. trailing-1: E dropped */
+#define SPAND_SECOND_ORDER_FULL 1      /* eq. trailing-2: E kept, only E^T E dropped */
+#define SPAND_SECOND_ORDER_SUPERFINE 2 /* eq. trailing-3: only E_2 kept (QR run to eps^2) */
+
+typedef struct spand_s* spand_t;
+
+/* Sparse SPD matrix A (§1, "A x = b, A sparse SPD").  Full symmetric
+ * pattern: both triangles present, column indices ascending within each row,
+ * 0-based int32 indices.  All three arrays are host pointers; analyze copies
+ * what it needs, the caller keeps ownership. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* rowptr; /* n+1 entries, rowptr[0] = 0, rowptr[n] = nnz */
+  const int32_t* colind; /* nnz entries */
+  const double* val;     /* nnz entries */
+} spand_csr;
+
+/* Optional knobs; pass NULL for the defaults shown. */
+typedef struct {
+  int32_t skip;           /* stages without scaling/sparsification; <0 = default
+                             clamp(4 - round(log2((n / 2^(ell-1)) / 25)), 0, ell-2),
+                             i.e. 4 at the paper's ell = round(log2(n/25)) (§4) */
+  int32_t maxit;          /* PCG iteration cap; <=0 = 500 */
+  int32_t true_res_every; /* replace the recursive residual by b - A x every this
+                             many iterations; <=0 = 50 */
+  int32_t max_restarts;   /* PCG restarts when the true residual misses tol; <0 = 2 */
+} spand_opts;
+
+/* Summary of a factorization (§4 notation). */
+typedef struct {
+  int32_t n;
+  int64_t nnz_a;           /* nnz(A) */
+  int64_t nnz_factor;      /* stored entries of L_s, W_s, Z_p, Householder V/tau, E-tilde */
+  double mu;               /* nnz_factor / nnz_a */
+  int32_t nlevels;         /* ell */
+  int32_t skip;
+  int32_t scheme;
+  double eps;
+  int32_t nstages;         /* = nlevels */
+  int32_t nclusters_total; /* sum over stages of the clusters alive at the stage start */
+  int32_t ninterfaces_sparsified;
+  double factor_ms;        /* wall time of the last spand_factor (host clock, synchronised) */
+  double pcg_ms;           /* wall time of the last spand_pcg */
+  int32_t pcg_iters;       /* iterations of the last spand_pcg */
+  double pcg_relres;       /* true relative residual at the end of the last spand_pcg */
+  int64_t kernel_launches; /* kernels launched by the last spand_factor */
+  int64_t device_bytes;    /* device memory held by the handle */
+} spand_stats;
+
+/* Symbolic analysis (the multilevel spaND partitioning of §3, built
+ * geometrically from grid coordinates).  Host-only: A is copied into the
+ * handle and uploaded to the device by the first call that needs it
+ * (spand_factor or spand_matvec), so analyze works without a GPU.
+ *   A       -- the matrix (host arrays, see spand_csr).
+ *   coords  -- host, n x dim row-major coordinates of the unknowns (grid
+ *              coordinates; only their order along each axis matters).
+ *   dim     -- 1..3.
+ *   nlevels -- ell >= 1: nested dissection to depth ell-1, ell stages.
+ *   eps     -- RRQR tolerance in [0, 1] (Algorithm 1); 0 gives an exact block
+ *              Cholesky factorization (§3.2).
+ *   scheme  -- SPAND_FIRST_ORDER / _SECOND_ORDER_FULL / _SECOND_ORDER_SUPERFINE.
+ *   out     -- receives the new handle (owned by the caller; spand_destroy).
+ * Errors: SPAND_EINVAL for a malformed CSR (unsorted or out-of-range columns,
+ * asymmetric pattern, missing diagonal), n < 1, dim out of range, eps outside
+ * [0, 1], nlevels < 1, an empty nested-dissection box, or scheme out of
+ * range.  No device memory is kept on failure. */
+int spand_analyze(const spand_csr* A, const double* coords, int dim, int nlevels,
+                  double eps, int scheme, const spand_opts* opts, spand_t* out);
+
+/* Numerical factorization, Algorithm 2: per level, eliminate interiors
+ * (block Cholesky), scale interfaces (eq. prescale), sparsify interfaces
+ * (Algorithm 1 + the chosen scheme), merge and recurse; the top separator is
+ * factored by dense Cholesky.  May be called again (refactor) on the same
+ * handle.  Synchronises the stream once per level to learn the ranks.
+ * Errors: SPAND_ENOTSPD (the handle stays valid but unfactored),
+ * SPAND_ENOMEM, SPAND_ECUDA. */
+int spand_factor(spand_t h, void* stream);
+
+/* z = M r with M = L^{-T} L^{-1} (Algorithm 2 caption).  r and z are device
+ * arrays of n doubles; they may alias.  Requires a successful spand_factor,
+ * else SPAND_ESTATE. */
+int spand_apply(spand_t h, const double* r, double* z, void* stream);
+
+/* Preconditioned CG on A x = b with M as preconditioner, x0 = 0, stopping
+ * when ||r_k||_2 / ||b||_2 < tol (§4).  b and x are device arrays of n
+ * doubles (x is overwritten).  iters and relres (host, may be NULL) receive
+ * the iteration count and the true relative residual ||b - A x|| / ||b||.
+ * Returns SPAND_ENOCONV if maxit is reached. */
+int spand_pcg(spand_t h, const double* b, double* x, double tol, int32_t* iters,
+              double* relres, void* stream);
+
+/* Same as spand_pcg with HOST arrays b and x: the host->device copy of b
+ * and the device->host copy of x are part of the call. */
+int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol,
+                   int32_t* iters, double* relres, void* stream);
+
+/* y = A x with the uploaded A (device arrays of n doubles). */
+int spand_matvec(spand_t h, const double* x, double* y, void* stream);
+
+/* Factorization summary; s is a host struct filled by the call. */
+int spand_info(spand_t h, spand_stats* s);
+
+/* Ranks decided by Algorithm 1, for parity checks.  For every stage k in
+ * 0..ell-1 and every cluster alive at the start of stage k (in cluster-id
+ * order), out[] receives three int32: the cluster's size at the start of the
+ * stage, its coarse rank (-1 when the stage does not sparsify or the cluster
+ * is an interior) and near-tie flags of its pivoted QR (bit 0: at some step
+ * the two largest candidate column norms were within 1e-12 relative; bit 1:
+ * a step's norm was within 1e-10 relative of the eps threshold; there, a
+ * differently rounded correct implementation may choose another pivot or
+ * rank).  *count receives the number of clusters; if cap (in clusters) is too
+ * small nothing is written and SPAND_EINVAL is returned with *count set.
+ * Host pointers.  Requires a successful spand_factor (else SPAND_ESTATE). */
+int spand_ranks(spand_t h, int32_t* out, int64_t cap, int64_t* count);
+
+/* Cluster id of every vertex at stage k (-1 for vertices already
+ * eliminated); out is a host array of n int32.  Available after analyze. */
+int spand_cluster_map(spand_t h, int stage, int32_t* out);
+
+/* Number of stages (ell) and of clusters alive at the start of stage k. */
+int spand_num_clusters(spand_t h, int stage, int32_t* nclusters);
+
+/* Per-kernel timing, for roofline measurements.  When enabled, every launch
+ * group of spand_factor / spand_apply / spand_pcg is bracketed by CUDA events
+ * on the caller's stream; the elapsed times are accumulated per kernel kind
+ * together with the kind's algorithmic work (FLOPs and bytes counted on the
+ * host from the task sizes, e.g. m^3/3 per Cholesky, 6 (m-t)(N-t) per QR step).
+ * Enabling or disabling clears the accumulated statistics. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double flops;
+  double bytes;
+} spand_kernel_stat;
+
+int spand_set_profiling(spand_t h, int on);
+/* out: host array of cap entries; *count receives the number of kernel kinds. */
+int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count);
+
+/* Frees every device and host resource of the handle.  NULL is ignored. */
+void spand_destroy(spand_t h);
+
+const char* spand_strerror(int code);
+const char* spand_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAND_H */

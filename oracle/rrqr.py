@@ -19,6 +19,11 @@ them, so these are the readings this project fixes):
 * reflector: x = R[t:, j], alpha = x[0], beta = -sign(alpha) ||x|| with
   sign(0) = +1, tau = (beta - alpha) / beta, v = x / (alpha - beta), v[0] = 1;
   a zero x gives tau = 0 (H = I);
+* a step is flagged as a near tie when the two largest candidate norms
+  differ by at most 1e-12 relative (bit 0 of ``flags``), or when nu_t^2 lies
+  within 1e-10 relative of a stopping threshold (bit 1).  There, rounding
+  differences between two correct implementations may pick another pivot or
+  rank, so parity is judged on the preconditioner's quality instead;
 * columns are never physically swapped: the result R is ``Q^T A_pw`` in the
   original column order, i.e. ``R Pi`` of the paper.  Its first r rows are
   ``Q_c^T A_pw = (R_cc R_cf) Pi^T`` and rows r..m-1 are
@@ -43,6 +48,7 @@ class RRQRResult:
     tau: np.ndarray  # nref
     R: np.ndarray  # m x N, Q^T A_pw in original column order
     piv: np.ndarray  # nref pivot columns, in step order
+    flags: int = 0  # bit 0: pivot near tie, bit 1: threshold near tie
 
 
 def rrqr(A: np.ndarray, eps: float, scheme: int = SECOND_ORDER_FULL) -> RRQRResult:
@@ -55,17 +61,25 @@ def rrqr(A: np.ndarray, eps: float, scheme: int = SECOND_ORDER_FULL) -> RRQRResu
     Vcols, taus, pivs = [], [], []
     r = None
     nu0sq = 0.0
+    flags = 0
     for t in range(min(m, N)):
         cand = np.nonzero(~pivoted)[0]
         normsq = np.sum(R[t:, cand] ** 2, axis=0)
         j_local = int(np.argmax(normsq))  # first maximum -> lowest column index
         j = int(cand[j_local])
         nusq = float(normsq[j_local])
+        if normsq.size > 1 and nusq > 0.0:
+            second = float(np.max(np.delete(normsq, j_local)))
+            if nusq - second <= 1e-12 * nusq:
+                flags |= 1
         if t == 0:
             nu0sq = nusq
             if nu0sq == 0.0:
                 r = 0
                 break
+        for thr in ((thr1, thr2) if scheme == SECOND_ORDER_SUPERFINE else (thr1,)):
+            if abs(nusq - thr * nu0sq) <= 1e-10 * thr * nu0sq:
+                flags |= 2
         if r is None and nusq < thr1 * nu0sq:
             r = t
             if scheme != SECOND_ORDER_SUPERFINE:
@@ -100,7 +114,7 @@ def rrqr(A: np.ndarray, eps: float, scheme: int = SECOND_ORDER_FULL) -> RRQRResu
         r = nref
     V = np.stack(Vcols, axis=1) if nref else np.zeros((m, 0))
     return RRQRResult(r=r, nref=nref, V=V, tau=np.array(taus, dtype=np.float64), R=R,
-                      piv=np.array(pivs, dtype=np.int64))
+                      piv=np.array(pivs, dtype=np.int64), flags=flags)
 
 
 def apply_qt(V: np.ndarray, tau: np.ndarray, z: np.ndarray) -> np.ndarray:

@@ -98,6 +98,7 @@ class Factor:
     stage_sizes: list = field(default_factory=list)
     stage_ranks: list = field(default_factory=list)
     stage_colours: list = field(default_factory=list)
+    stage_flags: list = field(default_factory=list)  # {interface key: near-tie flags}
     stage_keys: list = field(default_factory=list)
 
     def nnz_factor(self) -> int:
@@ -211,6 +212,7 @@ def factor(A, coords, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
 
         ranks = {}
         colours = {}
+        flags = {}
         if skip <= k < nlevels - 1 and keys:
             # 2. scale interfaces
             Z = {p: _chol(B[(p, p)], f"interface {p}") for p in keys}
@@ -249,8 +251,10 @@ def factor(A, coords, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
                                  Et=fine_block(res, scheme).copy(), wslots=wslots))
                 slots[p] = slots[p][:r]
                 ranks[p] = r
+                flags[p] = res.flags
         F.stage_ranks.append(ranks)
         F.stage_colours.append(colours)
+        F.stage_flags.append(flags)
 
         if k == nlevels - 1:
             assert not keys, "the last stage must eliminate everything"

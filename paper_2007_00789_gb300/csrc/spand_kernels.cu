@@ -1,0 +1,507 @@
+// Batched dense kernels of the spaND factorization (FP64, sm_103a).
+//
+// All blocks live in "panel rows": cluster c owns an m_c x ncols_c
+// column-major array (ld = m_c) holding its blocks A_cd for d in its
+// neighbour list (and itself), ordered by cluster id.  Every kernel below is
+// batched over a task array built by the host for one step of Algorithm 2
+// (§3): one CTA per task, variable sizes, no atomics, so results do not
+// depend on scheduling.
+#include <cstdio>
+
+#include "spand_internal.h"
+
+namespace spand {
+
+namespace {
+
+constexpr int kWarp = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Copies and scatters.
+// ---------------------------------------------------------------------------
+__global__ void k_copy(const CopyTask* __restrict__ tasks) {
+  const CopyTask t = tasks[blockIdx.x];
+  const int total = t.rows * t.cols;
+  if (!t.trans) {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int i = e % t.rows, j = e / t.rows;
+      t.dst[i + (size_t)j * t.dst_ld] = t.src[i + (size_t)j * t.src_ld];
+    }
+  } else {
+    // read src (cols x rows) along its columns, write dst transposed
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int j = e % t.cols, i = e / t.cols;
+      t.dst[i + (size_t)j * t.dst_ld] = t.src[j + (size_t)i * t.src_ld];
+    }
+  }
+}
+
+__global__ void k_scatter(const double* __restrict__ val, const int64_t* __restrict__ dst,
+                          double* __restrict__ base_lo, double* __restrict__ base_hi,
+                          int64_t split, int64_t nnz) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = dst[e];
+    if (d < 0) continue;
+    if (d < split) base_lo[d] = val[e];
+    else base_hi[d - split] = val[e];
+  }
+}
+
+__global__ void k_set_identity(const PotrfTask* __restrict__ tasks) {
+  const PotrfTask t = tasks[blockIdx.x];
+  const int total = t.m * t.m;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = e % t.m, j = e / t.m;
+    t.a[i + (size_t)j * t.ld] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched Cholesky A = L L^T (lower), in place.  Right-looking, one column
+// per step; the block is staged in shared memory when it fits.
+// ---------------------------------------------------------------------------
+__device__ void potrf_body(double* a, int m, int ld, int id, int* err, double* s_inv,
+                           int* s_fail) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const double d = a[j + (size_t)j * ld];
+      if (!(d > 0.0)) {
+        *s_fail = 1;
+        if (err) atomicCAS(err, 0, id + 1);
+      } else {
+        const double sq = sqrt(d);
+        a[j + (size_t)j * ld] = sq;
+        *s_inv = 1.0 / sq;
+      }
+    }
+    __syncthreads();
+    if (*s_fail) return;
+    const double inv = *s_inv;
+    for (int i = j + 1 + tid; i < m; i += nt) a[i + (size_t)j * ld] *= inv;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < m; c += nw) {
+      const double lc = a[c + (size_t)j * ld];
+      double* col = a + (size_t)c * ld;
+      const double* lj = a + (size_t)j * ld;
+      for (int r = c + lane; r < m; r += kWarp) col[r] -= lj[r] * lc;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_cap) {
+  extern __shared__ double sm[];
+  __shared__ double s_inv;
+  __shared__ int s_fail;
+  const PotrfTask t = tasks[blockIdx.x];
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  const int m = t.m;
+  if (m == 0) return;
+  if (m * m <= smem_cap) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      sm[e] = (i >= j) ? t.a[i + (size_t)j * t.ld] : 0.0;
+    }
+    __syncthreads();
+    potrf_body(sm, m, m, t.id, err, &s_inv, &s_fail);
+    __syncthreads();
+    if (s_fail) return;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      t.a[i + (size_t)j * t.ld] = sm[e];
+    }
+  } else {
+    potrf_body(t.a, m, t.ld, t.id, err, &s_inv, &s_fail);
+    __syncthreads();
+    if (s_fail) return;
+    // zero the strict upper triangle so the block is exactly L
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      if (i < j) t.a[i + (size_t)j * t.ld] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched triangular solve with a lower factor, 32 right-hand sides per CTA
+// (one warp, one right-hand side per lane, dot-product form).
+// ---------------------------------------------------------------------------
+constexpr int kTrsmNC = 32;
+
+__global__ void k_trsm(const TrsmTask* __restrict__ tasks, int smem_rows) {
+  extern __shared__ double sm[];  // smem_rows x kTrsmNC
+  const TrsmTask t = tasks[blockIdx.x];
+  const int m = t.m, nc = t.ncols;
+  const int c = threadIdx.x;
+  if (m == 0 || nc == 0) return;
+  const double* L = t.L;
+  const size_t ldl = t.ldl;
+  if (m <= smem_rows) {
+    // stage the right-hand sides: xs[i * NC + c]
+    if (!t.trans) {
+      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+        const int i = e % m, cc = e / m;
+        sm[i * kTrsmNC + cc] = t.X[i + (size_t)cc * t.ldx];
+      }
+    } else {
+      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+        const int cc = e % nc, i = e / nc;
+        sm[i * kTrsmNC + cc] = t.X[cc + (size_t)i * t.ldx];
+      }
+    }
+    __syncwarp();
+    if (c < nc) {
+      for (int i = 0; i < m; ++i) {
+        double s = sm[i * kTrsmNC + c];
+        const double* Li = L + i;
+        for (int j = 0; j < i; ++j) s -= Li[j * ldl] * sm[j * kTrsmNC + c];
+        sm[i * kTrsmNC + c] = s / Li[i * ldl];
+      }
+    }
+    __syncwarp();
+    if (!t.trans) {
+      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+        const int i = e % m, cc = e / m;
+        t.X[i + (size_t)cc * t.ldx] = sm[i * kTrsmNC + cc];
+      }
+    } else {
+      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+        const int cc = e % nc, i = e / nc;
+        t.X[cc + (size_t)i * t.ldx] = sm[i * kTrsmNC + cc];
+      }
+    }
+  } else if (c < nc) {
+    // large factor: solve in place in global memory
+    double* x = t.trans ? t.X + c : t.X + (size_t)c * t.ldx;
+    const size_t inc = t.trans ? (size_t)t.ldx : 1;
+    for (int i = 0; i < m; ++i) {
+      double s = x[i * inc];
+      const double* Li = L + i;
+      for (int j = 0; j < i; ++j) s -= Li[j * ldl] * x[j * inc];
+      x[i * inc] = s / Li[i * ldl];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Schur-complement tiles: T -= sum_c A_c^T B_c (K-chunks staged in smem),
+// written back to the target block and, transposed, to its mirror.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 32;
+constexpr int kKc = 32;
+
+__global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ tiles,
+                                               const SchurContrib* __restrict__ contribs) {
+  __shared__ double As[kKc][kTile + 1];
+  __shared__ double Bs[kKc][kTile + 1];
+  const SchurTile t = tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int ti = tid & 31;        // output row
+  const int tj = (tid >> 5) * 4;  // first of 4 output columns
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int ci = t.cbegin; ci < t.cend; ++ci) {
+    const SchurContrib c = contribs[ci];
+    const double* ca = c.a + (size_t)t.i0 * c.lda;
+    const double* cb = c.b + (size_t)t.j0 * c.ldb;
+    for (int k0 = 0; k0 < c.K; k0 += kKc) {
+      const int kk = min(kKc, c.K - k0);
+      for (int e = tid; e < kKc * kTile; e += 256) {
+        const int k = e % kKc, i = e / kKc;
+        As[k][i] = (k < kk && i < t.rows) ? ca[(k0 + k) + (size_t)i * c.lda] : 0.0;
+        Bs[k][i] = (k < kk && i < t.cols) ? cb[(k0 + k) + (size_t)i * c.ldb] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kKc; ++k) {
+        const double a = As[k][ti];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += a * Bs[k][tj + q];
+      }
+      __syncthreads();
+    }
+  }
+  if (ti < t.rows) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = tj + q;
+      if (j < t.cols) {
+        double* d = t.dst + ti + (size_t)j * t.ld;
+        const double v = *d - acc[q];
+        *d = v;
+        if (t.mirror) t.mirror[j + (size_t)ti * t.ld_mirror] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched early-stopping column-pivoted Householder QR (Algorithm 1), one CTA
+// per interface, in place on the interface's panel row.  Columns are never
+// swapped: the row ends up holding Q^T A_pw in the original column order
+// (coarse rows 0..r-1, E below).  Pivot: largest squared trailing norm,
+// recomputed at every step, ties to the lowest column; step t is taken while
+// nu_t^2 >= eps^2 nu_0^2 (the superfine scheme continues to eps^4 nu_0^2).
+// Afterwards the coarse rows are mirrored into the neighbours' rows, the
+// diagonal block becomes I_r and cur_size[p] = r.
+// ---------------------------------------------------------------------------
+constexpr int kQrThreads = 256;
+
+struct ArgMax {
+  double v;
+  int i;
+};
+
+__device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i && b.i >= 0)) return b;
+  return a;
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+    k_rrqr(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
+           int* __restrict__ cur_size, int* __restrict__ rank_out, int* __restrict__ nref_out,
+           int* __restrict__ flag_out, double eps, int scheme) {
+  extern __shared__ double sm[];
+  __shared__ ArgMax s_red[kQrThreads / kWarp];
+  __shared__ double s_sec[kQrThreads / kWarp];
+  const RRQRTask t = tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
+  const int m = t.m;
+  const size_t ld = t.ld;
+  double* norms = sm;                             // ncols_max
+  double* v = norms + t.ncols_max;                // m
+  int* cols = reinterpret_cast<int*>(v + m);      // ncols_max
+  int* segoff = cols + t.ncols_max;               // nseg + 1
+  const int nseg = t.seg_end - t.seg_begin;
+  if (tid == 0) {
+    int acc = 0;
+    for (int s = 0; s < nseg; ++s) {
+      segoff[s] = acc;
+      acc += cur_size[segs[t.seg_begin + s].cl];
+    }
+    segoff[nseg] = acc;
+  }
+  __syncthreads();
+  const int N = segoff[nseg];
+  for (int s = 0; s < nseg; ++s) {
+    const int base = segs[t.seg_begin + s].col, o = segoff[s], w = segoff[s + 1] - o;
+    for (int c = tid; c < w; c += kQrThreads) cols[o + c] = base + c;
+  }
+  __syncthreads();
+  // initial squared column norms
+  for (int c = warp; c < N; c += nw) {
+    const double* col = t.A + (size_t)cols[c] * ld;
+    double s = 0.0;
+    for (int i = lane; i < m; i += kWarp) s += col[i] * col[i];
+    s = warp_sum(s);
+    if (lane == 0) norms[c] = s;
+  }
+  __syncthreads();
+  const double thr1 = eps * eps;
+  const double thr2 = thr1 * thr1;
+  const int maxsteps = min(m, N);
+  int r = -1, nsteps = 0, flags = 0;
+  double nu0sq = 0.0;
+  for (int step = 0; step < maxsteps; ++step) {
+    // argmax over non-pivoted columns (pivoted ones hold -1)
+    ArgMax best{-1.0, -1};
+    for (int c = tid; c < N; c += kQrThreads) best = better(best, ArgMax{norms[c], c});
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMax other{__shfl_xor_sync(0xffffffffu, best.v, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+      best = better(best, other);
+    }
+    if (lane == 0) s_red[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+      ArgMax b = s_red[0];
+      for (int w = 1; w < nw; ++w) b = better(b, s_red[w]);
+      s_red[0] = b;
+    }
+    __syncthreads();
+    best = s_red[0];
+    __syncthreads();
+    const double nusq = best.v;
+    // second largest candidate norm, for the near-tie flag
+    {
+      double sec = -1.0;
+      for (int c = tid; c < N; c += kQrThreads)
+        if (c != best.i) sec = fmax(sec, norms[c]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sec = fmax(sec, __shfl_xor_sync(0xffffffffu, sec, o));
+      if (lane == 0) s_sec[warp] = sec;
+      __syncthreads();
+      if (tid == 0) {
+        double m2 = -1.0;
+        for (int w = 0; w < nw; ++w) m2 = fmax(m2, s_sec[w]);
+        if (m2 >= 0.0 && nusq > 0.0 && nusq - m2 <= 1e-12 * nusq) flags |= 1;
+      }
+      __syncthreads();
+    }
+    if (step == 0) {
+      nu0sq = nusq;
+      if (nu0sq == 0.0) {
+        r = 0;
+        break;
+      }
+    }
+    if (tid == 0) {
+      if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
+      if (scheme == SPAND_SECOND_ORDER_SUPERFINE && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq)
+        flags |= 2;
+    }
+    if (r < 0 && nusq < thr1 * nu0sq) {
+      r = step;
+      if (scheme != SPAND_SECOND_ORDER_SUPERFINE) break;
+    }
+    if (scheme == SPAND_SECOND_ORDER_SUPERFINE && nusq < thr2 * nu0sq) break;
+    double* pc = t.A + (size_t)cols[best.i] * ld;
+    const double alpha = pc[step];
+    const double normx = sqrt(nusq);
+    double beta, tau;
+    if (normx == 0.0) {
+      beta = alpha;
+      tau = 0.0;
+    } else {
+      beta = alpha >= 0.0 ? -normx : normx;
+      tau = (beta - alpha) / beta;
+    }
+    const double den = alpha - beta;
+    for (int i = tid; i < m; i += kQrThreads) {
+      double vi;
+      if (i < step) vi = 0.0;
+      else if (i == step) vi = 1.0;
+      else vi = (normx == 0.0) ? 0.0 : pc[i] / den;
+      v[i] = vi;
+      t.V[i + (size_t)step * m] = vi;
+    }
+    if (tid == 0) {
+      t.tau[step] = tau;
+      norms[best.i] = -1.0;
+    }
+    __syncthreads();
+    for (int i = step + tid; i < m; i += kQrThreads) pc[i] = (i == step) ? beta : 0.0;
+    // apply H_step to the other non-pivoted columns; refresh their norms
+    for (int c = warp; c < N; c += nw) {
+      if (norms[c] < 0.0) continue;
+      double* col = t.A + (size_t)cols[c] * ld;
+      double d = 0.0;
+      for (int i = step + lane; i < m; i += kWarp) d += v[i] * col[i];
+      d = warp_sum(d);
+      const double f = tau * d;
+      double s = 0.0;
+      for (int i = step + lane; i < m; i += kWarp) {
+        const double a = col[i] - f * v[i];
+        col[i] = a;
+        if (i > step) s += a * a;
+      }
+      s = warp_sum(s);
+      if (lane == 0) norms[c] = s;
+    }
+    __syncthreads();
+    nsteps = step + 1;
+  }
+  if (r < 0) r = nsteps;
+  if (tid == 0) {
+    rank_out[t.id] = r;
+    nref_out[t.id] = nsteps;
+    flag_out[t.id] = flags;
+  }
+  __syncthreads();
+  // coarse rows -> neighbours' rows (transposed), diagonal block -> I_r
+  for (int s = 0; s < nseg; ++s) {
+    const RRQRSeg g = segs[t.seg_begin + s];
+    const int w = segoff[s + 1] - segoff[s];
+    const int tot = w * r;
+    for (int e = tid; e < tot; e += kQrThreads) {
+      const int i = e % r, c = e / r;
+      g.mirror[c + (size_t)i * g.mirror_ld] = t.A[i + (size_t)(g.col + c) * ld];
+    }
+  }
+  for (int e = tid; e < r * r; e += kQrThreads) {
+    const int i = e % r, j = e / r;
+    t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) cur_size[t.id] = r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory per CTA we allow
+
+static void set_smem(const void* fn, int bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s) {
+  if (ntasks > 0) k_copy<<<ntasks, 256, 0, s>>>(t);
+}
+
+void launch_scatter(const double* val, const int64_t* dst_index, double* base_lo,
+                    double* base_hi, int64_t split, int64_t nnz, cudaStream_t s) {
+  if (nnz <= 0) return;
+  const int64_t nb = std::min<int64_t>((nnz + 255) / 256, 152 * 32);
+  k_scatter<<<(int)nb, 256, 0, s>>>(val, dst_index, base_lo, base_hi, split, nnz);
+}
+
+void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s) {
+  if (ntasks > 0) k_set_identity<<<ntasks, 256, 0, s>>>(t);
+}
+
+void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  int cap = max_m * max_m;
+  int bytes = cap * (int)sizeof(double);
+  if (bytes > kSmemBudget) {
+    cap = kSmemBudget / (int)sizeof(double);
+    bytes = kSmemBudget;
+  }
+  set_smem((const void*)k_potrf, bytes);
+  k_potrf<<<ntasks, 256, bytes, s>>>(t, err, cap);
+}
+
+void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  int rows = max_m;
+  int bytes = rows * kTrsmNC * (int)sizeof(double);
+  if (bytes > kSmemBudget) {
+    rows = kSmemBudget / (kTrsmNC * (int)sizeof(double));
+    bytes = rows * kTrsmNC * (int)sizeof(double);
+  }
+  set_smem((const void*)k_trsm, bytes);
+  k_trsm<<<ntasks, kTrsmNC, bytes, s>>>(t, rows);
+}
+
+void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s) {
+  if (ntiles > 0) k_schur<<<ntiles, 256, 0, s>>>(tiles, c);
+}
+
+int rrqr_smem_bytes(int max_m, int max_cols, int max_segs) {
+  // norms (double) + v (double) + cols (int) + segoff (int)
+  return max_cols * 8 + max_m * 8 + max_cols * 4 + (max_segs + 2) * 4;
+}
+
+void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
+                 int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
+                 int max_cols, int max_segs, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const int bytes = rrqr_smem_bytes(max_m, max_cols, max_segs);
+  set_smem((const void*)k_rrqr, bytes);
+  k_rrqr<<<ntasks, kQrThreads, bytes, s>>>(t, segs, cur_size, rank_out, nref_out, flag_out, eps,
+                                            scheme);
+}
+
+}  // namespace spand

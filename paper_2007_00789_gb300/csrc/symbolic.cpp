@@ -1,0 +1,281 @@
+// Symbolic phase of spaND on grid problems (host, C++).
+//
+// Builds the multilevel partition that the spaND algorithm (§3) runs on:
+// geometric nested dissection of the coordinate box, then, for every stage
+// k, the clusters alive at the stage start (interiors = the level-k
+// separators or leaves, interfaces = pieces of the higher separators), their
+// block adjacency before and after the interior eliminations (fill), a greedy
+// colouring of the interfaces for the sparsification order, and the merge map
+// to stage k+1.
+//
+// Partition rule.  The node at depth d cuts coordinate (d mod dim) at the
+// floor(cnt/2)-th smallest distinct coordinate value of its box; the vertices
+// on the cut are its separator (level nlevels-1-d), the others go to the lower
+// (2i+1) or upper (2i+2) child; leaves are at depth nlevels-1 (level 0).  At
+// stage k a vertex of level m > k on the separator of node S is keyed by a
+// walk down S's lower subtree through the nodes of depth < nlevels-1-k: cuts
+// parallel to S send the walk to the upper child unrecorded; other cuts record
+// the comparison (0 below, 1 on, 2 above), go down on 0 / 2 and stop on 1.
+// Clusters are the distinct (S, key) pairs, numbered in lexicographic order.
+// The key is packed two bits per depth, most significant first, so that
+// numeric order of (S, packed key) is that lexicographic order.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <unordered_map>
+
+#include "spand_internal.h"
+
+namespace spand {
+
+static inline int node_depth(int i) { return 31 - __builtin_clz((unsigned)(i + 1)); }
+
+int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err) {
+  t.n = n;
+  t.dim = dim;
+  t.nlevels = nlevels;
+  t.coords.assign(coords, coords + (size_t)n * dim);
+  const int dmax = nlevels - 1;
+  const int nint = (1 << dmax) - 1;
+  t.cut_dim.assign(std::max(nint, 1), -1);
+  t.cut_val.assign(std::max(nint, 1), 0.0);
+  t.node_of.assign(n, -1);
+  t.level_of.assign(n, -1);
+  std::vector<int> verts(n);
+  std::iota(verts.begin(), verts.end(), 0);
+  // frontier of (node, [begin, end) in a vertex buffer)
+  struct Box { int node, b, e; };
+  std::vector<Box> frontier{{0, 0, n}}, next;
+  std::vector<int> buf(n), lo, eq, hi;
+  std::vector<double> vals;
+  for (int depth = 0; depth <= dmax; ++depth) {
+    next.clear();
+    for (const Box& bx : frontier) {
+      if (bx.e <= bx.b) {
+        err = "empty nested-dissection box at node " + std::to_string(bx.node);
+        return SPAND_EINVAL;
+      }
+      if (depth == dmax) {
+        for (int i = bx.b; i < bx.e; ++i) {
+          t.node_of[verts[i]] = bx.node;
+          t.level_of[verts[i]] = 0;
+        }
+        continue;
+      }
+      const int c = depth % dim;
+      vals.clear();
+      for (int i = bx.b; i < bx.e; ++i) vals.push_back(coords[(size_t)verts[i] * dim + c]);
+      std::sort(vals.begin(), vals.end());
+      vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+      const double cut = vals[vals.size() / 2];
+      t.cut_dim[bx.node] = c;
+      t.cut_val[bx.node] = cut;
+      lo.clear();
+      hi.clear();
+      for (int i = bx.b; i < bx.e; ++i) {
+        const int v = verts[i];
+        const double x = coords[(size_t)v * dim + c];
+        if (x < cut) lo.push_back(v);
+        else if (x > cut) hi.push_back(v);
+        else {
+          t.node_of[v] = bx.node;
+          t.level_of[v] = dmax - depth;
+        }
+      }
+      // lower child's vertices, then upper child's, reuse the slice [b, e)
+      int p = bx.b;
+      for (int v : lo) verts[p++] = v;
+      const int mid = p;
+      for (int v : hi) verts[p++] = v;
+      next.push_back({2 * bx.node + 1, bx.b, mid});
+      next.push_back({2 * bx.node + 2, mid, p});
+    }
+    frontier.swap(next);
+  }
+  (void)buf;
+  (void)eq;
+  return SPAND_OK;
+}
+
+// Packed cluster key of vertex v at stage k (0 for interiors).
+static uint64_t vertex_key(const Tree& t, int v, int k) {
+  const int ell = t.nlevels;
+  const int node = t.node_of[v];
+  if (t.level_of[v] <= k) return 0;
+  uint64_t key = 0;
+  const int sdim = t.cut_dim[node];
+  const int limit = ell - 1 - k;
+  int cur = 2 * node + 1;
+  while (node_depth(cur) < limit) {
+    const int cd = t.cut_dim[cur];
+    if (cd == sdim) {
+      cur = 2 * cur + 2;
+      continue;
+    }
+    const double x = t.coords[(size_t)v * t.dim + cd];
+    const double cv = t.cut_val[cur];
+    const int cmp = x < cv ? 0 : (x > cv ? 2 : 1);
+    const int d = node_depth(cur);
+    key |= (uint64_t)(cmp + 1) << (2 * (ell - 1 - d));
+    if (cmp == 1) break;
+    cur = cmp == 0 ? 2 * cur + 1 : 2 * cur + 2;
+  }
+  return key;
+}
+
+int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
+  const int n = t.n;
+  std::vector<std::pair<std::pair<int, uint64_t>, int>> items;
+  items.reserve(n);
+  for (int v = 0; v < n; ++v)
+    if (t.level_of[v] >= k) items.push_back({{t.node_of[v], vertex_key(t, v, k)}, v});
+  std::sort(items.begin(), items.end());
+  cl.assign(n, -1);
+  int ncl = -1;
+  if (level_of_cluster) level_of_cluster->clear();
+  for (size_t i = 0; i < items.size(); ++i) {
+    if (i == 0 || items[i].first != items[i - 1].first) {
+      ++ncl;
+      if (level_of_cluster) level_of_cluster->push_back(t.level_of[items[i].second]);
+    }
+    cl[items[i].second] = ncl;
+  }
+  return ncl + 1;
+}
+
+static void add_edge(std::vector<std::vector<int>>& adj, int a, int b) {
+  if (a == b) return;
+  adj[a].push_back(b);
+  adj[b].push_back(a);
+}
+
+static void sort_unique(std::vector<std::vector<int>>& adj) {
+  for (auto& v : adj) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+}
+
+int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
+                 std::vector<StageSym>& st, std::string& err) {
+  const int ell = t.nlevels;
+  const int n = t.n;
+  st.assign(ell, StageSym());
+  std::vector<int> cl_prev, cl;
+  for (int k = 0; k < ell; ++k) {
+    StageSym& S = st[k];
+    S.ncl = cluster_map(t, k, cl, &S.level);
+    S.interior.assign(S.ncl, 0);
+    for (int c = 0; c < S.ncl; ++c) {
+      if (S.level[c] == k) {
+        S.interior[c] = 1;
+        S.interiors.push_back(c);
+      } else {
+        S.ifaces.push_back(c);
+      }
+    }
+    S.sparsify = (k >= skip) && (k < ell - 1);
+    S.adj0.assign(S.ncl, {});
+    if (k == 0) {
+      S.members0.assign(S.ncl, {});
+      for (int v = 0; v < n; ++v) S.members0[cl[v]].push_back(v);
+      for (int i = 0; i < n; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+          const int a = cl[i], b = cl[colind[e]];
+          if (a != b) S.adj0[a].push_back(b);
+        }
+      sort_unique(S.adj0);
+    } else {
+      StageSym& P = st[k - 1];
+      S.children.assign(S.ncl, {});
+      for (int p : P.ifaces) S.children[P.parent[p]].push_back(p);
+      for (int p : P.ifaces) {
+        const int a = P.parent[p];
+        for (int q : P.adj1[p]) {
+          const int b = P.parent[q];
+          if (a != b) S.adj0[a].push_back(b);
+        }
+      }
+      sort_unique(S.adj0);
+    }
+    for (int s : S.interiors)
+      for (int q : S.adj0[s])
+        if (S.interior[q]) {
+          err = "interiors of stage " + std::to_string(k) + " touch each other";
+          return SPAND_EINVAL;
+        }
+    // adjacency among interfaces after eliminating the interiors (fill)
+    S.adj1.assign(S.ncl, {});
+    for (int p : S.ifaces)
+      for (int q : S.adj0[p])
+        if (!S.interior[q]) S.adj1[p].push_back(q);
+    for (int s : S.interiors) {
+      const auto& N = S.adj0[s];
+      for (size_t a = 0; a < N.size(); ++a)
+        for (size_t b = a + 1; b < N.size(); ++b) add_edge(S.adj1, N[a], N[b]);
+    }
+    sort_unique(S.adj1);
+    // greedy colouring of the interface graph in id order
+    S.colour.assign(S.ncl, -1);
+    S.ncolours = 0;
+    std::vector<int> mark;
+    for (int p : S.ifaces) {
+      mark.assign(S.adj1[p].size() + 1, 0);
+      for (int q : S.adj1[p])
+        if (S.colour[q] >= 0 && S.colour[q] < (int)mark.size()) mark[S.colour[q]] = 1;
+      int c = 0;
+      while (mark[c]) ++c;
+      S.colour[p] = c;
+      S.ncolours = std::max(S.ncolours, c + 1);
+    }
+    S.by_colour.assign(S.ncolours, {});
+    for (int p : S.ifaces) S.by_colour[S.colour[p]].push_back(p);
+    // panel-row block lists
+    S.rowsegs.assign(S.ncl, {});
+    for (int c = 0; c < S.ncl; ++c) {
+      auto& rs = S.rowsegs[c];
+      rs = S.interior[c] ? S.adj0[c] : S.adj1[c];
+      rs.insert(std::lower_bound(rs.begin(), rs.end(), c), c);
+    }
+    // Schur targets (q >= r) and their contributing interiors
+    {
+      std::vector<std::pair<int64_t, int>> pairs;
+      for (int s : S.interiors) {
+        const auto& N = S.adj0[s];
+        for (size_t a = 0; a < N.size(); ++a)
+          for (size_t b = 0; b <= a; ++b)
+            pairs.push_back({(int64_t)N[a] * S.ncl + N[b], s});
+      }
+      std::sort(pairs.begin(), pairs.end());
+      S.schur_q.clear();
+      S.schur_r.clear();
+      S.schur_ptr.assign(1, 0);
+      S.schur_s.clear();
+      for (size_t i = 0; i < pairs.size(); ++i) {
+        if (i == 0 || pairs[i].first != pairs[i - 1].first) {
+          if (i > 0) S.schur_ptr.push_back((int)S.schur_s.size());
+          S.schur_q.push_back((int)(pairs[i].first / S.ncl));
+          S.schur_r.push_back((int)(pairs[i].first % S.ncl));
+        }
+        S.schur_s.push_back(pairs[i].second);
+      }
+      if (!pairs.empty()) S.schur_ptr.push_back((int)S.schur_s.size());
+    }
+    // parents at stage k+1
+    S.parent.assign(S.ncl, -1);
+    if (k + 1 < ell) {
+      std::vector<int> cl_next;
+      cluster_map(t, k + 1, cl_next, nullptr);
+      std::vector<int> first(S.ncl, -1);
+      for (int v = 0; v < n; ++v)
+        if (cl[v] >= 0 && first[cl[v]] < 0) first[cl[v]] = v;
+      for (int p : S.ifaces) S.parent[p] = cl_next[first[p]];
+    } else if (!S.ifaces.empty()) {
+      err = "interfaces left after the last stage";
+      return SPAND_EINVAL;
+    }
+  }
+  return SPAND_OK;
+}
+
+}  // namespace spand

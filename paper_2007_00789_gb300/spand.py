@@ -1,0 +1,228 @@
+"""ctypes binding of ``libspand.so`` (include/spand.h).
+
+Argument marshalling only: host arrays are passed as numpy buffers, device
+arrays as ``torch.Tensor.data_ptr()`` and streams as the raw ``cudaStream_t``
+of a ``torch.cuda.Stream``.  Every computation happens in the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libspand.so")
+
+SPAND_OK = 0
+SPAND_EINVAL = -1
+SPAND_ENOTSPD = -2
+SPAND_ENOMEM = -3
+SPAND_ECUDA = -4
+SPAND_ENOCONV = -5
+SPAND_ESTATE = -6
+
+# Every entry point declared in include/spand.h.
+EXPORTS = [
+    "spand_analyze", "spand_factor", "spand_apply", "spand_pcg", "spand_pcg_host",
+    "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
+    "spand_set_profiling", "spand_kernel_stats",
+    "spand_destroy", "spand_strerror", "spand_last_error",
+]
+
+
+class SpandError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"spand error {code}: {msg}")
+        self.code = code
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("skip", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz_a", ctypes.c_int64), ("nnz_factor", ctypes.c_int64),
+                ("mu", ctypes.c_double), ("nlevels", ctypes.c_int32), ("skip", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("eps", ctypes.c_double), ("nstages", ctypes.c_int32),
+                ("nclusters_total", ctypes.c_int32), ("ninterfaces_sparsified", ctypes.c_int32),
+                ("factor_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double),
+                ("pcg_iters", ctypes.c_int32), ("pcg_relres", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class _KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libspand.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "or python -m paper_2007_00789_gb300.build")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.spand_analyze.argtypes = [ctypes.POINTER(_CSR), vp, ctypes.c_int, ctypes.c_int, f64,
+                                ctypes.c_int, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+    L.spand_factor.argtypes = [vp, vp]
+    L.spand_apply.argtypes = [vp, vp, vp, vp]
+    L.spand_pcg.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
+    L.spand_pcg_host.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
+    L.spand_matvec.argtypes = [vp, vp, vp, vp]
+    L.spand_info.argtypes = [vp, ctypes.POINTER(_Stats)]
+    L.spand_ranks.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.spand_cluster_map.argtypes = [vp, ctypes.c_int, vp]
+    L.spand_num_clusters.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
+    L.spand_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.spand_kernel_stats.argtypes = [vp, ctypes.POINTER(_KStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.spand_destroy.argtypes = [vp]
+    L.spand_destroy.restype = None
+    L.spand_strerror.argtypes = [ctypes.c_int]
+    L.spand_strerror.restype = ctypes.c_char_p
+    L.spand_last_error.argtypes = []
+    L.spand_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("spand_destroy", "spand_strerror", "spand_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != SPAND_OK and rc not in allow:
+        L = load_library()
+        raise SpandError(rc, f"{L.spand_strerror(rc).decode()}: {L.spand_last_error().decode()}")
+    return rc
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+class Spand:
+    """One analysed (and possibly factored) SPD system A with grid coordinates."""
+
+    def __init__(self, rowptr, colind, val, coords, nlevels: int, eps: float, scheme: int = 1,
+                 skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
+                 max_restarts: int | None = None):
+        L = load_library()
+        self._lib = L
+        self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self._colind = np.ascontiguousarray(colind, dtype=np.int32)
+        self._val = np.ascontiguousarray(val, dtype=np.float64)
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        if coords.ndim == 1:
+            coords = coords[:, None]
+        self.n = int(self._rowptr.size - 1)
+        self.nnz = int(self._rowptr[-1])
+        csr = _CSR(self.n, self.nnz, self._rowptr.ctypes.data, self._colind.ctypes.data,
+                   self._val.ctypes.data)
+        opts = _Opts(-1 if skip is None else int(skip), 0 if maxit is None else int(maxit),
+                     0 if true_res_every is None else int(true_res_every),
+                     -1 if max_restarts is None else int(max_restarts))
+        h = ctypes.c_void_p()
+        _check(L.spand_analyze(ctypes.byref(csr), coords.ctypes.data, coords.shape[1], int(nlevels),
+                               float(eps), int(scheme), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.nlevels = int(nlevels)
+
+    @classmethod
+    def from_problem(cls, prob, nlevels, eps, scheme=1, **kw):
+        return cls(prob.rowptr, prob.colind, prob.val, prob.coords, nlevels, eps, scheme, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.spand_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self, stream=None):
+        _check(self._lib.spand_factor(self._h, _stream_ptr(stream)))
+
+    def apply(self, r, z, stream=None):
+        _check(self._lib.spand_apply(self._h, _dptr(r), _dptr(z), _stream_ptr(stream)))
+
+    def matvec(self, x, y, stream=None):
+        _check(self._lib.spand_matvec(self._h, _dptr(x), _dptr(y), _stream_ptr(stream)))
+
+    def pcg(self, b, x, tol: float, stream=None, allow_noconv: bool = False):
+        it = ctypes.c_int32()
+        rel = ctypes.c_double()
+        _check(self._lib.spand_pcg(self._h, _dptr(b), _dptr(x), float(tol), ctypes.byref(it),
+                                   ctypes.byref(rel), _stream_ptr(stream)),
+               allow=(SPAND_ENOCONV,) if allow_noconv else ())
+        return int(it.value), float(rel.value)
+
+    def pcg_host(self, b: np.ndarray, tol: float, stream=None):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        it = ctypes.c_int32()
+        rel = ctypes.c_double()
+        _check(self._lib.spand_pcg_host(self._h, b.ctypes.data, x.ctypes.data, float(tol),
+                                        ctypes.byref(it), ctypes.byref(rel), _stream_ptr(stream)))
+        return x, int(it.value), float(rel.value)
+
+    def info(self) -> dict:
+        s = _Stats()
+        _check(self._lib.spand_info(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def ranks(self) -> np.ndarray:
+        """(size at stage start, rank or -1, near-tie flags) for every cluster of every stage."""
+        cnt = ctypes.c_int64()
+        self._lib.spand_ranks(self._h, None, 0, ctypes.byref(cnt))
+        out = np.empty((cnt.value, 3), dtype=np.int32)
+        _check(self._lib.spand_ranks(self._h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return out
+
+    def set_profiling(self, on: bool):
+        _check(self._lib.spand_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self) -> list[dict]:
+        """Per kernel kind: launches, total_ms, algorithmic flops and bytes."""
+        arr = (_KStat * 64)()
+        cnt = ctypes.c_int()
+        _check(self._lib.spand_kernel_stats(self._h, arr, 64, ctypes.byref(cnt)))
+        return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches),
+                 "total_ms": float(arr[i].total_ms), "flops": float(arr[i].flops),
+                 "bytes": float(arr[i].bytes)} for i in range(cnt.value)]
+
+    def num_clusters(self, stage: int) -> int:
+        c = ctypes.c_int32()
+        _check(self._lib.spand_num_clusters(self._h, int(stage), ctypes.byref(c)))
+        return int(c.value)
+
+    def cluster_map(self, stage: int) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int32)
+        _check(self._lib.spand_cluster_map(self._h, int(stage), out.ctypes.data))
+        return out

@@ -1,0 +1,97 @@
+"""C-ABI checks that need no GPU.
+
+* libspand.so loads and exports every function declared in include/spand.h;
+* the host-only symbolic phase (spand_analyze) reproduces the oracle's
+  multilevel partition bit for bit (cluster of every vertex at every stage);
+* malformed input is rejected with SPAND_EINVAL.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import spand_inputs as si
+from oracle import partition as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_2007_00789_gb300 import spand as S
+    if not os.path.exists(S.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return S
+
+
+def test_exports_every_declared_symbol():
+    S = _lib()
+    L = S.load_library()
+    header = open(os.path.join(ROOT, "include", "spand.h")).read()
+    declared = set(re.findall(r"\b(spand_[a-z_]+)\s*\(", header))
+    assert declared, "no declarations found"
+    assert declared == set(S.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+    assert os.path.dirname(os.path.abspath(L._name)) == os.path.join(ROOT, "paper_2007_00789_gb300")
+
+
+@pytest.mark.parametrize("make,ell", [
+    (lambda: si.laplacian_2d(64), 6),
+    (lambda: si.laplacian_3d(16), 7),
+    (lambda: si.diffusion_grid((12, 10, 9), seed=1), 5),
+    (lambda: si.laplacian_grid((9, 7)), 4),
+    (lambda: si.laplacian_grid((5,)), 2),
+    (lambda: si.laplacian_2d(8), 1),
+])
+def test_partition_matches_oracle(make, ell):
+    S = _lib()
+    prob = make()
+    h = S.Spand.from_problem(prob, ell, 0.1, 1)
+    tree = P.nested_dissection(prob.coords, ell)
+    for k in range(ell):
+        sc = P.stage_clusters(tree, k)
+        want = np.full(prob.n, -1, dtype=np.int64)
+        for i, key in enumerate(sc.keys):
+            want[sc.members[key]] = i
+        assert h.num_clusters(k) == len(sc.keys)
+        assert np.array_equal(h.cluster_map(k), want), f"stage {k}"
+    h.close()
+
+
+def test_rejects_bad_input():
+    S = _lib()
+    prob = si.laplacian_2d(8)
+    with pytest.raises(S.SpandError) as e:
+        S.Spand.from_problem(prob, 3, 1.5, 1)
+    assert e.value.code == S.SPAND_EINVAL
+    with pytest.raises(S.SpandError):
+        S.Spand.from_problem(prob, 3, 0.1, 7)
+    with pytest.raises(S.SpandError):
+        S.Spand.from_problem(prob, 0, 0.1, 1)
+    with pytest.raises(S.SpandError):  # empty nested-dissection box
+        S.Spand.from_problem(prob, 6, 0.1, 1)
+    col = prob.colind.copy()
+    col[3], col[4] = col[4], col[3]  # unsorted row
+    with pytest.raises(S.SpandError):
+        S.Spand(prob.rowptr, col, prob.val, prob.coords, 3, 0.1, 1)
+    A = prob.to_scipy().tolil()
+    A[0, 9] = -0.5  # asymmetric pattern
+    A = A.tocsr()
+    A.sort_indices()
+    with pytest.raises(S.SpandError):
+        S.Spand(A.indptr, A.indices, A.data, prob.coords, 3, 0.1, 1)
+
+
+def test_factor_before_gpu_is_refused_cleanly():
+    """Without a GPU the numeric calls return an error code, never crash."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    S = _lib()
+    h = S.Spand.from_problem(si.laplacian_2d(8), 3, 0.1, 1)
+    with pytest.raises(S.SpandError) as e:
+        h.factor(stream=0)
+    assert e.value.code in (S.SPAND_ECUDA, S.SPAND_ENOMEM)
+    assert h.info()["n"] == 64
