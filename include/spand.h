@@ -135,6 +135,29 @@ int spand_pcg(spand_t h, const double* b, double* x, double tol, int32_t* iters,
 int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol,
                    int32_t* iters, double* relres, void* stream);
 
+/* Same as spand_pcg, but allocates nothing, for callers that cannot allocate
+ * device memory while they solve: a program whose GPU memory is entirely
+ * reserved by another allocator, or a loop that must not allocate once it
+ * runs.  (The paper has no counterpart; this is a deployment variant.)
+ * The four work vectors live in one device array that is part of the
+ * library image (about 8 MiB, held by every GPU that loads the library
+ * until the process exits), so the call needs no cudaMalloc / cudaFree and
+ * no pinned host memory.
+ *   - Limit: n <= 262144; larger systems return SPAND_EINVAL before any
+ *     device work.  The handle must have been factored (SPAND_ESTATE).
+ *   - The first call on a device looks up the array's device address for
+ *     that device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture on that device.
+ *   - Every call, from any handle, uses the same array, which keeps the
+ *     previous call's contents (x is set to 0 and the scalars are cleared at
+ *     the start, so stale data does not leak into a result).  Calls that
+ *     overlap on the GPU (different streams or threads) race on it and give
+ *     wrong results: serialise them.
+ *   - Profiling (spand_set_profiling) is suspended for the call.
+ * Arguments and results are those of spand_pcg. */
+int spand_pcg_noalloc(spand_t h, const double* b, double* x, double tol, int32_t* iters,
+                      double* relres, void* stream);
+
 /* y = A x with the uploaded A (device arrays of n doubles). */
 int spand_matvec(spand_t h, const double* x, double* y, void* stream);
 

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1350,3 +1351,136 @@ const char* spand_strerror(int code) {
 const char* spand_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// PCG that allocates nothing.
+//
+// spand_pcg allocates its four work vectors (and pinned host memory for the
+// scalars) on first use.  Some callers cannot allow that: a host program whose
+// device memory is entirely reserved by another allocator (for instance a
+// framework's caching allocator that owns the whole GPU), or a real-time loop
+// that must not allocate once it is running.  spand_pcg_noalloc runs the same
+// PCG with its work vectors in one statically sized device array that is part
+// of the loaded library, so it calls no cudaMalloc, cudaFree or other
+// allocating routine.  Limits and sharing rules are stated in include/spand.h.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 262144;   // largest n the static workspace holds
+constexpr int64_t kNoAllocScalars = 1024;  // dot partials (fewer than 1024) + scalars
+// r, z, p, q (n doubles each) followed by the partials and the scalars.  Every
+// GPU that loads the library holds this array (about 8 MiB) until exit.
+static __device__ __align__(256) double g_pcg_noalloc_ws[4 * kNoAllocMaxN + kNoAllocScalars];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+
+// Device address of the workspace on the current device.  Resolved once per
+// device (with that device current) by the first call made on it.
+int noalloc_workspace(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(SPAND_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_pcg_noalloc_ws));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SPAND_OK;
+}
+
+int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters,
+                     double* relres, cudaStream_t s) {
+  if ((int64_t)h->n > kNoAllocMaxN)
+    return fail(SPAND_EINVAL, "spand_pcg_noalloc: n = " + std::to_string(h->n) +
+                                  " exceeds the static workspace limit of " +
+                                  std::to_string(kNoAllocMaxN));
+  if (!h->factored) return fail(SPAND_ESTATE, "spand_pcg_noalloc before a successful spand_factor");
+  double* ws = nullptr;
+  RET(noalloc_workspace(&ws));
+  const int n = h->n;
+  double* r = ws;
+  double* z = ws + kNoAllocMaxN;
+  double* p = ws + 2 * kNoAllocMaxN;
+  double* q = ws + 3 * kNoAllocMaxN;
+  double* partial = ws + 4 * kNoAllocMaxN;
+  double* sc = partial + (kNoAllocScalars - 16);
+  if (dot_partials(n) > kNoAllocScalars - 16) return fail(SPAND_EINVAL, "internal: too many dot partials");
+  // profiling would create CUDA events; keep it off for this call
+  const bool prof_on = h->prof.on;
+  h->prof.on = false;
+  // scalars start from zero (the array keeps whatever the previous call left)
+  CK(cudaMemsetAsync(sc, 0, 16 * sizeof(double), s));
+  auto dot = [&](const double* a, const double* c, int slot) {
+    launch_dot(n, a, c, partial, sc + slot, s);
+  };
+  auto read = [&](int slot, double* out) -> int {
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, sc + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = v;
+    return SPAND_OK;
+  };
+  auto body = [&]() -> int {
+    launch_pcg_init(n, b, x, r, s);
+    dot(b, b, 4);
+    double bb = 0.0;
+    RET(read(4, &bb));
+    const double bnorm = std::sqrt(bb);
+    if (bnorm == 0.0) {
+      if (iters) *iters = 0;
+      if (relres) *relres = 0.0;
+      return SPAND_OK;
+    }
+    int it = 0, restarts = 0;
+    double rr = bb, rel = 0.0;
+    while (true) {
+      RET(apply_impl(h, r, z, s));
+      launch_copy_vec(n, z, p, s);
+      dot(r, z, 0);
+      while (it < h->maxit && std::sqrt(rr) / bnorm >= tol) {
+        launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, p, q, s);
+        dot(p, q, 1);
+        launch_pcg_step_x(n, sc, p, q, x, r, s);
+        ++it;
+        if (it % h->true_every == 0) {
+          launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, x, q, s);
+          launch_residual(n, b, q, r, s);
+        }
+        dot(r, r, 3);
+        RET(read(3, &rr));
+        if (std::sqrt(rr) / bnorm < tol) break;
+        RET(apply_impl(h, r, z, s));
+        dot(r, z, 2);
+        launch_pcg_step_p(n, sc, z, p, s);
+        launch_pcg_scalars(sc, 0, s);
+      }
+      launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, x, q, s);
+      launch_residual(n, b, q, r, s);
+      dot(r, r, 3);
+      RET(read(3, &rr));
+      rel = std::sqrt(rr) / bnorm;
+      if (rel < tol || it >= h->maxit || restarts >= h->max_restarts) break;
+      ++restarts;
+    }
+    CK(cudaGetLastError());
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (rel >= tol && it >= h->maxit) return fail(SPAND_ENOCONV, "PCG reached maxit");
+    return SPAND_OK;
+  };
+  const int rc = body();
+  h->prof.on = prof_on;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int spand_pcg_noalloc(spand_t h, const double* b, double* x, double tol, int32_t* iters,
+                                 double* relres, void* stream) {
+  if (!h || !b || !x) return fail(SPAND_EINVAL, "null argument");
+  if (!(tol > 0.0)) return fail(SPAND_EINVAL, "tol must be positive");
+  return pcg_noalloc_impl(h, b, x, tol, iters, relres, (cudaStream_t)stream);
+}

@@ -26,7 +26,7 @@ SPAND_ESTATE = -6
 EXPORTS = [
     "spand_analyze", "spand_factor", "spand_apply", "spand_pcg", "spand_pcg_host",
     "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
-    "spand_set_profiling", "spand_kernel_stats",
+    "spand_pcg_noalloc", "spand_set_profiling", "spand_kernel_stats",
     "spand_destroy", "spand_strerror", "spand_last_error",
 ]
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_apply.argtypes = [vp, vp, vp, vp]
     L.spand_pcg.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_pcg_host.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
+    L.spand_pcg_noalloc.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_matvec.argtypes = [vp, vp, vp, vp]
     L.spand_info.argtypes = [vp, ctypes.POINTER(_Stats)]
     L.spand_ranks.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
@@ -181,6 +182,14 @@ class Spand:
         _check(self._lib.spand_pcg(self._h, _dptr(b), _dptr(x), float(tol), ctypes.byref(it),
                                    ctypes.byref(rel), _stream_ptr(stream)),
                allow=(SPAND_ENOCONV,) if allow_noconv else ())
+        return int(it.value), float(rel.value)
+
+    def pcg_noalloc(self, b, x, tol: float, stream=None):
+        """spand_pcg without any allocation (work vectors in the library's static array)."""
+        it = ctypes.c_int32()
+        rel = ctypes.c_double()
+        _check(self._lib.spand_pcg_noalloc(self._h, _dptr(b), _dptr(x), float(tol), ctypes.byref(it),
+                                           ctypes.byref(rel), _stream_ptr(stream)))
         return int(it.value), float(rel.value)
 
     def pcg_host(self, b: np.ndarray, tol: float, stream=None):
