@@ -65,6 +65,9 @@ typedef struct {
   int32_t true_res_every; /* replace the recursive residual by b - A x every this
                              many iterations; <=0 = 50 */
   int32_t max_restarts;   /* PCG restarts when the true residual misses tol; <0 = 2 */
+  int32_t rrqr_kernel;    /* 0 = keep each interface block on chip (one CTA, or a thread-block
+                             cluster of up to 16 CTAs) where it fits, else stream it from global
+                             memory; 1 = always stream from global memory.  Same results. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */

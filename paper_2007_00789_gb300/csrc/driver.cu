@@ -144,11 +144,13 @@ struct Blob {
 // bytes are counted on the host from the task sizes.
 enum KernelKind {
   KK_PACK, KK_MERGE, KK_POTRF, KK_TRSM, KK_SCHUR, KK_SCALE_POTRF, KK_SCALE_TRSM, KK_SCALE_COPY,
-  KK_RRQR, KK_ECOPY, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT, KK_VEC, KK_COUNT
+  KK_RRQR, KK_ECOPY, KK_TRTRI, KK_FORMQ, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT,
+  KK_VEC, KK_COUNT
 };
 const char* const kKindName[KK_COUNT] = {
     "pack", "merge", "potrf", "trsm", "schur", "scale_potrf", "scale_trsm", "scale_copy",
-    "rrqr", "e_copy", "apply_interior", "apply_scale", "apply_qe", "spmv", "dot", "vector"};
+    "rrqr", "e_copy", "trtri", "form_qt", "apply_interior", "apply_scale", "apply_qe", "spmv",
+    "dot", "vector"};
 
 struct Prof {
   bool on = false;
@@ -211,29 +213,32 @@ struct Prof {
   }
 };
 
+constexpr int kQrClusterSmem = 200 * 1024;  // shared-memory slice per CTA of the on-chip RRQR
+constexpr int kNumSMs = 152;                 // GB300
+
 enum PhaseKind { PH_INTERIOR = 0, PH_SCALE = 1, PH_QE = 2 };
 struct Phase {
   int kind, begin, end, max_m;
   double flops, bytes;  // algorithmic, forward sweep (the backward one is the same)
+  int max_cols = 0;     // widest neighbour gather
 };
 
 struct ApInteriorP {
-  const double* L;
+  const double* Linv;
   const double* WT;
   int64_t slots, wslots;
-  int m, ldL, ncols;
+  int m, ncols;
 };
 struct ApScaleP {
-  const double* Z;
+  const double* Zinv;
   int64_t slots;
   int m;
 };
 struct ApQEP {
-  const double* V;
-  const double* tau;
+  const double* Qt;
   const double* E;
   int64_t slots, eslots;
-  int m, nref, r, nE, ncols;
+  int m, r, nE, ncols;
 };
 
 }  // namespace
@@ -280,6 +285,16 @@ struct spand_s {
   double pcg_ms = 0.0, pcg_relres = 0.0;
   int pcg_iters = 0;
   Prof prof;
+  int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel
+  int cluster_state[5] = {-1, -1, -1, -1, -1};
+  // whether a cluster of cs CTAs with the largest shared-memory slice can be resident
+  bool cluster_ok(int cs) {
+    if (rrqr_path == 1) return false;
+    int lc = 0;
+    while ((1 << lc) < cs) ++lc;
+    if (cluster_state[lc] < 0) cluster_state[lc] = rrqr_cluster_active(cs, kQrClusterSmem) > 0 ? 1 : 0;
+    return cluster_state[lc] == 1;
+  }
 };
 
 namespace {
@@ -309,8 +324,9 @@ void push_copy(std::vector<CopyTask>& v, const double* src, double* dst, int src
   }
 }
 
+// ident: X <- L^{-1} I (explicit inverse of the lower-triangular L, m x m).
 void push_trsm(std::vector<TrsmTask>& v, const double* L, int ldl, double* X, int m, int ldx,
-               int ncols, int trans) {
+               int ncols, int trans, bool ident = false) {
   if (m <= 0 || ncols <= 0) return;
   for (int c0 = 0; c0 < ncols; c0 += 32) {
     TrsmTask t;
@@ -320,7 +336,7 @@ void push_trsm(std::vector<TrsmTask>& v, const double* L, int ldl, double* X, in
     t.ldx = ldx;
     t.ncols = std::min(32, ncols - c0);
     t.trans = trans;
-    t.pad = 0;
+    t.pad = ident ? c0 : -1;
     t.X = trans ? X + c0 : X + (size_t)c0 * ldx;
     v.push_back(t);
   }
@@ -344,6 +360,18 @@ double potrf_bytes(const std::vector<PotrfTask>& v) {
 double trsm_flops(const std::vector<TrsmTask>& v) {
   double f = 0.0;
   for (auto& t : v) f += (double)t.m * t.m * t.ncols;
+  return f;
+}
+double trtri_flops(const std::vector<TrsmTask>& v) {
+  double f = 0.0;  // columns c0.. of L^{-1}: sum over columns of (m - c)^2 / 2 FMAs
+  for (auto& t : v)
+    for (int c = t.pad; c < t.pad + t.ncols; ++c) f += (double)(t.m - c) * (t.m - c);
+  return f;
+}
+double formqt_flops(const std::vector<FormQtTask>& v) {
+  double f = 0.0;
+  for (auto& t : v)
+    for (int s = 0; s < t.nref; ++s) f += 4.0 * (t.m - s) * t.ncols;
   return f;
 }
 double trsm_bytes(const std::vector<TrsmTask>& v) {
@@ -414,7 +442,12 @@ int factor_impl(spand_s* h, cudaStream_t s) {
   h->flags.assign(ell, {});
   int64_t nnzf = 0;
   CK(cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), s));
-  std::vector<CopyTask> pending_e;  // E-tilde compaction of the previous stage
+  // work of the previous stage that runs with the next stage's launches:
+  // E-tilde compaction and the explicit apply operators L^{-1}, Z^{-1}, Q^T
+  std::vector<CopyTask> pending_e;
+  std::vector<TrsmTask> pending_inv;
+  std::vector<FormQtTask> pending_qt;
+  int pending_inv_m = 0, pending_qt_m = 0;
 
   for (int k = 0; k < ell; ++k) {
     const StageSym& S = h->st[k];
@@ -585,7 +618,7 @@ int factor_impl(spand_s* h, cudaStream_t s) {
     std::vector<TrsmTask> ltrsm, rtrsm;
     std::vector<std::vector<RRQRTask>> qr_tasks;
     std::vector<RRQRSeg> qr_segs;
-    std::vector<int> qr_max_m, qr_max_cols, qr_max_segs;
+    std::vector<int> qr_max_m, qr_max_cols, qr_max_segs, qr_csize, qr_smem;
     int max_m_if = 0;
     Ly.Z.assign(ncl, nullptr);
     Ly.V.assign(ncl, nullptr);
@@ -624,11 +657,10 @@ int factor_impl(spand_s* h, cudaStream_t s) {
         }
         ident.push_back({Ly.row[p] + (size_t)dc * m, m, m, p, 0});
       }
-      qr_tasks.assign(S.ncolours, {});
-      qr_max_m.assign(S.ncolours, 0);
-      qr_max_cols.assign(S.ncolours, 0);
-      qr_max_segs.assign(S.ncolours, 0);
+      // one bucket per (colour, cluster size); cluster size 0 = the global-memory kernel
       for (int col = 0; col < S.ncolours; ++col) {
+        std::vector<RRQRTask> bucket[6];
+        int bm[6] = {0}, bc[6] = {0}, bs[6] = {0}, bsm[6] = {0};
         for (int p : S.by_colour[col]) {
           const int m = Ly.m[p];
           RRQRTask t;
@@ -656,14 +688,41 @@ int factor_impl(spand_s* h, cudaStream_t s) {
           }
           t.seg_end = (int)qr_segs.size();
           t.nseg_max = t.seg_end - t.seg_begin;
-          qr_tasks[col].push_back(t);
-          qr_max_m[col] = std::max(qr_max_m[col], m);
-          qr_max_cols[col] = std::max(qr_max_cols[col], t.ncols_max);
-          qr_max_segs[col] = std::max(qr_max_segs[col], t.nseg_max);
+          // Cluster size: the smallest that fits shared memory, raised until the
+          // colour's interfaces fill about two CTAs per SM, while keeping at least
+          // 32 columns per CTA.
+          const int ntask = (int)S.by_colour[col].size();
+          int want = 1;
+          while (want < 16 && want * ntask < 2 * kNumSMs && (2 * want) * 32 <= t.ncols_max) want *= 2;
+          int b = 0;  // bucket: 1..5 for cluster sizes 1, 2, 4, 8, 16; 0 = fallback
+          for (int lc = 0; lc <= 4; ++lc) {
+            const int cs = 1 << lc;
+            const int bytes = rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, cs);
+            if (bytes <= kQrClusterSmem && h->cluster_ok(cs)) {
+              int lw = lc;
+              while ((1 << lw) < want && lw < 4 && h->cluster_ok(1 << (lw + 1))) ++lw;
+              b = lw + 1;
+              bsm[b] = std::max(bsm[b], rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, 1 << lw));
+              break;
+            }
+          }
+          bucket[b].push_back(t);
+          bm[b] = std::max(bm[b], m);
+          bc[b] = std::max(bc[b], t.ncols_max);
+          bs[b] = std::max(bs[b], t.nseg_max);
         }
-        if (rrqr_smem_bytes(qr_max_m[col], qr_max_cols[col], qr_max_segs[col]) > 220 * 1024)
-          return fail(SPAND_ENOMEM, "interface block too wide for the on-chip RRQR workspace (stage " +
-                                        std::to_string(k) + ")");
+        for (int b = 0; b < 6; ++b) {
+          if (bucket[b].empty()) continue;
+          qr_tasks.push_back(bucket[b]);
+          qr_csize.push_back(b == 0 ? 0 : 1 << (b - 1));
+          qr_max_m.push_back(bm[b]);
+          qr_max_cols.push_back(bc[b]);
+          qr_max_segs.push_back(bs[b]);
+          qr_smem.push_back(bsm[b]);
+          if (b == 0 && rrqr_smem_bytes(bm[b], bc[b], bs[b]) > 220 * 1024)
+            return fail(SPAND_ENOMEM, "interface block too wide for the RRQR workspace (stage " +
+                                          std::to_string(k) + ")");
+        }
       }
     }
     std::vector<int> cur_size(Ly.m.begin(), Ly.m.end());
@@ -671,6 +730,8 @@ int factor_impl(spand_s* h, cudaStream_t s) {
 
     // ---- upload
     const size_t o_e = blob.add(pending_e);
+    const size_t o_inv = blob.add(pending_inv);
+    const size_t o_fq = blob.add(pending_qt);
     const size_t o_merge = blob.add(merge);
     const size_t o_pi = blob.add(potrf_int);
     const size_t o_ti = blob.add(trsm_int);
@@ -703,6 +764,12 @@ int factor_impl(spand_s* h, cudaStream_t s) {
     };
     run(KK_ECOPY, pending_e.size(), 0.0, copy_bytes(pending_e),
         [&] { launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), s); });
+    run(KK_TRTRI, pending_inv.size(), trtri_flops(pending_inv), trsm_bytes(pending_inv), [&] {
+      launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, s);
+    });
+    run(KK_FORMQ, pending_qt.size(), formqt_flops(pending_qt), 0.0, [&] {
+      launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, s);
+    });
     if (fbytes) CK(cudaMemsetAsync(fptr, 0, fbytes, s));
     if (sbytes) CK(cudaMemsetAsync(scr.p, 0, sbytes, s));
     if (k == 0) {
@@ -742,10 +809,16 @@ int factor_impl(spand_s* h, cudaStream_t s) {
           [&] { launch_set_identity((const PotrfTask*)(D + o_id), (int)ident.size(), s); });
       for (size_t c = 0; c < qr_tasks.size(); ++c) {
         run(KK_RRQR, qr_tasks[c].size(), 0.0, 0.0, [&] {
-          launch_rrqr((const RRQRTask*)(D + o_qr[c]), (int)qr_tasks[c].size(),
-                      (const RRQRSeg*)(D + o_seg), (int*)(D + o_cur), (int*)(D + o_rank),
-                      (int*)(D + o_nref), (int*)(D + o_flag), h->eps, h->scheme, qr_max_m[c],
-                      qr_max_cols[c], qr_max_segs[c], s);
+          if (qr_csize[c] == 0)
+            launch_rrqr((const RRQRTask*)(D + o_qr[c]), (int)qr_tasks[c].size(),
+                        (const RRQRSeg*)(D + o_seg), (int*)(D + o_cur), (int*)(D + o_rank),
+                        (int*)(D + o_nref), (int*)(D + o_flag), h->eps, h->scheme, qr_max_m[c],
+                        qr_max_cols[c], qr_max_segs[c], s);
+          else
+            launch_rrqr_cluster((const RRQRTask*)(D + o_qr[c]), (int)qr_tasks[c].size(),
+                                (const RRQRSeg*)(D + o_seg), (int*)(D + o_cur), (int*)(D + o_rank),
+                                (int*)(D + o_nref), (int*)(D + o_flag), h->eps, h->scheme,
+                                qr_csize[c], qr_smem[c], s);
         });
       }
     }
@@ -789,17 +862,31 @@ int factor_impl(spand_s* h, cudaStream_t s) {
       }
     }
 
-    // ---- apply operators of this stage
+    // ---- apply operators of this stage (explicit inverses and Q^T are formed
+    //      by tasks that run with the next stage's launches)
+    pending_e.clear();
+    pending_inv.clear();
+    pending_qt.clear();
+    pending_inv_m = pending_qt_m = 0;
+    auto explicit_inverse = [&](const double* L, int m, double** out) -> int {
+      void* ip = nullptr;
+      RET(h->farena.alloc(std::max<size_t>((size_t)m * m * 8, 16), &ip));
+      *out = (double*)ip;
+      push_trsm(pending_inv, L, m, *out, m, m, m, 0, true);
+      pending_inv_m = std::max(pending_inv_m, m);
+      return SPAND_OK;
+    };
     {
       Phase ph{PH_INTERIOR, (int)api.size(), 0, 0, 0.0, 0.0};
       for (int sidx : S.interiors) {
         const int m = Ly.m[sidx];
         ApInteriorP a;
         a.m = m;
-        a.ldL = m;
         a.ncols = Ly.ncols[sidx];
         const int dc = segc(sidx, sidx);
-        a.L = Ly.row[sidx] + (size_t)dc * m;
+        double* Linv = nullptr;
+        if (m > 0) RET(explicit_inverse(Ly.row[sidx] + (size_t)dc * m, m, &Linv));
+        a.Linv = Linv;
         a.WT = Ly.row[sidx];
         a.slots = Ly.slot_off[sidx];
         a.wslots = (int64_t)pool.size();
@@ -809,6 +896,7 @@ int factor_impl(spand_s* h, cudaStream_t s) {
         }
         api.push_back(a);
         ph.max_m = std::max(ph.max_m, m);
+        ph.max_cols = std::max(ph.max_cols, a.ncols);
         ph.flops += (double)m * m + 2.0 * m * (a.ncols - m);
         ph.bytes += 8.0 * ((double)m * (m + 1) / 2 + (double)m * (a.ncols - m)) + 24.0 * a.ncols;
         nnzf += (int64_t)m * (m + 1) / 2 + (int64_t)m * (a.ncols - m);
@@ -816,15 +904,17 @@ int factor_impl(spand_s* h, cudaStream_t s) {
       ph.end = (int)api.size();
       if (ph.end > ph.begin) phases.push_back(ph);
     }
-    pending_e.clear();
     if (S.sparsify) {
       Phase ph{PH_SCALE, (int)aps.size(), 0, 0, 0.0, 0.0};
       for (int p : S.ifaces) {
-        aps.push_back({Ly.Z[p], Ly.slot_off[p], Ly.m[p]});
-        ph.max_m = std::max(ph.max_m, Ly.m[p]);
-        ph.flops += (double)Ly.m[p] * Ly.m[p];
-        ph.bytes += 8.0 * (double)Ly.m[p] * (Ly.m[p] + 1) / 2 + 16.0 * Ly.m[p];
-        nnzf += (int64_t)Ly.m[p] * (Ly.m[p] + 1) / 2;
+        const int m = Ly.m[p];
+        double* Zinv = nullptr;
+        if (m > 0) RET(explicit_inverse(Ly.Z[p], m, &Zinv));
+        aps.push_back({Zinv, Ly.slot_off[p], m});
+        ph.max_m = std::max(ph.max_m, m);
+        ph.flops += (double)m * m;
+        ph.bytes += 8.0 * (double)m * (m + 1) / 2 + 16.0 * m;
+        nnzf += (int64_t)m * (m + 1) / 2;
       }
       ph.end = (int)aps.size();
       if (ph.end > ph.begin) phases.push_back(ph);
@@ -837,12 +927,27 @@ int factor_impl(spand_s* h, cudaStream_t s) {
           if (h->scheme == SPAND_SECOND_ORDER_FULL) nE = m - r;
           else if (h->scheme == SPAND_SECOND_ORDER_SUPERFINE) nE = nref - r;
           ApQEP a;
-          a.V = Ly.V[p];
-          a.tau = Ly.tau[p];
           a.m = m;
-          a.nref = nref;
           a.r = r;
           a.nE = nE;
+          a.Qt = nullptr;
+          if (m > 0) {
+            void* qp = nullptr;
+            RET(h->farena.alloc((size_t)m * m * 8, &qp));
+            a.Qt = (double*)qp;
+            for (int c0 = 0; c0 < m; c0 += 32) {
+              FormQtTask ft;
+              ft.V = Ly.V[p];
+              ft.tau = Ly.tau[p];
+              ft.Qt = (double*)a.Qt + (size_t)c0 * m;
+              ft.m = m;
+              ft.nref = nref;
+              ft.c0 = c0;
+              ft.ncols = std::min(32, m - c0);
+              pending_qt.push_back(ft);
+            }
+            pending_qt_m = std::max(pending_qt_m, m);
+          }
           a.slots = Ly.slot_off[p];
           a.eslots = (int64_t)pool.size();
           int ncols = 0;
@@ -874,9 +979,9 @@ int factor_impl(spand_s* h, cudaStream_t s) {
           }
           apq.push_back(a);
           pq.max_m = std::max(pq.max_m, m);
-          for (int t = 0; t < nref; ++t) pq.flops += 4.0 * (m - t);
-          pq.flops += 2.0 * a.nE * ncols;
-          pq.bytes += 8.0 * ((double)m * nref + (double)a.nE * ncols) + 16.0 * (m + ncols);
+          if (a.nE > 0) pq.max_cols = std::max(pq.max_cols, ncols);
+          pq.flops += 2.0 * m * m + 2.0 * a.nE * ncols;
+          pq.bytes += 8.0 * ((double)m * m + (double)a.nE * ncols) + 16.0 * (m + ncols);
           nnzf += (int64_t)m * nref + nref + (int64_t)a.nE * ncols;
         }
         pq.end = (int)apq.size();
@@ -888,11 +993,26 @@ int factor_impl(spand_s* h, cudaStream_t s) {
   {
     Blob blob;
     const size_t o_e = blob.add(pending_e);
+    const size_t o_inv = blob.add(pending_inv);
+    const size_t o_fq = blob.add(pending_qt);
     RET(h->tables.ensure(blob.h.size() + 16));
+    char* D = h->tables.p;
+    CK(cudaMemcpyAsync(D, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
     if (!pending_e.empty()) {
-      CK(cudaMemcpyAsync(h->tables.p, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
       h->prof.run(KK_ECOPY, s, 0.0, copy_bytes(pending_e), [&] {
-        launch_copy((const CopyTask*)(h->tables.p + o_e), (int)pending_e.size(), s);
+        launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), s);
+      });
+      h->launches += 1;
+    }
+    if (!pending_inv.empty()) {
+      h->prof.run(KK_TRTRI, s, trtri_flops(pending_inv), trsm_bytes(pending_inv), [&] {
+        launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, s);
+      });
+      h->launches += 1;
+    }
+    if (!pending_qt.empty()) {
+      h->prof.run(KK_FORMQ, s, formqt_flops(pending_qt), 0.0, [&] {
+        launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, s);
       });
       h->launches += 1;
     }
@@ -906,14 +1026,14 @@ int factor_impl(spand_s* h, cudaStream_t s) {
   const int* dpool = (const int*)pp;
   std::vector<ApInterior> vi(api.size());
   for (size_t i = 0; i < api.size(); ++i)
-    vi[i] = {api[i].L, api[i].WT, dpool + api[i].slots, dpool + api[i].wslots, api[i].m,
-             api[i].ldL, api[i].ncols, 0};
+    vi[i] = {api[i].Linv, api[i].WT, dpool + api[i].slots, dpool + api[i].wslots, api[i].m,
+             api[i].ncols};
   std::vector<ApScale> vs(aps.size());
-  for (size_t i = 0; i < aps.size(); ++i) vs[i] = {aps[i].Z, dpool + aps[i].slots, aps[i].m, 0};
+  for (size_t i = 0; i < aps.size(); ++i) vs[i] = {aps[i].Zinv, dpool + aps[i].slots, aps[i].m, 0};
   std::vector<ApQE> vq(apq.size());
   for (size_t i = 0; i < apq.size(); ++i)
-    vq[i] = {apq[i].V, apq[i].tau, apq[i].E, dpool + apq[i].slots, dpool + apq[i].eslots,
-             apq[i].m, apq[i].nref, apq[i].r, apq[i].nE, apq[i].ncols, 0};
+    vq[i] = {apq[i].Qt, apq[i].E, dpool + apq[i].slots, dpool + apq[i].eslots, apq[i].m,
+             apq[i].r, apq[i].nE, apq[i].ncols};
   if (!pool.empty()) CK(cudaMemcpyAsync(pp, pool.data(), pool.size() * 4, cudaMemcpyHostToDevice, s));
   if (!vi.empty()) CK(cudaMemcpyAsync(pa, vi.data(), vi.size() * sizeof(ApInterior), cudaMemcpyHostToDevice, s));
   if (!vs.empty()) CK(cudaMemcpyAsync(ps, vs.data(), vs.size() * sizeof(ApScale), cudaMemcpyHostToDevice, s));
@@ -941,9 +1061,10 @@ int apply_impl(spand_s* h, const double* r, double* z, cudaStream_t s) {
     const int nt = ph.end - ph.begin;
     const int kind = ph.kind == PH_INTERIOR ? KK_AP_INTERIOR : ph.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
     P.run(kind, s, ph.flops, ph.bytes, [&] {
-      if (ph.kind == PH_INTERIOR) launch_ap_interior(h->d_api + ph.begin, nt, ph.max_m, z, fwd, s);
+      if (ph.kind == PH_INTERIOR)
+        launch_ap_interior(h->d_api + ph.begin, nt, ph.max_m, ph.max_cols, z, fwd, s);
       else if (ph.kind == PH_SCALE) launch_ap_scale(h->d_aps + ph.begin, nt, ph.max_m, z, fwd, s);
-      else launch_ap_qe(h->d_apq + ph.begin, nt, ph.max_m, z, fwd, s);
+      else launch_ap_qe(h->d_apq + ph.begin, nt, ph.max_m, ph.max_cols, z, fwd, s);
     });
   };
   for (const Phase& ph : h->phases) one(ph, true);
@@ -1130,6 +1251,8 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     if (opts->maxit > 0) h->maxit = opts->maxit;
     if (opts->true_res_every > 0) h->true_every = opts->true_res_every;
     if (opts->max_restarts >= 0) h->max_restarts = opts->max_restarts;
+    if (opts->rrqr_kernel < 0 || opts->rrqr_kernel > 1) return fail(SPAND_EINVAL, "rrqr_kernel must be 0 or 1");
+    h->rrqr_path = opts->rrqr_kernel;
   }
   int rc = build_tree(coords, A->n, dim, nlevels, h->tree, err);
   if (rc != SPAND_OK) return fail(rc, err);

@@ -15,7 +15,7 @@ namespace spand {
 
 namespace {
 
-constexpr int kApThreads = 128;
+constexpr int kApThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -34,128 +34,147 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// z <- L^{-1} z (lower, column oriented) on a shared-memory vector.
-__device__ void trsv_lower(const double* L, int m, size_t ld, double* zs) {
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) zs[j] /= L[j + j * ld];
-    __syncthreads();
-    const double zj = zs[j];
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) zs[i] -= L[i + j * ld] * zj;
-    __syncthreads();
+// y = T x for a lower-triangular T (ld m), thread per row: FMA chains only.
+__device__ void lower_mv(const double* T, int m, const double* x, double* y) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 1 <= i; j += 2) {
+      s0 = fma(T[i + (size_t)j * m], x[j], s0);
+      s1 = fma(T[i + (size_t)(j + 1) * m], x[j + 1], s1);
+    }
+    if (j <= i) s0 = fma(T[i + (size_t)j * m], x[j], s0);
+    y[i] = s0 + s1;
   }
 }
 
-// z <- L^{-T} z.
-__device__ void trsv_lower_t(const double* L, int m, size_t ld, double* zs) {
-  for (int j = m - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) zs[j] /= L[j + j * ld];
-    __syncthreads();
-    const double zj = zs[j];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) zs[i] -= L[j + i * ld] * zj;
-    __syncthreads();
+// y = T^T x for a lower-triangular T: thread j walks column j of T.
+__device__ void lower_tmv(const double* T, int m, const double* x, double* y) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double* col = T + (size_t)j * m;
+    double s0 = 0.0, s1 = 0.0;
+    int i = j;
+    for (; i + 1 < m; i += 2) {
+      s0 = fma(col[i], x[i], s0);
+      s1 = fma(col[i + 1], x[i + 1], s1);
+    }
+    if (i < m) s0 = fma(col[i], x[i], s0);
+    y[j] = s0 + s1;
   }
 }
 
+// s = sum_c M[row + c*ld] * x[c] over c < n, 4 partial sums to keep loads in flight.
+__device__ __forceinline__ double row_dot(const double* __restrict__ M, size_t ld, int n,
+                                          const double* __restrict__ x) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 3 < n; c += 4) {
+    s0 = fma(M[(size_t)c * ld], x[c], s0);
+    s1 = fma(M[(size_t)(c + 1) * ld], x[c + 1], s1);
+    s2 = fma(M[(size_t)(c + 2) * ld], x[c + 2], s2);
+    s3 = fma(M[(size_t)(c + 3) * ld], x[c + 3], s3);
+  }
+  for (; c < n; ++c) s0 = fma(M[(size_t)c * ld], x[c], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// s = sum_i col[i] * x[i] over i < n (a contiguous column).
+__device__ __forceinline__ double col_dot(const double* __restrict__ col, int n,
+                                          const double* __restrict__ x) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = 0;
+  for (; i + 3 < n; i += 4) {
+    s0 = fma(col[i], x[i], s0);
+    s1 = fma(col[i + 1], x[i + 1], s1);
+    s2 = fma(col[i + 2], x[i + 2], s2);
+    s3 = fma(col[i + 3], x[i + 3], s3);
+  }
+  for (; i < n; ++i) s0 = fma(col[i], x[i], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Shared memory of the apply kernels: x (m), y (m), gathered neighbour values (ncols).
 __global__ void k_ap_interior(const ApInterior* __restrict__ tasks, double* __restrict__ z,
                               int forward) {
-  extern __shared__ double zs[];
+  extern __shared__ double sh[];
   const ApInterior t = tasks[blockIdx.x];
   const int m = t.m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = z[t.slots[i]];
+  double* xs = sh;
+  double* ys = sh + m;
+  double* zw = sh + 2 * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
+  if (!forward)
+    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) {
+      const int ws = t.wslots[c];
+      zw[c] = ws >= 0 ? z[ws] : 0.0;  // the diagonal segment contributes nothing
+    }
   __syncthreads();
   if (forward) {
-    trsv_lower(t.L, m, t.ldL, zs);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = zs[i];
-    // z_w -= W_s z_s with W_s = (W_s^T)^T stored as the panel row
-    for (int c = warp; c < t.ncols; c += nw) {
+    // z_s <- L_s^{-1} z_s, then z_w -= W_s z_s (column c of the panel row holds W_s^T[:, c])
+    lower_mv(t.Linv, m, xs, ys);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
+    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) {
       const int ws = t.wslots[c];
       if (ws < 0) continue;
-      const double* col = t.WT + (size_t)c * m;
-      double s = 0.0;
-      for (int i = lane; i < m; i += 32) s += col[i] * zs[i];
-      s = warp_sum(s);
-      if (lane == 0) atomicAdd(z + ws, -s);
+      atomicAdd(z + ws, -col_dot(t.WT + (size_t)c * m, m, ys));
     }
   } else {
     // z_s -= W_s^T z_w, then z_s <- L_s^{-T} z_s
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double s = 0.0;
-      for (int c = 0; c < t.ncols; ++c) {
-        const int ws = t.wslots[c];
-        if (ws >= 0) s += t.WT[i + (size_t)c * m] * z[ws];
-      }
-      zs[i] -= s;
-    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = xs[i] - row_dot(t.WT + i, m, t.ncols, zw);
     __syncthreads();
-    trsv_lower_t(t.L, m, t.ldL, zs);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = zs[i];
+    lower_tmv(t.Linv, m, ys, xs);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = xs[i];
   }
 }
 
 __global__ void k_ap_scale(const ApScale* __restrict__ tasks, double* __restrict__ z,
                            int forward) {
-  extern __shared__ double zs[];
+  extern __shared__ double sh[];
   const ApScale t = tasks[blockIdx.x];
   const int m = t.m;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = z[t.slots[i]];
+  double* xs = sh;
+  double* ys = sh + m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
   __syncthreads();
-  if (forward) trsv_lower(t.Z, m, m, zs);
-  else trsv_lower_t(t.Z, m, m, zs);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = zs[i];
+  if (forward) lower_mv(t.Zinv, m, xs, ys);
+  else lower_tmv(t.Zinv, m, xs, ys);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
 }
 
 __global__ void k_ap_qe(const ApQE* __restrict__ tasks, double* __restrict__ z, int forward) {
-  extern __shared__ double zs[];
-  __shared__ double red[32];
+  extern __shared__ double sh[];
   const ApQE t = tasks[blockIdx.x];
   const int m = t.m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] = z[t.slots[i]];
+  double* xs = sh;
+  double* ys = sh + m;
+  double* zw = sh + 2 * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
+  if (!forward && t.nE > 0)
+    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) zw[c] = z[t.eslots[c]];
   __syncthreads();
   if (forward) {
-    // z_p <- Q^T z_p = H_{nref-1} ... H_0 z_p
-    for (int s = 0; s < t.nref; ++s) {
-      const double* v = t.V + (size_t)s * m;
-      double d = 0.0;
-      for (int i = s + threadIdx.x; i < m; i += blockDim.x) d += v[i] * zs[i];
-      d = block_sum(d, red);
-      const double f = t.tau[s] * d;
-      for (int i = s + threadIdx.x; i < m; i += blockDim.x) zs[i] -= f * v[i];
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = zs[i];
+    // z_p <- Q^T z_p (row i of Q^T: Qt[i + j m] over j)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = row_dot(t.Qt + i, m, m, xs);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
     // z_w -= E-tilde^T z_f
-    if (t.nE > 0) {
-      for (int c = warp; c < t.ncols; c += nw) {
-        const double* col = t.E + (size_t)c * t.nE;
-        double s = 0.0;
-        for (int i = lane; i < t.nE; i += 32) s += col[i] * zs[t.r + i];
-        s = warp_sum(s);
-        if (lane == 0) atomicAdd(z + t.eslots[c], -s);
-      }
-    }
+    if (t.nE > 0)
+      for (int c = threadIdx.x; c < t.ncols; c += blockDim.x)
+        atomicAdd(z + t.eslots[c], -col_dot(t.E + (size_t)c * t.nE, t.nE, ys + t.r));
   } else {
     // z_f -= E-tilde z_w
     if (t.nE > 0) {
-      for (int i = threadIdx.x; i < t.nE; i += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < t.ncols; ++c) s += t.E[i + (size_t)c * t.nE] * z[t.eslots[c]];
-        zs[t.r + i] -= s;
-      }
+      for (int i = threadIdx.x; i < t.nE; i += blockDim.x)
+        xs[t.r + i] -= row_dot(t.E + i, t.nE, t.ncols, zw);
       __syncthreads();
     }
-    // z_p <- Q z_p = H_0 ... H_{nref-1} z_p
-    for (int s = t.nref - 1; s >= 0; --s) {
-      const double* v = t.V + (size_t)s * m;
-      double d = 0.0;
-      for (int i = s + threadIdx.x; i < m; i += blockDim.x) d += v[i] * zs[i];
-      d = block_sum(d, red);
-      const double f = t.tau[s] * d;
-      for (int i = s + threadIdx.x; i < m; i += blockDim.x) zs[i] -= f * v[i];
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = zs[i];
+    // z_p <- Q z_p = (Q^T)^T z_p: thread j walks column j of Q^T
+    for (int j = threadIdx.x; j < m; j += blockDim.x) ys[j] = col_dot(t.Qt + (size_t)j * m, m, xs);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
   }
 }
 
@@ -241,10 +260,10 @@ static void smem_attr(const void* fn, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, double* z, bool forward,
-                        cudaStream_t s) {
+void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, int max_cols, double* z,
+                        bool forward, cudaStream_t s) {
   if (ntasks <= 0) return;
-  const int bytes = std::max(max_m, 1) * 8;
+  const int bytes = std::max(2 * max_m + max_cols, 1) * 8;
   smem_attr((const void*)k_ap_interior, bytes);
   k_ap_interior<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
 }
@@ -252,14 +271,15 @@ void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, double* z, b
 void launch_ap_scale(const ApScale* t, int ntasks, int max_m, double* z, bool forward,
                      cudaStream_t s) {
   if (ntasks <= 0) return;
-  const int bytes = std::max(max_m, 1) * 8;
+  const int bytes = std::max(max_m, 1) * 16;
   smem_attr((const void*)k_ap_scale, bytes);
   k_ap_scale<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
 }
 
-void launch_ap_qe(const ApQE* t, int ntasks, int max_m, double* z, bool forward, cudaStream_t s) {
+void launch_ap_qe(const ApQE* t, int ntasks, int max_m, int max_cols, double* z, bool forward,
+                  cudaStream_t s) {
   if (ntasks <= 0) return;
-  const int bytes = std::max(max_m, 1) * 8;
+  const int bytes = std::max(2 * max_m + max_cols, 1) * 8;
   smem_attr((const void*)k_ap_qe, bytes);
   k_ap_qe<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
 }

@@ -75,10 +75,20 @@ struct PotrfTask {
 
 // trans == 0: X (m x ncols, ld ldx) <- L^{-1} X.
 // trans == 1: B (ncols x m, ld ldx) <- B L^{-T}, i.e. B^T <- L^{-1} B^T.
+// ident >= 0: X <- L^{-1} [e_ident .. e_{ident+ncols-1}] (columns of L^{-1}; X's
+// previous contents are ignored).
 struct TrsmTask {
   const double* L;
   double* X;
-  int m, ldl, ldx, ncols, trans, pad;
+  int m, ldl, ldx, ncols, trans, pad;  // pad: ident (first identity column) or -1
+};
+
+// Columns c0 .. c0+ncols-1 of Q^T = H_{nref-1} ... H_0 (m x m, ld m).
+struct FormQtTask {
+  const double* V;
+  const double* tau;
+  double* Qt;  // already offset to column c0
+  int m, nref, c0, ncols;
 };
 
 // One output tile (rows x cols <= 32 x 32) of a Schur target block:
@@ -114,26 +124,27 @@ struct RRQRTask {
   int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max;
 };
 
-// Preconditioner apply descriptors.
+// Preconditioner apply descriptors.  The triangular factors and Q_p are
+// applied through explicit matrices formed at the end of each stage
+// (L_s^{-1}, Z_p^{-1}, Q_p^T), so every apply step is a dense product.
 struct ApInterior {
-  const double* L;      // m x m lower (ld = ldL)
+  const double* Linv;   // m x m lower, L_s^{-1}, ld m
   const double* WT;     // panel row, m x ncols (ld = m); diag columns skipped via wslot < 0
   const int* slots;     // m vector positions
   const int* wslots;    // ncols vector positions (-1 for the diagonal segment)
-  int m, ldL, ncols, pad;
+  int m, ncols;
 };
 struct ApScale {
-  const double* Z;  // m x m lower, ld m
+  const double* Zinv;  // m x m lower, Z_p^{-1}, ld m
   const int* slots;
   int m, pad;
 };
 struct ApQE {
-  const double* V;    // m x nref, ld m
-  const double* tau;  // nref
+  const double* Qt;   // m x m, Q_p^T, ld m
   const double* E;    // nE x ncols, ld nE
   const int* slots;   // m positions (before sparsification)
   const int* eslots;  // ncols positions
-  int m, nref, r, nE, ncols, pad;
+  int m, r, nE, ncols;
 };
 
 // ---------------------------------------------------------------------------
@@ -146,17 +157,26 @@ void launch_scatter(const double* val, const int64_t* dst_index, double* base_lo
 void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s);
 void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s);
+void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s);
 int rrqr_smem_bytes(int max_m, int max_cols, int max_segs);
+// On-chip variant: C CTAs per interface (a thread-block cluster), the block in shared memory.
+int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
+// Clusters of this shape that can be resident at once (0: cannot be launched).
+int rrqr_cluster_active(int csize, int smem_bytes);
+void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
+                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
+                         int csize, int smem_bytes, cudaStream_t s);
 void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
                  int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
                  int max_cols, int max_segs, cudaStream_t s);
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, double* z, bool forward,
-                        cudaStream_t s);
+void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, int max_cols, double* z,
+                        bool forward, cudaStream_t s);
 void launch_ap_scale(const ApScale* t, int ntasks, int max_m, double* z, bool forward,
                      cudaStream_t s);
-void launch_ap_qe(const ApQE* t, int ntasks, int max_m, double* z, bool forward, cudaStream_t s);
+void launch_ap_qe(const ApQE* t, int ntasks, int max_m, int max_cols, double* z, bool forward,
+                  cudaStream_t s);
 
 void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
                  const double* x, double* y, cudaStream_t s);

@@ -6,6 +6,8 @@
 // batched over a task array built by the host for one step of Algorithm 2
 // (§3): one CTA per task, variable sizes, no atomics, so results do not
 // depend on scheduling.
+#include <cooperative_groups.h>
+
 #include <cstdio>
 
 #include "spand_internal.h"
@@ -133,22 +135,68 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_
 }
 
 // ---------------------------------------------------------------------------
-// Batched triangular solve with a lower factor, 32 right-hand sides per CTA
-// (one warp, one right-hand side per lane, dot-product form).
+// Batched triangular solve with a lower factor, 32 right-hand sides per CTA.
+// The right-hand sides are staged in shared memory (row-major, 32 wide) and
+// solved by 32-row blocks: warp 0 solves the 32 x 32 diagonal block (lane =
+// right-hand side, dot-product form), then all warps update the rows below
+// with the block's solution (4 partial sums per row).  Rows of an identity
+// right-hand side above its unit entry stay zero and are skipped.
 // ---------------------------------------------------------------------------
 constexpr int kTrsmNC = 32;
+constexpr int kTrsmThreads = 128;
 
-__global__ void k_trsm(const TrsmTask* __restrict__ tasks, int smem_rows) {
+__device__ void trsm_blocked(const double* __restrict__ L, size_t ldl, int m, double* xs,
+                             int row0, int nc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int rb = row0; rb < m; rb += 32) {
+    const int re = min(m, rb + 32);
+    if (warp == 0 && lane < nc) {
+      for (int i = rb; i < re; ++i) {
+        double s = xs[i * kTrsmNC + lane];
+        const double* Li = L + i;
+        for (int j = rb; j < i; ++j) s = fma(-Li[j * ldl], xs[j * kTrsmNC + lane], s);
+        xs[i * kTrsmNC + lane] = s / Li[i * ldl];
+      }
+    }
+    __syncthreads();
+    if (lane < nc) {
+      for (int i = re + warp; i < m; i += nw) {
+        const double* Li = L + i;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = rb;
+        for (; j + 3 < re; j += 4) {
+          s0 = fma(Li[j * ldl], xs[j * kTrsmNC + lane], s0);
+          s1 = fma(Li[(j + 1) * ldl], xs[(j + 1) * kTrsmNC + lane], s1);
+          s2 = fma(Li[(j + 2) * ldl], xs[(j + 2) * kTrsmNC + lane], s2);
+          s3 = fma(Li[(j + 3) * ldl], xs[(j + 3) * kTrsmNC + lane], s3);
+        }
+        for (; j < re; ++j) s0 = fma(Li[j * ldl], xs[j * kTrsmNC + lane], s0);
+        xs[i * kTrsmNC + lane] -= (s0 + s1) + (s2 + s3);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restrict__ tasks,
+                                                       int smem_rows) {
   extern __shared__ double sm[];  // smem_rows x kTrsmNC
   const TrsmTask t = tasks[blockIdx.x];
   const int m = t.m, nc = t.ncols;
-  const int c = threadIdx.x;
   if (m == 0 || nc == 0) return;
   const double* L = t.L;
   const size_t ldl = t.ldl;
   if (m <= smem_rows) {
-    // stage the right-hand sides: xs[i * NC + c]
-    if (!t.trans) {
+    int row0 = 0;
+    if (t.pad >= 0) {
+      // X = L^{-1} [e_{c0} .. e_{c0+nc-1}]
+      const int c0 = t.pad;
+      row0 = c0 - (c0 % 32);
+      for (int e = threadIdx.x; e < m * kTrsmNC; e += blockDim.x) {
+        const int i = e / kTrsmNC, cc = e % kTrsmNC;
+        sm[e] = (i == c0 + cc) ? 1.0 : 0.0;
+      }
+    } else if (!t.trans) {
       for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
         const int i = e % m, cc = e / m;
         sm[i * kTrsmNC + cc] = t.X[i + (size_t)cc * t.ldx];
@@ -159,17 +207,9 @@ __global__ void k_trsm(const TrsmTask* __restrict__ tasks, int smem_rows) {
         sm[i * kTrsmNC + cc] = t.X[cc + (size_t)i * t.ldx];
       }
     }
-    __syncwarp();
-    if (c < nc) {
-      for (int i = 0; i < m; ++i) {
-        double s = sm[i * kTrsmNC + c];
-        const double* Li = L + i;
-        for (int j = 0; j < i; ++j) s -= Li[j * ldl] * sm[j * kTrsmNC + c];
-        sm[i * kTrsmNC + c] = s / Li[i * ldl];
-      }
-    }
-    __syncwarp();
-    if (!t.trans) {
+    __syncthreads();
+    trsm_blocked(L, ldl, m, sm, row0, nc);
+    if (!t.trans || t.pad >= 0) {
       for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
         const int i = e % m, cc = e / m;
         t.X[i + (size_t)cc * t.ldx] = sm[i * kTrsmNC + cc];
@@ -180,8 +220,20 @@ __global__ void k_trsm(const TrsmTask* __restrict__ tasks, int smem_rows) {
         t.X[cc + (size_t)i * t.ldx] = sm[i * kTrsmNC + cc];
       }
     }
-  } else if (c < nc) {
-    // large factor: solve in place in global memory
+  } else if (threadIdx.x < nc && t.pad >= 0) {
+    // very large factor: one right-hand side per thread, in place in global memory
+    const int c = threadIdx.x;
+    double* x = t.X + (size_t)c * t.ldx;
+    const int cc = t.pad + c;
+    for (int i = 0; i < cc; ++i) x[i] = 0.0;
+    for (int i = cc; i < m; ++i) {
+      double s = (i == cc) ? 1.0 : 0.0;
+      const double* Li = L + i;
+      for (int j = cc; j < i; ++j) s -= Li[j * ldl] * x[j];
+      x[i] = s / Li[i * ldl];
+    }
+  } else if (threadIdx.x < nc) {
+    const int c = threadIdx.x;
     double* x = t.trans ? t.X + c : t.X + (size_t)c * t.ldx;
     const size_t inc = t.trans ? (size_t)t.ldx : 1;
     for (int i = 0; i < m; ++i) {
@@ -189,6 +241,46 @@ __global__ void k_trsm(const TrsmTask* __restrict__ tasks, int smem_rows) {
       const double* Li = L + i;
       for (int j = 0; j < i; ++j) s -= Li[j * ldl] * x[j * inc];
       x[i * inc] = s / Li[i * ldl];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Explicit Q^T = H_{nref-1} ... H_0 of an interface (for the apply), 32
+// columns per CTA: lane c builds column c0+c by applying the reflectors to
+// the unit vector, with plain FMA chains.
+// ---------------------------------------------------------------------------
+__global__ void k_form_qt(const FormQtTask* __restrict__ tasks, int smem_rows) {
+  extern __shared__ double sm[];  // smem_rows x kTrsmNC
+  const FormQtTask t = tasks[blockIdx.x];
+  const int m = t.m, nc = t.ncols, c = threadIdx.x;
+  if (m == 0 || nc == 0) return;
+  double* x;
+  size_t inc;
+  if (m <= smem_rows) {
+    x = sm + c;
+    inc = kTrsmNC;
+  } else {
+    x = t.Qt + (size_t)c * m;
+    inc = 1;
+  }
+  if (c < nc) {
+    const int j = t.c0 + c;
+    for (int i = 0; i < m; ++i) x[i * inc] = (i == j) ? 1.0 : 0.0;
+    for (int s = 0; s < t.nref; ++s) {
+      const double* v = t.V + (size_t)s * m;
+      double d = 0.0;
+      for (int i = s; i < m; ++i) d = fma(v[i], x[i * inc], d);
+      const double f = t.tau[s] * d;
+      if (f != 0.0)
+        for (int i = s; i < m; ++i) x[i * inc] = fma(-f, v[i], x[i * inc]);
+    }
+  }
+  if (m <= smem_rows) {
+    __syncwarp();
+    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+      const int i = e % m, cc = e / m;
+      t.Qt[i + (size_t)cc * m] = sm[i * kTrsmNC + cc];
     }
   }
 }
@@ -435,6 +527,258 @@ __global__ void __launch_bounds__(kQrThreads)
   if (tid == 0) cur_size[t.id] = r;
 }
 
+// ---------------------------------------------------------------------------
+// The same QR with the block held on chip: a thread-block cluster of C CTAs
+// (C = 1, 2, 4, 8 or 16) per interface, each CTA keeping a contiguous slice of
+// the columns in its shared memory for the whole factorization.  Per step the
+// CTAs exchange their local (largest, second largest) squared norms through
+// distributed shared memory, the CTA that owns the pivot column builds the
+// Householder vector, and the others copy it from the owner's shared memory.
+// Two cluster barriers per step; results are identical to k_rrqr's rules.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+// Candidate exchange of one step: the largest squared norm (as the int64 bit
+// pattern of a non-negative double, which orders like the value; pivoted
+// columns hold -1.0 and sort below every candidate), its column, and the second
+// largest.  Integer compares keep the pivot search off the FP64 pipe.
+struct QrSlot {
+  long long best, second;
+  int idx, pad;
+};
+
+__device__ __forceinline__ void slot_merge(QrSlot& a, const QrSlot& b) {
+  const bool take = (b.best > a.best) || (b.best == a.best && b.idx < a.idx);
+  if (take) {
+    a.second = max(max(a.second, b.second), a.best);
+    a.best = b.best;
+    a.idx = b.idx;
+  } else {
+    a.second = max(max(a.second, b.second), b.best);
+  }
+}
+
+constexpr long long kNoKey = (long long)0x8000000000000000ULL;
+
+// One thread per column: the dot product v^T a, the update a -= tau (v^T a) v
+// and the new trailing norm are plain FMA chains in each thread, with no
+// cross-lane reductions.  The block is stored row-major (row i of the local
+// columns contiguous) so that a warp reads consecutive addresses.
+__global__ void __launch_bounds__(kQrThreads)
+    k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
+                   int* __restrict__ cur_size, int* __restrict__ rank_out,
+                   int* __restrict__ nref_out, int* __restrict__ flag_out, double eps, int scheme,
+                   int csize) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const RRQRTask t = tasks[blockIdx.x / csize];
+  extern __shared__ double sm[];
+  __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
+  __shared__ QrSlot s_warp[kQrThreads / kWarp];
+  __shared__ QrSlot s_glob;
+  __shared__ double s_tau;   // owner's tau, read by the cluster
+  __shared__ int s_N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
+  const int m = t.m;
+  const size_t ld = t.ld;
+  const int nseg = t.seg_end - t.seg_begin;
+  const int ncl = (t.ncols_max + csize - 1) / csize;  // local column capacity (row length)
+  double* A = sm;                                      // m x ncl, row-major
+  double* v = A + (size_t)m * ncl;                     // m
+  double* norms = v + m;                               // ncl
+  int* pcol = reinterpret_cast<int*>(norms + ncl);     // ncl: column in the panel row
+  int* segid = pcol + ncl;                             // ncl: segment of the column
+  int* segoff = segid + ncl;                           // nseg + 1
+  if (tid == 0) {
+    int acc = 0;
+    for (int g = 0; g < nseg; ++g) {
+      segoff[g] = acc;
+      acc += cur_size[segs[t.seg_begin + g].cl];
+    }
+    segoff[nseg] = acc;
+    s_N = acc;
+  }
+  __syncthreads();
+  const int N = s_N;
+  const int cpb = (N + csize - 1) / csize;
+  const int g0 = crank * cpb;
+  const int nloc = max(0, min(N, g0 + cpb) - g0);
+  for (int l = tid; l < nloc; l += kQrThreads) {
+    const int g = g0 + l;
+    int lo = 0, hi = nseg - 1;  // last segment with segoff <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segoff[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    segid[l] = lo;
+    pcol[l] = segs[t.seg_begin + lo].col + (g - segoff[lo]);
+  }
+  __syncthreads();
+  for (int e = tid; e < m * nloc; e += kQrThreads) {
+    const int i = e % m, l = e / m;
+    A[(size_t)i * ncl + l] = t.A[i + (size_t)pcol[l] * ld];
+  }
+  __syncthreads();
+  for (int l = tid; l < nloc; l += kQrThreads) {
+    double s2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double a = A[(size_t)i * ncl + l];
+      s2 = fma(a, a, s2);
+    }
+    norms[l] = s2;
+  }
+  __syncthreads();
+  const double thr1 = eps * eps;
+  const double thr2 = thr1 * thr1;
+  const int maxsteps = min(m, N);
+  int r = -1, nsteps = 0, flags = 0;
+  double nu0sq = 0.0;
+  for (int step = 0; step < maxsteps; ++step) {
+    QrSlot mine{kNoKey, kNoKey, 0x7fffffff, 0};
+    for (int l = tid; l < nloc; l += kQrThreads) {
+      QrSlot c{__double_as_longlong(norms[l]), kNoKey, g0 + l, 0};
+      slot_merge(mine, c);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      QrSlot other;
+      other.best = __shfl_xor_sync(0xffffffffu, mine.best, o);
+      other.second = __shfl_xor_sync(0xffffffffu, mine.second, o);
+      other.idx = __shfl_xor_sync(0xffffffffu, mine.idx, o);
+      other.pad = 0;
+      slot_merge(mine, other);
+    }
+    if (lane == 0) s_warp[warp] = mine;
+    __syncthreads();
+    if (tid == 0) {
+      QrSlot a = s_warp[0];
+      for (int w = 1; w < nw; ++w) slot_merge(a, s_warp[w]);
+      s_slot = a;
+    }
+    cluster.sync();
+    if (tid == 0) {
+      QrSlot a{kNoKey, kNoKey, 0x7fffffff, 0};
+      for (int c = 0; c < csize; ++c) slot_merge(a, *cluster.map_shared_rank(&s_slot, c));
+      s_glob = a;
+    }
+    __syncthreads();
+    const QrSlot gb = s_glob;
+    const double nusq = __longlong_as_double(gb.best);
+    if (tid == 0 && gb.second >= 0 && nusq > 0.0) {
+      const double sec = __longlong_as_double(gb.second);
+      if (nusq - sec <= 1e-12 * nusq) flags |= 1;
+    }
+    if (step == 0) {
+      nu0sq = nusq;
+      if (!(nu0sq > 0.0)) {
+        r = 0;
+        break;
+      }
+    }
+    if (tid == 0) {
+      if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
+      if (scheme == SPAND_SECOND_ORDER_SUPERFINE && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq)
+        flags |= 2;
+    }
+    if (r < 0 && nusq < thr1 * nu0sq) {
+      r = step;
+      if (scheme != SPAND_SECOND_ORDER_SUPERFINE) break;
+    }
+    if (scheme == SPAND_SECOND_ORDER_SUPERFINE && nusq < thr2 * nu0sq) break;
+    const int owner = gb.idx / cpb;
+    if (crank == owner) {
+      const int l = gb.idx - g0;
+      const double alpha = A[(size_t)step * ncl + l];
+      const double normx = sqrt(nusq);
+      double beta, tau;
+      if (normx == 0.0) {
+        beta = alpha;
+        tau = 0.0;
+      } else {
+        beta = alpha >= 0.0 ? -normx : normx;
+        tau = (beta - alpha) / beta;
+      }
+      const double den = alpha - beta;
+      for (int i = tid; i < m; i += kQrThreads) {
+        double vi;
+        if (i < step) vi = 0.0;
+        else if (i == step) vi = 1.0;
+        else vi = (normx == 0.0) ? 0.0 : A[(size_t)i * ncl + l] / den;
+        v[i] = vi;
+        t.V[i + (size_t)step * m] = vi;
+      }
+      if (tid == 0) {
+        t.tau[step] = tau;
+        s_tau = tau;
+        norms[l] = -1.0;
+      }
+      __syncthreads();
+      for (int i = step + tid; i < m; i += kQrThreads) A[(size_t)i * ncl + l] = (i == step) ? beta : 0.0;
+    }
+    cluster.sync();
+    double tau;
+    if (crank != owner) {
+      const double* rv = cluster.map_shared_rank(v, owner);
+      for (int i = step + tid; i < m; i += kQrThreads) v[i] = rv[i];
+      tau = *cluster.map_shared_rank(&s_tau, owner);
+      __syncthreads();
+    } else {
+      tau = s_tau;
+    }
+    for (int l = tid; l < nloc; l += kQrThreads) {
+      if (norms[l] < 0.0) continue;
+      double* a = A + l;
+      double d0 = 0.0, d1 = 0.0;
+      int i = step;
+      for (; i + 1 < m; i += 2) {
+        d0 = fma(v[i], a[(size_t)i * ncl], d0);
+        d1 = fma(v[i + 1], a[(size_t)(i + 1) * ncl], d1);
+      }
+      if (i < m) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+      const double f = tau * (d0 + d1);
+      double s2 = 0.0;
+      {
+        const double x = fma(-f, v[step], a[(size_t)step * ncl]);
+        a[(size_t)step * ncl] = x;
+      }
+      for (i = step + 1; i < m; ++i) {
+        const double x = fma(-f, v[i], a[(size_t)i * ncl]);
+        a[(size_t)i * ncl] = x;
+        s2 = fma(x, x, s2);
+      }
+      norms[l] = s2;
+    }
+    __syncthreads();
+    nsteps = step + 1;
+  }
+  if (r < 0) r = nsteps;
+  // write the columns back, mirror the coarse rows into the neighbours' rows
+  for (int e = tid; e < m * nloc; e += kQrThreads) {
+    const int i = e % m, l = e / m;
+    t.A[i + (size_t)pcol[l] * ld] = A[(size_t)i * ncl + l];
+  }
+  for (int e = tid; e < r * nloc; e += kQrThreads) {
+    const int i = e % r, l = e / r;
+    const RRQRSeg g = segs[t.seg_begin + segid[l]];
+    const int c = g0 + l - segoff[segid[l]];
+    g.mirror[c + (size_t)i * g.mirror_ld] = A[(size_t)i * ncl + l];
+  }
+  if (crank == 0) {
+    for (int e = tid; e < r * r; e += kQrThreads) {
+      const int i = e % r, j = e / r;
+      t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid == 0) {
+      rank_out[t.id] = r;
+      nref_out[t.id] = nsteps;
+      cur_size[t.id] = r;
+      flag_out[t.id] = flags;
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -482,11 +826,77 @@ void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
     bytes = rows * kTrsmNC * (int)sizeof(double);
   }
   set_smem((const void*)k_trsm, bytes);
-  k_trsm<<<ntasks, kTrsmNC, bytes, s>>>(t, rows);
+  k_trsm<<<ntasks, kTrsmThreads, bytes, s>>>(t, rows);
+}
+
+void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  int rows = max_m;
+  int bytes = rows * kTrsmNC * (int)sizeof(double);
+  if (bytes > kSmemBudget) {
+    rows = kSmemBudget / (kTrsmNC * (int)sizeof(double));
+    bytes = rows * kTrsmNC * (int)sizeof(double);
+  }
+  set_smem((const void*)k_form_qt, bytes);
+  k_form_qt<<<ntasks, kTrsmNC, bytes, s>>>(t, rows);
 }
 
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s) {
   if (ntiles > 0) k_schur<<<ntiles, 256, 0, s>>>(tiles, c);
+}
+
+int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
+  const long ncl = (ncols_max + csize - 1) / csize;
+  const long b = 8L * m * ncl + 8L * m + 8L * ncl + 8L * ncl + 4L * (nseg + 2);
+  return (int)std::min<long>(b, 1L << 30);
+}
+
+void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
+                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
+                         int csize, int smem_bytes, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_bytes);
+  if (csize > 8)
+    cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ntasks * csize));
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, cur_size, rank_out, nref_out, flag_out, eps,
+                     scheme, csize);
+}
+
+int rrqr_cluster_active(int csize, int smem_bytes) {
+  cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_bytes);
+  if (csize > 8)
+    cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)csize);
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_rrqr_cluster, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 int rrqr_smem_bytes(int max_m, int max_cols, int max_segs) {

@@ -36,9 +36,9 @@ def _torch():
     return torch
 
 
-def _gpu_handle(prob, ell, eps, scheme, skip=None):
+def _gpu_handle(prob, ell, eps, scheme, skip=None, rrqr_kernel=0):
     from paper_2007_00789_gb300 import spand as S
-    h = S.Spand.from_problem(prob, ell, eps, scheme, skip=skip)
+    h = S.Spand.from_problem(prob, ell, eps, scheme, skip=skip, rrqr_kernel=rrqr_kernel)
     h.factor()
     return h
 
@@ -86,6 +86,8 @@ CASES = [
     ("diff_ragged_so", lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 3e-2, 1, 1, False),
     ("poisson3d_12_skip0", lambda: si.laplacian_3d(12), 6, 1e-1, 1, 0, True),
     ("diff2d_ragged_sf", lambda: si.diffusion_grid((45, 38), seed=9), 6, 1e-2, 2, 1, False),
+    # wide interfaces: on-chip QR in clusters of several CTAs (and the streamed kernel below)
+    ("diff3d_32_so", lambda: si.diffusion_3d(32, seed=6), 9, 1e-2, 1, None, False),
 ]
 
 
@@ -165,6 +167,20 @@ def test_eps_zero_is_exact(make, ell, scheme):
     it, rel = h.pcg(b, x, 1e-12)
     assert it == 1 and rel < 1e-12
     h.close()
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_streamed_and_on_chip_rrqr_agree(scheme):
+    """Both QR kernels follow the same rules: identical ranks, M r equal to 1e-12."""
+    prob = si.diffusion_3d(32, seed=6)
+    a = _gpu_handle(prob, 9, 1e-2, scheme, rrqr_kernel=0)
+    b = _gpu_handle(prob, 9, 1e-2, scheme, rrqr_kernel=1)
+    assert np.array_equal(a.ranks(), b.ranks())
+    r = np.random.default_rng(3).standard_normal(prob.n)
+    za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
+    assert np.abs(za - zb).max() <= 1e-12 * np.abs(za).max()
+    a.close()
+    b.close()
 
 
 def test_not_spd_reported():
