@@ -397,6 +397,93 @@ void schur_work(const std::vector<SchurTile>& tiles, const std::vector<SchurCont
   *bytes = b;
 }
 
+// Batched Cholesky of variable-size blocks.  Blocks of up to kPotrfSmall rows
+// are factored by one CTA each in shared memory; larger ones by a tiled
+// right-looking algorithm, all of them advancing one kPanel-column panel per
+// step: Cholesky of the diagonal tile, triangular solve of the panel below it,
+// and the update of the trailing lower triangle with Schur tiles.
+constexpr int kPotrfSmall = 128;
+constexpr int kPanel = 64;
+
+struct PotrfPlan {
+  std::vector<PotrfTask> small;
+  int small_max = 0;
+  struct Step {
+    std::vector<PotrfTask> diag;
+    std::vector<TrsmTask> trsm;
+    std::vector<SchurTile> tiles;
+    std::vector<SchurContrib> contribs;
+    size_t o_diag = 0, o_trsm = 0, o_tiles = 0, o_contribs = 0;
+  };
+  std::vector<Step> steps;
+  double flops = 0.0, bytes = 0.0;
+  size_t o_small = 0;
+};
+
+PotrfPlan plan_potrf(const std::vector<PotrfTask>& tasks) {
+  PotrfPlan P;
+  int nsteps = 0;
+  for (const auto& t : tasks) {
+    P.flops += (double)t.m * t.m * t.m / 3.0;
+    P.bytes += 16.0 * t.m * t.m;
+    if (t.m <= kPotrfSmall) {
+      P.small.push_back(t);
+      P.small_max = std::max(P.small_max, t.m);
+    } else {
+      nsteps = std::max(nsteps, (t.m + kPanel - 1) / kPanel);
+    }
+  }
+  P.steps.resize(nsteps);
+  for (const auto& t : tasks) {
+    if (t.m <= kPotrfSmall) continue;
+    for (int k = 0; k * kPanel < t.m; ++k) {
+      auto& st = P.steps[k];
+      const int k0 = k * kPanel, b = std::min(kPanel, t.m - k0), below = t.m - k0 - b;
+      double* dg = t.a + k0 + (size_t)k0 * t.ld;
+      st.diag.push_back({dg, b, t.ld, t.id, 0});
+      if (below <= 0) continue;
+      double* panel = dg + b;
+      push_trsm(st.trsm, dg, t.ld, panel, b, t.ld, below, 1);
+      const int cb = (int)st.contribs.size();
+      SchurContrib c;
+      c.a = panel;
+      c.b = panel;
+      c.K = b;
+      c.lda = t.ld;
+      c.ldb = t.ld;
+      c.pad = 1;
+      st.contribs.push_back(c);
+      double* trail = panel + (size_t)b * t.ld;
+      for (int i0 = 0; i0 < below; i0 += 32)
+        for (int j0 = 0; j0 <= i0; j0 += 32) {
+          SchurTile tl;
+          tl.dst = trail + i0 + (size_t)j0 * t.ld;
+          tl.mirror = nullptr;
+          tl.ld = t.ld;
+          tl.ld_mirror = 0;
+          tl.rows = std::min(32, below - i0);
+          tl.cols = std::min(32, below - j0);
+          tl.cbegin = cb;
+          tl.cend = cb + 1;
+          tl.i0 = i0;
+          tl.j0 = j0;
+          st.tiles.push_back(tl);
+        }
+    }
+  }
+  return P;
+}
+
+void plan_to_blob(PotrfPlan& P, Blob& blob) {
+  P.o_small = blob.add(P.small);
+  for (auto& st : P.steps) {
+    st.o_diag = blob.add(st.diag);
+    st.o_trsm = blob.add(st.trsm);
+    st.o_tiles = blob.add(st.tiles);
+    st.o_contribs = blob.add(st.contribs);
+  }
+}
+
 struct StageLayout {
   std::vector<int> m;                      // size at stage start
   std::vector<double*> row;                // panel row origin
@@ -733,12 +820,15 @@ int factor_impl(spand_s* h, cudaStream_t s) {
     const size_t o_inv = blob.add(pending_inv);
     const size_t o_fq = blob.add(pending_qt);
     const size_t o_merge = blob.add(merge);
-    const size_t o_pi = blob.add(potrf_int);
+    PotrfPlan plan_int = plan_potrf(potrf_int);
+    plan_to_blob(plan_int, blob);
+    PotrfPlan plan_z = plan_potrf(zpotrf);
+    plan_to_blob(plan_z, blob);
     const size_t o_ti = blob.add(trsm_int);
     const size_t o_tiles = blob.add(tiles);
     const size_t o_contr = blob.add(contribs);
     const size_t o_zc = blob.add(zcopy);
-    const size_t o_zp = blob.add(zpotrf);
+
     const size_t o_lt = blob.add(ltrsm);
     const size_t o_rt = blob.add(rtrsm);
     const size_t o_mi = blob.add(mirror);
@@ -780,9 +870,26 @@ int factor_impl(spand_s* h, cudaStream_t s) {
       run(KK_MERGE, merge.size(), 0.0, copy_bytes(merge),
           [&] { launch_copy((const CopyTask*)(D + o_merge), (int)merge.size(), s); });
     }
-    run(KK_POTRF, potrf_int.size(), potrf_flops(potrf_int), potrf_bytes(potrf_int), [&] {
-      launch_potrf((const PotrfTask*)(D + o_pi), (int)potrf_int.size(), max_m_int, h->d_err, s);
-    });
+    auto run_potrf = [&](int kind, PotrfPlan& PP) {
+      bool first = true;
+      auto fl = [&]() { double f = first ? PP.flops : 0.0; first = false; return f; };
+      run(kind, PP.small.size(), fl(), PP.bytes, [&] {
+        launch_potrf((const PotrfTask*)(D + PP.o_small), (int)PP.small.size(), PP.small_max, h->d_err, s);
+      });
+      for (auto& st : PP.steps) {
+        run(kind, st.diag.size(), fl(), 0.0, [&] {
+          launch_potrf((const PotrfTask*)(D + st.o_diag), (int)st.diag.size(), kPanel, h->d_err, s);
+        });
+        run(kind, st.trsm.size(), 0.0, 0.0, [&] {
+          launch_trsm((const TrsmTask*)(D + st.o_trsm), (int)st.trsm.size(), kPanel, s);
+        });
+        run(kind, st.tiles.size(), 0.0, 0.0, [&] {
+          launch_schur((const SchurTile*)(D + st.o_tiles), (int)st.tiles.size(),
+                       (const SchurContrib*)(D + st.o_contribs), s);
+        });
+      }
+    };
+    run_potrf(KK_POTRF, plan_int);
     run(KK_TRSM, trsm_int.size(), trsm_flops(trsm_int), trsm_bytes(trsm_int),
         [&] { launch_trsm((const TrsmTask*)(D + o_ti), (int)trsm_int.size(), max_m_int, s); });
     {
@@ -796,9 +903,7 @@ int factor_impl(spand_s* h, cudaStream_t s) {
     if (S.sparsify) {
       run(KK_SCALE_COPY, zcopy.size(), 0.0, copy_bytes(zcopy),
           [&] { launch_copy((const CopyTask*)(D + o_zc), (int)zcopy.size(), s); });
-      run(KK_SCALE_POTRF, zpotrf.size(), potrf_flops(zpotrf), potrf_bytes(zpotrf), [&] {
-        launch_potrf((const PotrfTask*)(D + o_zp), (int)zpotrf.size(), max_m_if, h->d_err, s);
-      });
+      run_potrf(KK_SCALE_POTRF, plan_z);
       run(KK_SCALE_TRSM, ltrsm.size(), trsm_flops(ltrsm), trsm_bytes(ltrsm),
           [&] { launch_trsm((const TrsmTask*)(D + o_lt), (int)ltrsm.size(), max_m_if, s); });
       run(KK_SCALE_TRSM, rtrsm.size(), trsm_flops(rtrsm), trsm_bytes(rtrsm),

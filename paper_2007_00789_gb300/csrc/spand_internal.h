@@ -99,8 +99,10 @@ struct SchurTile {
   double* mirror;
   int ld, ld_mirror, rows, cols, cbegin, cend, i0, j0;
 };
-// A_c: K x (i0 + rows) at a (lda), B_c: K x (j0 + cols) at b (ldb), both
-// column-major; the tile uses columns i0.. of A_c and j0.. of B_c.
+// A_c: K x (i0 + rows) at a (lda), B_c: K x (j0 + cols) at b (ldb); the tile
+// uses columns i0.. of A_c and j0.. of B_c.  pad = 0: element (k, i) at
+// k + i*ld (column-major); pad = 1: at k*ld + i (the transposed storage, e.g.
+// a column panel P whose product P P^T is wanted).
 struct SchurContrib {
   const double* a;
   const double* b;

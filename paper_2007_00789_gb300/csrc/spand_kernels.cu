@@ -247,41 +247,57 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restric
 
 // ---------------------------------------------------------------------------
 // Explicit Q^T = H_{nref-1} ... H_0 of an interface (for the apply), 32
-// columns per CTA: lane c builds column c0+c by applying the reflectors to
-// the unit vector, with plain FMA chains.
+// columns per CTA: lane c follows column c0+c from the unit vector through
+// the reflectors; the 4 warps share the rows of every dot product and update
+// (so that all four FP64 units of the SM work), combining partial sums in
+// shared memory.
 // ---------------------------------------------------------------------------
-__global__ void k_form_qt(const FormQtTask* __restrict__ tasks, int smem_rows) {
-  extern __shared__ double sm[];  // smem_rows x kTrsmNC
+constexpr int kFqThreads = 128;
+
+__global__ void __launch_bounds__(kFqThreads) k_form_qt(const FormQtTask* __restrict__ tasks,
+                                                        int smem_rows) {
+  extern __shared__ double sm[];  // smem_rows x kTrsmNC, then 4 x kTrsmNC partial sums
   const FormQtTask t = tasks[blockIdx.x];
-  const int m = t.m, nc = t.ncols, c = threadIdx.x;
+  const int m = t.m, nc = t.ncols;
   if (m == 0 || nc == 0) return;
-  double* x;
-  size_t inc;
-  if (m <= smem_rows) {
-    x = sm + c;
-    inc = kTrsmNC;
-  } else {
-    x = t.Qt + (size_t)c * m;
-    inc = 1;
-  }
-  if (c < nc) {
-    const int j = t.c0 + c;
-    for (int i = 0; i < m; ++i) x[i * inc] = (i == j) ? 1.0 : 0.0;
-    for (int s = 0; s < t.nref; ++s) {
-      const double* v = t.V + (size_t)s * m;
-      double d = 0.0;
-      for (int i = s; i < m; ++i) d = fma(v[i], x[i * inc], d);
-      const double f = t.tau[s] * d;
-      if (f != 0.0)
-        for (int i = s; i < m; ++i) x[i * inc] = fma(-f, v[i], x[i * inc]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* part = sm + (size_t)smem_rows * kTrsmNC;
+  if (m > smem_rows) {
+    // very large block: one column per lane of warp 0, in global memory
+    if (warp == 0 && lane < nc) {
+      double* x = t.Qt + (size_t)lane * m;
+      const int j = t.c0 + lane;
+      for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+      for (int s = 0; s < t.nref; ++s) {
+        const double* v = t.V + (size_t)s * m;
+        double d = 0.0;
+        for (int i = s; i < m; ++i) d = fma(v[i], x[i], d);
+        const double f = t.tau[s] * d;
+        for (int i = s; i < m; ++i) x[i] = fma(-f, v[i], x[i]);
+      }
     }
+    return;
   }
-  if (m <= smem_rows) {
-    __syncwarp();
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-      const int i = e % m, cc = e / m;
-      t.Qt[i + (size_t)cc * m] = sm[i * kTrsmNC + cc];
-    }
+  for (int e = threadIdx.x; e < m * kTrsmNC; e += blockDim.x) {
+    const int i = e / kTrsmNC, c = e % kTrsmNC;
+    sm[e] = (i == t.c0 + c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int s = 0; s < t.nref; ++s) {
+    const double* v = t.V + (size_t)s * m;
+    double d = 0.0;
+    for (int i = s + warp; i < m; i += nw) d = fma(v[i], sm[i * kTrsmNC + lane], d);
+    part[warp * kTrsmNC + lane] = d;
+    __syncthreads();
+    double dt = 0.0;
+    for (int w = 0; w < nw; ++w) dt += part[w * kTrsmNC + lane];
+    const double f = t.tau[s] * dt;
+    for (int i = s + warp; i < m; i += nw) sm[i * kTrsmNC + lane] = fma(-f, v[i], sm[i * kTrsmNC + lane]);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+    const int i = e % m, cc = e / m;
+    t.Qt[i + (size_t)cc * m] = sm[i * kTrsmNC + cc];
   }
 }
 
@@ -303,14 +319,25 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int ci = t.cbegin; ci < t.cend; ++ci) {
     const SchurContrib c = contribs[ci];
-    const double* ca = c.a + (size_t)t.i0 * c.lda;
-    const double* cb = c.b + (size_t)t.j0 * c.ldb;
+    // kind 0: element (k, i) at k + i*ld (columns of W^T); kind 1: at k*ld + i
+    const size_t sk_a = c.pad ? (size_t)c.lda : 1, si_a = c.pad ? 1 : (size_t)c.lda;
+    const size_t sk_b = c.pad ? (size_t)c.ldb : 1, si_b = c.pad ? 1 : (size_t)c.ldb;
+    const double* ca = c.a + (size_t)t.i0 * si_a;
+    const double* cb = c.b + (size_t)t.j0 * si_b;
     for (int k0 = 0; k0 < c.K; k0 += kKc) {
       const int kk = min(kKc, c.K - k0);
-      for (int e = tid; e < kKc * kTile; e += 256) {
-        const int k = e % kKc, i = e / kKc;
-        As[k][i] = (k < kk && i < t.rows) ? ca[(k0 + k) + (size_t)i * c.lda] : 0.0;
-        Bs[k][i] = (k < kk && i < t.cols) ? cb[(k0 + k) + (size_t)i * c.ldb] : 0.0;
+      if (!c.pad) {
+        for (int e = tid; e < kKc * kTile; e += 256) {
+          const int k = e % kKc, i = e / kKc;
+          As[k][i] = (k < kk && i < t.rows) ? ca[(k0 + k) * sk_a + i * si_a] : 0.0;
+          Bs[k][i] = (k < kk && i < t.cols) ? cb[(k0 + k) * sk_b + i * si_b] : 0.0;
+        }
+      } else {
+        for (int e = tid; e < kKc * kTile; e += 256) {
+          const int i = e % kTile, k = e / kTile;
+          As[k][i] = (k < kk && i < t.rows) ? ca[(k0 + k) * sk_a + i * si_a] : 0.0;
+          Bs[k][i] = (k < kk && i < t.cols) ? cb[(k0 + k) * sk_b + i * si_b] : 0.0;
+        }
       }
       __syncthreads();
 #pragma unroll 8
@@ -544,6 +571,7 @@ namespace cg = cooperative_groups;
 // largest.  Integer compares keep the pivot search off the FP64 pipe.
 struct QrSlot {
   long long best, second;
+  double alpha;  // the candidate column's entry in the pivot row (the reflector's alpha)
   int idx, pad;
 };
 
@@ -553,6 +581,7 @@ __device__ __forceinline__ void slot_merge(QrSlot& a, const QrSlot& b) {
     a.second = max(max(a.second, b.second), a.best);
     a.best = b.best;
     a.idx = b.idx;
+    a.alpha = b.alpha;
   } else {
     a.second = max(max(a.second, b.second), b.best);
   }
@@ -560,10 +589,28 @@ __device__ __forceinline__ void slot_merge(QrSlot& a, const QrSlot& b) {
 
 constexpr long long kNoKey = (long long)0x8000000000000000ULL;
 
+__device__ __forceinline__ QrSlot warp_merge(QrSlot mine) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    QrSlot other;
+    other.best = __shfl_xor_sync(0xffffffffu, mine.best, o);
+    other.second = __shfl_xor_sync(0xffffffffu, mine.second, o);
+    other.idx = __shfl_xor_sync(0xffffffffu, mine.idx, o);
+    other.alpha = __shfl_xor_sync(0xffffffffu, mine.alpha, o);
+    other.pad = 0;
+    slot_merge(mine, other);
+  }
+  return mine;
+}
+
 // One thread per column: the dot product v^T a, the update a -= tau (v^T a) v
 // and the new trailing norm are plain FMA chains in each thread, with no
-// cross-lane reductions.  The block is stored row-major (row i of the local
-// columns contiguous) so that a warp reads consecutive addresses.
+// cross-lane reductions; each thread also keeps the best candidate among its
+// columns for the next step.  The block is stored row-major (row i of the
+// local columns contiguous) so that a warp reads consecutive addresses.  Per
+// step: one block barrier and two cluster barriers; every warp reads the
+// CTAs' candidates itself, and the owner of the pivot column pushes v and tau
+// into every CTA's shared memory.
 __global__ void __launch_bounds__(kQrThreads)
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int* __restrict__ cur_size, int* __restrict__ rank_out,
@@ -575,8 +622,7 @@ __global__ void __launch_bounds__(kQrThreads)
   extern __shared__ double sm[];
   __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
   __shared__ QrSlot s_warp[kQrThreads / kWarp];
-  __shared__ QrSlot s_glob;
-  __shared__ double s_tau;   // owner's tau, read by the cluster
+  __shared__ double s_tau;   // tau of the current step, written by the owner
   __shared__ int s_N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
   const int m = t.m;
@@ -620,6 +666,7 @@ __global__ void __launch_bounds__(kQrThreads)
     A[(size_t)i * ncl + l] = t.A[i + (size_t)pcol[l] * ld];
   }
   __syncthreads();
+  QrSlot mine{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
   for (int l = tid; l < nloc; l += kQrThreads) {
     double s2 = 0.0;
     for (int i = 0; i < m; ++i) {
@@ -627,28 +674,16 @@ __global__ void __launch_bounds__(kQrThreads)
       s2 = fma(a, a, s2);
     }
     norms[l] = s2;
+    QrSlot c{__double_as_longlong(s2), kNoKey, m > 0 ? A[l] : 0.0, g0 + l, 0};
+    slot_merge(mine, c);
   }
-  __syncthreads();
   const double thr1 = eps * eps;
   const double thr2 = thr1 * thr1;
   const int maxsteps = min(m, N);
   int r = -1, nsteps = 0, flags = 0;
   double nu0sq = 0.0;
   for (int step = 0; step < maxsteps; ++step) {
-    QrSlot mine{kNoKey, kNoKey, 0x7fffffff, 0};
-    for (int l = tid; l < nloc; l += kQrThreads) {
-      QrSlot c{__double_as_longlong(norms[l]), kNoKey, g0 + l, 0};
-      slot_merge(mine, c);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      QrSlot other;
-      other.best = __shfl_xor_sync(0xffffffffu, mine.best, o);
-      other.second = __shfl_xor_sync(0xffffffffu, mine.second, o);
-      other.idx = __shfl_xor_sync(0xffffffffu, mine.idx, o);
-      other.pad = 0;
-      slot_merge(mine, other);
-    }
+    mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
     if (tid == 0) {
@@ -657,13 +692,9 @@ __global__ void __launch_bounds__(kQrThreads)
       s_slot = a;
     }
     cluster.sync();
-    if (tid == 0) {
-      QrSlot a{kNoKey, kNoKey, 0x7fffffff, 0};
-      for (int c = 0; c < csize; ++c) slot_merge(a, *cluster.map_shared_rank(&s_slot, c));
-      s_glob = a;
-    }
-    __syncthreads();
-    const QrSlot gb = s_glob;
+    QrSlot gb{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
+    if (lane < csize) gb = *cluster.map_shared_rank(&s_slot, lane);
+    gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
     const double nusq = __longlong_as_double(gb.best);
     if (tid == 0 && gb.second >= 0 && nusq > 0.0) {
       const double sec = __longlong_as_double(gb.second);
@@ -689,43 +720,41 @@ __global__ void __launch_bounds__(kQrThreads)
     const int owner = gb.idx / cpb;
     if (crank == owner) {
       const int l = gb.idx - g0;
-      const double alpha = A[(size_t)step * ncl + l];
-      const double normx = sqrt(nusq);
-      double beta, tau;
-      if (normx == 0.0) {
-        beta = alpha;
-        tau = 0.0;
-      } else {
-        beta = alpha >= 0.0 ? -normx : normx;
-        tau = (beta - alpha) / beta;
+      double beta = 0.0, tau = 0.0, inv = 0.0;
+      if (lane == 0) {
+        // alpha travels with the candidate: reading it from A here would race
+        // with the threads of other warps that overwrite the pivot column below
+        const double alpha = gb.alpha;
+        const double normx = sqrt(nusq);
+        if (normx == 0.0) {
+          beta = alpha;
+          tau = 0.0;
+        } else {
+          beta = alpha >= 0.0 ? -normx : normx;
+          tau = (beta - alpha) / beta;
+          inv = 1.0 / (alpha - beta);
+        }
       }
-      const double den = alpha - beta;
-      for (int i = tid; i < m; i += kQrThreads) {
-        double vi;
-        if (i < step) vi = 0.0;
-        else if (i == step) vi = 1.0;
-        else vi = (normx == 0.0) ? 0.0 : A[(size_t)i * ncl + l] / den;
-        v[i] = vi;
+      beta = __shfl_sync(0xffffffffu, beta, 0);
+      tau = __shfl_sync(0xffffffffu, tau, 0);
+      inv = __shfl_sync(0xffffffffu, inv, 0);
+      for (int i = step + tid; i < m; i += kQrThreads) {
+        double* ai = A + (size_t)i * ncl + l;
+        const double vi = (i == step) ? 1.0 : (*ai) * inv;
+        *ai = (i == step) ? beta : 0.0;
         t.V[i + (size_t)step * m] = vi;
+        for (int c = 0; c < csize; ++c) cluster.map_shared_rank(v, c)[i] = vi;
       }
+      for (int i = tid; i < step; i += kQrThreads) t.V[i + (size_t)step * m] = 0.0;
       if (tid == 0) {
         t.tau[step] = tau;
-        s_tau = tau;
         norms[l] = -1.0;
+        for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_tau, c) = tau;
       }
-      __syncthreads();
-      for (int i = step + tid; i < m; i += kQrThreads) A[(size_t)i * ncl + l] = (i == step) ? beta : 0.0;
     }
     cluster.sync();
-    double tau;
-    if (crank != owner) {
-      const double* rv = cluster.map_shared_rank(v, owner);
-      for (int i = step + tid; i < m; i += kQrThreads) v[i] = rv[i];
-      tau = *cluster.map_shared_rank(&s_tau, owner);
-      __syncthreads();
-    } else {
-      tau = s_tau;
-    }
+    const double tau = s_tau;
+    mine = QrSlot{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
     for (int l = tid; l < nloc; l += kQrThreads) {
       if (norms[l] < 0.0) continue;
       double* a = A + l;
@@ -748,11 +777,14 @@ __global__ void __launch_bounds__(kQrThreads)
         s2 = fma(x, x, s2);
       }
       norms[l] = s2;
+      QrSlot c{__double_as_longlong(s2), kNoKey, step + 1 < m ? a[(size_t)(step + 1) * ncl] : 0.0,
+               g0 + l, 0};
+      slot_merge(mine, c);
     }
-    __syncthreads();
     nsteps = step + 1;
   }
   if (r < 0) r = nsteps;
+  __syncthreads();
   // write the columns back, mirror the coarse rows into the neighbours' rows
   for (int e = tid; e < m * nloc; e += kQrThreads) {
     const int i = e % m, l = e / m;
@@ -832,13 +864,14 @@ void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
 void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s) {
   if (ntasks <= 0) return;
   int rows = max_m;
-  int bytes = rows * kTrsmNC * (int)sizeof(double);
+  const int extra = 4 * kTrsmNC * (int)sizeof(double);
+  int bytes = rows * kTrsmNC * (int)sizeof(double) + extra;
   if (bytes > kSmemBudget) {
-    rows = kSmemBudget / (kTrsmNC * (int)sizeof(double));
-    bytes = rows * kTrsmNC * (int)sizeof(double);
+    rows = (kSmemBudget - extra) / (kTrsmNC * (int)sizeof(double));
+    bytes = rows * kTrsmNC * (int)sizeof(double) + extra;
   }
   set_smem((const void*)k_form_qt, bytes);
-  k_form_qt<<<ntasks, kTrsmNC, bytes, s>>>(t, rows);
+  k_form_qt<<<ntasks, kFqThreads, bytes, s>>>(t, rows);
 }
 
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s) {

@@ -169,12 +169,14 @@ def test_eps_zero_is_exact(make, ell, scheme):
     h.close()
 
 
-@pytest.mark.parametrize("scheme", [1, 2])
-def test_streamed_and_on_chip_rrqr_agree(scheme):
-    """Both QR kernels follow the same rules: identical ranks, M r equal to 1e-12."""
-    prob = si.diffusion_3d(32, seed=6)
-    a = _gpu_handle(prob, 9, 1e-2, scheme, rrqr_kernel=0)
-    b = _gpu_handle(prob, 9, 1e-2, scheme, rrqr_kernel=1)
+@pytest.mark.parametrize("d,ell,scheme", [(32, 9, 1), (32, 9, 2), (64, 12, 1)])
+def test_streamed_and_on_chip_rrqr_agree(d, ell, scheme):
+    """Both QR kernels follow the same rules: identical ranks, M r equal to 1e-12.
+
+    At 64^3 the upper levels use clusters of up to 16 CTAs per interface."""
+    prob = si.diffusion_3d(d, seed=6)
+    a = _gpu_handle(prob, ell, 1e-2, scheme, rrqr_kernel=0)
+    b = _gpu_handle(prob, ell, 1e-2, scheme, rrqr_kernel=1)
     assert np.array_equal(a.ranks(), b.ranks())
     r = np.random.default_rng(3).standard_normal(prob.n)
     za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
