@@ -221,7 +221,49 @@ struct Phase {
   int kind, begin, end, max_m;
   double flops, bytes;  // algorithmic, forward sweep (the backward one is the same)
   int max_cols = 0;     // widest neighbour gather
+  int K = 1;            // CTAs per operator (thread-block cluster)
 };
+
+// CTAs per apply operator: enough that each handles about 12k FMAs.
+inline int ap_cluster(double fmas) {
+  int K = 1;
+  while (K < 16 && fmas / K > 12288.0) K *= 2;
+  return K;
+}
+
+// Split [ph.begin, ph.end) of the descriptor vector v into one phase per
+// cluster size; the operators of a phase are independent, so their order
+// within the phase is free.
+template <class T>
+void split_phase(std::vector<Phase>& phases, std::vector<T>& v, const Phase& ph,
+                 const std::vector<int>& Ks, const std::vector<double>& fl,
+                 const std::vector<double>& by, const std::vector<int>& ms,
+                 const std::vector<int>& cols) {
+  std::vector<int> order(ph.end - ph.begin);
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Ks[a] < Ks[b]; });
+  std::vector<T> seg(order.size());
+  for (size_t i = 0; i < order.size(); ++i) seg[i] = v[ph.begin + order[i]];
+  std::copy(seg.begin(), seg.end(), v.begin() + ph.begin);
+  size_t i = 0;
+  while (i < order.size()) {
+    Phase q = ph;
+    q.K = Ks[order[i]];
+    q.begin = ph.begin + (int)i;
+    q.max_m = 0;
+    q.max_cols = 0;
+    q.flops = q.bytes = 0.0;
+    while (i < order.size() && Ks[order[i]] == q.K) {
+      q.max_m = std::max(q.max_m, ms[order[i]]);
+      q.max_cols = std::max(q.max_cols, cols[order[i]]);
+      q.flops += fl[order[i]];
+      q.bytes += by[order[i]];
+      ++i;
+    }
+    q.end = ph.begin + (int)i;
+    phases.push_back(q);
+  }
+}
 
 struct ApInteriorP {
   const double* Linv;
@@ -983,6 +1025,8 @@ int factor_impl(spand_s* h, cudaStream_t s) {
     };
     {
       Phase ph{PH_INTERIOR, (int)api.size(), 0, 0, 0.0, 0.0};
+      std::vector<int> Ks, ms, cols;
+      std::vector<double> fl, by;
       for (int sidx : S.interiors) {
         const int m = Ly.m[sidx];
         ApInteriorP a;
@@ -1000,31 +1044,40 @@ int factor_impl(spand_s* h, cudaStream_t s) {
             pool.push_back(d == sidx ? -1 : pool[Ly.slot_off[d] + i]);
         }
         api.push_back(a);
-        ph.max_m = std::max(ph.max_m, m);
-        ph.max_cols = std::max(ph.max_cols, a.ncols);
-        ph.flops += (double)m * m + 2.0 * m * (a.ncols - m);
-        ph.bytes += 8.0 * ((double)m * (m + 1) / 2 + (double)m * (a.ncols - m)) + 24.0 * a.ncols;
+        const double fm = (double)m * (m + 1) / 2 + (double)m * (a.ncols - m);
+        Ks.push_back(ap_cluster(fm));
+        ms.push_back(m);
+        cols.push_back(a.ncols);
+        fl.push_back(2.0 * fm);
+        by.push_back(8.0 * fm + 24.0 * a.ncols);
         nnzf += (int64_t)m * (m + 1) / 2 + (int64_t)m * (a.ncols - m);
       }
       ph.end = (int)api.size();
-      if (ph.end > ph.begin) phases.push_back(ph);
+      if (ph.end > ph.begin) split_phase(phases, api, ph, Ks, fl, by, ms, cols);
     }
     if (S.sparsify) {
       Phase ph{PH_SCALE, (int)aps.size(), 0, 0, 0.0, 0.0};
+      std::vector<int> Ks, ms, cols;
+      std::vector<double> fl, by;
       for (int p : S.ifaces) {
         const int m = Ly.m[p];
         double* Zinv = nullptr;
         if (m > 0) RET(explicit_inverse(Ly.Z[p], m, &Zinv));
         aps.push_back({Zinv, Ly.slot_off[p], m});
-        ph.max_m = std::max(ph.max_m, m);
-        ph.flops += (double)m * m;
-        ph.bytes += 8.0 * (double)m * (m + 1) / 2 + 16.0 * m;
+        const double fm = (double)m * (m + 1) / 2;
+        Ks.push_back(ap_cluster(fm));
+        ms.push_back(m);
+        cols.push_back(0);
+        fl.push_back(2.0 * fm);
+        by.push_back(8.0 * fm + 16.0 * m);
         nnzf += (int64_t)m * (m + 1) / 2;
       }
       ph.end = (int)aps.size();
-      if (ph.end > ph.begin) phases.push_back(ph);
+      if (ph.end > ph.begin) split_phase(phases, aps, ph, Ks, fl, by, ms, cols);
       for (int col = 0; col < S.ncolours; ++col) {
         Phase pq{PH_QE, (int)apq.size(), 0, 0, 0.0, 0.0};
+        std::vector<int> Ks, ms, cols;
+        std::vector<double> fl, by;
         for (int p : S.by_colour[col]) {
           const int m = Ly.m[p];
           const int r = h->ranks[k][p], nref = h->nrefs[k][p];
@@ -1083,14 +1136,16 @@ int factor_impl(spand_s* h, cudaStream_t s) {
             a.nE = 0;
           }
           apq.push_back(a);
-          pq.max_m = std::max(pq.max_m, m);
-          if (a.nE > 0) pq.max_cols = std::max(pq.max_cols, ncols);
-          pq.flops += 2.0 * m * m + 2.0 * a.nE * ncols;
-          pq.bytes += 8.0 * ((double)m * m + (double)a.nE * ncols) + 16.0 * (m + ncols);
+          const double fm = (double)m * m + (double)a.nE * ncols;
+          Ks.push_back(ap_cluster(fm));
+          ms.push_back(m);
+          cols.push_back(a.nE > 0 ? ncols : 0);
+          fl.push_back(2.0 * fm);
+          by.push_back(8.0 * fm + 16.0 * (m + ncols));
           nnzf += (int64_t)m * nref + nref + (int64_t)a.nE * ncols;
         }
         pq.end = (int)apq.size();
-        if (pq.end > pq.begin) phases.push_back(pq);
+        if (pq.end > pq.begin) split_phase(phases, apq, pq, Ks, fl, by, ms, cols);
       }
     }
   }
@@ -1167,9 +1222,10 @@ int apply_impl(spand_s* h, const double* r, double* z, cudaStream_t s) {
     const int kind = ph.kind == PH_INTERIOR ? KK_AP_INTERIOR : ph.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
     P.run(kind, s, ph.flops, ph.bytes, [&] {
       if (ph.kind == PH_INTERIOR)
-        launch_ap_interior(h->d_api + ph.begin, nt, ph.max_m, ph.max_cols, z, fwd, s);
-      else if (ph.kind == PH_SCALE) launch_ap_scale(h->d_aps + ph.begin, nt, ph.max_m, z, fwd, s);
-      else launch_ap_qe(h->d_apq + ph.begin, nt, ph.max_m, ph.max_cols, z, fwd, s);
+        launch_ap_interior(h->d_api + ph.begin, nt, ph.K, ph.max_m, ph.max_cols, z, fwd, s);
+      else if (ph.kind == PH_SCALE)
+        launch_ap_scale(h->d_aps + ph.begin, nt, ph.K, ph.max_m, z, fwd, s);
+      else launch_ap_qe(h->d_apq + ph.begin, nt, ph.K, ph.max_m, ph.max_cols, z, fwd, s);
     });
   };
   for (const Phase& ph : h->phases) one(ph, true);

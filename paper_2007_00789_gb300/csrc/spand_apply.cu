@@ -9,6 +9,8 @@
 // Each phase below is one launch batched over the operators of one stage (or
 // one colour), which touch disjoint slots except for the accumulation into
 // neighbour slots, done with atomics.
+#include <cooperative_groups.h>
+
 #include "spand_internal.h"
 
 namespace spand {
@@ -34,147 +36,198 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// y = T x for a lower-triangular T (ld m), thread per row: FMA chains only.
-__device__ void lower_mv(const double* T, int m, const double* x, double* y) {
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;
-    int j = 0;
-    for (; j + 1 <= i; j += 2) {
-      s0 = fma(T[i + (size_t)j * m], x[j], s0);
-      s1 = fma(T[i + (size_t)(j + 1) * m], x[j + 1], s1);
+namespace cg = cooperative_groups;
+
+// Tiled matrix-vector products used by every apply step.  A CTA works on 32
+// outputs at a time (lane = output); its warps split the reduction dimension,
+// each keeping 4 partial sums, and warp 0 adds the warps' results from shared
+// memory.  The serial chain per thread is reduction length / (4 warps-worth),
+// not the full length, which is what bounds the latency of the large
+// operators of the upper levels.
+constexpr int kApWarps = kApThreads / 32;
+
+// out(r, sum_{c < C(r0)} M[r + c*ld] x[c]) for rows r in [r0, r1); ccap(rt) bounds
+// the columns a 32-row tile starting at rt needs (C for a full matrix, rt + 32
+// for a lower-triangular one whose strict upper part is zero).
+template <class Cap, class Out>
+__device__ void gemv_n(const double* __restrict__ M, size_t ld, int r0, int r1, Cap ccap,
+                       const double* __restrict__ x, double* red, Out out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rt = r0; rt < r1; rt += 32) {
+    const int r = rt + lane;
+    const int C = ccap(rt);
+    const int per = (C + kApWarps - 1) / kApWarps;
+    const int cb = warp * per, ce = min(C, cb + per);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (r < r1) {
+      const double* Mr = M + r;
+      int c = cb;
+      for (; c + 3 < ce; c += 4) {
+        s0 = fma(Mr[(size_t)c * ld], x[c], s0);
+        s1 = fma(Mr[(size_t)(c + 1) * ld], x[c + 1], s1);
+        s2 = fma(Mr[(size_t)(c + 2) * ld], x[c + 2], s2);
+        s3 = fma(Mr[(size_t)(c + 3) * ld], x[c + 3], s3);
+      }
+      for (; c < ce; ++c) s0 = fma(Mr[(size_t)c * ld], x[c], s0);
     }
-    if (j <= i) s0 = fma(T[i + (size_t)j * m], x[j], s0);
-    y[i] = s0 + s1;
-  }
-}
-
-// y = T^T x for a lower-triangular T: thread j walks column j of T.
-__device__ void lower_tmv(const double* T, int m, const double* x, double* y) {
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const double* col = T + (size_t)j * m;
-    double s0 = 0.0, s1 = 0.0;
-    int i = j;
-    for (; i + 1 < m; i += 2) {
-      s0 = fma(col[i], x[i], s0);
-      s1 = fma(col[i + 1], x[i + 1], s1);
+    red[warp * 32 + lane] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (warp == 0 && r < r1) {
+      double t = 0.0;
+      for (int w = 0; w < kApWarps; ++w) t += red[w * 32 + lane];
+      out(r, t);
     }
-    if (i < m) s0 = fma(col[i], x[i], s0);
-    y[j] = s0 + s1;
+    __syncthreads();
   }
 }
 
-// s = sum_c M[row + c*ld] * x[c] over c < n, 4 partial sums to keep loads in flight.
-__device__ __forceinline__ double row_dot(const double* __restrict__ M, size_t ld, int n,
-                                          const double* __restrict__ x) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 3 < n; c += 4) {
-    s0 = fma(M[(size_t)c * ld], x[c], s0);
-    s1 = fma(M[(size_t)(c + 1) * ld], x[c + 1], s1);
-    s2 = fma(M[(size_t)(c + 2) * ld], x[c + 2], s2);
-    s3 = fma(M[(size_t)(c + 3) * ld], x[c + 3], s3);
+// out(c, sum_{r in [rlo(ct), R)} M[r + c*ld] x[r]) for columns c in [c0, c1);
+// rlo(ct) is the first row a 32-column tile starting at ct needs (0 for a full
+// matrix, ct for the transpose of a lower-triangular one).
+template <class Lo, class Out>
+__device__ void gemv_t(const double* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
+                       const double* __restrict__ x, double* red, Out out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int ct = c0; ct < c1; ct += 32) {
+    const int c = ct + lane;
+    const int rb0 = rlo(ct);
+    const int per = (R - rb0 + kApWarps - 1) / kApWarps;
+    const int rb = rb0 + warp * per, re = min(R, rb + per);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (c < c1) {
+      const double* col = M + (size_t)c * ld;
+      int r = rb;
+      for (; r + 3 < re; r += 4) {
+        s0 = fma(col[r], x[r], s0);
+        s1 = fma(col[r + 1], x[r + 1], s1);
+        s2 = fma(col[r + 2], x[r + 2], s2);
+        s3 = fma(col[r + 3], x[r + 3], s3);
+      }
+      for (; r < re; ++r) s0 = fma(col[r], x[r], s0);
+    }
+    red[warp * 32 + lane] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (warp == 0 && c < c1) {
+      double t = 0.0;
+      for (int w = 0; w < kApWarps; ++w) t += red[w * 32 + lane];
+      out(c, t);
+    }
+    __syncthreads();
   }
-  for (; c < n; ++c) s0 = fma(M[(size_t)c * ld], x[c], s0);
-  return (s0 + s1) + (s2 + s3);
 }
 
-// s = sum_i col[i] * x[i] over i < n (a contiguous column).
-__device__ __forceinline__ double col_dot(const double* __restrict__ col, int n,
-                                          const double* __restrict__ x) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int i = 0;
-  for (; i + 3 < n; i += 4) {
-    s0 = fma(col[i], x[i], s0);
-    s1 = fma(col[i + 1], x[i + 1], s1);
-    s2 = fma(col[i + 2], x[i + 2], s2);
-    s3 = fma(col[i + 3], x[i + 3], s3);
-  }
-  for (; i < n; ++i) s0 = fma(col[i], x[i], s0);
-  return (s0 + s1) + (s2 + s3);
+namespace cg = cooperative_groups;
+
+// Every operator is applied by a thread-block cluster of K CTAs (K from the
+// launch; 1 for small operators); CTA k produces the contiguous slice
+// [n k / K, n (k+1) / K) of each output.  When a later step needs a whole
+// intermediate vector, each CTA stores its slice into every CTA's shared
+// memory and the cluster synchronises.  Shared memory: x (m), y (m),
+// gathered neighbour values (ncols), and the warps' partial sums.
+__device__ __forceinline__ int part_lo(int n, int k, int K) { return (int)(((long)n * k) / K); }
+
+__device__ __forceinline__ void share(cg::cluster_group& cl, int K, double* buf, int i, double val) {
+  for (int c = 0; c < K; ++c) cl.map_shared_rank(buf, c)[i] = val;
 }
 
-// Shared memory of the apply kernels: x (m), y (m), gathered neighbour values (ncols).
-__global__ void k_ap_interior(const ApInterior* __restrict__ tasks, double* __restrict__ z,
-                              int forward) {
+__global__ void __launch_bounds__(kApThreads)
+    k_ap_interior(const ApInterior* __restrict__ tasks, double* __restrict__ z, int forward) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ double sh[];
-  const ApInterior t = tasks[blockIdx.x];
-  const int m = t.m;
+  __shared__ double red[kApThreads];
+  const ApInterior t = tasks[blockIdx.x / K];
+  const int m = t.m, nc = t.ncols;
   double* xs = sh;
   double* ys = sh + m;
   double* zw = sh + 2 * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
   if (!forward)
-    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) {
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       const int ws = t.wslots[c];
       zw[c] = ws >= 0 ? z[ws] : 0.0;  // the diagonal segment contributes nothing
     }
   __syncthreads();
+  const int lo = part_lo(m, k, K), hi = part_lo(m, k + 1, K);
   if (forward) {
-    // z_s <- L_s^{-1} z_s, then z_w -= W_s z_s (column c of the panel row holds W_s^T[:, c])
-    lower_mv(t.Linv, m, xs, ys);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
-    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) {
-      const int ws = t.wslots[c];
-      if (ws < 0) continue;
-      atomicAdd(z + ws, -col_dot(t.WT + (size_t)c * m, m, ys));
-    }
+    // y = L_s^{-1} x, then z_s = y and z_w -= W_s y (column c of the panel row is W_s^T[:, c])
+    gemv_n(t.Linv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, red,
+           [&](int r, double v) { share(cl, K, ys, r, v); });
+    cl.sync();
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) z[t.slots[i]] = ys[i];
+    gemv_t(t.WT, m, part_lo(nc, k, K), part_lo(nc, k + 1, K), m, [](int) { return 0; }, ys, red,
+           [&](int c, double v) {
+             const int ws = t.wslots[c];
+             if (ws >= 0) atomicAdd(z + ws, -v);
+           });
   } else {
-    // z_s -= W_s^T z_w, then z_s <- L_s^{-T} z_s
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = xs[i] - row_dot(t.WT + i, m, t.ncols, zw);
-    __syncthreads();
-    lower_tmv(t.Linv, m, ys, xs);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = xs[i];
+    // y = x - W_s^T z_w, then z_s = L_s^{-T} y
+    gemv_n(t.WT, m, lo, hi, [&](int) { return nc; }, zw, red,
+           [&](int r, double v) { share(cl, K, ys, r, xs[r] - v); });
+    cl.sync();
+    gemv_t(t.Linv, m, lo, hi, m, [](int ct) { return ct; }, ys, red,
+           [&](int j, double v) { z[t.slots[j]] = v; });
   }
 }
 
-__global__ void k_ap_scale(const ApScale* __restrict__ tasks, double* __restrict__ z,
-                           int forward) {
+__global__ void __launch_bounds__(kApThreads)
+    k_ap_scale(const ApScale* __restrict__ tasks, double* __restrict__ z, int forward) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ double sh[];
-  const ApScale t = tasks[blockIdx.x];
+  __shared__ double red[kApThreads];
+  const ApScale t = tasks[blockIdx.x / K];
   const int m = t.m;
   double* xs = sh;
-  double* ys = sh + m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
-  __syncthreads();
-  if (forward) lower_mv(t.Zinv, m, xs, ys);
-  else lower_tmv(t.Zinv, m, xs, ys);
-  __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
+  cl.sync();  // every CTA has read z_p before any CTA overwrites part of it
+  const int lo = part_lo(m, k, K), hi = part_lo(m, k + 1, K);
+  if (forward)
+    gemv_n(t.Zinv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, red,
+           [&](int r, double v) { z[t.slots[r]] = v; });
+  else
+    gemv_t(t.Zinv, m, lo, hi, m, [](int ct) { return ct; }, xs, red,
+           [&](int j, double v) { z[t.slots[j]] = v; });
 }
 
-__global__ void k_ap_qe(const ApQE* __restrict__ tasks, double* __restrict__ z, int forward) {
+__global__ void __launch_bounds__(kApThreads)
+    k_ap_qe(const ApQE* __restrict__ tasks, double* __restrict__ z, int forward) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ double sh[];
-  const ApQE t = tasks[blockIdx.x];
-  const int m = t.m;
+  __shared__ double red[kApThreads];
+  const ApQE t = tasks[blockIdx.x / K];
+  const int m = t.m, nc = t.ncols, nE = t.nE;
   double* xs = sh;
   double* ys = sh + m;
   double* zw = sh + 2 * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
-  if (!forward && t.nE > 0)
-    for (int c = threadIdx.x; c < t.ncols; c += blockDim.x) zw[c] = z[t.eslots[c]];
+  if (!forward && nE > 0)
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) zw[c] = z[t.eslots[c]];
   __syncthreads();
+  const int lo = part_lo(m, k, K), hi = part_lo(m, k + 1, K);
   if (forward) {
-    // z_p <- Q^T z_p (row i of Q^T: Qt[i + j m] over j)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = row_dot(t.Qt + i, m, m, xs);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
-    // z_w -= E-tilde^T z_f
-    if (t.nE > 0)
-      for (int c = threadIdx.x; c < t.ncols; c += blockDim.x)
-        atomicAdd(z + t.eslots[c], -col_dot(t.E + (size_t)c * t.nE, t.nE, ys + t.r));
+    // y = Q^T x; z_p = y; z_w -= E-tilde^T y_f
+    gemv_n(t.Qt, m, lo, hi, [&](int) { return m; }, xs, red,
+           [&](int r, double v) { share(cl, K, ys, r, v); });
+    cl.sync();
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) z[t.slots[i]] = ys[i];
+    if (nE > 0)
+      gemv_t(t.E, nE, part_lo(nc, k, K), part_lo(nc, k + 1, K), nE, [](int) { return 0; },
+             ys + t.r, red, [&](int c, double v) { atomicAdd(z + t.eslots[c], -v); });
   } else {
-    // z_f -= E-tilde z_w
-    if (t.nE > 0) {
-      for (int i = threadIdx.x; i < t.nE; i += blockDim.x)
-        xs[t.r + i] -= row_dot(t.E + i, t.nE, t.ncols, zw);
-      __syncthreads();
+    // x_f -= E-tilde z_w, then z_p = Q x
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+      if (i < t.r || i >= t.r + nE) share(cl, K, ys, i, xs[i]);
+    if (nE > 0) {
+      const int flo = max(lo, t.r) - t.r, fhi = min(hi, t.r + nE) - t.r;
+      if (fhi > flo)
+        gemv_n(t.E, nE, flo, fhi, [&](int) { return nc; }, zw, red,
+               [&](int r, double v) { share(cl, K, ys, t.r + r, xs[t.r + r] - v); });
     }
-    // z_p <- Q z_p = (Q^T)^T z_p: thread j walks column j of Q^T
-    for (int j = threadIdx.x; j < m; j += blockDim.x) ys[j] = col_dot(t.Qt + (size_t)j * m, m, xs);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) z[t.slots[i]] = ys[i];
+    cl.sync();
+    gemv_t(t.Qt, m, lo, hi, m, [](int) { return 0; }, ys, red,
+           [&](int j, double v) { z[t.slots[j]] = v; });
   }
 }
 
@@ -260,28 +313,40 @@ static void smem_attr(const void* fn, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, int max_cols, double* z,
+template <class Task>
+static void launch_ap(void (*kern)(const Task*, double*, int), const Task* t, int ntasks, int K,
+                      int bytes, double* z, bool forward, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  smem_attr((const void*)kern, bytes);
+  if (K > 8) cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ntasks * K));
+  cfg.blockDim = dim3(kApThreads);
+  cfg.dynamicSmemBytes = (size_t)bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, t, z, forward ? 1 : 0);
+}
+
+void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, double* z,
                         bool forward, cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const int bytes = std::max(2 * max_m + max_cols, 1) * 8;
-  smem_attr((const void*)k_ap_interior, bytes);
-  k_ap_interior<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
+  launch_ap(k_ap_interior, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
 }
 
-void launch_ap_scale(const ApScale* t, int ntasks, int max_m, double* z, bool forward,
+void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, double* z, bool forward,
                      cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const int bytes = std::max(max_m, 1) * 16;
-  smem_attr((const void*)k_ap_scale, bytes);
-  k_ap_scale<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
+  launch_ap(k_ap_scale, t, ntasks, K, std::max(max_m, 1) * 8, z, forward, s);
 }
 
-void launch_ap_qe(const ApQE* t, int ntasks, int max_m, int max_cols, double* z, bool forward,
+void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, double* z, bool forward,
                   cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const int bytes = std::max(2 * max_m + max_cols, 1) * 8;
-  smem_attr((const void*)k_ap_qe, bytes);
-  k_ap_qe<<<ntasks, kApThreads, bytes, s>>>(t, z, forward ? 1 : 0);
+  launch_ap(k_ap_qe, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
 }
 
 void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,

@@ -173,12 +173,13 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_si
                  int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
                  int max_cols, int max_segs, cudaStream_t s);
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int max_m, int max_cols, double* z,
+// K: CTAs per operator (a thread-block cluster), 1..16.
+void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, double* z,
                         bool forward, cudaStream_t s);
-void launch_ap_scale(const ApScale* t, int ntasks, int max_m, double* z, bool forward,
+void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, double* z, bool forward,
                      cudaStream_t s);
-void launch_ap_qe(const ApQE* t, int ntasks, int max_m, int max_cols, double* z, bool forward,
-                  cudaStream_t s);
+void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, double* z,
+                  bool forward, cudaStream_t s);
 
 void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
                  const double* x, double* y, cudaStream_t s);

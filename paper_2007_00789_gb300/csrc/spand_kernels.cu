@@ -628,7 +628,9 @@ __global__ void __launch_bounds__(kQrThreads)
   const int m = t.m;
   const size_t ld = t.ld;
   const int nseg = t.seg_end - t.seg_begin;
-  const int ncl = (t.ncols_max + csize - 1) / csize;  // local column capacity (row length)
+  // local column capacity = row length of the row-major block, odd so that the
+  // rows touched by one column's threads fall in different banks
+  const int ncl = ((t.ncols_max + csize - 1) / csize) | 1;
   double* A = sm;                                      // m x ncl, row-major
   double* v = A + (size_t)m * ncl;                     // m
   double* norms = v + m;                               // ncl
@@ -649,6 +651,12 @@ __global__ void __launch_bounds__(kQrThreads)
   const int cpb = (N + csize - 1) / csize;
   const int g0 = crank * cpb;
   const int nloc = max(0, min(N, g0 + cpb) - g0);
+  // tpc threads share a column (its rows split among them), enough to keep all
+  // warps busy when the CTA holds few columns
+  int tpc = 1;
+  while (tpc < 8 && nloc * tpc * 2 <= kQrThreads) tpc *= 2;
+  const int ngrp = kQrThreads / tpc, grp = tid / tpc, sl = tid % tpc;
+  const unsigned gmask = (tpc == 32) ? 0xffffffffu : (((1u << tpc) - 1u) << (lane & ~(tpc - 1)));
   for (int l = tid; l < nloc; l += kQrThreads) {
     const int g = g0 + l;
     int lo = 0, hi = nseg - 1;  // last segment with segoff <= g
@@ -667,15 +675,18 @@ __global__ void __launch_bounds__(kQrThreads)
   }
   __syncthreads();
   QrSlot mine{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
-  for (int l = tid; l < nloc; l += kQrThreads) {
+  for (int l = grp; l < nloc; l += ngrp) {
     double s2 = 0.0;
-    for (int i = 0; i < m; ++i) {
+    for (int i = sl; i < m; i += tpc) {
       const double a = A[(size_t)i * ncl + l];
       s2 = fma(a, a, s2);
     }
-    norms[l] = s2;
-    QrSlot c{__double_as_longlong(s2), kNoKey, m > 0 ? A[l] : 0.0, g0 + l, 0};
-    slot_merge(mine, c);
+    for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
+    if (sl == 0) {
+      norms[l] = s2;
+      QrSlot c{__double_as_longlong(s2), kNoKey, m > 0 ? A[l] : 0.0, g0 + l, 0};
+      slot_merge(mine, c);
+    }
   }
   const double thr1 = eps * eps;
   const double thr2 = thr1 * thr1;
@@ -755,31 +766,33 @@ __global__ void __launch_bounds__(kQrThreads)
     cluster.sync();
     const double tau = s_tau;
     mine = QrSlot{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
-    for (int l = tid; l < nloc; l += kQrThreads) {
-      if (norms[l] < 0.0) continue;
+    for (int l = grp; l < nloc; l += ngrp) {
+      if (norms[l] < 0.0) continue;  // the same l for the whole group
       double* a = A + l;
       double d0 = 0.0, d1 = 0.0;
-      int i = step;
-      for (; i + 1 < m; i += 2) {
+      int i = step + sl;
+      for (; i + tpc < m; i += 2 * tpc) {
         d0 = fma(v[i], a[(size_t)i * ncl], d0);
-        d1 = fma(v[i + 1], a[(size_t)(i + 1) * ncl], d1);
+        d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
       }
       if (i < m) d0 = fma(v[i], a[(size_t)i * ncl], d0);
-      const double f = tau * (d0 + d1);
+      double d = d0 + d1;
+      for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
+      const double f = tau * d;
       double s2 = 0.0;
-      {
-        const double x = fma(-f, v[step], a[(size_t)step * ncl]);
-        a[(size_t)step * ncl] = x;
-      }
-      for (i = step + 1; i < m; ++i) {
+      for (i = step + sl; i < m; i += tpc) {
         const double x = fma(-f, v[i], a[(size_t)i * ncl]);
         a[(size_t)i * ncl] = x;
-        s2 = fma(x, x, s2);
+        if (i > step) s2 = fma(x, x, s2);
       }
-      norms[l] = s2;
-      QrSlot c{__double_as_longlong(s2), kNoKey, step + 1 < m ? a[(size_t)(step + 1) * ncl] : 0.0,
-               g0 + l, 0};
-      slot_merge(mine, c);
+      for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
+      __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
+      if (sl == 0) {
+        norms[l] = s2;
+        QrSlot c{__double_as_longlong(s2), kNoKey,
+                 step + 1 < m ? a[(size_t)(step + 1) * ncl] : 0.0, g0 + l, 0};
+        slot_merge(mine, c);
+      }
     }
     nsteps = step + 1;
   }
@@ -879,7 +892,7 @@ void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cud
 }
 
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
-  const long ncl = (ncols_max + csize - 1) / csize;
+  const long ncl = ((ncols_max + csize - 1) / csize) | 1;
   const long b = 8L * m * ncl + 8L * m + 8L * ncl + 8L * ncl + 4L * (nseg + 2);
   return (int)std::min<long>(b, 1L << 30);
 }
