@@ -168,6 +168,10 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP64 factor+apply; 1: FP32 factor+apply (PCG stays FP64)")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip timing the other precision")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -193,7 +197,7 @@ def main():
     prob, ell, b = make_problem(args.workload)
     tol = 1e-12
     stream = torch.cuda.current_stream()
-    h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme)
+    h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     iters = rel = None
@@ -236,7 +240,7 @@ def main():
         for i in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme)
+            he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision)
             he.factor(stream)
             x_host, it_e, rel_e = he.pcg_host(b, tol, stream)
             torch.cuda.synchronize()
@@ -246,6 +250,30 @@ def main():
         d2h = 8 * prob.n + 12 * sum(1 for _ in range(ell))
         e2e = {"value": min(times[1:] or times), "unit": "s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+
+    # ---- the other precision, same workload and timing rules (reported beside the line)
+    variant = None
+    if not args.no_variant:
+        other = 1 - args.precision
+        hv = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=other)
+        xv = torch.zeros_like(bd)
+        for _ in range(args.warmup):
+            hv.factor(stream)
+            itv, relv = hv.pcg(bd, xv, tol, stream)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            hv.factor(stream)
+            itv, relv = hv.pcg(bd, xv, tol, stream)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        true_rel = float(np.linalg.norm(b - prob.to_scipy() @ xv.cpu().numpy()) / np.linalg.norm(b))
+        variant = {"precision": "fp32 factor+apply, fp64 PCG" if other == 1 else "fp64",
+                   "value": v0.elapsed_time(v1) / args.steps / 1e3, "unit": "s",
+                   "cg_iters": itv, "relres": relv, "true_relres_host": true_rel}
+        hv.close()
 
     # ---- roofline of the dominant kernel (FP64 ALU bound)
     dom = max(kstats, key=lambda k: k["total_ms"])
@@ -259,12 +287,14 @@ def main():
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32 factor/apply + f64 pcg",
+        "data": "synthetic",
         "config": {"workload": args.workload, "n": prob.n, "nnz": prob.nnz, "nlevels": ell,
                    "eps": args.eps, "scheme": args.scheme, "tol": tol, "cg_iters": iters,
                    "relres": rel, "mu": info["mu"], "skip": info["skip"],
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "clocks": clk.summary(),
+        "variant": variant,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,

@@ -68,6 +68,10 @@ typedef struct {
   int32_t rrqr_kernel;    /* 0 = keep each interface block on chip (one CTA, or a thread-block
                              cluster of up to 16 CTAs) where it fits, else stream it from global
                              memory; 1 = always stream from global memory.  Same results. */
+  int32_t precision;      /* 0 = FP64 factorization and apply (the default);
+                             1 = FP32 factorization and apply, with the RRQR rank decisions
+                             (nu_0 and every step within 1e-4 of the threshold) taken on norms
+                             recomputed in FP64; PCG, its dot products and residuals stay FP64 */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */
@@ -157,6 +161,7 @@ int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol,
  *     overlap on the GPU (different streams or threads) race on it and give
  *     wrong results: serialise them.
  *   - Profiling (spand_set_profiling) is suspended for the call.
+ *   - Handles analysed with precision = 1 are refused with SPAND_EINVAL.
  * Arguments and results are those of spand_pcg. */
 int spand_pcg_noalloc(spand_t h, const double* b, double* x, double tol, int32_t* iters,
                       double* relres, void* stream);

@@ -19,7 +19,15 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspand.so")
 
-SOURCES = ["symbolic.cpp", "spand_kernels.cu", "spand_apply.cu", "driver.cu"]
+# (source, extra flags): the factor/apply translation units are compiled once per precision
+_F32 = ["-DSPAND_REAL=float", "-DSPAND_NS=f32"]
+_F64 = ["-DSPAND_REAL=double", "-DSPAND_NS=f64"]
+SOURCES = [
+    ("symbolic.cpp", []), ("api.cu", []), ("spand_pcg.cu", []),
+    ("factor_core.cu", _F64), ("factor_core.cu", _F32),
+    ("spand_kernels.cu", _F64), ("spand_kernels.cu", _F32),
+    ("spand_apply.cu", _F64), ("spand_apply.cu", _F32),
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -31,11 +39,13 @@ def nvcc() -> str:
     return path
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(item, extra: list[str]) -> str:
+    src, flags = item
+    tag = "_f32" if "-DSPAND_NS=f32" in flags else ("_f64" if flags else "")
+    obj = os.path.join(BUILD, os.path.splitext(src)[0] + tag + ".o")
+    cmd = [nvcc(), *ARCH, *COMMON, *flags, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
-        cmd = [nvcc(), *COMMON, *extra, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *COMMON, *flags, *extra, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"compiling {src} failed:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")

@@ -1,0 +1,593 @@
+// The C ABI of include/spand.h: handle life cycle, the host-only symbolic
+// analysis, dispatch of the factorization and apply to the FP64 or FP32
+// orchestration, and PCG (always FP64) on top of the preconditioner.
+#include <memory>
+#include <mutex>
+
+#include "spand_handle.h"
+
+namespace spand {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+}  // namespace spand
+
+using namespace spand;
+
+// First device use of a handle: upload A and the stage-0 pack map.
+int spand::ensure_device(spand_s* h) {
+  if (h->d_rowptr) return SPAND_OK;
+  const size_t n = (size_t)h->n, nnz = (size_t)std::max<int64_t>(h->nnz, 1);
+  CK(cudaMalloc(&h->d_rowptr, (n + 1) * 4));
+  CK(cudaMalloc(&h->d_colind, nnz * 4));
+  CK(cudaMalloc(&h->d_val, nnz * 8));
+  CK(cudaMalloc(&h->d_pack, nnz * 8));
+  CK(cudaMalloc(&h->d_err, 4 * sizeof(int)));
+  CK(cudaMemcpy(h->d_rowptr, h->h_rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_colind, h->h_colind.data(), (size_t)h->nnz * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_val, h->h_val.data(), (size_t)h->nnz * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_pack, h->h_pack.data(), (size_t)h->nnz * 8, cudaMemcpyHostToDevice));
+  return SPAND_OK;
+}
+
+namespace {
+
+int factor_impl(spand_s* h, cudaStream_t s) {
+  return h->precision == 0 ? f64::factor(h, s) : f32::factor(h, s);
+}
+
+// z = M r on FP64 vectors; an FP32 preconditioner is applied to an FP32 copy.
+int apply_any(spand_s* h, const double* r, double* z, cudaStream_t s) {
+  if (!h->factored) return fail(SPAND_ESTATE, "spand_apply before a successful spand_factor");
+  if (h->precision == 0) return f64::apply(h, r, z, s);
+  if (!h->d_rf) CK(cudaMalloc(&h->d_rf, (size_t)h->n * sizeof(float)));
+  launch_d2f(h->n, r, h->d_rf, s);
+  RET(f32::apply(h, h->d_rf, h->d_rf, s));
+  launch_f2d(h->n, h->d_rf, z, s);
+  return SPAND_OK;
+}
+
+int ensure_pcg(spand_s* h) {
+  if (h->d_r) return SPAND_OK;
+  const size_t n = (size_t)h->n;
+  CK(cudaMalloc(&h->d_r, n * 8));
+  CK(cudaMalloc(&h->d_z, n * 8));
+  CK(cudaMalloc(&h->d_p, n * 8));
+  CK(cudaMalloc(&h->d_q, n * 8));
+  CK(cudaMalloc(&h->d_scal, 16 * 8));
+  CK(cudaMalloc(&h->d_partial, (size_t)dot_partials(h->n) * 8));
+  CK(cudaMallocHost(&h->h_scal, 16 * 8));
+  return SPAND_OK;
+}
+
+// scal slots: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
+int pcg_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters, double* relres,
+             cudaStream_t s) {
+  if (!h->factored) return fail(SPAND_ESTATE, "spand_pcg before a successful spand_factor");
+  RET(ensure_pcg(h));
+  auto t0 = std::chrono::steady_clock::now();
+  const int n = h->n;
+  double* sc = h->d_scal;
+  Prof& P = h->prof;
+  const double nnz = (double)h->nnz;
+  auto dot = [&](const double* a, const double* c, int slot) {
+    P.run(KK_DOT, s, 2.0 * n, 16.0 * n, [&] { launch_dot(n, a, c, h->d_partial, sc + slot, s); });
+  };
+  auto spmv = [&](const double* xin, double* yout) {
+    P.run(KK_SPMV, s, 2.0 * nnz, 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n,
+          [&] { launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, xin, yout, s); });
+  };
+  auto read = [&](int slot, double* out) -> int {
+    CK(cudaMemcpyAsync(h->h_scal + slot, sc + slot, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (P.on) P.resolve();
+    *out = h->h_scal[slot];
+    return SPAND_OK;
+  };
+  P.run(KK_VEC, s, 0.0, 24.0 * n, [&] { launch_pcg_init(n, b, x, h->d_r, s); });
+  dot(b, b, 4);
+  double bb = 0.0;
+  RET(read(4, &bb));
+  const double bnorm = std::sqrt(bb);
+  int it = 0, restarts = 0;
+  double rel = 0.0;
+  int rc = SPAND_OK;
+  if (bnorm == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return SPAND_OK;
+  }
+  double rr = bb;
+  while (true) {
+    RET(apply_any(h, h->d_r, h->d_z, s));
+    P.run(KK_VEC, s, 0.0, 16.0 * n, [&] { launch_copy_vec(n, h->d_z, h->d_p, s); });
+    dot(h->d_r, h->d_z, 0);
+    while (it < h->maxit && std::sqrt(rr) / bnorm >= tol) {
+      spmv(h->d_p, h->d_q);
+      dot(h->d_p, h->d_q, 1);
+      P.run(KK_VEC, s, 4.0 * n, 48.0 * n, [&] { launch_pcg_step_x(n, sc, h->d_p, h->d_q, x, h->d_r, s); });
+      ++it;
+      if (it % h->true_every == 0) {
+        spmv(x, h->d_q);
+        P.run(KK_VEC, s, 1.0 * n, 24.0 * n, [&] { launch_residual(n, b, h->d_q, h->d_r, s); });
+      }
+      dot(h->d_r, h->d_r, 3);
+      RET(read(3, &rr));
+      if (std::sqrt(rr) / bnorm < tol) break;
+      RET(apply_any(h, h->d_r, h->d_z, s));
+      dot(h->d_r, h->d_z, 2);
+      P.run(KK_VEC, s, 2.0 * n, 24.0 * n, [&] { launch_pcg_step_p(n, sc, h->d_z, h->d_p, s); });
+      launch_pcg_scalars(sc, 0, s);
+    }
+    // true residual
+    spmv(x, h->d_q);
+    P.run(KK_VEC, s, 1.0 * n, 24.0 * n, [&] { launch_residual(n, b, h->d_q, h->d_r, s); });
+    dot(h->d_r, h->d_r, 3);
+    RET(read(3, &rr));
+    rel = std::sqrt(rr) / bnorm;
+    if (rel < tol || it >= h->maxit || restarts >= h->max_restarts) break;
+    ++restarts;
+  }
+  CK(cudaGetLastError());
+  if (rel >= tol && it >= h->maxit) rc = fail(SPAND_ENOCONV, "PCG reached maxit");
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  h->pcg_iters = it;
+  h->pcg_relres = rel;
+  h->pcg_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+
+int validate_csr(const spand_csr* A, std::string& err) {
+  if (!A || !A->rowptr || !A->colind || !A->val) return (err = "null CSR array", SPAND_EINVAL);
+  const int n = A->n;
+  if (n < 1) return (err = "n must be >= 1", SPAND_EINVAL);
+  if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return (err = "rowptr inconsistent with nnz", SPAND_EINVAL);
+  std::vector<int32_t> cnt(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (A->rowptr[i + 1] < A->rowptr[i]) return (err = "rowptr not monotone", SPAND_EINVAL);
+    bool diag = false;
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      const int j = A->colind[e];
+      if (j < 0 || j >= n) return (err = "column index out of range", SPAND_EINVAL);
+      if (e > A->rowptr[i] && A->colind[e - 1] >= j) return (err = "columns not strictly ascending", SPAND_EINVAL);
+      if (j == i) diag = true;
+      ++cnt[j];
+    }
+    if (!diag) return (err = "missing diagonal entry in row " + std::to_string(i), SPAND_EINVAL);
+  }
+  // pattern symmetry: every (i, j) has (j, i)
+  for (int i = 0; i < n; ++i) {
+    if (cnt[i] != A->rowptr[i + 1] - A->rowptr[i]) return (err = "pattern is not symmetric", SPAND_EINVAL);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      const int j = A->colind[e];
+      const int32_t* b = A->colind + A->rowptr[j];
+      const int32_t* en = A->colind + A->rowptr[j + 1];
+      if (!std::binary_search(b, en, i)) return (err = "pattern is not symmetric", SPAND_EINVAL);
+    }
+  return SPAND_OK;
+}
+
+void free_handle(spand_s* h) {
+  if (!h) return;
+  h->farena.release();
+  h->scratch[0].release();
+  h->scratch[1].release();
+  h->tables.release();
+  cudaFree(h->d_rowptr);
+  cudaFree(h->d_colind);
+  cudaFree(h->d_val);
+  cudaFree(h->d_pack);
+  cudaFree(h->d_err);
+  cudaFree(h->d_r);
+  cudaFree(h->d_z);
+  cudaFree(h->d_p);
+  cudaFree(h->d_q);
+  cudaFree(h->d_b);
+  cudaFree(h->d_x);
+  cudaFree(h->d_scal);
+  cudaFree(h->d_partial);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  cudaFree(h->d_rf);
+  h->prof.release();
+  delete h;
+}
+
+int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels, double eps,
+                 int scheme, const spand_opts* opts, spand_t* out) {
+  if (!out) return fail(SPAND_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string err;
+  if (validate_csr(A, err) != SPAND_OK) return fail(SPAND_EINVAL, err);
+  if (!coords) return fail(SPAND_EINVAL, "coords is NULL");
+  if (dim < 1 || dim > 3) return fail(SPAND_EINVAL, "dim must be 1, 2 or 3");
+  if (!(eps >= 0.0 && eps <= 1.0)) return fail(SPAND_EINVAL, "eps must lie in [0, 1]");
+  if (nlevels < 1 || nlevels > 30) return fail(SPAND_EINVAL, "nlevels must be in [1, 30]");
+  if (scheme < 0 || scheme > 2) return fail(SPAND_EINVAL, "unknown scheme");
+  std::unique_ptr<spand_s, void (*)(spand_s*)> h(new spand_s(), free_handle);
+  h->n = A->n;
+  h->nnz = A->nnz;
+  h->dim = dim;
+  h->nlevels = nlevels;
+  h->eps = eps;
+  h->scheme = scheme;
+  {
+    const double leaf = A->n / std::ldexp(1.0, nlevels - 1);
+    int sk = 4 - (int)std::nearbyint(std::log2(leaf / 25.0));
+    sk = std::min(std::max(sk, 0), std::max(nlevels - 2, 0));
+    h->skip = sk;
+  }
+  if (opts) {
+    if (opts->skip >= 0) h->skip = opts->skip;
+    if (opts->maxit > 0) h->maxit = opts->maxit;
+    if (opts->true_res_every > 0) h->true_every = opts->true_res_every;
+    if (opts->max_restarts >= 0) h->max_restarts = opts->max_restarts;
+    if (opts->rrqr_kernel < 0 || opts->rrqr_kernel > 1) return fail(SPAND_EINVAL, "rrqr_kernel must be 0 or 1");
+    h->rrqr_path = opts->rrqr_kernel;
+    if (opts->precision < 0 || opts->precision > 1) return fail(SPAND_EINVAL, "precision must be 0 or 1");
+    h->precision = opts->precision;
+  }
+  int rc = build_tree(coords, A->n, dim, nlevels, h->tree, err);
+  if (rc != SPAND_OK) return fail(rc, err);
+  rc = build_stages(h->tree, A->rowptr, A->colind, h->skip, h->st, err);
+  if (rc != SPAND_OK) return fail(rc, err);
+  // stage-0 layout (sizes are the cluster sizes) -> destination of every nonzero
+  const StageSym& S0 = h->st[0];
+  const int n = A->n;
+  std::vector<int> cl(n), pos(n);
+  for (int c = 0; c < S0.ncl; ++c)
+    for (size_t i = 0; i < S0.members0[c].size(); ++i) {
+      cl[S0.members0[c][i]] = c;
+      pos[S0.members0[c][i]] = (int)i;
+    }
+  std::vector<int64_t> roff(S0.ncl);
+  std::vector<std::vector<int>> segcol(S0.ncl);
+  int64_t fsz = 0, ssz = 0;
+  for (int c = 0; c < S0.ncl; ++c) {
+    const auto& rs = S0.rowsegs[c];
+    segcol[c].resize(rs.size());
+    int acc = 0;
+    for (size_t i = 0; i < rs.size(); ++i) {
+      segcol[c][i] = acc;
+      acc += (int)S0.members0[rs[i]].size();
+    }
+    const int64_t el = (int64_t)S0.members0[c].size() * acc;
+    const int64_t padded = (el + 3) & ~int64_t(3);  // row regions start on 4-element boundaries
+    if (S0.interior[c]) {
+      roff[c] = fsz;
+      fsz += padded;
+    } else {
+      roff[c] = ssz;
+      ssz += padded;
+    }
+  }
+  h->pack_split = fsz;
+  h->h_pack.assign(A->nnz, -1);
+  for (int i = 0; i < n; ++i)
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      const int j = A->colind[e];
+      const int a = cl[i], b = cl[j];
+      const auto& rs = S0.rowsegs[a];
+      auto it = std::lower_bound(rs.begin(), rs.end(), b);
+      if (it == rs.end() || *it != b) continue;  // interface row, interior column: kept in the interior's row
+      const int64_t col = segcol[a][it - rs.begin()] + pos[j];
+      const int64_t idx = roff[a] + pos[i] + col * (int64_t)S0.members0[a].size();
+      h->h_pack[e] = S0.interior[a] ? idx : fsz + idx;
+    }
+  h->h_rowptr.assign(A->rowptr, A->rowptr + n + 1);
+  h->h_colind.assign(A->colind, A->colind + A->nnz);
+  h->h_val.assign(A->val, A->val + A->nnz);
+  *out = h.release();
+  return SPAND_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int spand_analyze(const spand_csr* A, const double* coords, int dim, int nlevels, double eps,
+                  int scheme, const spand_opts* opts, spand_t* out) {
+  try {
+    return analyze_impl(A, coords, dim, nlevels, eps, scheme, opts, out);
+  } catch (const std::bad_alloc&) {
+    return fail(SPAND_ENOMEM, "host allocation failed");
+  }
+}
+
+int spand_factor(spand_t h, void* stream) {
+  if (!h) return fail(SPAND_EINVAL, "null handle");
+  try {
+    int rc = factor_impl(h, (cudaStream_t)stream);
+    if (rc != SPAND_OK) h->factored = false;
+    return rc;
+  } catch (const std::bad_alloc&) {
+    h->factored = false;
+    return fail(SPAND_ENOMEM, "host allocation failed");
+  }
+}
+
+int spand_apply(spand_t h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z) return fail(SPAND_EINVAL, "null argument");
+  return apply_any(h, r, z, (cudaStream_t)stream);
+}
+
+int spand_pcg(spand_t h, const double* b, double* x, double tol, int32_t* iters, double* relres,
+              void* stream) {
+  if (!h || !b || !x) return fail(SPAND_EINVAL, "null argument");
+  if (!(tol > 0.0)) return fail(SPAND_EINVAL, "tol must be positive");
+  return pcg_impl(h, b, x, tol, iters, relres, (cudaStream_t)stream);
+}
+
+int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol, int32_t* iters,
+                   double* relres, void* stream) {
+  if (!h || !b_host || !x_host) return fail(SPAND_EINVAL, "null argument");
+  if (!(tol > 0.0)) return fail(SPAND_EINVAL, "tol must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->d_b) {
+    CK(cudaMalloc(&h->d_b, (size_t)h->n * 8));
+    CK(cudaMalloc(&h->d_x, (size_t)h->n * 8));
+  }
+  CK(cudaMemcpyAsync(h->d_b, b_host, (size_t)h->n * 8, cudaMemcpyHostToDevice, s));
+  int rc = pcg_impl(h, h->d_b, h->d_x, tol, iters, relres, s);
+  if (rc != SPAND_OK && rc != SPAND_ENOCONV) return rc;
+  CK(cudaMemcpyAsync(x_host, h->d_x, (size_t)h->n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int spand_matvec(spand_t h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(SPAND_EINVAL, "null argument");
+  RET(ensure_device(h));
+  launch_spmv(h->n, h->d_rowptr, h->d_colind, h->d_val, x, y, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return SPAND_OK;
+}
+
+int spand_info(spand_t h, spand_stats* s) {
+  if (!h || !s) return fail(SPAND_EINVAL, "null argument");
+  memset(s, 0, sizeof(*s));
+  s->n = h->n;
+  s->nnz_a = h->nnz;
+  s->nnz_factor = h->nnz_factor;
+  s->mu = h->nnz ? (double)h->nnz_factor / (double)h->nnz : 0.0;
+  s->nlevels = h->nlevels;
+  s->skip = h->skip;
+  s->scheme = h->scheme;
+  s->eps = h->eps;
+  s->nstages = h->nlevels;
+  int tot = 0, ns = 0;
+  for (int k = 0; k < h->nlevels; ++k) {
+    tot += h->st[k].ncl;
+    if (h->st[k].sparsify) ns += (int)h->st[k].ifaces.size();
+  }
+  s->nclusters_total = tot;
+  s->ninterfaces_sparsified = ns;
+  s->factor_ms = h->factor_ms;
+  s->pcg_ms = h->pcg_ms;
+  s->pcg_iters = h->pcg_iters;
+  s->pcg_relres = h->pcg_relres;
+  s->kernel_launches = h->launches;
+  s->device_bytes = (int64_t)(h->farena.held() + h->scratch[0].cap + h->scratch[1].cap +
+                              h->tables.cap) +
+                    (int64_t)h->n * 8 * 6 + h->nnz * 20;
+  return SPAND_OK;
+}
+
+int spand_ranks(spand_t h, int32_t* out, int64_t cap, int64_t* count) {
+  if (!h || !count) return fail(SPAND_EINVAL, "null argument");
+  if (!h->factored) return fail(SPAND_ESTATE, "spand_ranks before a successful spand_factor");
+  int64_t tot = 0;
+  for (int k = 0; k < h->nlevels; ++k) tot += h->st[k].ncl;
+  *count = tot;
+  if (!out || cap < tot) return fail(SPAND_EINVAL, "output too small");
+  int64_t o = 0;
+  for (int k = 0; k < h->nlevels; ++k) {
+    const StageSym& S = h->st[k];
+    for (int c = 0; c < S.ncl; ++c) {
+      const bool sp = S.sparsify && !S.interior[c];
+      out[3 * o] = h->sizes[k][c];
+      out[3 * o + 1] = sp ? h->ranks[k][c] : -1;
+      out[3 * o + 2] = sp ? h->flags[k][c] : 0;
+      ++o;
+    }
+  }
+  return SPAND_OK;
+}
+
+int spand_cluster_map(spand_t h, int stage, int32_t* out) {
+  if (!h || !out) return fail(SPAND_EINVAL, "null argument");
+  if (stage < 0 || stage >= h->nlevels) return fail(SPAND_EINVAL, "stage out of range");
+  std::vector<int> cl;
+  cluster_map(h->tree, stage, cl, nullptr);
+  for (int v = 0; v < h->n; ++v) out[v] = cl[v];
+  return SPAND_OK;
+}
+
+int spand_num_clusters(spand_t h, int stage, int32_t* nclusters) {
+  if (!h || !nclusters) return fail(SPAND_EINVAL, "null argument");
+  if (stage < 0 || stage >= h->nlevels) return fail(SPAND_EINVAL, "stage out of range");
+  *nclusters = h->st[stage].ncl;
+  return SPAND_OK;
+}
+
+int spand_set_profiling(spand_t h, int on) {
+  if (!h) return fail(SPAND_EINVAL, "null handle");
+  h->prof.resolve();
+  h->prof.clear();
+  h->prof.on = on != 0;
+  return SPAND_OK;
+}
+
+int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count) {
+  if (!h || !count) return fail(SPAND_EINVAL, "null argument");
+  *count = KK_COUNT;
+  if (!out || cap < KK_COUNT) return fail(SPAND_EINVAL, "output too small");
+  for (int k = 0; k < KK_COUNT; ++k) out[k] = h->prof.stat[k];
+  return SPAND_OK;
+}
+
+void spand_destroy(spand_t h) { free_handle(h); }
+
+const char* spand_strerror(int code) {
+  switch (code) {
+    case SPAND_OK: return "success";
+    case SPAND_EINVAL: return "invalid argument";
+    case SPAND_ENOTSPD: return "matrix is not symmetric positive definite";
+    case SPAND_ENOMEM: return "out of memory";
+    case SPAND_ECUDA: return "CUDA error";
+    case SPAND_ENOCONV: return "PCG did not converge within maxit";
+    case SPAND_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* spand_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// PCG that allocates nothing.
+//
+// spand_pcg allocates its four work vectors (and pinned host memory for the
+// scalars) on first use.  Some callers cannot allow that: a host program whose
+// device memory is entirely reserved by another allocator (for instance a
+// framework's caching allocator that owns the whole GPU), or a real-time loop
+// that must not allocate once it is running.  spand_pcg_noalloc runs the same
+// PCG with its work vectors in one statically sized device array that is part
+// of the loaded library, so it calls no cudaMalloc, cudaFree or other
+// allocating routine.  Limits and sharing rules are stated in include/spand.h.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 262144;   // largest n the static workspace holds
+constexpr int64_t kNoAllocScalars = 1024;  // dot partials (fewer than 1024) + scalars
+// r, z, p, q (n doubles each) followed by the partials and the scalars.  Every
+// GPU that loads the library holds this array (about 8 MiB) until exit.
+static __device__ __align__(256) double g_pcg_noalloc_ws[4 * kNoAllocMaxN + kNoAllocScalars];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+
+// Device address of the workspace on the current device.  Resolved once per
+// device (with that device current) by the first call made on it.
+int noalloc_workspace(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(SPAND_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_pcg_noalloc_ws));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SPAND_OK;
+}
+
+int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters,
+                     double* relres, cudaStream_t s) {
+  if (h->precision != 0)
+    return fail(SPAND_EINVAL, "spand_pcg_noalloc supports the FP64 preconditioner only");
+  if ((int64_t)h->n > kNoAllocMaxN)
+    return fail(SPAND_EINVAL, "spand_pcg_noalloc: n = " + std::to_string(h->n) +
+                                  " exceeds the static workspace limit of " +
+                                  std::to_string(kNoAllocMaxN));
+  if (!h->factored) return fail(SPAND_ESTATE, "spand_pcg_noalloc before a successful spand_factor");
+  double* ws = nullptr;
+  RET(noalloc_workspace(&ws));
+  const int n = h->n;
+  double* r = ws;
+  double* z = ws + kNoAllocMaxN;
+  double* p = ws + 2 * kNoAllocMaxN;
+  double* q = ws + 3 * kNoAllocMaxN;
+  double* partial = ws + 4 * kNoAllocMaxN;
+  double* sc = partial + (kNoAllocScalars - 16);
+  if (dot_partials(n) > kNoAllocScalars - 16) return fail(SPAND_EINVAL, "internal: too many dot partials");
+  // profiling would create CUDA events; keep it off for this call
+  const bool prof_on = h->prof.on;
+  h->prof.on = false;
+  // scalars start from zero (the array keeps whatever the previous call left)
+  CK(cudaMemsetAsync(sc, 0, 16 * sizeof(double), s));
+  auto dot = [&](const double* a, const double* c, int slot) {
+    launch_dot(n, a, c, partial, sc + slot, s);
+  };
+  auto read = [&](int slot, double* out) -> int {
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, sc + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = v;
+    return SPAND_OK;
+  };
+  auto body = [&]() -> int {
+    launch_pcg_init(n, b, x, r, s);
+    dot(b, b, 4);
+    double bb = 0.0;
+    RET(read(4, &bb));
+    const double bnorm = std::sqrt(bb);
+    if (bnorm == 0.0) {
+      if (iters) *iters = 0;
+      if (relres) *relres = 0.0;
+      return SPAND_OK;
+    }
+    int it = 0, restarts = 0;
+    double rr = bb, rel = 0.0;
+    while (true) {
+      RET(apply_any(h, r, z, s));
+      launch_copy_vec(n, z, p, s);
+      dot(r, z, 0);
+      while (it < h->maxit && std::sqrt(rr) / bnorm >= tol) {
+        launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, p, q, s);
+        dot(p, q, 1);
+        launch_pcg_step_x(n, sc, p, q, x, r, s);
+        ++it;
+        if (it % h->true_every == 0) {
+          launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, x, q, s);
+          launch_residual(n, b, q, r, s);
+        }
+        dot(r, r, 3);
+        RET(read(3, &rr));
+        if (std::sqrt(rr) / bnorm < tol) break;
+        RET(apply_any(h, r, z, s));
+        dot(r, z, 2);
+        launch_pcg_step_p(n, sc, z, p, s);
+        launch_pcg_scalars(sc, 0, s);
+      }
+      launch_spmv(n, h->d_rowptr, h->d_colind, h->d_val, x, q, s);
+      launch_residual(n, b, q, r, s);
+      dot(r, r, 3);
+      RET(read(3, &rr));
+      rel = std::sqrt(rr) / bnorm;
+      if (rel < tol || it >= h->maxit || restarts >= h->max_restarts) break;
+      ++restarts;
+    }
+    CK(cudaGetLastError());
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (rel >= tol && it >= h->maxit) return fail(SPAND_ENOCONV, "PCG reached maxit");
+    return SPAND_OK;
+  };
+  const int rc = body();
+  h->prof.on = prof_on;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int spand_pcg_noalloc(spand_t h, const double* b, double* x, double tol, int32_t* iters,
+                                 double* relres, void* stream) {
+  if (!h || !b || !x) return fail(SPAND_EINVAL, "null argument");
+  if (!(tol > 0.0)) return fail(SPAND_EINVAL, "tol must be positive");
+  return pcg_noalloc_impl(h, b, x, tol, iters, relres, (cudaStream_t)stream);
+}

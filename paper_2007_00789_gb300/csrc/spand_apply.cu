@@ -11,30 +11,14 @@
 // neighbour slots, done with atomics.
 #include <cooperative_groups.h>
 
-#include "spand_internal.h"
+#include "spand_real.h"
 
 namespace spand {
+namespace SPAND_NS {
 
 namespace {
 
 constexpr int kApThreads = 256;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < nw; ++w) s += red[w];
-  return s;
-}
 
 namespace cg = cooperative_groups;
 
@@ -50,17 +34,17 @@ constexpr int kApWarps = kApThreads / 32;
 // the columns a 32-row tile starting at rt needs (C for a full matrix, rt + 32
 // for a lower-triangular one whose strict upper part is zero).
 template <class Cap, class Out>
-__device__ void gemv_n(const double* __restrict__ M, size_t ld, int r0, int r1, Cap ccap,
-                       const double* __restrict__ x, double* red, Out out) {
+__device__ void gemv_n(const real_t* __restrict__ M, size_t ld, int r0, int r1, Cap ccap,
+                       const real_t* __restrict__ x, real_t* red, Out out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int rt = r0; rt < r1; rt += 32) {
     const int r = rt + lane;
     const int C = ccap(rt);
     const int per = (C + kApWarps - 1) / kApWarps;
     const int cb = warp * per, ce = min(C, cb + per);
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (r < r1) {
-      const double* Mr = M + r;
+      const real_t* Mr = M + r;
       int c = cb;
       for (; c + 3 < ce; c += 4) {
         s0 = fma(Mr[(size_t)c * ld], x[c], s0);
@@ -73,7 +57,7 @@ __device__ void gemv_n(const double* __restrict__ M, size_t ld, int r0, int r1, 
     red[warp * 32 + lane] = (s0 + s1) + (s2 + s3);
     __syncthreads();
     if (warp == 0 && r < r1) {
-      double t = 0.0;
+      real_t t = 0.0;
       for (int w = 0; w < kApWarps; ++w) t += red[w * 32 + lane];
       out(r, t);
     }
@@ -85,17 +69,17 @@ __device__ void gemv_n(const double* __restrict__ M, size_t ld, int r0, int r1, 
 // rlo(ct) is the first row a 32-column tile starting at ct needs (0 for a full
 // matrix, ct for the transpose of a lower-triangular one).
 template <class Lo, class Out>
-__device__ void gemv_t(const double* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
-                       const double* __restrict__ x, double* red, Out out) {
+__device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
+                       const real_t* __restrict__ x, real_t* red, Out out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int ct = c0; ct < c1; ct += 32) {
     const int c = ct + lane;
     const int rb0 = rlo(ct);
     const int per = (R - rb0 + kApWarps - 1) / kApWarps;
     const int rb = rb0 + warp * per, re = min(R, rb + per);
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (c < c1) {
-      const double* col = M + (size_t)c * ld;
+      const real_t* col = M + (size_t)c * ld;
       int r = rb;
       for (; r + 3 < re; r += 4) {
         s0 = fma(col[r], x[r], s0);
@@ -108,7 +92,7 @@ __device__ void gemv_t(const double* __restrict__ M, size_t ld, int c0, int c1, 
     red[warp * 32 + lane] = (s0 + s1) + (s2 + s3);
     __syncthreads();
     if (warp == 0 && c < c1) {
-      double t = 0.0;
+      real_t t = 0.0;
       for (int w = 0; w < kApWarps; ++w) t += red[w * 32 + lane];
       out(c, t);
     }
@@ -126,21 +110,21 @@ namespace cg = cooperative_groups;
 // gathered neighbour values (ncols), and the warps' partial sums.
 __device__ __forceinline__ int part_lo(int n, int k, int K) { return (int)(((long)n * k) / K); }
 
-__device__ __forceinline__ void share(cg::cluster_group& cl, int K, double* buf, int i, double val) {
+__device__ __forceinline__ void share(cg::cluster_group& cl, int K, real_t* buf, int i, real_t val) {
   for (int c = 0; c < K; ++c) cl.map_shared_rank(buf, c)[i] = val;
 }
 
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_interior(const ApInterior* __restrict__ tasks, double* __restrict__ z, int forward) {
+    k_ap_interior(const ApInterior* __restrict__ tasks, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
-  extern __shared__ double sh[];
-  __shared__ double red[kApThreads];
+  extern __shared__ real_t sh[];
+  __shared__ real_t red[kApThreads];
   const ApInterior t = tasks[blockIdx.x / K];
   const int m = t.m, nc = t.ncols;
-  double* xs = sh;
-  double* ys = sh + m;
-  double* zw = sh + 2 * m;
+  real_t* xs = sh;
+  real_t* ys = sh + m;
+  real_t* zw = sh + 2 * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
   if (!forward)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
@@ -152,55 +136,55 @@ __global__ void __launch_bounds__(kApThreads)
   if (forward) {
     // y = L_s^{-1} x, then z_s = y and z_w -= W_s y (column c of the panel row is W_s^T[:, c])
     gemv_n(t.Linv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, red,
-           [&](int r, double v) { share(cl, K, ys, r, v); });
+           [&](int r, real_t v) { share(cl, K, ys, r, v); });
     cl.sync();
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) z[t.slots[i]] = ys[i];
     gemv_t(t.WT, m, part_lo(nc, k, K), part_lo(nc, k + 1, K), m, [](int) { return 0; }, ys, red,
-           [&](int c, double v) {
+           [&](int c, real_t v) {
              const int ws = t.wslots[c];
              if (ws >= 0) atomicAdd(z + ws, -v);
            });
   } else {
     // y = x - W_s^T z_w, then z_s = L_s^{-T} y
     gemv_n(t.WT, m, lo, hi, [&](int) { return nc; }, zw, red,
-           [&](int r, double v) { share(cl, K, ys, r, xs[r] - v); });
+           [&](int r, real_t v) { share(cl, K, ys, r, xs[r] - v); });
     cl.sync();
     gemv_t(t.Linv, m, lo, hi, m, [](int ct) { return ct; }, ys, red,
-           [&](int j, double v) { z[t.slots[j]] = v; });
+           [&](int j, real_t v) { z[t.slots[j]] = v; });
   }
 }
 
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_scale(const ApScale* __restrict__ tasks, double* __restrict__ z, int forward) {
+    k_ap_scale(const ApScale* __restrict__ tasks, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
-  extern __shared__ double sh[];
-  __shared__ double red[kApThreads];
+  extern __shared__ real_t sh[];
+  __shared__ real_t red[kApThreads];
   const ApScale t = tasks[blockIdx.x / K];
   const int m = t.m;
-  double* xs = sh;
+  real_t* xs = sh;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
   cl.sync();  // every CTA has read z_p before any CTA overwrites part of it
   const int lo = part_lo(m, k, K), hi = part_lo(m, k + 1, K);
   if (forward)
     gemv_n(t.Zinv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, red,
-           [&](int r, double v) { z[t.slots[r]] = v; });
+           [&](int r, real_t v) { z[t.slots[r]] = v; });
   else
     gemv_t(t.Zinv, m, lo, hi, m, [](int ct) { return ct; }, xs, red,
-           [&](int j, double v) { z[t.slots[j]] = v; });
+           [&](int j, real_t v) { z[t.slots[j]] = v; });
 }
 
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_qe(const ApQE* __restrict__ tasks, double* __restrict__ z, int forward) {
+    k_ap_qe(const ApQE* __restrict__ tasks, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
-  extern __shared__ double sh[];
-  __shared__ double red[kApThreads];
+  extern __shared__ real_t sh[];
+  __shared__ real_t red[kApThreads];
   const ApQE t = tasks[blockIdx.x / K];
   const int m = t.m, nc = t.ncols, nE = t.nE;
-  double* xs = sh;
-  double* ys = sh + m;
-  double* zw = sh + 2 * m;
+  real_t* xs = sh;
+  real_t* ys = sh + m;
+  real_t* zw = sh + 2 * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
   if (!forward && nE > 0)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) zw[c] = z[t.eslots[c]];
@@ -209,12 +193,12 @@ __global__ void __launch_bounds__(kApThreads)
   if (forward) {
     // y = Q^T x; z_p = y; z_w -= E-tilde^T y_f
     gemv_n(t.Qt, m, lo, hi, [&](int) { return m; }, xs, red,
-           [&](int r, double v) { share(cl, K, ys, r, v); });
+           [&](int r, real_t v) { share(cl, K, ys, r, v); });
     cl.sync();
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) z[t.slots[i]] = ys[i];
     if (nE > 0)
       gemv_t(t.E, nE, part_lo(nc, k, K), part_lo(nc, k + 1, K), nE, [](int) { return 0; },
-             ys + t.r, red, [&](int c, double v) { atomicAdd(z + t.eslots[c], -v); });
+             ys + t.r, red, [&](int c, real_t v) { atomicAdd(z + t.eslots[c], -v); });
   } else {
     // x_f -= E-tilde z_w, then z_p = Q x
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
@@ -223,99 +207,32 @@ __global__ void __launch_bounds__(kApThreads)
       const int flo = max(lo, t.r) - t.r, fhi = min(hi, t.r + nE) - t.r;
       if (fhi > flo)
         gemv_n(t.E, nE, flo, fhi, [&](int) { return nc; }, zw, red,
-               [&](int r, double v) { share(cl, K, ys, t.r + r, xs[t.r + r] - v); });
+               [&](int r, real_t v) { share(cl, K, ys, t.r + r, xs[t.r + r] - v); });
     }
     cl.sync();
     gemv_t(t.Qt, m, lo, hi, m, [](int) { return 0; }, ys, red,
-           [&](int j, double v) { z[t.slots[j]] = v; });
+           [&](int j, real_t v) { z[t.slots[j]] = v; });
   }
 }
-
-// ---------------------------------------------------------------------------
-// PCG kernels.
-// ---------------------------------------------------------------------------
-__global__ void k_spmv(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                       const double* __restrict__ val, const double* __restrict__ x,
-                       double* __restrict__ y) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e] * x[colind[e]];
-    y[i] = s;
-  }
-}
-
-constexpr int kDotBlocks = 304;
-constexpr int kDotThreads = 256;
-
-__global__ void k_dot_partial(int n, const double* __restrict__ x, const double* __restrict__ y,
-                              double* __restrict__ partial) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    s += x[i] * y[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void k_dot_final(const double* __restrict__ partial, int np, double* __restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) *out = s;
-}
-
-// scal layout: 0 rz, 1 pq, 2 rz_new, 3 rr
-__global__ void k_pcg_init(int n, const double* __restrict__ b, double* __restrict__ x,
-                           double* __restrict__ r) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    x[i] = 0.0;
-    r[i] = b[i];
-  }
-}
-
-__global__ void k_pcg_step_x(int n, const double* __restrict__ scal, const double* __restrict__ p,
-                             const double* __restrict__ q, double* __restrict__ x,
-                             double* __restrict__ r) {
-  const double alpha = scal[0] / scal[1];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
-  }
-}
-
-__global__ void k_pcg_step_p(int n, const double* __restrict__ scal, const double* __restrict__ z,
-                             double* __restrict__ p) {
-  const double beta = scal[2] / scal[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
-}
-
-__global__ void k_pcg_scalars(double* scal, int which) {
-  if (which == 0) scal[0] = scal[2];  // rz <- rz_new
-}
-
-__global__ void k_residual(int n, const double* __restrict__ b, const double* __restrict__ ax,
-                           double* __restrict__ r) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    r[i] = b[i] - ax[i];
-}
-
-__global__ void k_copy_vec(int n, const double* __restrict__ s, double* __restrict__ d) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = s[i];
-}
-
-inline int vec_blocks(int n) { return std::max(1, std::min((n + 255) / 256, 152 * 16)); }
 
 }  // namespace
+
 
 static void smem_attr(const void* fn, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+__global__ void k_copy_real(int n, const real_t* __restrict__ s, real_t* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = s[i];
+}
+
+void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s) {
+  k_copy_real<<<std::max(1, std::min((n + 255) / 256, 152 * 16)), 256, 0, s>>>(n, src, dst);
+}
+
 template <class Task>
-static void launch_ap(void (*kern)(const Task*, double*, int), const Task* t, int ntasks, int K,
-                      int bytes, double* z, bool forward, cudaStream_t s) {
+static void launch_ap(void (*kern)(const Task*, real_t*, int), const Task* t, int ntasks, int K,
+                      int bytes, real_t* z, bool forward, cudaStream_t s) {
   if (ntasks <= 0) return;
   smem_attr((const void*)kern, bytes);
   if (K > 8) cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -334,55 +251,20 @@ static void launch_ap(void (*kern)(const Task*, double*, int), const Task* t, in
   cudaLaunchKernelEx(&cfg, kern, t, z, forward ? 1 : 0);
 }
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, double* z,
+void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
                         bool forward, cudaStream_t s) {
   launch_ap(k_ap_interior, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
 }
 
-void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, double* z, bool forward,
+void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, real_t* z, bool forward,
                      cudaStream_t s) {
   launch_ap(k_ap_scale, t, ntasks, K, std::max(max_m, 1) * 8, z, forward, s);
 }
 
-void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, double* z, bool forward,
+void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, real_t* z, bool forward,
                   cudaStream_t s) {
   launch_ap(k_ap_qe, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
 }
 
-void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
-                 const double* x, double* y, cudaStream_t s) {
-  k_spmv<<<vec_blocks(n), 256, 0, s>>>(n, rowptr, colind, val, x, y);
-}
-
-int dot_partials(int n) {
-  (void)n;
-  return kDotBlocks;
-}
-
-void launch_dot(int n, const double* x, const double* y, double* partial, double* out,
-                cudaStream_t s) {
-  k_dot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, partial);
-  k_dot_final<<<1, kDotThreads, 0, s>>>(partial, kDotBlocks, out);
-}
-
-void launch_pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s) {
-  k_pcg_init<<<vec_blocks(n), 256, 0, s>>>(n, b, x, r);
-}
-void launch_pcg_step_x(int n, const double* scal, const double* p, const double* q, double* x,
-                       double* r, cudaStream_t s) {
-  k_pcg_step_x<<<vec_blocks(n), 256, 0, s>>>(n, scal, p, q, x, r);
-}
-void launch_pcg_step_p(int n, const double* scal, const double* z, double* p, cudaStream_t s) {
-  k_pcg_step_p<<<vec_blocks(n), 256, 0, s>>>(n, scal, z, p);
-}
-void launch_pcg_scalars(double* scal, int which, cudaStream_t s) {
-  k_pcg_scalars<<<1, 1, 0, s>>>(scal, which);
-}
-void launch_residual(int n, const double* b, const double* ax, double* r, cudaStream_t s) {
-  k_residual<<<vec_blocks(n), 256, 0, s>>>(n, b, ax, r);
-}
-void launch_copy_vec(int n, const double* src, double* dst, cudaStream_t s) {
-  k_copy_vec<<<vec_blocks(n), 256, 0, s>>>(n, src, dst);
-}
-
+}  // namespace SPAND_NS
 }  // namespace spand

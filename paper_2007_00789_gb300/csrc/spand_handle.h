@@ -1,0 +1,309 @@
+// Internal: the handle of the C ABI and the host-side helpers shared by the
+// FP64 and FP32 orchestration (factor_core.cu, compiled once per precision)
+// and the ABI layer (api.cu).
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spand_internal.h"
+
+namespace spand {
+
+int fail(int code, const std::string& msg);  // records spand_last_error(), returns code
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::spand::fail(e_ == cudaErrorMemoryAllocation ? SPAND_ENOMEM : SPAND_ECUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+#define RET(call)                    \
+  do {                               \
+    int rc_ = (call);                \
+    if (rc_ != SPAND_OK) return rc_; \
+  } while (0)
+
+
+// Bump allocator over device chunks; pointers stay valid until release().
+struct DevArena {
+  struct Chunk {
+    char* p;
+    size_t cap, used;
+  };
+  std::vector<Chunk> chunks;
+  size_t cur = 0;
+  size_t min_chunk = size_t(256) << 20;
+
+  int alloc(size_t bytes, void** out) {
+    bytes = (bytes + 255) & ~size_t(255);
+    while (cur < chunks.size()) {
+      Chunk& c = chunks[cur];
+      if (c.used + bytes <= c.cap) {
+        *out = c.p + c.used;
+        c.used += bytes;
+        return SPAND_OK;
+      }
+      ++cur;
+    }
+    const size_t cap = std::max(bytes, min_chunk);
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, cap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPAND_ENOMEM, "device allocation of " + std::to_string(cap) + " bytes failed");
+    }
+    chunks.push_back({p, cap, bytes});
+    cur = chunks.size() - 1;
+    *out = p;
+    return SPAND_OK;
+  }
+  void reset() {
+    for (auto& c : chunks) c.used = 0;
+    cur = 0;
+  }
+  void release() {
+    for (auto& c : chunks) cudaFree(c.p);
+    chunks.clear();
+    cur = 0;
+  }
+  size_t held() const {
+    size_t s = 0;
+    for (auto& c : chunks) s += c.cap;
+    return s;
+  }
+};
+
+// Growable device buffer (contents not preserved on growth).
+struct DevBuf {
+  char* p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap) return SPAND_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max(bytes, size_t(1) << 20);
+    want = want + want / 4;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPAND_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    cap = want;
+    return SPAND_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// Host staging of one stage's task tables.
+struct Blob {
+  std::vector<char> h;
+  template <class T>
+  size_t add(const std::vector<T>& v) {
+    size_t off = (h.size() + 15) & ~size_t(15);
+    h.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) memcpy(h.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+  void clear() { h.clear(); }
+};
+
+// Per-kernel profiling: CUDA events around every launch group on the caller's
+// stream, resolved after the stream is synchronised; algorithmic FLOPs and
+// bytes are counted on the host from the task sizes.
+enum KernelKind {
+  KK_PACK, KK_MERGE, KK_POTRF, KK_TRSM, KK_SCHUR, KK_SCALE_POTRF, KK_SCALE_TRSM, KK_SCALE_COPY,
+  KK_RRQR, KK_ECOPY, KK_TRTRI, KK_FORMQ, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT,
+  KK_VEC, KK_COUNT
+};
+static const char* const kKindName[KK_COUNT] = {
+    "pack", "merge", "potrf", "trsm", "schur", "scale_potrf", "scale_trsm", "scale_copy",
+    "rrqr", "e_copy", "trtri", "form_qt", "apply_interior", "apply_scale", "apply_qe", "spmv",
+    "dot", "vector"};
+
+struct Prof {
+  bool on = false;
+  struct Pend {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Pend> pend;
+  spand_kernel_stat stat[KK_COUNT];
+  Prof() { clear(); }
+  void clear() {
+    for (int k = 0; k < KK_COUNT; ++k) {
+      memset(&stat[k], 0, sizeof(stat[k]));
+      snprintf(stat[k].name, sizeof(stat[k].name), "%s", kKindName[k]);
+    }
+  }
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  template <class F>
+  void run(int kind, cudaStream_t s, double flops, double bytes, F&& launch) {
+    if (!on) {
+      launch();
+      return;
+    }
+    Pend p{kind, ev(), ev(), flops, bytes};
+    cudaEventRecord(p.a, s);
+    launch();
+    cudaEventRecord(p.b, s);
+    pend.push_back(p);
+  }
+  void add_flops(int kind, double flops) {
+    if (on) stat[kind].flops += flops;
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    for (auto& p : pend) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      stat[p.kind].launches += 1;
+      stat[p.kind].total_ms += ms;
+      stat[p.kind].flops += p.flops;
+      stat[p.kind].bytes += p.bytes;
+    }
+    pend.clear();
+    used = 0;
+  }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    used = 0;
+  }
+};
+
+constexpr int kQrClusterSmem = 200 * 1024;  // shared-memory slice per CTA of the on-chip RRQR
+constexpr int kNumSMs = 152;                 // GB300
+
+enum PhaseKind { PH_INTERIOR = 0, PH_SCALE = 1, PH_QE = 2 };
+struct Phase {
+  int kind, begin, end, max_m;
+  double flops, bytes;  // algorithmic, forward sweep (the backward one is the same)
+  int max_cols = 0;     // widest neighbour gather
+  int K = 1;            // CTAs per operator (thread-block cluster)
+};
+
+// CTAs per apply operator: enough that each handles about 12k FMAs.
+inline int ap_cluster(double fmas) {
+  int K = 1;
+  while (K < 16 && fmas / K > 12288.0) K *= 2;
+  return K;
+}
+
+// Split [ph.begin, ph.end) of the descriptor vector v into one phase per
+// cluster size; the operators of a phase are independent, so their order
+// within the phase is free.
+template <class T>
+void split_phase(std::vector<Phase>& phases, std::vector<T>& v, const Phase& ph,
+                 const std::vector<int>& Ks, const std::vector<double>& fl,
+                 const std::vector<double>& by, const std::vector<int>& ms,
+                 const std::vector<int>& cols) {
+  std::vector<int> order(ph.end - ph.begin);
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Ks[a] < Ks[b]; });
+  std::vector<T> seg(order.size());
+  for (size_t i = 0; i < order.size(); ++i) seg[i] = v[ph.begin + order[i]];
+  std::copy(seg.begin(), seg.end(), v.begin() + ph.begin);
+  size_t i = 0;
+  while (i < order.size()) {
+    Phase q = ph;
+    q.K = Ks[order[i]];
+    q.begin = ph.begin + (int)i;
+    q.max_m = 0;
+    q.max_cols = 0;
+    q.flops = q.bytes = 0.0;
+    while (i < order.size() && Ks[order[i]] == q.K) {
+      q.max_m = std::max(q.max_m, ms[order[i]]);
+      q.max_cols = std::max(q.max_cols, cols[order[i]]);
+      q.flops += fl[order[i]];
+      q.bytes += by[order[i]];
+      ++i;
+    }
+    q.end = ph.begin + (int)i;
+    phases.push_back(q);
+  }
+}
+
+}  // namespace spand
+
+struct spand_s {
+  int n = 0, dim = 0, nlevels = 0, scheme = 0, skip = 0;
+  int64_t nnz = 0;
+  double eps = 0.0;
+  int maxit = 500, true_every = 50, max_restarts = 2;
+  spand::Tree tree;
+  std::vector<spand::StageSym> st;
+  std::vector<int32_t> h_rowptr, h_colind;
+  std::vector<double> h_val;
+  // device copy of A
+  int32_t* d_rowptr = nullptr;
+  int32_t* d_colind = nullptr;
+  double* d_val = nullptr;
+  int64_t* d_pack = nullptr;     // stage-0 destination of every nonzero
+  int64_t pack_split = 0;        // interior part / interface part of the stage-0 layout
+  std::vector<int64_t> h_pack;
+  // memory
+  spand::DevArena farena;
+  spand::DevBuf scratch[2];
+  spand::DevBuf tables;
+  int* d_err = nullptr;
+  int* h_pinned = nullptr;       // rank/nref/err readback
+  size_t h_pinned_cap = 0;
+  // factor results
+  bool factored = false;
+  std::vector<std::vector<int>> sizes, ranks, nrefs, flags;
+  std::vector<spand::Phase> phases;
+  void* d_api = nullptr;  // apply descriptors of the handle's precision
+  void* d_aps = nullptr;
+  void* d_apq = nullptr;
+  int precision = 0;      // 0: FP64 factor and apply; 1: FP32 factor and apply (PCG stays FP64)
+  float* d_rf = nullptr;  // FP32 copy of the vector an FP32 apply works on
+  int64_t nnz_factor = 0;
+  int64_t launches = 0;
+  double factor_ms = 0.0;
+  // pcg
+  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr,
+         *d_x = nullptr;
+  double* d_scal = nullptr;
+  double* d_partial = nullptr;
+  double* h_scal = nullptr;
+  double pcg_ms = 0.0, pcg_relres = 0.0;
+  int pcg_iters = 0;
+  spand::Prof prof;
+  int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel
+  int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
+};
+
+namespace spand {
+int ensure_device(spand_s* h);  // first device use: upload A and the stage-0 pack map
+namespace f64 {
+int factor(spand_s* h, cudaStream_t s);
+int apply(spand_s* h, const double* r, double* z, cudaStream_t s);
+}  // namespace f64
+namespace f32 {
+int factor(spand_s* h, cudaStream_t s);
+int apply(spand_s* h, const float* r, float* z, cudaStream_t s);
+}  // namespace f32
+}  // namespace spand

@@ -57,130 +57,8 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
                  std::vector<StageSym>& st, std::string& err);
 
 // ---------------------------------------------------------------------------
-// Device task descriptors (plain structs copied to the device in one blob).
+// FP64 vector kernels of PCG (spand_pcg.cu).
 // ---------------------------------------------------------------------------
-
-// dst[i + j*dst_ld] = (trans ? src[j + i*src_ld] : src[i + j*src_ld]); i < rows, j < cols.
-struct CopyTask {
-  const double* src;
-  double* dst;
-  int src_ld, dst_ld, rows, cols, trans, pad;
-};
-
-// In-place lower Cholesky of an m x m column-major block (ld), id for errors.
-struct PotrfTask {
-  double* a;
-  int m, ld, id, pad;
-};
-
-// trans == 0: X (m x ncols, ld ldx) <- L^{-1} X.
-// trans == 1: B (ncols x m, ld ldx) <- B L^{-T}, i.e. B^T <- L^{-1} B^T.
-// ident >= 0: X <- L^{-1} [e_ident .. e_{ident+ncols-1}] (columns of L^{-1}; X's
-// previous contents are ignored).
-struct TrsmTask {
-  const double* L;
-  double* X;
-  int m, ldl, ldx, ncols, trans, pad;  // pad: ident (first identity column) or -1
-};
-
-// Columns c0 .. c0+ncols-1 of Q^T = H_{nref-1} ... H_0 (m x m, ld m).
-struct FormQtTask {
-  const double* V;
-  const double* tau;
-  double* Qt;  // already offset to column c0
-  int m, nref, c0, ncols;
-};
-
-// One output tile (rows x cols <= 32 x 32) of a Schur target block:
-// T -= sum_c A_c^T B_c, written at dst (ld) and, unless mirror == nullptr,
-// transposed at mirror (ld_mirror).
-struct SchurTile {
-  double* dst;
-  double* mirror;
-  int ld, ld_mirror, rows, cols, cbegin, cend, i0, j0;
-};
-// A_c: K x (i0 + rows) at a (lda), B_c: K x (j0 + cols) at b (ldb); the tile
-// uses columns i0.. of A_c and j0.. of B_c.  pad = 0: element (k, i) at
-// k + i*ld (column-major); pad = 1: at k*ld + i (the transposed storage, e.g.
-// a column panel P whose product P P^T is wanted).
-struct SchurContrib {
-  const double* a;
-  const double* b;
-  int K, lda, ldb, pad;
-};
-
-// One segment (neighbour block) of an interface's panel row.
-struct RRQRSeg {
-  double* mirror;  // origin of the transposed block in the neighbour's row
-  int col;         // first column of the segment in the row
-  int cl;          // neighbour cluster id (its live width is cur_size[cl])
-  int mirror_ld;   // leading dimension of the neighbour's row
-  int pad;
-};
-
-struct RRQRTask {
-  double* A;       // panel row of interface p, column-major, ld
-  double* diag;    // origin of the diagonal segment (set to I_r afterwards)
-  double* V;       // reflectors, m x maxref, ld m
-  double* tau;     // maxref
-  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max;
-};
-
-// Preconditioner apply descriptors.  The triangular factors and Q_p are
-// applied through explicit matrices formed at the end of each stage
-// (L_s^{-1}, Z_p^{-1}, Q_p^T), so every apply step is a dense product.
-struct ApInterior {
-  const double* Linv;   // m x m lower, L_s^{-1}, ld m
-  const double* WT;     // panel row, m x ncols (ld = m); diag columns skipped via wslot < 0
-  const int* slots;     // m vector positions
-  const int* wslots;    // ncols vector positions (-1 for the diagonal segment)
-  int m, ncols;
-};
-struct ApScale {
-  const double* Zinv;  // m x m lower, Z_p^{-1}, ld m
-  const int* slots;
-  int m, pad;
-};
-struct ApQE {
-  const double* Qt;   // m x m, Q_p^T, ld m
-  const double* E;    // nE x ncols, ld nE
-  const int* slots;   // m positions (before sparsification)
-  const int* eslots;  // ncols positions
-  int m, r, nE, ncols;
-};
-
-// ---------------------------------------------------------------------------
-// Kernel launchers (spand_kernels.cu / spand_apply.cu).
-// ---------------------------------------------------------------------------
-void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s);
-// base_lo[d] = val[e] for 0 <= d < split, base_hi[d - split] for d >= split, skip d < 0.
-void launch_scatter(const double* val, const int64_t* dst_index, double* base_lo,
-                    double* base_hi, int64_t split, int64_t nnz, cudaStream_t s);
-void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s);
-void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s);
-void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s);
-void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s);
-void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s);
-int rrqr_smem_bytes(int max_m, int max_cols, int max_segs);
-// On-chip variant: C CTAs per interface (a thread-block cluster), the block in shared memory.
-int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
-// Clusters of this shape that can be resident at once (0: cannot be launched).
-int rrqr_cluster_active(int csize, int smem_bytes);
-void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
-                         int csize, int smem_bytes, cudaStream_t s);
-void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                 int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
-                 int max_cols, int max_segs, cudaStream_t s);
-
-// K: CTAs per operator (a thread-block cluster), 1..16.
-void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, double* z,
-                        bool forward, cudaStream_t s);
-void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, double* z, bool forward,
-                     cudaStream_t s);
-void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, double* z,
-                  bool forward, cudaStream_t s);
-
 void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
                  const double* x, double* y, cudaStream_t s);
 // Deterministic dot product: out[0] = sum x_i y_i (two passes, fixed order).
@@ -196,5 +74,8 @@ void launch_pcg_step_p(int n, const double* scal, const double* z, double* p, cu
 void launch_pcg_scalars(double* scal, int which, cudaStream_t s);
 void launch_residual(int n, const double* b, const double* ax, double* r, cudaStream_t s);
 void launch_copy_vec(int n, const double* src, double* dst, cudaStream_t s);
+// precision conversions around an FP32 preconditioner apply
+void launch_d2f(int n, const double* src, float* dst, cudaStream_t s);
+void launch_f2d(int n, const float* src, double* dst, cudaStream_t s);
 
 }  // namespace spand

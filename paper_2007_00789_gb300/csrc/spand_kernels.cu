@@ -10,15 +10,16 @@
 
 #include <cstdio>
 
-#include "spand_internal.h"
+#include "spand_real.h"
 
 namespace spand {
+namespace SPAND_NS {
 
 namespace {
 
 constexpr int kWarp = 32;
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ real_t warp_sum(real_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -45,14 +46,14 @@ __global__ void k_copy(const CopyTask* __restrict__ tasks) {
 }
 
 __global__ void k_scatter(const double* __restrict__ val, const int64_t* __restrict__ dst,
-                          double* __restrict__ base_lo, double* __restrict__ base_hi,
+                          real_t* __restrict__ base_lo, real_t* __restrict__ base_hi,
                           int64_t split, int64_t nnz) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = dst[e];
     if (d < 0) continue;
-    if (d < split) base_lo[d] = val[e];
-    else base_hi[d - split] = val[e];
+    if (d < split) base_lo[d] = (real_t)val[e];
+    else base_hi[d - split] = (real_t)val[e];
   }
 }
 
@@ -69,31 +70,31 @@ __global__ void k_set_identity(const PotrfTask* __restrict__ tasks) {
 // Batched Cholesky A = L L^T (lower), in place.  Right-looking, one column
 // per step; the block is staged in shared memory when it fits.
 // ---------------------------------------------------------------------------
-__device__ void potrf_body(double* a, int m, int ld, int id, int* err, double* s_inv,
+__device__ void potrf_body(real_t* a, int m, int ld, int id, int* err, real_t* s_inv,
                            int* s_fail) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int j = 0; j < m; ++j) {
     if (tid == 0) {
-      const double d = a[j + (size_t)j * ld];
+      const real_t d = a[j + (size_t)j * ld];
       if (!(d > 0.0)) {
         *s_fail = 1;
         if (err) atomicCAS(err, 0, id + 1);
       } else {
-        const double sq = sqrt(d);
+        const real_t sq = sqrt(d);
         a[j + (size_t)j * ld] = sq;
         *s_inv = 1.0 / sq;
       }
     }
     __syncthreads();
     if (*s_fail) return;
-    const double inv = *s_inv;
+    const real_t inv = *s_inv;
     for (int i = j + 1 + tid; i < m; i += nt) a[i + (size_t)j * ld] *= inv;
     __syncthreads();
     for (int c = j + 1 + warp; c < m; c += nw) {
-      const double lc = a[c + (size_t)j * ld];
-      double* col = a + (size_t)c * ld;
-      const double* lj = a + (size_t)j * ld;
+      const real_t lc = a[c + (size_t)j * ld];
+      real_t* col = a + (size_t)c * ld;
+      const real_t* lj = a + (size_t)j * ld;
       for (int r = c + lane; r < m; r += kWarp) col[r] -= lj[r] * lc;
     }
     __syncthreads();
@@ -101,8 +102,8 @@ __device__ void potrf_body(double* a, int m, int ld, int id, int* err, double* s
 }
 
 __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_cap) {
-  extern __shared__ double sm[];
-  __shared__ double s_inv;
+  extern __shared__ real_t sm[];
+  __shared__ real_t s_inv;
   __shared__ int s_fail;
   const PotrfTask t = tasks[blockIdx.x];
   if (threadIdx.x == 0) s_fail = 0;
@@ -145,15 +146,15 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_
 constexpr int kTrsmNC = 32;
 constexpr int kTrsmThreads = 128;
 
-__device__ void trsm_blocked(const double* __restrict__ L, size_t ldl, int m, double* xs,
+__device__ void trsm_blocked(const real_t* __restrict__ L, size_t ldl, int m, real_t* xs,
                              int row0, int nc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int rb = row0; rb < m; rb += 32) {
     const int re = min(m, rb + 32);
     if (warp == 0 && lane < nc) {
       for (int i = rb; i < re; ++i) {
-        double s = xs[i * kTrsmNC + lane];
-        const double* Li = L + i;
+        real_t s = xs[i * kTrsmNC + lane];
+        const real_t* Li = L + i;
         for (int j = rb; j < i; ++j) s = fma(-Li[j * ldl], xs[j * kTrsmNC + lane], s);
         xs[i * kTrsmNC + lane] = s / Li[i * ldl];
       }
@@ -161,8 +162,8 @@ __device__ void trsm_blocked(const double* __restrict__ L, size_t ldl, int m, do
     __syncthreads();
     if (lane < nc) {
       for (int i = re + warp; i < m; i += nw) {
-        const double* Li = L + i;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const real_t* Li = L + i;
+        real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = rb;
         for (; j + 3 < re; j += 4) {
           s0 = fma(Li[j * ldl], xs[j * kTrsmNC + lane], s0);
@@ -180,11 +181,11 @@ __device__ void trsm_blocked(const double* __restrict__ L, size_t ldl, int m, do
 
 __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restrict__ tasks,
                                                        int smem_rows) {
-  extern __shared__ double sm[];  // smem_rows x kTrsmNC
+  extern __shared__ real_t sm[];  // smem_rows x kTrsmNC
   const TrsmTask t = tasks[blockIdx.x];
   const int m = t.m, nc = t.ncols;
   if (m == 0 || nc == 0) return;
-  const double* L = t.L;
+  const real_t* L = t.L;
   const size_t ldl = t.ldl;
   if (m <= smem_rows) {
     int row0 = 0;
@@ -223,22 +224,22 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restric
   } else if (threadIdx.x < nc && t.pad >= 0) {
     // very large factor: one right-hand side per thread, in place in global memory
     const int c = threadIdx.x;
-    double* x = t.X + (size_t)c * t.ldx;
+    real_t* x = t.X + (size_t)c * t.ldx;
     const int cc = t.pad + c;
     for (int i = 0; i < cc; ++i) x[i] = 0.0;
     for (int i = cc; i < m; ++i) {
-      double s = (i == cc) ? 1.0 : 0.0;
-      const double* Li = L + i;
+      real_t s = (i == cc) ? 1.0 : 0.0;
+      const real_t* Li = L + i;
       for (int j = cc; j < i; ++j) s -= Li[j * ldl] * x[j];
       x[i] = s / Li[i * ldl];
     }
   } else if (threadIdx.x < nc) {
     const int c = threadIdx.x;
-    double* x = t.trans ? t.X + c : t.X + (size_t)c * t.ldx;
+    real_t* x = t.trans ? t.X + c : t.X + (size_t)c * t.ldx;
     const size_t inc = t.trans ? (size_t)t.ldx : 1;
     for (int i = 0; i < m; ++i) {
-      double s = x[i * inc];
-      const double* Li = L + i;
+      real_t s = x[i * inc];
+      const real_t* Li = L + i;
       for (int j = 0; j < i; ++j) s -= Li[j * ldl] * x[j * inc];
       x[i * inc] = s / Li[i * ldl];
     }
@@ -256,23 +257,23 @@ constexpr int kFqThreads = 128;
 
 __global__ void __launch_bounds__(kFqThreads) k_form_qt(const FormQtTask* __restrict__ tasks,
                                                         int smem_rows) {
-  extern __shared__ double sm[];  // smem_rows x kTrsmNC, then 4 x kTrsmNC partial sums
+  extern __shared__ real_t sm[];  // smem_rows x kTrsmNC, then 4 x kTrsmNC partial sums
   const FormQtTask t = tasks[blockIdx.x];
   const int m = t.m, nc = t.ncols;
   if (m == 0 || nc == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* part = sm + (size_t)smem_rows * kTrsmNC;
+  real_t* part = sm + (size_t)smem_rows * kTrsmNC;
   if (m > smem_rows) {
     // very large block: one column per lane of warp 0, in global memory
     if (warp == 0 && lane < nc) {
-      double* x = t.Qt + (size_t)lane * m;
+      real_t* x = t.Qt + (size_t)lane * m;
       const int j = t.c0 + lane;
       for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
       for (int s = 0; s < t.nref; ++s) {
-        const double* v = t.V + (size_t)s * m;
-        double d = 0.0;
+        const real_t* v = t.V + (size_t)s * m;
+        real_t d = 0.0;
         for (int i = s; i < m; ++i) d = fma(v[i], x[i], d);
-        const double f = t.tau[s] * d;
+        const real_t f = t.tau[s] * d;
         for (int i = s; i < m; ++i) x[i] = fma(-f, v[i], x[i]);
       }
     }
@@ -284,14 +285,14 @@ __global__ void __launch_bounds__(kFqThreads) k_form_qt(const FormQtTask* __rest
   }
   __syncthreads();
   for (int s = 0; s < t.nref; ++s) {
-    const double* v = t.V + (size_t)s * m;
-    double d = 0.0;
+    const real_t* v = t.V + (size_t)s * m;
+    real_t d = 0.0;
     for (int i = s + warp; i < m; i += nw) d = fma(v[i], sm[i * kTrsmNC + lane], d);
     part[warp * kTrsmNC + lane] = d;
     __syncthreads();
-    double dt = 0.0;
+    real_t dt = 0.0;
     for (int w = 0; w < nw; ++w) dt += part[w * kTrsmNC + lane];
-    const double f = t.tau[s] * dt;
+    const real_t f = t.tau[s] * dt;
     for (int i = s + warp; i < m; i += nw) sm[i * kTrsmNC + lane] = fma(-f, v[i], sm[i * kTrsmNC + lane]);
     __syncthreads();
   }
@@ -310,20 +311,20 @@ constexpr int kKc = 32;
 
 __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ tiles,
                                                const SchurContrib* __restrict__ contribs) {
-  __shared__ double As[kKc][kTile + 1];
-  __shared__ double Bs[kKc][kTile + 1];
+  __shared__ real_t As[kKc][kTile + 1];
+  __shared__ real_t Bs[kKc][kTile + 1];
   const SchurTile t = tiles[blockIdx.x];
   const int tid = threadIdx.x;
   const int ti = tid & 31;        // output row
   const int tj = (tid >> 5) * 4;  // first of 4 output columns
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  real_t acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int ci = t.cbegin; ci < t.cend; ++ci) {
     const SchurContrib c = contribs[ci];
     // kind 0: element (k, i) at k + i*ld (columns of W^T); kind 1: at k*ld + i
     const size_t sk_a = c.pad ? (size_t)c.lda : 1, si_a = c.pad ? 1 : (size_t)c.lda;
     const size_t sk_b = c.pad ? (size_t)c.ldb : 1, si_b = c.pad ? 1 : (size_t)c.ldb;
-    const double* ca = c.a + (size_t)t.i0 * si_a;
-    const double* cb = c.b + (size_t)t.j0 * si_b;
+    const real_t* ca = c.a + (size_t)t.i0 * si_a;
+    const real_t* cb = c.b + (size_t)t.j0 * si_b;
     for (int k0 = 0; k0 < c.K; k0 += kKc) {
       const int kk = min(kKc, c.K - k0);
       if (!c.pad) {
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
       __syncthreads();
 #pragma unroll 8
       for (int k = 0; k < kKc; ++k) {
-        const double a = As[k][ti];
+        const real_t a = As[k][ti];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += a * Bs[k][tj + q];
       }
@@ -354,8 +355,8 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
     for (int q = 0; q < 4; ++q) {
       const int j = tj + q;
       if (j < t.cols) {
-        double* d = t.dst + ti + (size_t)j * t.ld;
-        const double v = *d - acc[q];
+        real_t* d = t.dst + ti + (size_t)j * t.ld;
+        const real_t v = *d - acc[q];
         *d = v;
         if (t.mirror) t.mirror[j + (size_t)ti * t.ld_mirror] = v;
       }
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
 constexpr int kQrThreads = 256;
 
 struct ArgMax {
-  double v;
+  real_t v;
   int i;
 };
 
@@ -389,15 +390,15 @@ __global__ void __launch_bounds__(kQrThreads)
     k_rrqr(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
            int* __restrict__ cur_size, int* __restrict__ rank_out, int* __restrict__ nref_out,
            int* __restrict__ flag_out, double eps, int scheme) {
-  extern __shared__ double sm[];
+  extern __shared__ real_t sm[];
   __shared__ ArgMax s_red[kQrThreads / kWarp];
   __shared__ double s_sec[kQrThreads / kWarp];
   const RRQRTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
   const int m = t.m;
   const size_t ld = t.ld;
-  double* norms = sm;                             // ncols_max
-  double* v = norms + t.ncols_max;                // m
+  real_t* norms = sm;                             // ncols_max
+  real_t* v = norms + t.ncols_max;                // m
   int* cols = reinterpret_cast<int*>(v + m);      // ncols_max
   int* segoff = cols + t.ncols_max;               // nseg + 1
   const int nseg = t.seg_end - t.seg_begin;
@@ -418,8 +419,8 @@ __global__ void __launch_bounds__(kQrThreads)
   __syncthreads();
   // initial squared column norms
   for (int c = warp; c < N; c += nw) {
-    const double* col = t.A + (size_t)cols[c] * ld;
-    double s = 0.0;
+    const real_t* col = t.A + (size_t)cols[c] * ld;
+    real_t s = 0.0;
     for (int i = lane; i < m; i += kWarp) s += col[i] * col[i];
     s = warp_sum(s);
     if (lane == 0) norms[c] = s;
@@ -449,10 +450,32 @@ __global__ void __launch_bounds__(kQrThreads)
     __syncthreads();
     best = s_red[0];
     __syncthreads();
-    const double nusq = best.v;
+    double nusq = (double)best.v;
+    if (sizeof(real_t) < sizeof(double)) {
+      // FP32 storage: nu_0 and near-threshold decisions use the FP64 norm
+      const bool nearthr = step == 0 || fabs(nusq - thr1 * nu0sq) <= 1e-4 * thr1 * nu0sq ||
+                           (scheme == SPAND_SECOND_ORDER_SUPERFINE &&
+                            fabs(nusq - thr2 * nu0sq) <= 1e-4 * thr2 * nu0sq);
+      if (nearthr && best.i >= 0) {
+        if (warp == 0) {
+          const real_t* pc0 = t.A + (size_t)cols[best.i] * ld;
+          double s64 = 0.0;
+          for (int i = step + lane; i < m; i += kWarp) {
+            const double a = (double)pc0[i];
+            s64 = fma(a, a, s64);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          if (lane == 0) s_sec[0] = s64;
+        }
+        __syncthreads();
+        nusq = s_sec[0];
+        __syncthreads();
+      }
+    }
     // second largest candidate norm, for the near-tie flag
     {
-      double sec = -1.0;
+      real_t sec = -1.0;
       for (int c = tid; c < N; c += kQrThreads)
         if (c != best.i) sec = fmax(sec, norms[c]);
 #pragma unroll
@@ -483,7 +506,7 @@ __global__ void __launch_bounds__(kQrThreads)
       if (scheme != SPAND_SECOND_ORDER_SUPERFINE) break;
     }
     if (scheme == SPAND_SECOND_ORDER_SUPERFINE && nusq < thr2 * nu0sq) break;
-    double* pc = t.A + (size_t)cols[best.i] * ld;
+    real_t* pc = t.A + (size_t)cols[best.i] * ld;
     const double alpha = pc[step];
     const double normx = sqrt(nusq);
     double beta, tau;
@@ -496,10 +519,10 @@ __global__ void __launch_bounds__(kQrThreads)
     }
     const double den = alpha - beta;
     for (int i = tid; i < m; i += kQrThreads) {
-      double vi;
+      real_t vi;
       if (i < step) vi = 0.0;
       else if (i == step) vi = 1.0;
-      else vi = (normx == 0.0) ? 0.0 : pc[i] / den;
+      else vi = (normx == 0.0) ? 0.0 : (real_t)(pc[i] / den);
       v[i] = vi;
       t.V[i + (size_t)step * m] = vi;
     }
@@ -512,14 +535,14 @@ __global__ void __launch_bounds__(kQrThreads)
     // apply H_step to the other non-pivoted columns; refresh their norms
     for (int c = warp; c < N; c += nw) {
       if (norms[c] < 0.0) continue;
-      double* col = t.A + (size_t)cols[c] * ld;
-      double d = 0.0;
+      real_t* col = t.A + (size_t)cols[c] * ld;
+      real_t d = 0.0;
       for (int i = step + lane; i < m; i += kWarp) d += v[i] * col[i];
       d = warp_sum(d);
-      const double f = tau * d;
-      double s = 0.0;
+      const real_t f = tau * d;
+      real_t s = 0.0;
       for (int i = step + lane; i < m; i += kWarp) {
-        const double a = col[i] - f * v[i];
+        const real_t a = col[i] - f * v[i];
         col[i] = a;
         if (i > step) s += a * a;
       }
@@ -566,7 +589,7 @@ __global__ void __launch_bounds__(kQrThreads)
 namespace cg = cooperative_groups;
 
 // Candidate exchange of one step: the largest squared norm (as the int64 bit
-// pattern of a non-negative double, which orders like the value; pivoted
+// pattern of a non-negative real_t, which orders like the value; pivoted
 // columns hold -1.0 and sort below every candidate), its column, and the second
 // largest.  Integer compares keep the pivot search off the FP64 pipe.
 struct QrSlot {
@@ -619,10 +642,11 @@ __global__ void __launch_bounds__(kQrThreads)
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const RRQRTask t = tasks[blockIdx.x / csize];
-  extern __shared__ double sm[];
+  extern __shared__ real_t sm[];
   __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
   __shared__ QrSlot s_warp[kQrThreads / kWarp];
   __shared__ double s_tau;   // tau of the current step, written by the owner
+  __shared__ double s_nu64;  // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
   const int m = t.m;
@@ -631,9 +655,9 @@ __global__ void __launch_bounds__(kQrThreads)
   // local column capacity = row length of the row-major block, odd so that the
   // rows touched by one column's threads fall in different banks
   const int ncl = ((t.ncols_max + csize - 1) / csize) | 1;
-  double* A = sm;                                      // m x ncl, row-major
-  double* v = A + (size_t)m * ncl;                     // m
-  double* norms = v + m;                               // ncl
+  real_t* A = sm;                                      // m x ncl, row-major
+  real_t* v = A + (size_t)m * ncl;                     // m
+  real_t* norms = v + m;                               // ncl
   int* pcol = reinterpret_cast<int*>(norms + ncl);     // ncl: column in the panel row
   int* segid = pcol + ncl;                             // ncl: segment of the column
   int* segoff = segid + ncl;                           // nseg + 1
@@ -676,9 +700,9 @@ __global__ void __launch_bounds__(kQrThreads)
   __syncthreads();
   QrSlot mine{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
   for (int l = grp; l < nloc; l += ngrp) {
-    double s2 = 0.0;
+    real_t s2 = 0.0;
     for (int i = sl; i < m; i += tpc) {
-      const double a = A[(size_t)i * ncl + l];
+      const real_t a = A[(size_t)i * ncl + l];
       s2 = fma(a, a, s2);
     }
     for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
@@ -706,7 +730,30 @@ __global__ void __launch_bounds__(kQrThreads)
     QrSlot gb{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
     if (lane < csize) gb = *cluster.map_shared_rank(&s_slot, lane);
     gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
-    const double nusq = __longlong_as_double(gb.best);
+    double nusq = __longlong_as_double(gb.best);
+    if (sizeof(real_t) < sizeof(double)) {
+      // FP32 storage: the decisions that set the rank (nu_0 and any step close
+      // to the threshold) use the pivot column's norm recomputed in FP64
+      const bool nearthr = step == 0 || fabs(nusq - thr1 * nu0sq) <= 1e-4 * thr1 * nu0sq ||
+                           (scheme == SPAND_SECOND_ORDER_SUPERFINE &&
+                            fabs(nusq - thr2 * nu0sq) <= 1e-4 * thr2 * nu0sq);
+      if (nearthr && gb.idx >= 0 && gb.idx < N) {
+        if (crank == gb.idx / cpb && warp == 0) {
+          const int l = gb.idx - g0;
+          double s64 = 0.0;
+          for (int i = step + lane; i < m; i += kWarp) {
+            const double a = (double)A[(size_t)i * ncl + l];
+            s64 = fma(a, a, s64);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          if (lane == 0)
+            for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_nu64, c) = s64;
+        }
+        cluster.sync();
+        nusq = s_nu64;
+      }
+    }
     if (tid == 0 && gb.second >= 0 && nusq > 0.0) {
       const double sec = __longlong_as_double(gb.second);
       if (nusq - sec <= 1e-12 * nusq) flags |= 1;
@@ -750,8 +797,8 @@ __global__ void __launch_bounds__(kQrThreads)
       tau = __shfl_sync(0xffffffffu, tau, 0);
       inv = __shfl_sync(0xffffffffu, inv, 0);
       for (int i = step + tid; i < m; i += kQrThreads) {
-        double* ai = A + (size_t)i * ncl + l;
-        const double vi = (i == step) ? 1.0 : (*ai) * inv;
+        real_t* ai = A + (size_t)i * ncl + l;
+        const real_t vi = (i == step) ? 1.0 : (*ai) * inv;
         *ai = (i == step) ? beta : 0.0;
         t.V[i + (size_t)step * m] = vi;
         for (int c = 0; c < csize; ++c) cluster.map_shared_rank(v, c)[i] = vi;
@@ -764,24 +811,24 @@ __global__ void __launch_bounds__(kQrThreads)
       }
     }
     cluster.sync();
-    const double tau = s_tau;
+    const real_t tau = (real_t)s_tau;
     mine = QrSlot{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < 0.0) continue;  // the same l for the whole group
-      double* a = A + l;
-      double d0 = 0.0, d1 = 0.0;
+      real_t* a = A + l;
+      real_t d0 = 0.0, d1 = 0.0;
       int i = step + sl;
       for (; i + tpc < m; i += 2 * tpc) {
         d0 = fma(v[i], a[(size_t)i * ncl], d0);
         d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
       }
       if (i < m) d0 = fma(v[i], a[(size_t)i * ncl], d0);
-      double d = d0 + d1;
+      real_t d = d0 + d1;
       for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
-      const double f = tau * d;
-      double s2 = 0.0;
+      const real_t f = tau * d;
+      real_t s2 = 0.0;
       for (i = step + sl; i < m; i += tpc) {
-        const double x = fma(-f, v[i], a[(size_t)i * ncl]);
+        const real_t x = fma(-f, v[i], a[(size_t)i * ncl]);
         a[(size_t)i * ncl] = x;
         if (i > step) s2 = fma(x, x, s2);
       }
@@ -839,8 +886,8 @@ void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s) {
   if (ntasks > 0) k_copy<<<ntasks, 256, 0, s>>>(t);
 }
 
-void launch_scatter(const double* val, const int64_t* dst_index, double* base_lo,
-                    double* base_hi, int64_t split, int64_t nnz, cudaStream_t s) {
+void launch_scatter(const double* val, const int64_t* dst_index, real_t* base_lo,
+                    real_t* base_hi, int64_t split, int64_t nnz, cudaStream_t s) {
   if (nnz <= 0) return;
   const int64_t nb = std::min<int64_t>((nnz + 255) / 256, 152 * 32);
   k_scatter<<<(int)nb, 256, 0, s>>>(val, dst_index, base_lo, base_hi, split, nnz);
@@ -853,9 +900,9 @@ void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s) {
 void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s) {
   if (ntasks <= 0) return;
   int cap = max_m * max_m;
-  int bytes = cap * (int)sizeof(double);
+  int bytes = cap * (int)sizeof(real_t);
   if (bytes > kSmemBudget) {
-    cap = kSmemBudget / (int)sizeof(double);
+    cap = kSmemBudget / (int)sizeof(real_t);
     bytes = kSmemBudget;
   }
   set_smem((const void*)k_potrf, bytes);
@@ -865,10 +912,10 @@ void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStrea
 void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
   if (ntasks <= 0) return;
   int rows = max_m;
-  int bytes = rows * kTrsmNC * (int)sizeof(double);
+  int bytes = rows * kTrsmNC * (int)sizeof(real_t);
   if (bytes > kSmemBudget) {
-    rows = kSmemBudget / (kTrsmNC * (int)sizeof(double));
-    bytes = rows * kTrsmNC * (int)sizeof(double);
+    rows = kSmemBudget / (kTrsmNC * (int)sizeof(real_t));
+    bytes = rows * kTrsmNC * (int)sizeof(real_t);
   }
   set_smem((const void*)k_trsm, bytes);
   k_trsm<<<ntasks, kTrsmThreads, bytes, s>>>(t, rows);
@@ -877,11 +924,11 @@ void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
 void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s) {
   if (ntasks <= 0) return;
   int rows = max_m;
-  const int extra = 4 * kTrsmNC * (int)sizeof(double);
-  int bytes = rows * kTrsmNC * (int)sizeof(double) + extra;
+  const int extra = 4 * kTrsmNC * (int)sizeof(real_t);
+  int bytes = rows * kTrsmNC * (int)sizeof(real_t) + extra;
   if (bytes > kSmemBudget) {
-    rows = (kSmemBudget - extra) / (kTrsmNC * (int)sizeof(double));
-    bytes = rows * kTrsmNC * (int)sizeof(double) + extra;
+    rows = (kSmemBudget - extra) / (kTrsmNC * (int)sizeof(real_t));
+    bytes = rows * kTrsmNC * (int)sizeof(real_t) + extra;
   }
   set_smem((const void*)k_form_qt, bytes);
   k_form_qt<<<ntasks, kFqThreads, bytes, s>>>(t, rows);
@@ -893,7 +940,8 @@ void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cud
 
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
   const long ncl = ((ncols_max + csize - 1) / csize) | 1;
-  const long b = 8L * m * ncl + 8L * m + 8L * ncl + 8L * ncl + 4L * (nseg + 2);
+  const long e = (long)sizeof(real_t);
+  const long b = e * m * ncl + e * m + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
   return (int)std::min<long>(b, 1L << 30);
 }
 
@@ -946,8 +994,9 @@ int rrqr_cluster_active(int csize, int smem_bytes) {
 }
 
 int rrqr_smem_bytes(int max_m, int max_cols, int max_segs) {
-  // norms (double) + v (double) + cols (int) + segoff (int)
-  return max_cols * 8 + max_m * 8 + max_cols * 4 + (max_segs + 2) * 4;
+  // norms (real_t) + v (real_t) + cols (int) + segoff (int)
+  return max_cols * (int)sizeof(real_t) + max_m * (int)sizeof(real_t) + max_cols * 4 +
+         (max_segs + 2) * 4 + 16;
 }
 
 void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
@@ -960,4 +1009,5 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_si
                                             scheme);
 }
 
+}  // namespace SPAND_NS
 }  // namespace spand

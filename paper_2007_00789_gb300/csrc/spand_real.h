@@ -1,0 +1,152 @@
+// Precision-dependent declarations: task descriptors and kernel launchers of
+// the factorization and the apply, written against real_t.  This header is
+// included by the translation units that are compiled twice, once with
+// SPAND_REAL=double / SPAND_NS=f64 and once with SPAND_REAL=float /
+// SPAND_NS=f32, so every name lives in namespace spand::SPAND_NS.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "spand.h"
+
+#ifndef SPAND_REAL
+#define SPAND_REAL double
+#define SPAND_NS f64
+#endif
+
+namespace spand {
+namespace SPAND_NS {
+
+typedef SPAND_REAL real_t;
+
+// ---------------------------------------------------------------------------
+// Device task descriptors (plain structs copied to the device in one blob).
+// ---------------------------------------------------------------------------
+
+// dst[i + j*dst_ld] = (trans ? src[j + i*src_ld] : src[i + j*src_ld]); i < rows, j < cols.
+struct CopyTask {
+  const real_t* src;
+  real_t* dst;
+  int src_ld, dst_ld, rows, cols, trans, pad;
+};
+
+// In-place lower Cholesky of an m x m column-major block (ld), id for errors.
+struct PotrfTask {
+  real_t* a;
+  int m, ld, id, pad;
+};
+
+// trans == 0: X (m x ncols, ld ldx) <- L^{-1} X.
+// trans == 1: B (ncols x m, ld ldx) <- B L^{-T}, i.e. B^T <- L^{-1} B^T.
+// ident >= 0: X <- L^{-1} [e_ident .. e_{ident+ncols-1}] (columns of L^{-1}; X's
+// previous contents are ignored).
+struct TrsmTask {
+  const real_t* L;
+  real_t* X;
+  int m, ldl, ldx, ncols, trans, pad;  // pad: ident (first identity column) or -1
+};
+
+// Columns c0 .. c0+ncols-1 of Q^T = H_{nref-1} ... H_0 (m x m, ld m).
+struct FormQtTask {
+  const real_t* V;
+  const real_t* tau;
+  real_t* Qt;  // already offset to column c0
+  int m, nref, c0, ncols;
+};
+
+// One output tile (rows x cols <= 32 x 32) of a Schur target block:
+// T -= sum_c A_c^T B_c, written at dst (ld) and, unless mirror == nullptr,
+// transposed at mirror (ld_mirror).
+struct SchurTile {
+  real_t* dst;
+  real_t* mirror;
+  int ld, ld_mirror, rows, cols, cbegin, cend, i0, j0;
+};
+// A_c: K x (i0 + rows) at a (lda), B_c: K x (j0 + cols) at b (ldb); the tile
+// uses columns i0.. of A_c and j0.. of B_c.  pad = 0: element (k, i) at
+// k + i*ld (column-major); pad = 1: at k*ld + i (the transposed storage, e.g.
+// a column panel P whose product P P^T is wanted).
+struct SchurContrib {
+  const real_t* a;
+  const real_t* b;
+  int K, lda, ldb, pad;
+};
+
+// One segment (neighbour block) of an interface's panel row.
+struct RRQRSeg {
+  real_t* mirror;  // origin of the transposed block in the neighbour's row
+  int col;         // first column of the segment in the row
+  int cl;          // neighbour cluster id (its live width is cur_size[cl])
+  int mirror_ld;   // leading dimension of the neighbour's row
+  int pad;
+};
+
+struct RRQRTask {
+  real_t* A;       // panel row of interface p, column-major, ld
+  real_t* diag;    // origin of the diagonal segment (set to I_r afterwards)
+  real_t* V;       // reflectors, m x maxref, ld m
+  real_t* tau;     // maxref
+  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max;
+};
+
+// Preconditioner apply descriptors.  The triangular factors and Q_p are
+// applied through explicit matrices formed at the end of each stage
+// (L_s^{-1}, Z_p^{-1}, Q_p^T), so every apply step is a dense product.
+struct ApInterior {
+  const real_t* Linv;   // m x m lower, L_s^{-1}, ld m
+  const real_t* WT;     // panel row, m x ncols (ld = m); diag columns skipped via wslot < 0
+  const int* slots;     // m vector positions
+  const int* wslots;    // ncols vector positions (-1 for the diagonal segment)
+  int m, ncols;
+};
+struct ApScale {
+  const real_t* Zinv;  // m x m lower, Z_p^{-1}, ld m
+  const int* slots;
+  int m, pad;
+};
+struct ApQE {
+  const real_t* Qt;   // m x m, Q_p^T, ld m
+  const real_t* E;    // nE x ncols, ld nE
+  const int* slots;   // m positions (before sparsification)
+  const int* eslots;  // ncols positions
+  int m, r, nE, ncols;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (spand_kernels.cu / spand_apply.cu).
+// ---------------------------------------------------------------------------
+void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s);
+// base_lo[d] = val[e] for 0 <= d < split, base_hi[d - split] for d >= split, skip d < 0.
+void launch_scatter(const double* val, const int64_t* dst_index, real_t* base_lo,
+                    real_t* base_hi, int64_t split, int64_t nnz, cudaStream_t s);
+void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s);
+void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s);
+void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s);
+void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s);
+void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s);
+void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s);
+int rrqr_smem_bytes(int max_m, int max_cols, int max_segs);
+// On-chip variant: C CTAs per interface (a thread-block cluster), the block in shared memory.
+int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
+// Clusters of this shape that can be resident at once (0: cannot be launched).
+int rrqr_cluster_active(int csize, int smem_bytes);
+void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
+                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
+                         int csize, int smem_bytes, cudaStream_t s);
+void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
+                 int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
+                 int max_cols, int max_segs, cudaStream_t s);
+
+// K: CTAs per operator (a thread-block cluster), 1..16.
+void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
+                        bool forward, cudaStream_t s);
+void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, real_t* z, bool forward,
+                     cudaStream_t s);
+void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
+                  bool forward, cudaStream_t s);
+
+
+}  // namespace SPAND_NS
+}  // namespace spand

@@ -45,7 +45,7 @@ class _CSR(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("skip", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
-                ("rrqr_kernel", ctypes.c_int32)]
+                ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -131,7 +131,7 @@ class Spand:
 
     def __init__(self, rowptr, colind, val, coords, nlevels: int, eps: float, scheme: int = 1,
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
-                 max_restarts: int | None = None, rrqr_kernel: int = 0):
+                 max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0):
         L = load_library()
         self._lib = L
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
@@ -146,7 +146,8 @@ class Spand:
                    self._val.ctypes.data)
         opts = _Opts(-1 if skip is None else int(skip), 0 if maxit is None else int(maxit),
                      0 if true_res_every is None else int(true_res_every),
-                     -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel))
+                     -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
+                     int(precision))
         h = ctypes.c_void_p()
         _check(L.spand_analyze(ctypes.byref(csr), coords.ctypes.data, coords.shape[1], int(nlevels),
                                float(eps), int(scheme), ctypes.byref(opts), ctypes.byref(h)))
