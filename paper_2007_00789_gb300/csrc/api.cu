@@ -198,6 +198,7 @@ void free_handle(spand_s* h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   cudaFree(h->d_rf);
+  h->free_graphs();
   h->prof.release();
   delete h;
 }
@@ -515,9 +516,10 @@ int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t
   double* partial = ws + 4 * kNoAllocMaxN;
   double* sc = partial + (kNoAllocScalars - 16);
   if (dot_partials(n) > kNoAllocScalars - 16) return fail(SPAND_EINVAL, "internal: too many dot partials");
-  // profiling would create CUDA events; keep it off for this call
+  // profiling would create CUDA events and a graph capture allocates: plain launches only
   const bool prof_on = h->prof.on;
   h->prof.on = false;
+  h->no_graph = true;
   // scalars start from zero (the array keeps whatever the previous call left)
   CK(cudaMemsetAsync(sc, 0, 16 * sizeof(double), s));
   auto dot = [&](const double* a, const double* c, int slot) {
@@ -580,6 +582,7 @@ int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t
   };
   const int rc = body();
   h->prof.on = prof_on;
+  h->no_graph = false;
   return rc;
 }
 

@@ -250,12 +250,63 @@ bool cluster_ok(spand_s* h, int cs) {
 
 }  // namespace
 
+// Replays the stage graphs of the previous factorization; returns 1 if a
+// stage produced other ranks than the ones the graphs were built with (the
+// caller then rebuilds), SPAND_OK on success, or an error code.
+int factor_replay(spand_s* h, cudaStream_t s) {
+  const int ell = h->nlevels;
+  CK(cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), s));
+  for (int k = 0; k <= ell; ++k) {
+    auto& g = h->sgraph[k];
+    if (g.exec) CK(cudaGraphLaunch(g.exec, s));
+    if (k == ell) break;
+    int* hp = h->h_pinned;
+    const int ncl = g.ncl;
+    CK(cudaMemcpyAsync(hp, g.d_blob + g.o_rank, ncl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + ncl, g.d_blob + g.o_nref, ncl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 2 * ncl, g.d_blob + g.o_flag, ncl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 3 * ncl, h->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hp[3 * ncl] != 0)
+      return fail(SPAND_ENOTSPD, "non-positive Cholesky pivot at stage " + std::to_string(k) +
+                                     ", cluster " + std::to_string(hp[3 * ncl] - 1));
+    if (!std::equal(g.ranks.begin(), g.ranks.end(), hp) ||
+        !std::equal(g.nrefs.begin(), g.nrefs.end(), hp + ncl))
+      return 1;
+    h->flags[k].assign(hp + 2 * ncl, hp + 3 * ncl);
+  }
+  CK(cudaStreamSynchronize(s));
+  return SPAND_OK;
+}
+
 int factor(spand_s* h, cudaStream_t s) {
   auto t0 = std::chrono::steady_clock::now();
   RET(ensure_device(h));
+  const int precision = sizeof(real_t) == 4 ? 1 : 0;
+  if (h->graph_valid && h->graph_prec == precision && !h->prof.on && h->factored) {
+    const int rc = factor_replay(h, s);
+    if (rc == SPAND_OK) {
+      h->factor_ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      return SPAND_OK;
+    }
+    if (rc != 1) {
+      h->factored = false;
+      return rc;
+    }
+  }
+  // full factorization; stage graphs are (re)built unless profiling is on
+  h->drop_graphs();
+  const bool capture = !h->prof.on;
+  if (capture && !h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (capture) h->sgraph.resize(h->nlevels + 1);
+  h->graph_prec = precision;
   h->factored = false;
   h->farena.reset();
   h->launches = 0;
+  // scratch generations seen by each stage's graph; a later reallocation of a
+  // buffer that an earlier graph uses leaves that graph pointing at freed memory
+  std::vector<std::pair<int, int>> used_gen;
   const int ell = h->nlevels;
   std::vector<StageLayout> L(ell);
   std::vector<int> pool;  // slot pool (vector positions), uploaded at the end
@@ -579,12 +630,37 @@ int factor(spand_s* h, cudaStream_t s) {
     for (size_t c = 0; c < qr_tasks.size(); ++c) o_qr[c] = blob.add(qr_tasks[c]);
     const size_t o_seg = blob.add(qr_segs);
     const size_t o_cur = blob.add(cur_size);
+    const size_t o_cur0 = blob.add(cur_size);
     const size_t o_rank = blob.add(rank_init);
     const size_t o_nref = blob.add(rank_init);
     const size_t o_flag = blob.add(rank_init);
-    RET(h->tables.ensure(blob.h.size() + 16));
-    char* D = h->tables.p;
+    char* D = nullptr;
+    if (capture) {
+      auto& g = h->sgraph[k];
+      if (g.cap < blob.h.size() + 16) {
+        if (g.d_blob) cudaFree(g.d_blob);
+        g.d_blob = nullptr;
+        g.cap = 0;
+        CK(cudaMalloc(&g.d_blob, blob.h.size() + 16));
+        g.cap = blob.h.size() + 16;
+      }
+      D = g.d_blob;
+    } else {
+      RET(h->tables.ensure(blob.h.size() + 16));
+      D = h->tables.p;
+    }
     CK(cudaMemcpyAsync(D, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
+    // launches go to the capture stream (recorded into the stage graph) or to s
+    cudaStream_t cs = s;
+    if (capture) {
+      used_gen.push_back({h->scratch[0].gen, h->scratch[1].gen});
+      CK(cudaStreamSynchronize(s));
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cs = h->cap_stream;
+      // the RRQR kernels shrink the widths in place: start from the pristine copy
+      CK(cudaMemcpyAsync(D + o_cur, D + o_cur0, cur_size.size() * sizeof(int),
+                         cudaMemcpyDeviceToDevice, cs));
+    }
 
     // ---- kernels
     int nl = 0;
@@ -592,85 +668,100 @@ int factor(spand_s* h, cudaStream_t s) {
     auto run = [&](int kind, size_t ntasks, double flops, double bytes, auto&& launch) {
       if (ntasks == 0) return;
       ++nl;
-      P.run(kind, s, flops, bytes, launch);
+      P.run(kind, cs, flops, bytes, launch);
     };
     run(KK_ECOPY, pending_e.size(), 0.0, copy_bytes(pending_e),
-        [&] { launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), s); });
+        [&] { launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), cs); });
     run(KK_TRTRI, pending_inv.size(), trtri_flops(pending_inv), trsm_bytes(pending_inv), [&] {
-      launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, s);
+      launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, cs);
     });
     run(KK_FORMQ, pending_qt.size(), formqt_flops(pending_qt), 0.0, [&] {
-      launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, s);
+      launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, cs);
     });
-    if (fbytes) CK(cudaMemsetAsync(fptr, 0, fbytes, s));
-    if (sbytes) CK(cudaMemsetAsync(scr.p, 0, sbytes, s));
+    if (fbytes) CK(cudaMemsetAsync(fptr, 0, fbytes, cs));
+    if (sbytes) CK(cudaMemsetAsync(scr.p, 0, sbytes, cs));
     if (k == 0) {
       run(KK_PACK, 1, 0.0, 16.0 * h->nnz, [&] {
-        launch_scatter(h->d_val, h->d_pack, (real_t*)fptr, (real_t*)scr.p, h->pack_split, h->nnz, s);
+        launch_scatter(h->d_val, h->d_pack, (real_t*)fptr, (real_t*)scr.p, h->pack_split, h->nnz, cs);
       });
     } else {
       run(KK_MERGE, merge.size(), 0.0, copy_bytes(merge),
-          [&] { launch_copy((const CopyTask*)(D + o_merge), (int)merge.size(), s); });
+          [&] { launch_copy((const CopyTask*)(D + o_merge), (int)merge.size(), cs); });
     }
     auto run_potrf = [&](int kind, PotrfPlan& PP) {
       bool first = true;
       auto fl = [&]() { double f = first ? PP.flops : 0.0; first = false; return f; };
       run(kind, PP.small.size(), fl(), PP.bytes, [&] {
-        launch_potrf((const PotrfTask*)(D + PP.o_small), (int)PP.small.size(), PP.small_max, h->d_err, s);
+        launch_potrf((const PotrfTask*)(D + PP.o_small), (int)PP.small.size(), PP.small_max, h->d_err, cs);
       });
       for (auto& st : PP.steps) {
         run(kind, st.diag.size(), fl(), 0.0, [&] {
-          launch_potrf((const PotrfTask*)(D + st.o_diag), (int)st.diag.size(), kPanel, h->d_err, s);
+          launch_potrf((const PotrfTask*)(D + st.o_diag), (int)st.diag.size(), kPanel, h->d_err, cs);
         });
         run(kind, st.trsm.size(), 0.0, 0.0, [&] {
-          launch_trsm((const TrsmTask*)(D + st.o_trsm), (int)st.trsm.size(), kPanel, s);
+          launch_trsm((const TrsmTask*)(D + st.o_trsm), (int)st.trsm.size(), kPanel, cs);
         });
         run(kind, st.tiles.size(), 0.0, 0.0, [&] {
           launch_schur((const SchurTile*)(D + st.o_tiles), (int)st.tiles.size(),
-                       (const SchurContrib*)(D + st.o_contribs), s);
+                       (const SchurContrib*)(D + st.o_contribs), cs);
         });
       }
     };
     run_potrf(KK_POTRF, plan_int);
     run(KK_TRSM, trsm_int.size(), trsm_flops(trsm_int), trsm_bytes(trsm_int),
-        [&] { launch_trsm((const TrsmTask*)(D + o_ti), (int)trsm_int.size(), max_m_int, s); });
+        [&] { launch_trsm((const TrsmTask*)(D + o_ti), (int)trsm_int.size(), max_m_int, cs); });
     {
       double fl = 0.0, by = 0.0;
       schur_work(tiles, contribs, &fl, &by);
       run(KK_SCHUR, tiles.size(), fl, by, [&] {
         launch_schur((const SchurTile*)(D + o_tiles), (int)tiles.size(),
-                     (const SchurContrib*)(D + o_contr), s);
+                     (const SchurContrib*)(D + o_contr), cs);
       });
     }
     if (S.sparsify) {
       run(KK_SCALE_COPY, zcopy.size(), 0.0, copy_bytes(zcopy),
-          [&] { launch_copy((const CopyTask*)(D + o_zc), (int)zcopy.size(), s); });
+          [&] { launch_copy((const CopyTask*)(D + o_zc), (int)zcopy.size(), cs); });
       run_potrf(KK_SCALE_POTRF, plan_z);
       run(KK_SCALE_TRSM, ltrsm.size(), trsm_flops(ltrsm), trsm_bytes(ltrsm),
-          [&] { launch_trsm((const TrsmTask*)(D + o_lt), (int)ltrsm.size(), max_m_if, s); });
+          [&] { launch_trsm((const TrsmTask*)(D + o_lt), (int)ltrsm.size(), max_m_if, cs); });
       run(KK_SCALE_TRSM, rtrsm.size(), trsm_flops(rtrsm), trsm_bytes(rtrsm),
-          [&] { launch_trsm((const TrsmTask*)(D + o_rt), (int)rtrsm.size(), max_m_if, s); });
+          [&] { launch_trsm((const TrsmTask*)(D + o_rt), (int)rtrsm.size(), max_m_if, cs); });
       run(KK_SCALE_COPY, mirror.size(), 0.0, copy_bytes(mirror),
-          [&] { launch_copy((const CopyTask*)(D + o_mi), (int)mirror.size(), s); });
+          [&] { launch_copy((const CopyTask*)(D + o_mi), (int)mirror.size(), cs); });
       run(KK_SCALE_COPY, ident.size(), 0.0, potrf_bytes(ident) / 2,
-          [&] { launch_set_identity((const PotrfTask*)(D + o_id), (int)ident.size(), s); });
+          [&] { launch_set_identity((const PotrfTask*)(D + o_id), (int)ident.size(), cs); });
       for (size_t c = 0; c < qr_tasks.size(); ++c) {
         run(KK_RRQR, qr_tasks[c].size(), 0.0, 0.0, [&] {
           if (qr_csize[c] == 0)
             launch_rrqr((const RRQRTask*)(D + o_qr[c]), (int)qr_tasks[c].size(),
                         (const RRQRSeg*)(D + o_seg), (int*)(D + o_cur), (int*)(D + o_rank),
                         (int*)(D + o_nref), (int*)(D + o_flag), h->eps, h->scheme, qr_max_m[c],
-                        qr_max_cols[c], qr_max_segs[c], s);
+                        qr_max_cols[c], qr_max_segs[c], cs);
           else
             launch_rrqr_cluster((const RRQRTask*)(D + o_qr[c]), (int)qr_tasks[c].size(),
                                 (const RRQRSeg*)(D + o_seg), (int*)(D + o_cur), (int*)(D + o_rank),
                                 (int*)(D + o_nref), (int*)(D + o_flag), h->eps, h->scheme,
-                                qr_csize[c], qr_smem[c], s);
+                                qr_csize[c], qr_smem[c], cs);
         });
       }
     }
     CK(cudaGetLastError());
     h->launches += nl;
+    if (capture) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamEndCapture(h->cap_stream, &graph));
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      auto& g = h->sgraph[k];
+      g.exec = exec;
+      g.o_rank = o_rank;
+      g.o_nref = o_nref;
+      g.o_flag = o_flag;
+      g.ncl = ncl;
+      CK(cudaGraphLaunch(exec, s));
+    }
     // ---- read back ranks and the error flag (the sync of this stage)
     const size_t need = 3 * (size_t)ncl + 2;
     if (need > h->h_pinned_cap) {
@@ -693,6 +784,10 @@ int factor(spand_s* h, cudaStream_t s) {
     h->ranks[k].assign(hp, hp + ncl);
     h->nrefs[k].assign(hp + ncl, hp + 2 * ncl);
     h->flags[k].assign(hp + 2 * ncl, hp + 3 * ncl);
+    if (capture) {
+      h->sgraph[k].ranks = h->ranks[k];
+      h->sgraph[k].nrefs = h->nrefs[k];
+    }
     if (P.on) {
       P.resolve();
       if (S.sparsify) {
@@ -855,26 +950,56 @@ int factor(spand_s* h, cudaStream_t s) {
     const size_t o_e = blob.add(pending_e);
     const size_t o_inv = blob.add(pending_inv);
     const size_t o_fq = blob.add(pending_qt);
-    RET(h->tables.ensure(blob.h.size() + 16));
-    char* D = h->tables.p;
+    char* D = nullptr;
+    if (capture) {
+      auto& g = h->sgraph[ell];
+      if (g.cap < blob.h.size() + 16) {
+        if (g.d_blob) cudaFree(g.d_blob);
+        g.d_blob = nullptr;
+        g.cap = 0;
+        CK(cudaMalloc(&g.d_blob, blob.h.size() + 16));
+        g.cap = blob.h.size() + 16;
+      }
+      D = g.d_blob;
+    } else {
+      RET(h->tables.ensure(blob.h.size() + 16));
+      D = h->tables.p;
+    }
     CK(cudaMemcpyAsync(D, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
+    const bool any = !pending_e.empty() || !pending_inv.empty() || !pending_qt.empty();
+    cudaStream_t cs = s;
+    if (capture && any) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cs = h->cap_stream;
+    }
     if (!pending_e.empty()) {
-      h->prof.run(KK_ECOPY, s, 0.0, copy_bytes(pending_e), [&] {
-        launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), s);
+      h->prof.run(KK_ECOPY, cs, 0.0, copy_bytes(pending_e), [&] {
+        launch_copy((const CopyTask*)(D + o_e), (int)pending_e.size(), cs);
       });
       h->launches += 1;
     }
     if (!pending_inv.empty()) {
-      h->prof.run(KK_TRTRI, s, trtri_flops(pending_inv), trsm_bytes(pending_inv), [&] {
-        launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, s);
+      h->prof.run(KK_TRTRI, cs, trtri_flops(pending_inv), trsm_bytes(pending_inv), [&] {
+        launch_trsm((const TrsmTask*)(D + o_inv), (int)pending_inv.size(), pending_inv_m, cs);
       });
       h->launches += 1;
     }
     if (!pending_qt.empty()) {
-      h->prof.run(KK_FORMQ, s, formqt_flops(pending_qt), 0.0, [&] {
-        launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, s);
+      h->prof.run(KK_FORMQ, cs, formqt_flops(pending_qt), 0.0, [&] {
+        launch_form_qt((const FormQtTask*)(D + o_fq), (int)pending_qt.size(), pending_qt_m, cs);
       });
       h->launches += 1;
+    }
+    if (capture && any) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamEndCapture(h->cap_stream, &graph));
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      h->sgraph[ell].exec = exec;
+      CK(cudaGraphLaunch(exec, s));
     }
   }
   // ---- apply plan: slot pool + descriptors into the factor arena
@@ -907,12 +1032,41 @@ int factor(spand_s* h, cudaStream_t s) {
   h->phases = phases;
   h->nnz_factor = nnzf;
   h->factored = true;
+  h->graph_valid = capture;
+  for (const auto& g : used_gen)
+    if (g.first != h->scratch[0].gen || g.second != h->scratch[1].gen) h->graph_valid = false;
   h->factor_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return SPAND_OK;
 }
 
+int apply_launches(spand_s* h, const real_t* r, real_t* z, cudaStream_t s);
+
+// The whole apply as one CUDA graph (built on first use for these vectors),
+// or as plain launches while profiling.
 int apply(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
+  if (h->prof.on || h->no_graph) return apply_launches(h, r, z, s);
+  if (!(h->apply_exec && h->apply_r == (const void*)r && h->apply_z == (void*)z)) {
+    if (h->apply_exec) cudaGraphExecDestroy(h->apply_exec);
+    h->apply_exec = nullptr;
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = apply_launches(h, r, z, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    RET(rc);
+    CK(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&h->apply_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    h->apply_r = r;
+    h->apply_z = z;
+  }
+  CK(cudaGraphLaunch(h->apply_exec, s));
+  return SPAND_OK;
+}
+
+int apply_launches(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
   Prof& P = h->prof;
   const int n = h->n;
   if (r != z) P.run(KK_VEC, s, 0.0, 2.0 * sizeof(real_t) * n, [&] { launch_copy_real(n, r, z, s); });

@@ -85,8 +85,10 @@ struct DevArena {
 struct DevBuf {
   char* p = nullptr;
   size_t cap = 0;
+  int gen = 0;  // bumped whenever p changes (graphs that captured the old p are stale)
   int ensure(size_t bytes) {
     if (bytes <= cap) return SPAND_OK;
+    ++gen;
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -294,6 +296,44 @@ struct spand_s {
   spand::Prof prof;
   int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
+  // CUDA-graph replay of a refactorization: one graph per stage (plus one for
+  // the work after the last stage), valid while every stage reproduces the
+  // ranks it was built with; and one graph of the whole apply sweep.
+  struct StageGraph {
+    char* d_blob = nullptr;  // the stage's task tables (kept: the graph reads them)
+    size_t cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    size_t o_rank = 0, o_nref = 0, o_flag = 0;
+    int ncl = 0;
+    std::vector<int> ranks, nrefs, flags;
+  };
+  std::vector<StageGraph> sgraph;
+  bool graph_valid = false;
+  int graph_prec = -1;
+  cudaStream_t cap_stream = nullptr;  // capture needs a stream other than the legacy one
+  cudaGraphExec_t apply_exec = nullptr;
+  bool no_graph = false;  // plain launches only (set by the allocation-free PCG)
+  const void* apply_r = nullptr;
+  void* apply_z = nullptr;
+  void drop_graphs() {
+    for (auto& g : sgraph) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    graph_valid = false;
+    if (apply_exec) cudaGraphExecDestroy(apply_exec);
+    apply_exec = nullptr;
+    apply_r = nullptr;
+    apply_z = nullptr;
+  }
+  void free_graphs() {
+    drop_graphs();
+    for (auto& g : sgraph)
+      if (g.d_blob) cudaFree(g.d_blob);
+    sgraph.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+  }
 };
 
 namespace spand {

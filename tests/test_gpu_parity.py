@@ -204,6 +204,32 @@ def test_not_spd_reported():
     h.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_refactor_replays_graphs(precision):
+    """Refactorizations replay the stage graphs of the previous one (same
+    ranks): results must be those of a fresh factorization, several times over."""
+    torch = _torch()
+    from paper_2007_00789_gb300 import spand as S
+    prob = si.diffusion_3d(48, seed=3)
+    h = S.Spand.from_problem(prob, 11, 1e-2, 1, precision=precision)
+    r = np.random.default_rng(1).standard_normal(prob.n)
+    b = torch.from_numpy(si.rhs_normal(prob.n, seed=2)).cuda()
+    ref = None
+    for _ in range(4):
+        h.factor()
+        z = _gpu_apply(h, r)
+        x = torch.zeros_like(b)
+        it, rel = h.pcg(b, x, 1e-12)
+        assert rel <= 1e-12
+        if ref is None:
+            ref = (h.ranks(), z, it)
+        else:
+            assert np.array_equal(h.ranks()[:, :2], ref[0][:, :2])
+            assert np.abs(z - ref[1]).max() <= 1e-6 * np.abs(ref[1]).max()
+            assert abs(it - ref[2]) <= 1
+    h.close()
+
+
 def test_refactor_is_deterministic():
     prob = si.diffusion_3d(16, seed=4)
     h = _gpu_handle(prob, 7, 1e-2, 1)
