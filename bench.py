@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "factor+PCG time to rel. residual 1e-12, CG its; served solves/s, p99 latency"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (the profiling recipe's figure); no measured FP64 peak is provided
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 152 SMs x 2070 MHz x 128 FP32 FMA/clk/SM
 
 WORKLOADS = {
     # name: (factory, dim, ell, rhs)
@@ -157,23 +158,153 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local, dist):
+    """64 independent problems (2D 128^2..512^2 and 3D 24^3..48^3 FV diffusion,
+    a = 10^U(-2,2)): one step = batch factorization + batch PCG of all of them."""
+    import numpy as np
+    import torch
+
+    import spand_inputs as si
+    from paper_2007_00789_gb300 import spand
+
+    tol = 1e-12
+    work = si.batch_workload(64)
+    stream = torch.cuda.current_stream()
+    hs = [spand.Spand.from_problem(p, ell, args.eps, args.scheme, precision=args.precision,
+                                   rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches)
+          for p, ell, _ in work]
+    batch = spand.SpandBatch(hs)
+    bs = [torch.from_numpy(b).cuda() for _, _, b in work]
+    xs = [torch.zeros_like(b) for b in bs]
+    its = rels = None
+    for _ in range(args.warmup):
+        batch.factor(stream)
+        its, rels = batch.pcg(bs, xs, tol, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fac_ms = []
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.factor(stream)
+            fac_ms.append(batch.info()["factor_ms"])
+            its, rels = batch.pcg(bs, xs, tol, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    info = batch.info()
+    batch.set_profiling(True)
+    for _ in range(args.steps):
+        batch.factor(stream)
+        batch.pcg(bs, xs, tol, stream)
+    torch.cuda.synchronize()
+    kstats = batch.kernel_stats()
+    batch.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    true_rel = max(float(np.linalg.norm(b - p.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b))
+                   for (p, _, b), x in zip(work, xs))
+    # end to end: analyze + batch factor + batch PCG with the H2D copies of every
+    # problem's matrix and right-hand side and the D2H copies of the solutions
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        he = [spand.Spand.from_problem(p, ell, args.eps, args.scheme, precision=args.precision,
+                                       rrqr_kernel=args.rrqr_kernel) for p, ell, _ in work]
+        be = spand.SpandBatch(he)
+        be.factor(stream)
+        pin = [torch.from_numpy(b).pin_memory() for _, _, b in work]
+        bd = [t.cuda(non_blocking=True) for t in pin]
+        xd = [torch.zeros_like(b) for b in bd]
+        be.pcg(bd, xd, tol, stream)
+        xh = [x.cpu() for x in xd]
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        be.close()
+        for h in he:
+            h.close()
+        h2d = sum(4 * (p.n + 1) + 12 * p.nnz + 8 * p.n for p, _, _ in work)
+        d2h = sum(8 * p.n for p, _, _ in work)
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "includes": "host analysis of all 64 problems"}
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    achieved = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["total_ms"] > 0 else 0.0
+    peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
+    roof = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived from the SM count and clock (FP32: 128 FMA/clk/SM; FP64: the"
+                           " recipe's nominal figure)",
+            "avg_launch_ms": dom["total_ms"] / max(dom["launches"], 1),
+            "launches_per_step": dom["launches"] / args.steps}
+    n_total = sum(p.n for p, _, _ in work)
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f32 factor/apply + f64 pcg",
+        "data": "synthetic",
+        "config": {"workload": "batch64", "problems": len(work), "n_total": n_total,
+                   "nnz_total": sum(p.nnz for p, _, _ in work), "eps": args.eps,
+                   "scheme": args.scheme, "tol": tol, "nlevels": "round(log2(n/25)) per problem",
+                   "cg_iters_max": int(max(its)), "cg_iters_mean": float(np.mean(its)),
+                   "relres_max": float(max(rels)), "true_relres_max_host": true_rel,
+                   "factor_ms": float(np.median(fac_ms)), "pcg_ticks": info["ticks"],
+                   "solves_per_s": len(work) / (ms / 1e3),
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                   "cuda_graphs": not args.plain_launches},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(sum(k["launches"] for k in kstats) // args.steps),
+        "roofline": roof,
+        "kernels": {k["name"]: {"ms_per_step": k["total_ms"] / args.steps,
+                                "launches_per_step": k["launches"] / args.steps,
+                                "gflop_per_step": k["flops"] / args.steps / 1e9}
+                    for k in kstats if k["launches"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for h in hs:
+        h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="spand", choices=["spand", "reference"])
-    ap.add_argument("--workload", default="poisson3d_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="poisson3d_64", choices=sorted(WORKLOADS) + ["batch64"],
+                    help="batch64: 64 independent 2D/3D diffusion problems factored and solved"
+                         " as one batch (FP32 factor by default)")
     ap.add_argument("--scheme", type=int, default=1)
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--precision", type=int, default=None, choices=[0, 1],
                     help="0: FP64 factor+apply; 1: FP32 factor+apply (PCG stays FP64)")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip timing the other precision")
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="no CUDA graphs: every kernel launched on its own (for profilers)")
+    ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="0: on-chip RRQR in clusters of up to 16 CTAs; 1: global-memory RRQR;"
+                         " 2: on-chip RRQR in clusters of up to 8 CTAs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.precision is None:
+        args.precision = 1 if args.workload == "batch64" else 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,11 +324,15 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "batch64":
+        run_batch(args, rank, world, local, dist)
+        return
 
     prob, ell, b = make_problem(args.workload)
     tol = 1e-12
     stream = torch.cuda.current_stream()
-    h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision)
+    h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
+                                 rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     iters = rel = None
@@ -246,7 +381,9 @@ def main():
         for i in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision)
+            he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
+                                          rrqr_kernel=args.rrqr_kernel,
+                                          plain_launches=args.plain_launches)
             he.factor(stream)
             x_host, it_e, rel_e = he.pcg_host(b, tol, stream)
             torch.cuda.synchronize()
@@ -261,7 +398,9 @@ def main():
     variant = None
     if not args.no_variant:
         other = 1 - args.precision
-        hv = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=other)
+        hv = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=other,
+                                      rrqr_kernel=args.rrqr_kernel,
+                                      plain_launches=args.plain_launches)
         xv = torch.zeros_like(bd)
         for _ in range(args.warmup):
             hv.factor(stream)
@@ -299,7 +438,8 @@ def main():
         "config": {"workload": args.workload, "n": prob.n, "nnz": prob.nnz, "nlevels": ell,
                    "eps": args.eps, "scheme": args.scheme, "tol": tol, "cg_iters": iters,
                    "relres": rel, "mu": info["mu"], "skip": info["skip"],
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                   "cuda_graphs": not args.plain_launches, "rrqr_kernel": args.rrqr_kernel},
         "clocks": clk.summary(),
         "variant": variant,
         "e2e": e2e,

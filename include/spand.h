@@ -67,11 +67,16 @@ typedef struct {
   int32_t max_restarts;   /* PCG restarts when the true residual misses tol; <0 = 2 */
   int32_t rrqr_kernel;    /* 0 = keep each interface block on chip (one CTA, or a thread-block
                              cluster of up to 16 CTAs) where it fits, else stream it from global
-                             memory; 1 = always stream from global memory.  Same results. */
+                             memory; 1 = always stream from global memory; 2 = as 0 with
+                             clusters of at most 8 CTAs (the portable cluster size).  Same
+                             results. */
   int32_t precision;      /* 0 = FP64 factorization and apply (the default);
                              1 = FP32 factorization and apply, with the RRQR rank decisions
                              (nu_0 and every step within 1e-4 of the threshold) taken on norms
                              recomputed in FP64; PCG, its dot products and residuals stay FP64 */
+  int32_t plain_launches; /* 0 = replay refactorizations and applies from CUDA graphs (the
+                             default); 1 = plain kernel launches only.  Same kernels, same
+                             results; meant for profilers that cannot replay graph nodes. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */
@@ -209,6 +214,48 @@ typedef struct {
 int spand_set_profiling(spand_t h, int on);
 /* out: host array of cap entries; *count receives the number of kernel kinds. */
 int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent problems.
+ *
+ * A batch groups analysed handles of one precision.  spand_batch_factor runs
+ * the numerical factorization of all of them together: stage k of every
+ * problem (k counted from the leaves) goes into the same launches, one launch
+ * per kernel step, so many small and uneven problems fill the GPU as one large
+ * one does (Algorithm 2 is applied to each problem exactly as by
+ * spand_factor; the results are the same as factoring each handle on its
+ * own).  Refactorizations with unchanged ranks replay CUDA graphs of the whole
+ * batch, as spand_factor does for one handle.
+ *
+ * spand_batch_pcg solves A_i x_i = b_i for every problem i with the PCG of §4
+ * (x0 = 0, per-problem tol, maxit, true-residual and restart rules), all
+ * problems advancing together; each step of all problems is one launch, and
+ * the preconditioner applies are merged across problems.
+ *
+ * Ownership: the batch references the handles, which the caller keeps alive
+ * (and does not destroy) until spand_batch_destroy.  Factoring a member
+ * handle on its own in between is allowed; the batch then rebuilds its graphs.
+ * Errors: SPAND_EINVAL (null, empty, mixed precisions, a handle listed twice),
+ * the errors of spand_factor (SPAND_ENOTSPD names the problem index), and of
+ * spand_pcg (SPAND_ENOCONV if any problem reached maxit; the others are
+ * still solved).  Stream-ordered; the calls synchronise the stream.
+ * --------------------------------------------------------------------------- */
+typedef struct spand_batch_s* spand_batch_t;
+
+/* handles: host array of count analysed handles. */
+int spand_batch_create(const spand_t* handles, int32_t count, spand_batch_t* out);
+int spand_batch_factor(spand_batch_t b, void* stream);
+/* b, x: host arrays of count DEVICE pointers (n_i doubles each); iters, relres:
+ * host arrays of count entries (NULL allowed); relres is the true residual. */
+int spand_batch_pcg(spand_batch_t b, const double* const* bvec, double* const* xvec, double tol,
+                    int32_t* iters, double* relres, void* stream);
+/* Wall time of the last factor and PCG calls, kernel launches of the last
+ * factorization, and host synchronisations (ticks) of the last PCG. */
+int spand_batch_info(spand_batch_t b, double* factor_ms, double* pcg_ms, int64_t* launches,
+                     int64_t* ticks);
+int spand_batch_set_profiling(spand_batch_t b, int on);
+int spand_batch_kernel_stats(spand_batch_t b, spand_kernel_stat* out, int cap, int* count);
+void spand_batch_destroy(spand_batch_t b);
 
 /* Frees every device and host resource of the handle.  NULL is ignored. */
 void spand_destroy(spand_t h);

@@ -114,13 +114,30 @@ __device__ __forceinline__ void share(cg::cluster_group& cl, int K, real_t* buf,
   for (int c = 0; c < K; ++c) cl.map_shared_rank(buf, c)[i] = val;
 }
 
+// The operator of global task index `task`: the item whose range holds it
+// (items are sorted by `first`), and the vector of that item's problem.
+__device__ __forceinline__ const void* item_op(const ApItem* __restrict__ items, int nitems,
+                                               int task, size_t op_bytes, int64_t* zoff) {
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].first <= task) lo = mid;
+    else hi = mid - 1;
+  }
+  const ApItem it = items[lo];
+  *zoff = it.zoff;
+  return (const char*)it.ops + (size_t)(task - it.first) * op_bytes;
+}
+
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_interior(const ApInterior* __restrict__ tasks, real_t* __restrict__ z, int forward) {
+    k_ap_interior(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
   __shared__ real_t red[kApThreads];
-  const ApInterior t = tasks[blockIdx.x / K];
+  int64_t zoff;
+  const ApInterior t = *(const ApInterior*)item_op(items, nitems, (int)(blockIdx.x / K), sizeof(ApInterior), &zoff);
+  z += zoff;
   const int m = t.m, nc = t.ncols;
   real_t* xs = sh;
   real_t* ys = sh + m;
@@ -155,12 +172,14 @@ __global__ void __launch_bounds__(kApThreads)
 }
 
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_scale(const ApScale* __restrict__ tasks, real_t* __restrict__ z, int forward) {
+    k_ap_scale(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
   __shared__ real_t red[kApThreads];
-  const ApScale t = tasks[blockIdx.x / K];
+  int64_t zoff;
+  const ApScale t = *(const ApScale*)item_op(items, nitems, (int)(blockIdx.x / K), sizeof(ApScale), &zoff);
+  z += zoff;
   const int m = t.m;
   real_t* xs = sh;
   for (int i = threadIdx.x; i < m; i += blockDim.x) xs[i] = z[t.slots[i]];
@@ -175,12 +194,14 @@ __global__ void __launch_bounds__(kApThreads)
 }
 
 __global__ void __launch_bounds__(kApThreads)
-    k_ap_qe(const ApQE* __restrict__ tasks, real_t* __restrict__ z, int forward) {
+    k_ap_qe(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
   __shared__ real_t red[kApThreads];
-  const ApQE t = tasks[blockIdx.x / K];
+  int64_t zoff;
+  const ApQE t = *(const ApQE*)item_op(items, nitems, (int)(blockIdx.x / K), sizeof(ApQE), &zoff);
+  z += zoff;
   const int m = t.m, nc = t.ncols, nE = t.nE;
   real_t* xs = sh;
   real_t* ys = sh + m;
@@ -230,9 +251,9 @@ void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s) {
   k_copy_real<<<std::max(1, std::min((n + 255) / 256, 152 * 16)), 256, 0, s>>>(n, src, dst);
 }
 
-template <class Task>
-static void launch_ap(void (*kern)(const Task*, real_t*, int), const Task* t, int ntasks, int K,
-                      int bytes, real_t* z, bool forward, cudaStream_t s) {
+static void launch_ap(void (*kern)(const ApItem*, int, real_t*, int), const ApItem* items,
+                      int nitems, int ntasks, int K, int bytes, real_t* z, bool forward,
+                      cudaStream_t s) {
   if (ntasks <= 0) return;
   smem_attr((const void*)kern, bytes);
   if (K > 8) cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -248,22 +269,25 @@ static void launch_ap(void (*kern)(const Task*, real_t*, int), const Task* t, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, t, z, forward ? 1 : 0);
+  cudaLaunchKernelEx(&cfg, kern, items, nitems, z, forward ? 1 : 0);
 }
 
-void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
-                        bool forward, cudaStream_t s) {
-  launch_ap(k_ap_interior, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
+void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,
+                        int max_cols, real_t* z, bool forward, cudaStream_t s) {
+  launch_ap(k_ap_interior, items, nitems, ntasks, K,
+            std::max(2 * max_m + max_cols, 1) * (int)sizeof(real_t), z, forward, s);
 }
 
-void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, real_t* z, bool forward,
-                     cudaStream_t s) {
-  launch_ap(k_ap_scale, t, ntasks, K, std::max(max_m, 1) * 8, z, forward, s);
+void launch_ap_scale(const ApItem* items, int nitems, int ntasks, int K, int max_m, real_t* z,
+                     bool forward, cudaStream_t s) {
+  launch_ap(k_ap_scale, items, nitems, ntasks, K, std::max(max_m, 1) * (int)sizeof(real_t), z,
+            forward, s);
 }
 
-void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, real_t* z, bool forward,
-                  cudaStream_t s) {
-  launch_ap(k_ap_qe, t, ntasks, K, std::max(2 * max_m + max_cols, 1) * 8, z, forward, s);
+void launch_ap_qe(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_cols,
+                  real_t* z, bool forward, cudaStream_t s) {
+  launch_ap(k_ap_qe, items, nitems, ntasks, K,
+            std::max(2 * max_m + max_cols, 1) * (int)sizeof(real_t), z, forward, s);
 }
 
 }  // namespace SPAND_NS

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -205,6 +206,7 @@ struct Phase {
   double flops, bytes;  // algorithmic, forward sweep (the backward one is the same)
   int max_cols = 0;     // widest neighbour gather
   int K = 1;            // CTAs per operator (thread-block cluster)
+  int stage = 0, colour = 0;  // position in the sweep: (stage, kind, colour) orders the phases
 };
 
 // CTAs per apply operator: enough that each handles about 12k FMAs.
@@ -248,6 +250,91 @@ void split_phase(std::vector<Phase>& phases, std::vector<T>& v, const Phase& ph,
   }
 }
 
+// CUDA-graph replay of the refactorization of one problem or of a batch of
+// problems factored together: one graph per stage (plus one for the work after
+// the last stage).  The graphs stay valid while every stage reproduces the
+// ranks they were built with and no problem of the group has been factored
+// another way since (its arena layout may then differ).
+struct FactorGroup {
+  struct StageGraph {
+    char* d_blob = nullptr;  // the stage's task tables (kept: the graph reads them)
+    size_t cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    // counters of the stage: problem index, offset and cluster count per problem
+    std::vector<int> who, ncl;
+    std::vector<size_t> ioff;
+    size_t nints = 0;
+    std::vector<int> expect;  // per problem: ranks then reflector counts at capture
+  };
+  std::vector<StageGraph> sg;
+  bool valid = false;
+  int prec = -1;
+  std::vector<uint64_t> layouts;  // layout_id of every problem when the graphs were built
+  DevBuf ints;                     // live counters of the running stage (device)
+  DevBuf tables;                   // task tables when not capturing
+  int* h_ints = nullptr;           // pinned readback of the counters
+  size_t h_cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  void drop() {
+    for (auto& g : sg) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    valid = false;
+  }
+  void release() {
+    drop();
+    for (auto& g : sg)
+      if (g.d_blob) cudaFree(g.d_blob);
+    sg.clear();
+    ints.release();
+    tables.release();
+    if (h_ints) cudaFreeHost(h_ints);
+    h_ints = nullptr;
+    h_cap = 0;
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+  }
+};
+
+// A merged preconditioner apply over several problems whose vectors sit in
+// one concatenated vector: problem i's operators act on z + zoff_i.  The
+// phases of all problems with the same (stage, kind, colour, cluster size)
+// become one launch; each problem's own phase order is kept.  The plan (and a
+// CUDA graph of it) is cached for the last set of problems and offsets.
+struct ApSeg {
+  spand_s* h;
+  int64_t zoff;
+};
+struct MultiApply {
+  std::vector<std::pair<const spand_s*, int64_t>> key;
+  std::vector<uint64_t> layouts;
+  struct Launch {
+    int kind, K, max_m, max_cols, nitems, ntasks;
+    size_t item0;
+    double flops, bytes;
+  };
+  std::vector<Launch> launches;  // forward order
+  DevBuf items;
+  cudaGraphExec_t exec = nullptr;
+  const void* gz = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  void drop() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    gz = nullptr;
+    key.clear();
+    layouts.clear();
+    launches.clear();
+  }
+  void release() {
+    drop();
+    items.release();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+  }
+};
+
 }  // namespace spand
 
 struct spand_s {
@@ -280,6 +367,7 @@ struct spand_s {
   void* d_api = nullptr;  // apply descriptors of the handle's precision
   void* d_aps = nullptr;
   void* d_apq = nullptr;
+  void* d_items = nullptr;  // one apply item per phase (the handle's own apply)
   int precision = 0;      // 0: FP64 factor and apply; 1: FP32 factor and apply (PCG stays FP64)
   float* d_rf = nullptr;  // FP32 copy of the vector an FP32 apply works on
   int64_t nnz_factor = 0;
@@ -294,33 +382,17 @@ struct spand_s {
   double pcg_ms = 0.0, pcg_relres = 0.0;
   int pcg_iters = 0;
   spand::Prof prof;
-  int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel
+  int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel; 2: clusters <= 8
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
-  // CUDA-graph replay of a refactorization: one graph per stage (plus one for
-  // the work after the last stage), valid while every stage reproduces the
-  // ranks it was built with; and one graph of the whole apply sweep.
-  struct StageGraph {
-    char* d_blob = nullptr;  // the stage's task tables (kept: the graph reads them)
-    size_t cap = 0;
-    cudaGraphExec_t exec = nullptr;
-    size_t o_rank = 0, o_nref = 0, o_flag = 0;
-    int ncl = 0;
-    std::vector<int> ranks, nrefs, flags;
-  };
-  std::vector<StageGraph> sgraph;
-  bool graph_valid = false;
-  int graph_prec = -1;
+  spand::FactorGroup fg;      // stage graphs of this problem factored on its own
+  uint64_t layout_id = 0;     // new value at every full factorization (arena layout changes)
   cudaStream_t cap_stream = nullptr;  // capture needs a stream other than the legacy one
   cudaGraphExec_t apply_exec = nullptr;
   bool no_graph = false;  // plain launches only (set by the allocation-free PCG)
   const void* apply_r = nullptr;
   void* apply_z = nullptr;
   void drop_graphs() {
-    for (auto& g : sgraph) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      g.exec = nullptr;
-    }
-    graph_valid = false;
+    fg.drop();
     if (apply_exec) cudaGraphExecDestroy(apply_exec);
     apply_exec = nullptr;
     apply_r = nullptr;
@@ -328,9 +400,7 @@ struct spand_s {
   }
   void free_graphs() {
     drop_graphs();
-    for (auto& g : sgraph)
-      if (g.d_blob) cudaFree(g.d_blob);
-    sgraph.clear();
+    fg.release();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
   }
@@ -340,10 +410,18 @@ namespace spand {
 int ensure_device(spand_s* h);  // first device use: upload A and the stage-0 pack map
 namespace f64 {
 int factor(spand_s* h, cudaStream_t s);
+// Factors count problems of this precision together: every kernel step of a
+// stage is one launch over the tasks of all problems.
+int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStream_t s);
 int apply(spand_s* h, const double* r, double* z, cudaStream_t s);
+int apply_multi(const ApSeg* segs, int nseg, double* z, MultiApply& M, Prof& P, bool graph,
+                cudaStream_t s);
 }  // namespace f64
 namespace f32 {
 int factor(spand_s* h, cudaStream_t s);
+int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStream_t s);
 int apply(spand_s* h, const float* r, float* z, cudaStream_t s);
+int apply_multi(const ApSeg* segs, int nseg, float* z, MultiApply& M, Prof& P, bool graph,
+                cudaStream_t s);
 }  // namespace f32
 }  // namespace spand

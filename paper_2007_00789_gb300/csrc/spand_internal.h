@@ -78,4 +78,45 @@ void launch_copy_vec(int n, const double* src, double* dst, cudaStream_t s);
 void launch_d2f(int n, const double* src, float* dst, cudaStream_t s);
 void launch_f2d(int n, const float* src, double* dst, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Segmented FP64 vector kernels (spand_pcg.cu): the PCG of many independent
+// problems (or right-hand sides) whose vectors are concatenated.  A segment
+// is one vector; a chunk is a range of at most kSegChunk entries inside one
+// segment, at a fixed offset from the segment start; each kernel runs one CTA
+// per chunk of the list it is given.  Per-segment scalars live in
+// sc[kSegScal * seg + j]: j = 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb.
+// ---------------------------------------------------------------------------
+constexpr int kSegChunk = 4096;
+constexpr int kSegScal = 8;
+struct VSeg {
+  const int32_t* rowptr;  // the segment's matrix (CSR, device)
+  const int32_t* colind;
+  const double* val;
+  int64_t off;            // first entry of the segment in the concatenated vectors
+  int n, pad;
+};
+struct VChunk {
+  int64_t begin, end;     // absolute positions, inside one segment
+  int seg, mode;          // mode: per-kernel flag (step_p: 1 = restart the direction)
+};
+struct VSegRef {          // one segment of a list: its chunks in that list
+  int seg, chunk0, nchunks, pad;
+};
+void launch_seg_spmv(const VChunk* ch, int nch, const VSeg* segs, const double* x, double* y,
+                     cudaStream_t s);
+void launch_seg_dot(const VChunk* ch, int nch, const VSegRef* refs, int nref, const double* x,
+                    const double* y, double* partial, double* sc, int slot, cudaStream_t s);
+void launch_seg_init(const VChunk* ch, int nch, const double* b, double* x, double* r,
+                     cudaStream_t s);
+void launch_seg_step_x(const VChunk* ch, int nch, const double* sc, const double* p,
+                       const double* q, double* x, double* r, cudaStream_t s);
+// p update per chunk mode, then rz <- rz_new for the listed segments
+void launch_seg_step_p(const VChunk* ch, int nch, const VSegRef* refs, int nref, double* sc,
+                       const double* z, double* p, cudaStream_t s);
+void launch_seg_residual(const VChunk* ch, int nch, const double* b, const double* ax, double* r,
+                         cudaStream_t s);
+void launch_seg_copy(const VChunk* ch, int nch, const double* src, double* dst, cudaStream_t s);
+void launch_seg_d2f(const VChunk* ch, int nch, const double* src, float* dst, cudaStream_t s);
+void launch_seg_f2d(const VChunk* ch, int nch, const float* src, double* dst, cudaStream_t s);
+
 }  // namespace spand

@@ -101,7 +101,7 @@ __device__ void potrf_body(real_t* a, int m, int ld, int id, int* err, real_t* s
   }
 }
 
-__global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_cap) {
+__global__ void k_potrf(const PotrfTask* __restrict__ tasks, int smem_cap) {
   extern __shared__ real_t sm[];
   __shared__ real_t s_inv;
   __shared__ int s_fail;
@@ -116,7 +116,7 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_
       sm[e] = (i >= j) ? t.a[i + (size_t)j * t.ld] : 0.0;
     }
     __syncthreads();
-    potrf_body(sm, m, m, t.id, err, &s_inv, &s_fail);
+    potrf_body(sm, m, m, t.id, t.err, &s_inv, &s_fail);
     __syncthreads();
     if (s_fail) return;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
@@ -124,7 +124,7 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int* err, int smem_
       t.a[i + (size_t)j * t.ld] = sm[e];
     }
   } else {
-    potrf_body(t.a, m, t.ld, t.id, err, &s_inv, &s_fail);
+    potrf_body(t.a, m, t.ld, t.id, t.err, &s_inv, &s_fail);
     __syncthreads();
     if (s_fail) return;
     // zero the strict upper triangle so the block is exactly L
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
 // recomputed at every step, ties to the lowest column; step t is taken while
 // nu_t^2 >= eps^2 nu_0^2 (the superfine scheme continues to eps^4 nu_0^2).
 // Afterwards the coarse rows are mirrored into the neighbours' rows, the
-// diagonal block becomes I_r and cur_size[p] = r.
+// diagonal block becomes I_r and t.cur[p] = r.
 // ---------------------------------------------------------------------------
 constexpr int kQrThreads = 256;
 
@@ -387,9 +387,7 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
 }
 
 __global__ void __launch_bounds__(kQrThreads)
-    k_rrqr(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
-           int* __restrict__ cur_size, int* __restrict__ rank_out, int* __restrict__ nref_out,
-           int* __restrict__ flag_out, double eps, int scheme) {
+    k_rrqr(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs) {
   extern __shared__ real_t sm[];
   __shared__ ArgMax s_red[kQrThreads / kWarp];
   __shared__ double s_sec[kQrThreads / kWarp];
@@ -406,7 +404,7 @@ __global__ void __launch_bounds__(kQrThreads)
     int acc = 0;
     for (int s = 0; s < nseg; ++s) {
       segoff[s] = acc;
-      acc += cur_size[segs[t.seg_begin + s].cl];
+      acc += t.cur[segs[t.seg_begin + s].cl];
     }
     segoff[nseg] = acc;
   }
@@ -426,6 +424,8 @@ __global__ void __launch_bounds__(kQrThreads)
     if (lane == 0) norms[c] = s;
   }
   __syncthreads();
+  const double eps = t.eps;
+  const int scheme = t.scheme;
   const double thr1 = eps * eps;
   const double thr2 = thr1 * thr1;
   const int maxsteps = min(m, N);
@@ -554,9 +554,9 @@ __global__ void __launch_bounds__(kQrThreads)
   }
   if (r < 0) r = nsteps;
   if (tid == 0) {
-    rank_out[t.id] = r;
-    nref_out[t.id] = nsteps;
-    flag_out[t.id] = flags;
+    t.rank[t.id] = r;
+    t.nref[t.id] = nsteps;
+    t.flag[t.id] = flags;
   }
   __syncthreads();
   // coarse rows -> neighbours' rows (transposed), diagonal block -> I_r
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kQrThreads)
     t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (tid == 0) cur_size[t.id] = r;
+  if (tid == 0) t.cur[t.id] = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -636,8 +636,6 @@ __device__ __forceinline__ QrSlot warp_merge(QrSlot mine) {
 // into every CTA's shared memory.
 __global__ void __launch_bounds__(kQrThreads)
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
-                   int* __restrict__ cur_size, int* __restrict__ rank_out,
-                   int* __restrict__ nref_out, int* __restrict__ flag_out, double eps, int scheme,
                    int csize) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
@@ -665,7 +663,7 @@ __global__ void __launch_bounds__(kQrThreads)
     int acc = 0;
     for (int g = 0; g < nseg; ++g) {
       segoff[g] = acc;
-      acc += cur_size[segs[t.seg_begin + g].cl];
+      acc += t.cur[segs[t.seg_begin + g].cl];
     }
     segoff[nseg] = acc;
     s_N = acc;
@@ -712,6 +710,8 @@ __global__ void __launch_bounds__(kQrThreads)
       slot_merge(mine, c);
     }
   }
+  const double eps = t.eps;
+  const int scheme = t.scheme;
   const double thr1 = eps * eps;
   const double thr2 = thr1 * thr1;
   const int maxsteps = min(m, N);
@@ -862,10 +862,10 @@ __global__ void __launch_bounds__(kQrThreads)
       t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
     }
     if (tid == 0) {
-      rank_out[t.id] = r;
-      nref_out[t.id] = nsteps;
-      cur_size[t.id] = r;
-      flag_out[t.id] = flags;
+      t.rank[t.id] = r;
+      t.nref[t.id] = nsteps;
+      t.cur[t.id] = r;
+      t.flag[t.id] = flags;
     }
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
@@ -897,7 +897,7 @@ void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s) {
   if (ntasks > 0) k_set_identity<<<ntasks, 256, 0, s>>>(t);
 }
 
-void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s) {
+void launch_potrf(const PotrfTask* t, int ntasks, int max_m, cudaStream_t s) {
   if (ntasks <= 0) return;
   int cap = max_m * max_m;
   int bytes = cap * (int)sizeof(real_t);
@@ -906,7 +906,7 @@ void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStrea
     bytes = kSmemBudget;
   }
   set_smem((const void*)k_potrf, bytes);
-  k_potrf<<<ntasks, 256, bytes, s>>>(t, err, cap);
+  k_potrf<<<ntasks, 256, bytes, s>>>(t, cap);
 }
 
 void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s) {
@@ -945,9 +945,8 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
   return (int)std::min<long>(b, 1L << 30);
 }
 
-void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
-                         int csize, int smem_bytes, cudaStream_t s) {
+void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
+                         int smem_bytes, cudaStream_t s) {
   if (ntasks <= 0) return;
   cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem_bytes);
@@ -965,8 +964,7 @@ void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, cur_size, rank_out, nref_out, flag_out, eps,
-                     scheme, csize);
+  cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, csize);
 }
 
 int rrqr_cluster_active(int csize, int smem_bytes) {
@@ -999,14 +997,12 @@ int rrqr_smem_bytes(int max_m, int max_cols, int max_segs) {
          (max_segs + 2) * 4 + 16;
 }
 
-void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                 int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
-                 int max_cols, int max_segs, cudaStream_t s) {
+void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs,
+                 int max_m, int max_cols, int max_segs, cudaStream_t s) {
   if (ntasks <= 0) return;
   const int bytes = rrqr_smem_bytes(max_m, max_cols, max_segs);
   set_smem((const void*)k_rrqr, bytes);
-  k_rrqr<<<ntasks, kQrThreads, bytes, s>>>(t, segs, cur_size, rank_out, nref_out, flag_out, eps,
-                                            scheme);
+  k_rrqr<<<ntasks, kQrThreads, bytes, s>>>(t, segs);
 }
 
 }  // namespace SPAND_NS

@@ -106,6 +106,114 @@ __global__ void k_f2d(int n, const float* __restrict__ s, double* __restrict__ d
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = (double)s[i];
 }
 
+// ---- segmented kernels: many independent vectors in one concatenated array.
+// Each CTA works on one chunk (a range inside one segment); chunk boundaries
+// are fixed relative to the segment start and every reduction has a fixed
+// order, so a segment's results do not depend on the other segments.
+constexpr int kSegThreads = 256;
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_spmv(const VChunk* __restrict__ ch, const VSeg* __restrict__ segs,
+               const double* __restrict__ x, double* __restrict__ y) {
+  const VChunk c = ch[blockIdx.x];
+  const VSeg g = segs[c.seg];
+  const double* xs = x + g.off;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) {
+    const int il = (int)(i - g.off);
+    double s = 0.0;
+    for (int e = g.rowptr[il]; e < g.rowptr[il + 1]; ++e) s += g.val[e] * xs[g.colind[e]];
+    y[i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_dot(const VChunk* __restrict__ ch, const double* __restrict__ x,
+              const double* __restrict__ y, double* __restrict__ partial) {
+  __shared__ double red[32];
+  const VChunk c = ch[blockIdx.x];
+  double s = 0.0;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) s += x[i] * y[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// One thread per segment of the list: the sum of its chunks' partials, in order.
+__global__ void k_seg_dot_final(const VSegRef* __restrict__ refs, int nref,
+                                const double* __restrict__ partial, double* __restrict__ sc,
+                                int slot) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nref) return;
+  const VSegRef r = refs[j];
+  double s = 0.0;
+  for (int c = 0; c < r.nchunks; ++c) s += partial[r.chunk0 + c];
+  sc[kSegScal * r.seg + slot] = s;
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_init(const VChunk* __restrict__ ch, const double* __restrict__ b, double* __restrict__ x,
+               double* __restrict__ r) {
+  const VChunk c = ch[blockIdx.x];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) {
+    x[i] = 0.0;
+    r[i] = b[i];
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_step_x(const VChunk* __restrict__ ch, const double* __restrict__ sc,
+                 const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                 double* __restrict__ r) {
+  const VChunk c = ch[blockIdx.x];
+  const double alpha = sc[kSegScal * c.seg + 0] / sc[kSegScal * c.seg + 1];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// mode (c.mode) 0: p = z + (rz_new / rz) p; 1: p = z (start or restart)
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_step_p(const VChunk* __restrict__ ch, const double* __restrict__ sc,
+                 const double* __restrict__ z, double* __restrict__ p) {
+  const VChunk c = ch[blockIdx.x];
+  if (c.mode == 1) {
+    for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) p[i] = z[i];
+  } else {
+    const double beta = sc[kSegScal * c.seg + 2] / sc[kSegScal * c.seg + 0];
+    for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) p[i] = z[i] + beta * p[i];
+  }
+}
+
+__global__ void k_seg_rz(const VSegRef* __restrict__ refs, int nref, double* __restrict__ sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nref) sc[kSegScal * refs[j].seg + 0] = sc[kSegScal * refs[j].seg + 2];
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_residual(const VChunk* __restrict__ ch, const double* __restrict__ b,
+                   const double* __restrict__ ax, double* __restrict__ r) {
+  const VChunk c = ch[blockIdx.x];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) r[i] = b[i] - ax[i];
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_copy(const VChunk* __restrict__ ch, const double* __restrict__ s, double* __restrict__ d) {
+  const VChunk c = ch[blockIdx.x];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = s[i];
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_d2f(const VChunk* __restrict__ ch, const double* __restrict__ s, float* __restrict__ d) {
+  const VChunk c = ch[blockIdx.x];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = (float)s[i];
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_f2d(const VChunk* __restrict__ ch, const float* __restrict__ s, double* __restrict__ d) {
+  const VChunk c = ch[blockIdx.x];
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = (double)s[i];
+}
+
 }  // namespace
 
 void launch_spmv(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
@@ -149,6 +257,44 @@ void launch_d2f(int n, const double* src, float* dst, cudaStream_t s) {
 }
 void launch_f2d(int n, const float* src, double* dst, cudaStream_t s) {
   k_f2d<<<vec_blocks(n), 256, 0, s>>>(n, src, dst);
+}
+
+void launch_seg_spmv(const VChunk* ch, int nch, const VSeg* segs, const double* x, double* y,
+                     cudaStream_t s) {
+  if (nch > 0) k_seg_spmv<<<nch, kSegThreads, 0, s>>>(ch, segs, x, y);
+}
+void launch_seg_dot(const VChunk* ch, int nch, const VSegRef* refs, int nref, const double* x,
+                    const double* y, double* partial, double* sc, int slot, cudaStream_t s) {
+  if (nch <= 0 || nref <= 0) return;
+  k_seg_dot<<<nch, kSegThreads, 0, s>>>(ch, x, y, partial);
+  k_seg_dot_final<<<(nref + 127) / 128, 128, 0, s>>>(refs, nref, partial, sc, slot);
+}
+void launch_seg_init(const VChunk* ch, int nch, const double* b, double* x, double* r,
+                     cudaStream_t s) {
+  if (nch > 0) k_seg_init<<<nch, kSegThreads, 0, s>>>(ch, b, x, r);
+}
+void launch_seg_step_x(const VChunk* ch, int nch, const double* sc, const double* p,
+                       const double* q, double* x, double* r, cudaStream_t s) {
+  if (nch > 0) k_seg_step_x<<<nch, kSegThreads, 0, s>>>(ch, sc, p, q, x, r);
+}
+void launch_seg_step_p(const VChunk* ch, int nch, const VSegRef* refs, int nref, double* sc,
+                       const double* z, double* p, cudaStream_t s) {
+  if (nch <= 0) return;
+  k_seg_step_p<<<nch, kSegThreads, 0, s>>>(ch, sc, z, p);
+  k_seg_rz<<<(nref + 127) / 128, 128, 0, s>>>(refs, nref, sc);
+}
+void launch_seg_residual(const VChunk* ch, int nch, const double* b, const double* ax, double* r,
+                         cudaStream_t s) {
+  if (nch > 0) k_seg_residual<<<nch, kSegThreads, 0, s>>>(ch, b, ax, r);
+}
+void launch_seg_copy(const VChunk* ch, int nch, const double* src, double* dst, cudaStream_t s) {
+  if (nch > 0) k_seg_copy<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
+}
+void launch_seg_d2f(const VChunk* ch, int nch, const double* src, float* dst, cudaStream_t s) {
+  if (nch > 0) k_seg_d2f<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
+}
+void launch_seg_f2d(const VChunk* ch, int nch, const float* src, double* dst, cudaStream_t s) {
+  if (nch > 0) k_seg_f2d<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
 }
 
 }  // namespace spand

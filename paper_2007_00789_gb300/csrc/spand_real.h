@@ -32,9 +32,11 @@ struct CopyTask {
   int src_ld, dst_ld, rows, cols, trans, pad;
 };
 
-// In-place lower Cholesky of an m x m column-major block (ld), id for errors.
+// In-place lower Cholesky of an m x m column-major block (ld).  A non-positive
+// pivot stores id + 1 in *err (the first failure wins).
 struct PotrfTask {
   real_t* a;
+  int* err;
   int m, ld, id, pad;
 };
 
@@ -88,7 +90,13 @@ struct RRQRTask {
   real_t* diag;    // origin of the diagonal segment (set to I_r afterwards)
   real_t* V;       // reflectors, m x maxref, ld m
   real_t* tau;     // maxref
-  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max;
+  int* cur;        // live width of every cluster of the problem (read, and cur[id] = r)
+  int* rank;       // outputs, indexed by cluster id: rank r, reflectors taken, near-tie flags
+  int* nref;
+  int* flag;
+  double eps;      // relative tolerance of the problem (Algorithm 1)
+  int scheme;      // SPAND_FIRST_ORDER, SPAND_SECOND_ORDER_FULL or SPAND_SECOND_ORDER_SUPERFINE
+  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max, pad;
 };
 
 // Preconditioner apply descriptors.  The triangular factors and Q_p are
@@ -114,6 +122,16 @@ struct ApQE {
   int m, r, nE, ncols;
 };
 
+// A run of `count` operators of one problem (descriptors at ops, of the
+// launch's kind) applied to the vector z + zoff; in a launch the items are
+// sorted by `first`, the launch-wide index of their first operator.  One
+// launch can so cover the operators of several problems.
+struct ApItem {
+  const void* ops;
+  int64_t zoff;
+  int count, first;
+};
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (spand_kernels.cu / spand_apply.cu).
 // ---------------------------------------------------------------------------
@@ -121,7 +139,7 @@ void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s);
 // base_lo[d] = val[e] for 0 <= d < split, base_hi[d - split] for d >= split, skip d < 0.
 void launch_scatter(const double* val, const int64_t* dst_index, real_t* base_lo,
                     real_t* base_hi, int64_t split, int64_t nnz, cudaStream_t s);
-void launch_potrf(const PotrfTask* t, int ntasks, int max_m, int* err, cudaStream_t s);
+void launch_potrf(const PotrfTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s);
 void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s);
@@ -132,20 +150,19 @@ int rrqr_smem_bytes(int max_m, int max_cols, int max_segs);
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
 // Clusters of this shape that can be resident at once (0: cannot be launched).
 int rrqr_cluster_active(int csize, int smem_bytes);
-void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                         int* rank_out, int* nref_out, int* flag_out, double eps, int scheme,
-                         int csize, int smem_bytes, cudaStream_t s);
-void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int* cur_size,
-                 int* rank_out, int* nref_out, int* flag_out, double eps, int scheme, int max_m,
-                 int max_cols, int max_segs, cudaStream_t s);
+void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
+                         int smem_bytes, cudaStream_t s);
+void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, int max_cols,
+                 int max_segs, cudaStream_t s);
 
-// K: CTAs per operator (a thread-block cluster), 1..16.
-void launch_ap_interior(const ApInterior* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
-                        bool forward, cudaStream_t s);
-void launch_ap_scale(const ApScale* t, int ntasks, int K, int max_m, real_t* z, bool forward,
-                     cudaStream_t s);
-void launch_ap_qe(const ApQE* t, int ntasks, int K, int max_m, int max_cols, real_t* z,
-                  bool forward, cudaStream_t s);
+// K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
+// over all nitems items (device array).
+void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,
+                        int max_cols, real_t* z, bool forward, cudaStream_t s);
+void launch_ap_scale(const ApItem* items, int nitems, int ntasks, int K, int max_m, real_t* z,
+                     bool forward, cudaStream_t s);
+void launch_ap_qe(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_cols,
+                  real_t* z, bool forward, cudaStream_t s);
 
 
 }  // namespace SPAND_NS

@@ -27,8 +27,11 @@ EXPORTS = [
     "spand_analyze", "spand_factor", "spand_apply", "spand_pcg", "spand_pcg_host",
     "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
     "spand_pcg_noalloc", "spand_set_profiling", "spand_kernel_stats",
+    "spand_batch_create", "spand_batch_factor", "spand_batch_pcg", "spand_batch_info",
+    "spand_batch_set_profiling", "spand_batch_kernel_stats", "spand_batch_destroy",
     "spand_destroy", "spand_strerror", "spand_last_error",
 ]
+_VOID = ("spand_destroy", "spand_batch_destroy", "spand_strerror", "spand_last_error")
 
 
 class SpandError(RuntimeError):
@@ -45,7 +48,8 @@ class _CSR(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("skip", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
-                ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("plain_launches", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -90,6 +94,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_num_clusters.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
     L.spand_set_profiling.argtypes = [vp, ctypes.c_int]
     L.spand_kernel_stats.argtypes = [vp, ctypes.POINTER(_KStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.spand_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+    L.spand_batch_factor.argtypes = [vp, vp]
+    L.spand_batch_pcg.argtypes = [vp, vp, vp, f64, vp, vp, vp]
+    L.spand_batch_info.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(f64),
+                                   ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.spand_batch_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.spand_batch_kernel_stats.argtypes = [vp, ctypes.POINTER(_KStat), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
+    L.spand_batch_destroy.argtypes = [vp]
+    L.spand_batch_destroy.restype = None
     L.spand_destroy.argtypes = [vp]
     L.spand_destroy.restype = None
     L.spand_strerror.argtypes = [ctypes.c_int]
@@ -97,7 +111,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_last_error.argtypes = []
     L.spand_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("spand_destroy", "spand_strerror", "spand_last_error"):
+        if name not in _VOID:
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -131,7 +145,8 @@ class Spand:
 
     def __init__(self, rowptr, colind, val, coords, nlevels: int, eps: float, scheme: int = 1,
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
-                 max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0):
+                 max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0,
+                 plain_launches: bool = False):
         L = load_library()
         self._lib = L
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
@@ -147,7 +162,7 @@ class Spand:
         opts = _Opts(-1 if skip is None else int(skip), 0 if maxit is None else int(maxit),
                      0 if true_res_every is None else int(true_res_every),
                      -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
-                     int(precision))
+                     int(precision), 1 if plain_launches else 0)
         h = ctypes.c_void_p()
         _check(L.spand_analyze(ctypes.byref(csr), coords.ctypes.data, coords.shape[1], int(nlevels),
                                float(eps), int(scheme), ctypes.byref(opts), ctypes.byref(h)))
@@ -237,3 +252,68 @@ class Spand:
         out = np.empty(self.n, dtype=np.int32)
         _check(self._lib.spand_cluster_map(self._h, int(stage), out.ctypes.data))
         return out
+
+
+def _kstats(fn, h) -> list[dict]:
+    arr = (_KStat * 64)()
+    cnt = ctypes.c_int()
+    _check(fn(h, arr, 64, ctypes.byref(cnt)))
+    return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches),
+             "total_ms": float(arr[i].total_ms), "flops": float(arr[i].flops),
+             "bytes": float(arr[i].bytes)} for i in range(cnt.value)]
+
+
+class SpandBatch:
+    """Independent problems factored and solved together (spand_batch_*).
+
+    The member ``Spand`` objects must stay open while the batch exists."""
+
+    def __init__(self, members):
+        self._lib = load_library()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        h = ctypes.c_void_p()
+        _check(self._lib.spand_batch_create(arr, len(self.members), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.spand_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self, stream=None):
+        _check(self._lib.spand_batch_factor(self._h, _stream_ptr(stream)))
+
+    def pcg(self, bs, xs, tol: float, stream=None, allow_noconv: bool = False):
+        """bs, xs: lists of float64 CUDA tensors; returns (iterations, true relative residuals)."""
+        k = len(self.members)
+        if len(bs) != k or len(xs) != k:
+            raise ValueError("one right-hand side and one solution vector per member")
+        bp = (ctypes.c_void_p * k)(*[_dptr(b) for b in bs])
+        xp = (ctypes.c_void_p * k)(*[_dptr(x) for x in xs])
+        it = np.zeros(k, dtype=np.int32)
+        rel = np.zeros(k, dtype=np.float64)
+        _check(self._lib.spand_batch_pcg(self._h, bp, xp, float(tol), it.ctypes.data,
+                                         rel.ctypes.data, _stream_ptr(stream)),
+               allow=(SPAND_ENOCONV,) if allow_noconv else ())
+        return it, rel
+
+    def info(self) -> dict:
+        fm, pm = ctypes.c_double(), ctypes.c_double()
+        nl, nt = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.spand_batch_info(self._h, ctypes.byref(fm), ctypes.byref(pm),
+                                          ctypes.byref(nl), ctypes.byref(nt)))
+        return {"factor_ms": fm.value, "pcg_ms": pm.value, "launches": int(nl.value),
+                "ticks": int(nt.value)}
+
+    def set_profiling(self, on: bool):
+        _check(self._lib.spand_batch_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self) -> list[dict]:
+        return _kstats(self._lib.spand_batch_kernel_stats, self._h)

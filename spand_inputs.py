@@ -210,3 +210,30 @@ WORKLOADS = {
     "diffusion3d_128": dict(problem=lambda: diffusion_3d(128, seed=0), nlevels=15, eps=1e-2,
                             rhs=lambda n: rhs_normal(n, seed=1)),
 }
+
+
+def paper_nlevels(n: int) -> int:
+    """The paper's depth rule for leaves of about 25 unknowns: round(log2(n / 25)) (§4)."""
+    return max(2, int(np.round(np.log2(n / 25.0))))
+
+
+def batch_workload(count: int = 64, lo: float = -2.0, hi: float = 2.0):
+    """Independent SPD problems of uneven sizes: even i a 2D 5-point FV grid with
+    side 128 .. 512, odd i a 3D 7-point FV grid with side 24 .. 48 (sides spread
+    evenly over the problems of each kind), coefficients a = 10**U(lo, hi) per
+    cell from seed i, RHS N(0, 1) from seed 1000 + i, depth by the paper's rule.
+
+    Returns a list of (problem, nlevels, rhs)."""
+    n2 = (count + 1) // 2
+    n3 = count // 2
+    out = []
+    for i in range(count):
+        j = i // 2
+        if i % 2 == 0:
+            d = 128 + int(round(384 * j / max(n2 - 1, 1)))
+            prob = diffusion_grid((d, d), seed=i, lo=lo, hi=hi)
+        else:
+            d = 24 + int(round(24 * j / max(n3 - 1, 1)))
+            prob = diffusion_grid((d, d, d), seed=i, lo=lo, hi=hi)
+        out.append((prob, paper_nlevels(prob.n), rhs_normal(prob.n, seed=1000 + i)))
+    return out

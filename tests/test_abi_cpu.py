@@ -95,3 +95,21 @@ def test_factor_before_gpu_is_refused_cleanly():
         h.factor(stream=0)
     assert e.value.code in (S.SPAND_ECUDA, S.SPAND_ENOMEM)
     assert h.info()["n"] == 64
+
+
+def test_batch_arguments_checked_without_gpu():
+    """Batch creation is host-only: bad member lists are refused with EINVAL."""
+    from paper_2007_00789_gb300 import spand as S
+    p = si.laplacian_2d(8)
+    a = S.Spand.from_problem(p, 3, 1e-2, 1)
+    b = S.Spand.from_problem(p, 3, 1e-2, 1, precision=1)
+    with pytest.raises(S.SpandError) as e:
+        S.SpandBatch([a, a])
+    assert e.value.code == S.SPAND_EINVAL
+    with pytest.raises(S.SpandError) as e:
+        S.SpandBatch([a, b])
+    assert e.value.code == S.SPAND_EINVAL
+    batch = S.SpandBatch([a])
+    batch.close()
+    a.close()
+    b.close()
