@@ -40,6 +40,12 @@ METRIC = "factor+PCG time to rel. residual 1e-12, CG its; served solves/s, p99 l
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (the profiling recipe's figure); no measured FP64 peak is provided
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 152 SMs x 2070 MHz x 128 FP32 FMA/clk/SM
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
+# capture of this bench's command (profiles/launches_poisson3d_64_fp64.txt):
+# (workload, precision, kernel kind) -> bytes per launch.  Only valid for the
+# kernel version that was captured; absent entries report null.
+TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 18.63e6}
+
 WORKLOADS = {
     # name: (factory, dim, ell, rhs)
     "poisson3d_64": ("laplacian_3d(64)", 12, "rhs_normal"),
@@ -167,12 +173,21 @@ def run_batch(args, rank, world, local, dist):
     import spand_inputs as si
     from paper_2007_00789_gb300 import spand
 
+    import concurrent.futures as cf
+
     tol = 1e-12
     work = si.batch_workload(64)
     stream = torch.cuda.current_stream()
-    hs = [spand.Spand.from_problem(p, ell, args.eps, args.scheme, precision=args.precision,
-                                   rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches)
-          for p, ell, _ in work]
+
+    def analyze_all(plain):
+        # the host analyses are independent: one thread per problem (the C call releases the GIL)
+        with cf.ThreadPoolExecutor(16) as ex:
+            return list(ex.map(lambda w: spand.Spand.from_problem(
+                w[0], w[1], args.eps, args.scheme, precision=args.precision,
+                rrqr_kernel=args.rrqr_kernel, plain_launches=plain,
+                rrqr_threads=args.rrqr_threads), work))
+
+    hs = analyze_all(args.plain_launches)
     batch = spand.SpandBatch(hs)
     bs = [torch.from_numpy(b).cuda() for _, _, b in work]
     xs = [torch.zeros_like(b) for b in bs]
@@ -218,8 +233,7 @@ def run_batch(args, rank, world, local, dist):
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        he = [spand.Spand.from_problem(p, ell, args.eps, args.scheme, precision=args.precision,
-                                       rrqr_kernel=args.rrqr_kernel) for p, ell, _ in work]
+        he = analyze_all(False)
         be = spand.SpandBatch(he)
         be.factor(stream)
         pin = [torch.from_numpy(b).pin_memory() for _, _, b in work]
@@ -235,7 +249,7 @@ def run_batch(args, rank, world, local, dist):
         h2d = sum(4 * (p.n + 1) + 12 * p.nnz + 8 * p.n for p, _, _ in work)
         d2h = sum(8 * p.n for p, _, _ in work)
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "includes": "host analysis of all 64 problems"}
+               "includes": "host analysis of all 64 problems (16 threads)"}
     dom = max(kstats, key=lambda k: k["total_ms"])
     achieved = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["total_ms"] > 0 else 0.0
     peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
@@ -279,13 +293,97 @@ def run_batch(args, rank, world, local, dist):
         dist.destroy_process_group()
 
 
+def run_serve(args, rank, world, local, dist):
+    """Serving trace: a resident 96^3 diffusion problem plus new problems of
+    n = 16k..500k arriving with a Poisson process of requests of 1..32
+    right-hand sides; PCG to 1e-10.  Reports solves/s and request latency."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    import torch
+
+    import spand_inputs as si
+    from paper_2007_00789_gb300 import spand
+
+    tol = 1e-10
+    probs, trace = si.serve_workload()
+    max_n = max(p.n for p, _ in probs)
+    srv = spand.SpandServer(precision=args.precision, tol=tol, max_segments=512,
+                            max_entries=6 * 32 * ((max_n + 31) // 32 * 32))
+    # analysis (host) of every problem happens before the trace starts
+    with cf.ThreadPoolExecutor(16) as ex:
+        hs = list(ex.map(lambda pe: spand.Spand.from_problem(pe[0], pe[1], args.eps, args.scheme,
+                                                             precision=args.precision), probs))
+    mids = [srv.add(h, pinned=(i == 0)) for i, h in enumerate(hs)]
+    # warm-up: the resident problem is factored and one request solved
+    rng0 = np.random.default_rng(1)
+    srv.wait(srv.submit(mids[0], rng0.standard_normal((1, probs[0][0].n))))
+    rhs = {k: np.random.default_rng(sd).standard_normal((nr, probs[pi][0].n))
+           for k, (_, pi, nr, sd) in enumerate(trace)}
+    results = [None] * len(trace)
+    start = time.perf_counter()
+
+    def waiter(k, rid):
+        results[k] = srv.wait(rid)
+
+    with ClockSampler(local) as clk, cf.ThreadPoolExecutor(64) as pool:
+        futs = []
+        for k, (t, pi, nr, _) in enumerate(trace):
+            dt = start + t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            futs.append(pool.submit(waiter, k, srv.submit(mids[pi], rhs[k])))
+        for fu in futs:
+            fu.result()
+    wall = time.perf_counter() - start
+    st = srv.stats()
+    worst = 0.0
+    for k, (_, pi, nr, _) in enumerate(trace):
+        x, it, rel, lat = results[k]
+        A = probs[pi][0].to_scipy()
+        b = rhs[k]
+        worst = max(worst, max(np.linalg.norm(b[j] - A @ x[j]) / np.linalg.norm(b[j])
+                               for j in range(nr)))
+    lat = np.array([results[k][3] for k in range(len(trace))])
+    solves = sum(nr for _, _, nr, _ in trace)
+    iters = np.concatenate([results[k][1] for k in range(len(trace))])
+    h2d = sum(8 * nr * probs[pi][0].n for _, pi, nr, _ in trace)
+    line = {
+        "metric": METRIC, "value": solves / wall, "unit": "solves/s", "n_gpus": world,
+        "steps": len(trace), "warmup": 1, "ms_per_step": wall * 1e3 / len(trace),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f32 factor/apply + f64 pcg",
+        "data": "synthetic",
+        "config": {"workload": "serve", "resident": "diffusion_3d(96), a=10^U(-3,3)",
+                   "new_problems": len(probs) - 1, "requests": len(trace), "solves": solves,
+                   "arrival_rate_per_s": 20.0, "nrhs": "1..32", "tol": tol,
+                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "max_ms": float(lat.max()), "wall_s": wall, "cg_iters_max": int(iters.max()),
+                   "cg_iters_mean": float(iters.mean()), "true_relres_max_host": worst,
+                   "server": {k: st[k] for k in ("ticks", "max_inflight", "resident_problems",
+                                                 "resident_bytes", "solves_per_s")},
+                   "timing": "host wall clock from first submission (requests' b and x in host"
+                             " memory, copies and factorizations of new problems included)"},
+        "clocks": clk.summary(),
+        "e2e": {"value": solves / wall, "unit": "solves/s", "h2d_bytes_per_step": h2d // len(trace),
+                "d2h_bytes_per_step": h2d // len(trace)},
+        "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    srv.close()
+    for h in hs:
+        h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="spand", choices=["spand", "reference"])
-    ap.add_argument("--workload", default="poisson3d_64", choices=sorted(WORKLOADS) + ["batch64"],
+    ap.add_argument("--workload", default="poisson3d_64",
+                    choices=sorted(WORKLOADS) + ["batch64", "serve"],
                     help="batch64: 64 independent 2D/3D diffusion problems factored and solved"
                          " as one batch (FP32 factor by default)")
     ap.add_argument("--scheme", type=int, default=1)
@@ -298,13 +396,15 @@ def main():
                     help="skip timing the other precision")
     ap.add_argument("--plain-launches", action="store_true",
                     help="no CUDA graphs: every kernel launched on its own (for profilers)")
+    ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512, 1024],
+                    help="threads per CTA of the on-chip RRQR (0: the library's choice)")
     ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="0: on-chip RRQR in clusters of up to 16 CTAs; 1: global-memory RRQR;"
                          " 2: on-chip RRQR in clusters of up to 8 CTAs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.precision is None:
-        args.precision = 1 if args.workload == "batch64" else 0
+        args.precision = 1 if args.workload in ("batch64", "serve") else 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,12 +427,16 @@ def main():
     if args.workload == "batch64":
         run_batch(args, rank, world, local, dist)
         return
+    if args.workload == "serve":
+        run_serve(args, rank, world, local, dist)
+        return
 
     prob, ell, b = make_problem(args.workload)
     tol = 1e-12
     stream = torch.cuda.current_stream()
     h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
-                                 rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches)
+                                 rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches,
+                                 rrqr_threads=args.rrqr_threads)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     iters = rel = None
@@ -383,7 +487,8 @@ def main():
             t0 = time.perf_counter()
             he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
                                           rrqr_kernel=args.rrqr_kernel,
-                                          plain_launches=args.plain_launches)
+                                          plain_launches=args.plain_launches,
+                                          rrqr_threads=args.rrqr_threads)
             he.factor(stream)
             x_host, it_e, rel_e = he.pcg_host(b, tol, stream)
             torch.cuda.synchronize()
@@ -400,7 +505,8 @@ def main():
         other = 1 - args.precision
         hv = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=other,
                                       rrqr_kernel=args.rrqr_kernel,
-                                      plain_launches=args.plain_launches)
+                                      plain_launches=args.plain_launches,
+                                      rrqr_threads=args.rrqr_threads)
         xv = torch.zeros_like(bd)
         for _ in range(args.warmup):
             hv.factor(stream)
@@ -424,9 +530,14 @@ def main():
     dom = max(kstats, key=lambda k: k["total_ms"])
     dom_launch_ms = dom["total_ms"] / max(dom["launches"], 1)
     achieved = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["total_ms"] > 0 else 0.0
-    roof = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "fallback (profiling recipe's nominal FP64 1.25 TFLOP/s; FP64 is not in the measured peaks)",
+    peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
+    roof = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, args.precision, dom["name"])),
+            "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+            "peak_source": ("fallback (profiling recipe's nominal FP64 1.25 TFLOP/s; FP64 is not in"
+                            " the measured peaks)") if args.precision == 0 else
+                           "derived: 152 SMs x 2070 MHz x 128 FP32 FMA/clk/SM",
             "avg_launch_ms": dom_launch_ms, "launches_per_step": dom["launches"] / args.steps,
             "measured": "per-launch CUDA events in a second pass of the same K steps (plain launches)"}
     launches = sum(k["launches"] for k in kstats) // args.steps
@@ -439,7 +550,8 @@ def main():
                    "eps": args.eps, "scheme": args.scheme, "tol": tol, "cg_iters": iters,
                    "relres": rel, "mu": info["mu"], "skip": info["skip"],
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
-                   "cuda_graphs": not args.plain_launches, "rrqr_kernel": args.rrqr_kernel},
+                   "cuda_graphs": not args.plain_launches, "rrqr_kernel": args.rrqr_kernel,
+                   "rrqr_threads": args.rrqr_threads},
         "clocks": clk.summary(),
         "variant": variant,
         "e2e": e2e,

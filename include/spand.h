@@ -77,6 +77,8 @@ typedef struct {
   int32_t plain_launches; /* 0 = replay refactorizations and applies from CUDA graphs (the
                              default); 1 = plain kernel launches only.  Same kernels, same
                              results; meant for profilers that cannot replay graph nodes. */
+  int32_t rrqr_threads;   /* threads per CTA of the on-chip RRQR: 256, 512 or 1024; 0 = the
+                             library's choice.  Changes only the order of some FP sums. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */
@@ -171,6 +173,19 @@ int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol,
 int spand_pcg_noalloc(spand_t h, const double* b, double* x, double tol, int32_t* iters,
                       double* relres, void* stream);
 
+/* Several right-hand sides at once (the block form of spand_apply and
+ * spand_pcg): column j of r, z, b, x starts at element j * ld (device arrays,
+ * ld >= n).  spand_apply_many computes z_j = M r_j for every column with one
+ * launch per apply phase over all columns (r == z allowed); spand_pcg_many
+ * runs the PCG of spand_pcg for every column, all columns advancing together
+ * (iters, relres: host arrays of nrhs entries, NULL allowed).  Results per
+ * column equal those of the single-column calls up to the order of the
+ * dot-product sums and the apply's atomic accumulation.  Errors as spand_apply
+ * and spand_pcg; SPAND_EINVAL for nrhs < 1 or ld < n. */
+int spand_apply_many(spand_t h, const double* r, double* z, int32_t nrhs, int64_t ld, void* stream);
+int spand_pcg_many(spand_t h, const double* b, double* x, int32_t nrhs, int64_t ld, double tol,
+                   int32_t* iters, double* relres, void* stream);
+
 /* y = A x with the uploaded A (device arrays of n doubles). */
 int spand_matvec(spand_t h, const double* x, double* y, void* stream);
 
@@ -256,6 +271,67 @@ int spand_batch_info(spand_batch_t b, double* factor_ms, double* pcg_ms, int64_t
 int spand_batch_set_profiling(spand_batch_t b, int on);
 int spand_batch_kernel_stats(spand_batch_t b, spand_kernel_stat* out, int cap, int* count);
 void spand_batch_destroy(spand_batch_t b);
+
+/* ---------------------------------------------------------------------------
+ * Solve server (continuous batching).
+ *
+ * The server keeps factored problems resident in device memory and answers
+ * requests of 1 or more right-hand sides with the PCG of §4.  Two internal
+ * host threads: one factors problems as their first request arrives (on its
+ * own stream, admitting a problem when its estimated factor footprint fits
+ * hbm_budget, evicting idle unpinned problems least recently used first),
+ * the other advances every admitted right-hand side of every problem by one
+ * PCG step per tick (one launch per step over all of them, merged applies).
+ * Requests join between ticks as segment slots and vector space free up and
+ * leave as soon as their right-hand sides are done, so a factorization, new
+ * requests and requests already in flight overlap on the GPU.  A right-hand
+ * side's iterates do not depend on the other requests in flight (fixed
+ * per-right-hand-side reduction order); only the apply's atomic accumulation
+ * order can change the last bits.
+ *
+ * Handles are caller-owned, analysed with the server's precision, and must
+ * outlive the server; while added they must not be used directly.  Host
+ * buffers of a request (b: n x nrhs column-major, x: the same) must stay
+ * valid until spand_server_wait returns for it.  The calls are thread-safe.
+ * --------------------------------------------------------------------------- */
+typedef struct spand_server_s* spand_server_t;
+typedef struct {
+  size_t hbm_budget;      /* device bytes for resident factors; 0 = 60% of the free memory */
+  int64_t max_entries;    /* entries of the PCG work vectors over all admitted right-hand sides
+                             (each right-hand side takes n rounded up to 32); 0 = 32 Mi */
+  int32_t max_segments;   /* right-hand sides in flight at most; 0 = 256 */
+  int32_t precision;      /* factorization and apply precision of every problem (0 FP64, 1 FP32) */
+  double tol;             /* PCG tolerance on ||r|| / ||b||; 0 = 1e-10 */
+} spand_server_opts;
+typedef struct {
+  int64_t requests;       /* completed requests */
+  int64_t solves;         /* completed right-hand sides */
+  double p50_ms, p99_ms, max_ms;  /* request latency, submission to completion */
+  double elapsed_s;       /* first submission to last completion */
+  double solves_per_s;
+  int64_t ticks;          /* PCG ticks run */
+  int32_t max_inflight;   /* most right-hand sides in flight at once */
+  int32_t resident_problems;
+  int64_t resident_bytes;
+} spand_server_stats;
+
+int spand_server_create(const spand_server_opts* opts, spand_server_t* out);
+/* Registers an analysed handle; pinned != 0 factors it at once and never
+ * evicts it.  *mid receives the problem id used by spand_server_submit. */
+int spand_server_add(spand_server_t s, spand_t h, int32_t pinned, int32_t* mid);
+/* Queues a request of nrhs right-hand sides; *rid identifies it. */
+int spand_server_submit(spand_server_t s, int32_t mid, int32_t nrhs, const double* b, double* x,
+                        int64_t* rid);
+/* Blocks until the request is done; iters, relres: host arrays of nrhs entries
+ * (NULL allowed), relres the true relative residual; *latency_ms the time from
+ * submission to completion.  Returns the request's status (SPAND_ENOCONV if a
+ * right-hand side reached maxit, the factorization's error if it failed). */
+int spand_server_wait(spand_server_t s, int64_t rid, int32_t* iters, double* relres,
+                      double* latency_ms);
+int spand_server_get_stats(spand_server_t s, spand_server_stats* st);
+/* Stops the threads (requests still queued are abandoned) and frees the
+ * server's memory; the handles stay with the caller. */
+void spand_server_destroy(spand_server_t s);
 
 /* Frees every device and host resource of the handle.  NULL is ignored. */
 void spand_destroy(spand_t h);

@@ -198,6 +198,8 @@ void free_handle(spand_s* h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   cudaFree(h->d_rf);
+  spand::destroy_engine(h->eng);
+  h->eng = nullptr;
   h->free_graphs();
   h->prof.release();
   delete h;
@@ -239,6 +241,10 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     if (opts->plain_launches < 0 || opts->plain_launches > 1)
       return fail(SPAND_EINVAL, "plain_launches must be 0 or 1");
     h->no_graph = opts->plain_launches == 1;
+    if (opts->rrqr_threads != 0 && opts->rrqr_threads != 256 && opts->rrqr_threads != 512 &&
+        opts->rrqr_threads != 1024)
+      return fail(SPAND_EINVAL, "rrqr_threads must be 0, 256, 512 or 1024");
+    h->rrqr_threads = opts->rrqr_threads;
   }
   int rc = build_tree(coords, A->n, dim, nlevels, h->tree, err);
   if (rc != SPAND_OK) return fail(rc, err);

@@ -16,6 +16,8 @@
 // become L_s and W_s^T in place); interface rows live in two ping-pong scratch
 // buffers.  Each stage's task tables are built on the host and uploaded in
 // one copy.
+#include <atomic>
+
 #include "spand_handle.h"
 #include "spand_real.h"
 
@@ -244,7 +246,7 @@ bool cluster_ok(spand_s* h, int cs) {
   int lc = 0;
   while ((1 << lc) < cs) ++lc;
   int& st = h->cluster_state[sizeof(real_t) == 4 ? 1 : 0][lc];
-  if (st < 0) st = rrqr_cluster_active(cs, kQrClusterSmem) > 0 ? 1 : 0;
+  if (st < 0) st = rrqr_cluster_active(cs, kQrClusterSmem, 256) > 0 ? 1 : 0;
   return st == 1;
 }
 
@@ -305,9 +307,10 @@ struct StageWork {
   struct QrGroup {
     std::vector<RRQRTask> tasks;
     int max_m = 0, max_cols = 0, max_segs = 0, smem = 0;
+    int bucket = 0, threads = 256;
   };
-  // (colour, bucket) -> tasks; bucket b >= 1: thread-block clusters of
-  // 2^(b-1) CTAs, bucket 0: the global-memory kernel
+  // (colour, bucket * 4096 + CTA size) -> tasks; bucket b >= 1: thread-block
+  // clusters of 2^(b-1) CTAs, bucket 0: the global-memory kernel
   std::map<std::pair<int, int>, QrGroup> qr;
   std::vector<RRQRSeg> qr_segs;
   std::vector<int> ints;  // pristine counters of every problem of the stage
@@ -585,7 +588,16 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
             break;
           }
         }
-        auto& g = W.qr[{col, b}];
+        // CTA size: the handle's choice, else 256 threads
+        int thr = 256;
+        if (b > 0 && h->rrqr_threads > 0) {
+          thr = h->rrqr_threads;
+          const int cs = 1 << (b - 1);
+          if (rrqr_cluster_active(cs, bytes_b, thr) <= 0) thr = 256;
+        }
+        auto& g = W.qr[{col, b * 4096 + thr}];
+        g.threads = thr;
+        g.bucket = b;
         g.tasks.push_back(t);
         g.max_m = std::max(g.max_m, m);
         g.max_cols = std::max(g.max_cols, t.ncols_max);
@@ -707,8 +719,8 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
       [&] { launch_set_identity((const PotrfTask*)(D + O.id), (int)W.ident.size(), cs); });
   size_t gi = 0;
   for (auto& kv : W.qr) {
-    const int b = kv.first.second;
     const auto& g = kv.second;
+    const int b = g.bucket;
     const size_t off = O.qr[gi++];
     run(KK_RRQR, g.tasks.size(), 0.0, 0.0, [&] {
       if (b == 0)
@@ -716,7 +728,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
                     g.max_m, g.max_cols, g.max_segs, cs);
       else
         launch_rrqr_cluster((const RRQRTask*)(D + off), (int)g.tasks.size(),
-                            (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, cs);
+                            (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, g.threads, cs);
     });
   }
   CK(cudaGetLastError());
@@ -948,7 +960,7 @@ int ensure_pinned(FactorGroup& G, size_t n) {
 }
 
 uint64_t next_layout_id() {
-  static uint64_t counter = 0;  // host threads must not factor concurrently (handles are not thread-safe)
+  static std::atomic<uint64_t> counter{0};  // distinct handles may be factored by different threads
   return ++counter;
 }
 

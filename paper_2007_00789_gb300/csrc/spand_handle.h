@@ -41,7 +41,7 @@ struct DevArena {
   };
   std::vector<Chunk> chunks;
   size_t cur = 0;
-  size_t min_chunk = size_t(256) << 20;
+  size_t min_chunk = size_t(64) << 20;
 
   int alloc(size_t bytes, void** out) {
     bytes = (bytes + 255) & ~size_t(255);
@@ -306,6 +306,8 @@ struct ApSeg {
   spand_s* h;
   int64_t zoff;
 };
+struct Engine;                  // multi-segment PCG (engine.cu)
+void destroy_engine(Engine* e);
 struct MultiApply {
   std::vector<std::pair<const spand_s*, int64_t>> key;
   std::vector<uint64_t> layouts;
@@ -383,7 +385,9 @@ struct spand_s {
   int pcg_iters = 0;
   spand::Prof prof;
   int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel; 2: clusters <= 8
+  int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512, 1024); 0 = automatic
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
+  spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own
   uint64_t layout_id = 0;     // new value at every full factorization (arena layout changes)
   cudaStream_t cap_stream = nullptr;  // capture needs a stream other than the legacy one

@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
 // diagonal block becomes I_r and t.cur[p] = r.
 // ---------------------------------------------------------------------------
 constexpr int kQrThreads = 256;
+constexpr int kQrcMaxThreads = 1024;  // the cluster RRQR runs 256, 512 or 1024 threads per CTA
 
 struct ArgMax {
   real_t v;
@@ -634,7 +635,7 @@ __device__ __forceinline__ QrSlot warp_merge(QrSlot mine) {
 // step: one block barrier and two cluster barriers; every warp reads the
 // CTAs' candidates itself, and the owner of the pivot column pushes v and tau
 // into every CTA's shared memory.
-__global__ void __launch_bounds__(kQrThreads)
+__global__ void __launch_bounds__(kQrcMaxThreads)
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int csize) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -642,11 +643,12 @@ __global__ void __launch_bounds__(kQrThreads)
   const RRQRTask t = tasks[blockIdx.x / csize];
   extern __shared__ real_t sm[];
   __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
-  __shared__ QrSlot s_warp[kQrThreads / kWarp];
+  __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
   __shared__ double s_tau;   // tau of the current step, written by the owner
   __shared__ double s_nu64;  // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
+  const int nthr = (int)blockDim.x;  // 256, 512 or 1024
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
   const int m = t.m;
   const size_t ld = t.ld;
   const int nseg = t.seg_end - t.seg_begin;
@@ -676,10 +678,10 @@ __global__ void __launch_bounds__(kQrThreads)
   // tpc threads share a column (its rows split among them), enough to keep all
   // warps busy when the CTA holds few columns
   int tpc = 1;
-  while (tpc < 8 && nloc * tpc * 2 <= kQrThreads) tpc *= 2;
-  const int ngrp = kQrThreads / tpc, grp = tid / tpc, sl = tid % tpc;
+  while (tpc < 8 && nloc * tpc * 2 <= nthr) tpc *= 2;
+  const int ngrp = nthr / tpc, grp = tid / tpc, sl = tid % tpc;
   const unsigned gmask = (tpc == 32) ? 0xffffffffu : (((1u << tpc) - 1u) << (lane & ~(tpc - 1)));
-  for (int l = tid; l < nloc; l += kQrThreads) {
+  for (int l = tid; l < nloc; l += nthr) {
     const int g = g0 + l;
     int lo = 0, hi = nseg - 1;  // last segment with segoff <= g
     while (lo < hi) {
@@ -691,7 +693,7 @@ __global__ void __launch_bounds__(kQrThreads)
     pcol[l] = segs[t.seg_begin + lo].col + (g - segoff[lo]);
   }
   __syncthreads();
-  for (int e = tid; e < m * nloc; e += kQrThreads) {
+  for (int e = tid; e < m * nloc; e += nthr) {
     const int i = e % m, l = e / m;
     A[(size_t)i * ncl + l] = t.A[i + (size_t)pcol[l] * ld];
   }
@@ -721,10 +723,11 @@ __global__ void __launch_bounds__(kQrThreads)
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    if (tid == 0) {
-      QrSlot a = s_warp[0];
-      for (int w = 1; w < nw; ++w) slot_merge(a, s_warp[w]);
-      s_slot = a;
+    if (warp == 0) {
+      QrSlot a{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
+      if (lane < nw) a = s_warp[lane];
+      a = warp_merge(a);
+      if (lane == 0) s_slot = a;
     }
     cluster.sync();
     QrSlot gb{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
@@ -796,14 +799,14 @@ __global__ void __launch_bounds__(kQrThreads)
       beta = __shfl_sync(0xffffffffu, beta, 0);
       tau = __shfl_sync(0xffffffffu, tau, 0);
       inv = __shfl_sync(0xffffffffu, inv, 0);
-      for (int i = step + tid; i < m; i += kQrThreads) {
+      for (int i = step + tid; i < m; i += nthr) {
         real_t* ai = A + (size_t)i * ncl + l;
         const real_t vi = (i == step) ? 1.0 : (*ai) * inv;
         *ai = (i == step) ? beta : 0.0;
         t.V[i + (size_t)step * m] = vi;
         for (int c = 0; c < csize; ++c) cluster.map_shared_rank(v, c)[i] = vi;
       }
-      for (int i = tid; i < step; i += kQrThreads) t.V[i + (size_t)step * m] = 0.0;
+      for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0.0;
       if (tid == 0) {
         t.tau[step] = tau;
         norms[l] = -1.0;
@@ -846,18 +849,18 @@ __global__ void __launch_bounds__(kQrThreads)
   if (r < 0) r = nsteps;
   __syncthreads();
   // write the columns back, mirror the coarse rows into the neighbours' rows
-  for (int e = tid; e < m * nloc; e += kQrThreads) {
+  for (int e = tid; e < m * nloc; e += nthr) {
     const int i = e % m, l = e / m;
     t.A[i + (size_t)pcol[l] * ld] = A[(size_t)i * ncl + l];
   }
-  for (int e = tid; e < r * nloc; e += kQrThreads) {
+  for (int e = tid; e < r * nloc; e += nthr) {
     const int i = e % r, l = e / r;
     const RRQRSeg g = segs[t.seg_begin + segid[l]];
     const int c = g0 + l - segoff[segid[l]];
     g.mirror[c + (size_t)i * g.mirror_ld] = A[(size_t)i * ncl + l];
   }
   if (crank == 0) {
-    for (int e = tid; e < r * r; e += kQrThreads) {
+    for (int e = tid; e < r * r; e += nthr) {
       const int i = e % r, j = e / r;
       t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
     }
@@ -946,7 +949,7 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
 }
 
 void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
-                         int smem_bytes, cudaStream_t s) {
+                         int smem_bytes, int threads, cudaStream_t s) {
   if (ntasks <= 0) return;
   cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem_bytes);
@@ -954,7 +957,7 @@ void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int
     cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ntasks * csize));
-  cfg.blockDim = dim3(kQrThreads);
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = (size_t)smem_bytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -967,14 +970,14 @@ void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int
   cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, csize);
 }
 
-int rrqr_cluster_active(int csize, int smem_bytes) {
+int rrqr_cluster_active(int csize, int smem_bytes, int threads) {
   cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem_bytes);
   if (csize > 8)
     cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)csize);
-  cfg.blockDim = dim3(kQrThreads);
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = (size_t)smem_bytes;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

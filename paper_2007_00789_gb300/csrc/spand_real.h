@@ -149,9 +149,10 @@ int rrqr_smem_bytes(int max_m, int max_cols, int max_segs);
 // On-chip variant: C CTAs per interface (a thread-block cluster), the block in shared memory.
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
 // Clusters of this shape that can be resident at once (0: cannot be launched).
-int rrqr_cluster_active(int csize, int smem_bytes);
+int rrqr_cluster_active(int csize, int smem_bytes, int threads);
+// threads: CTA size, 256, 512 or 1024
 void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
-                         int smem_bytes, cudaStream_t s);
+                         int smem_bytes, int threads, cudaStream_t s);
 void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, int max_cols,
                  int max_segs, cudaStream_t s);
 

@@ -27,11 +27,15 @@ EXPORTS = [
     "spand_analyze", "spand_factor", "spand_apply", "spand_pcg", "spand_pcg_host",
     "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
     "spand_pcg_noalloc", "spand_set_profiling", "spand_kernel_stats",
+    "spand_apply_many", "spand_pcg_many",
     "spand_batch_create", "spand_batch_factor", "spand_batch_pcg", "spand_batch_info",
     "spand_batch_set_profiling", "spand_batch_kernel_stats", "spand_batch_destroy",
+    "spand_server_create", "spand_server_add", "spand_server_submit", "spand_server_wait",
+    "spand_server_get_stats", "spand_server_destroy",
     "spand_destroy", "spand_strerror", "spand_last_error",
 ]
-_VOID = ("spand_destroy", "spand_batch_destroy", "spand_strerror", "spand_last_error")
+_VOID = ("spand_destroy", "spand_batch_destroy", "spand_server_destroy", "spand_strerror",
+         "spand_last_error")
 
 
 class SpandError(RuntimeError):
@@ -49,7 +53,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("skip", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("plain_launches", ctypes.c_int32)]
+                ("plain_launches", ctypes.c_int32), ("rrqr_threads", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -60,6 +64,20 @@ class _Stats(ctypes.Structure):
                 ("factor_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double),
                 ("pcg_iters", ctypes.c_int32), ("pcg_relres", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_entries", ctypes.c_int64),
+                ("max_segments", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tol", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("solves", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("ticks", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("resident_problems", ctypes.c_int32), ("resident_bytes", ctypes.c_int64)]
 
 
 class _KStat(ctypes.Structure):
@@ -88,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_pcg_host.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_pcg_noalloc.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_matvec.argtypes = [vp, vp, vp, vp]
+    L.spand_apply_many.argtypes = [vp, vp, vp, i32, i64, vp]
+    L.spand_pcg_many.argtypes = [vp, vp, vp, i32, i64, f64, vp, vp, vp]
     L.spand_info.argtypes = [vp, ctypes.POINTER(_Stats)]
     L.spand_ranks.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     L.spand_cluster_map.argtypes = [vp, ctypes.c_int, vp]
@@ -104,6 +124,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                            ctypes.POINTER(ctypes.c_int)]
     L.spand_batch_destroy.argtypes = [vp]
     L.spand_batch_destroy.restype = None
+    L.spand_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(vp)]
+    L.spand_server_add.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    L.spand_server_submit.argtypes = [vp, i32, i32, vp, vp, ctypes.POINTER(i64)]
+    L.spand_server_wait.argtypes = [vp, i64, vp, vp, ctypes.POINTER(f64)]
+    L.spand_server_get_stats.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+    L.spand_server_destroy.argtypes = [vp]
+    L.spand_server_destroy.restype = None
     L.spand_destroy.argtypes = [vp]
     L.spand_destroy.restype = None
     L.spand_strerror.argtypes = [ctypes.c_int]
@@ -146,7 +173,7 @@ class Spand:
     def __init__(self, rowptr, colind, val, coords, nlevels: int, eps: float, scheme: int = 1,
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
                  max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0,
-                 plain_launches: bool = False):
+                 plain_launches: bool = False, rrqr_threads: int = 0):
         L = load_library()
         self._lib = L
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
@@ -162,7 +189,7 @@ class Spand:
         opts = _Opts(-1 if skip is None else int(skip), 0 if maxit is None else int(maxit),
                      0 if true_res_every is None else int(true_res_every),
                      -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
-                     int(precision), 1 if plain_launches else 0)
+                     int(precision), 1 if plain_launches else 0, int(rrqr_threads))
         h = ctypes.c_void_p()
         _check(L.spand_analyze(ctypes.byref(csr), coords.ctypes.data, coords.shape[1], int(nlevels),
                                float(eps), int(scheme), ctypes.byref(opts), ctypes.byref(h)))
@@ -200,6 +227,26 @@ class Spand:
                                    ctypes.byref(rel), _stream_ptr(stream)),
                allow=(SPAND_ENOCONV,) if allow_noconv else ())
         return int(it.value), float(rel.value)
+
+    def apply_many(self, r, z, stream=None):
+        """z[j] = M r[j] for the rows of 2-D float64 CUDA tensors (nrhs, ld >= n)."""
+        nrhs, ld = r.shape
+        if z.shape != r.shape or r.stride(1) != 1 or z.stride(1) != 1:
+            raise ValueError("r and z: same shape, contiguous rows")
+        _check(self._lib.spand_apply_many(self._h, _dptr(r), _dptr(z), nrhs, r.stride(0),
+                                          _stream_ptr(stream)))
+
+    def pcg_many(self, b, x, tol: float, stream=None, allow_noconv: bool = False):
+        """PCG for every row of b (nrhs, ld >= n) into x; returns (iterations, relres) arrays."""
+        nrhs = b.shape[0]
+        if x.shape != b.shape or b.stride(1) != 1 or x.stride(1) != 1:
+            raise ValueError("b and x: same shape, contiguous rows")
+        it = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        _check(self._lib.spand_pcg_many(self._h, _dptr(b), _dptr(x), nrhs, b.stride(0), float(tol),
+                                        it.ctypes.data, rel.ctypes.data, _stream_ptr(stream)),
+               allow=(SPAND_ENOCONV,) if allow_noconv else ())
+        return it, rel
 
     def pcg_noalloc(self, b, x, tol: float, stream=None):
         """spand_pcg without any allocation (work vectors in the library's static array)."""
@@ -317,3 +364,71 @@ class SpandBatch:
 
     def kernel_stats(self) -> list[dict]:
         return _kstats(self._lib.spand_batch_kernel_stats, self._h)
+
+
+class SpandServer:
+    """Resident factored problems answering multi-RHS solve requests (spand_server_*).
+
+    ``submit`` returns at once; ``wait`` blocks (without the GIL) until the
+    request is done.  Added ``Spand`` objects must stay open while the server
+    exists and must not be used directly meanwhile."""
+
+    def __init__(self, hbm_budget: int = 0, max_entries: int = 0, max_segments: int = 0,
+                 precision: int = 0, tol: float = 1e-10):
+        self._lib = load_library()
+        o = _ServerOpts(int(hbm_budget), int(max_entries), int(max_segments), int(precision),
+                        float(tol))
+        h = ctypes.c_void_p()
+        _check(self._lib.spand_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._mats = {}
+        self._pending = {}
+
+    def add(self, problem: "Spand", pinned: bool = False) -> int:
+        mid = ctypes.c_int32()
+        _check(self._lib.spand_server_add(self._h, problem._h, 1 if pinned else 0, ctypes.byref(mid)))
+        self._mats[int(mid.value)] = problem
+        return int(mid.value)
+
+    def submit(self, mid: int, b: np.ndarray) -> int:
+        """b: (n,) or (nrhs, n) float64; returns the request id."""
+        n = self._mats[mid].n
+        b = np.ascontiguousarray(np.atleast_2d(b), dtype=np.float64)
+        if b.shape[1] != n:
+            raise ValueError("right-hand sides must have n entries")
+        x = np.empty_like(b)
+        rid = ctypes.c_int64()
+        _check(self._lib.spand_server_submit(self._h, int(mid), b.shape[0], b.ctypes.data,
+                                             x.ctypes.data, ctypes.byref(rid)))
+        self._pending[int(rid.value)] = (b, x)
+        return int(rid.value)
+
+    def wait(self, rid: int, allow_noconv: bool = False):
+        """Returns (x (nrhs, n), iterations, true relative residuals, latency in ms)."""
+        b, x = self._pending[rid]
+        it = np.zeros(b.shape[0], dtype=np.int32)
+        rel = np.zeros(b.shape[0], dtype=np.float64)
+        lat = ctypes.c_double()
+        try:
+            _check(self._lib.spand_server_wait(self._h, int(rid), it.ctypes.data, rel.ctypes.data,
+                                               ctypes.byref(lat)),
+                   allow=(SPAND_ENOCONV,) if allow_noconv else ())
+        finally:
+            self._pending.pop(rid, None)
+        return x, it, rel, float(lat.value)
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(self._lib.spand_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.spand_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

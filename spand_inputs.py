@@ -237,3 +237,28 @@ def batch_workload(count: int = 64, lo: float = -2.0, hi: float = 2.0):
             prob = diffusion_grid((d, d, d), seed=i, lo=lo, hi=hi)
         out.append((prob, paper_nlevels(prob.n), rhs_normal(prob.n, seed=1000 + i)))
     return out
+
+
+def serve_workload(requests: int = 120, rate: float = 20.0, new_problems: int = 12,
+                   p_new: float = 0.3, seed: int = 0):
+    """A seeded serving trace: a resident 3D FV diffusion problem on 96^3 with
+    a = 10**U(-3, 3) (seed 0), new 3D 7-point FV problems of n = 16k .. 500k
+    (sides 25 .. 79 spread evenly, a = 10**U(-3, 3) from seeds 1, 2, ...), and
+    requests arriving as a Poisson process of the given rate (per second); a
+    request targets a new problem with probability p_new (else the resident
+    one) and carries 1 .. 32 right-hand sides N(0, 1).
+
+    Returns (problems, trace): problems = [(problem, nlevels)] with the
+    resident one first; trace = [(arrival time s, problem index, nrhs, rhs seed)]."""
+    rng = np.random.default_rng(seed)
+    probs = [(diffusion_3d(96, seed=0), paper_nlevels(96 ** 3))]
+    for i in range(new_problems):
+        d = 25 + int(round(54 * i / max(new_problems - 1, 1)))
+        probs.append((diffusion_3d(d, seed=1 + i), paper_nlevels(d ** 3)))
+    t = 0.0
+    trace = []
+    for k in range(requests):
+        t += rng.exponential(1.0 / rate)
+        pi = 0 if rng.uniform() >= p_new else 1 + int(rng.integers(new_problems))
+        trace.append((t, pi, int(rng.integers(1, 33)), 5000 + k))
+    return probs, trace

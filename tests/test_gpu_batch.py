@@ -158,3 +158,39 @@ def test_batch_not_spd_names_problem():
     assert ei.value.code == S.SPAND_ENOTSPD
     assert "problem 1" in str(ei.value)
     batch.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_many_rhs_match_single(precision):
+    """spand_apply_many / spand_pcg_many (padded leading dimension) against the single-column calls."""
+    torch = _torch()
+    from paper_2007_00789_gb300 import spand as S
+    p = si.diffusion_3d(20, seed=9, lo=-2, hi=2)
+    h = S.Spand.from_problem(p, 8, 1e-2, 1, precision=precision)
+    h.factor()
+    nrhs, ld = 5, p.n + 5
+    rng = np.random.default_rng(4)
+    R = torch.zeros((nrhs, ld), dtype=torch.float64, device="cuda")
+    R[:, :p.n] = torch.from_numpy(rng.standard_normal((nrhs, p.n))).cuda()
+    Z = torch.zeros_like(R)
+    h.apply_many(R, Z)
+    its, rels = h.pcg_many(R, torch.zeros_like(R), 1e-12)
+    X = torch.zeros_like(R)
+    its, rels = h.pcg_many(R, X, 1e-12)
+    torch.cuda.synchronize()
+    A = p.to_scipy()
+    for j in range(nrhs):
+        r = R[j, :p.n].contiguous()
+        z1 = torch.empty_like(r)
+        h.apply(r, z1)
+        x1 = torch.zeros_like(r)
+        it1, _ = h.pcg(r, x1, 1e-12)
+        torch.cuda.synchronize()
+        err = float((Z[j, :p.n] - z1).abs().max() / z1.abs().max())
+        assert err <= (1e-12 if precision == 0 else 1e-5), err
+        assert abs(int(its[j]) - it1) <= 1
+        x = X[j, :p.n].cpu().numpy()
+        b = r.cpu().numpy()
+        assert rels[j] <= 1e-12 and np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-12
+    assert float(Z[:, p.n:].abs().max()) == 0.0  # padding untouched
+    h.close()
