@@ -47,19 +47,21 @@ FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 152 SMs x 2070 MHz x 128 FP3
 TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 18.63e6}
 
 WORKLOADS = {
-    # name: (factory, dim, ell, rhs)
-    "poisson3d_64": ("laplacian_3d(64)", 12, "rhs_normal"),
-    "poisson2d_64": ("laplacian_2d(64)", 6, "rhs_uniform"),
-    "diffusion3d_64": ("diffusion_3d(64, seed=0)", 12, "rhs_normal"),
-    "poisson3d_32": ("laplacian_3d(32)", 9, "rhs_normal"),
+    # name: (factory, ell, rhs, rhs seed)
+    "poisson3d_64": ("laplacian_3d(64)", 12, "rhs_normal", 0),
+    "poisson2d_64": ("laplacian_2d(64)", 6, "rhs_uniform", 0),
+    "diffusion3d_64": ("diffusion_3d(64, seed=0)", 12, "rhs_normal", 0),
+    "poisson3d_32": ("laplacian_3d(32)", 9, "rhs_normal", 0),
+    # 3D high-contrast diffusion, a = 10^U(-3,3) per cell (seed 0), b ~ N(0,1) from seed 1
+    "diffusion3d_128": ("diffusion_3d(128, seed=0)", 15, "rhs_normal", 1),
 }
 
 
 def make_problem(name):
     import spand_inputs as si
-    expr, ell, rhs = WORKLOADS[name]
+    expr, ell, rhs, seed = WORKLOADS[name]
     prob = eval("si." + expr, {"si": si})
-    b = getattr(si, rhs)(prob.n, seed=0)
+    b = getattr(si, rhs)(prob.n, seed=seed)
     return prob, ell, b
 
 
@@ -306,7 +308,7 @@ def run_serve(args, rank, world, local, dist):
     from paper_2007_00789_gb300 import spand
 
     tol = 1e-10
-    probs, trace = si.serve_workload()
+    probs, trace = si.serve_workload(rate=args.serve_rate)
     max_n = max(p.n for p, _ in probs)
     srv = spand.SpandServer(precision=args.precision, tol=tol, max_segments=512,
                             max_entries=6 * 32 * ((max_n + 31) // 32 * 32))
@@ -356,7 +358,7 @@ def run_serve(args, rank, world, local, dist):
         "data": "synthetic",
         "config": {"workload": "serve", "resident": "diffusion_3d(96), a=10^U(-3,3)",
                    "new_problems": len(probs) - 1, "requests": len(trace), "solves": solves,
-                   "arrival_rate_per_s": 20.0, "nrhs": "1..32", "tol": tol,
+                   "arrival_rate_per_s": args.serve_rate, "nrhs": "1..32", "tol": tol,
                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                    "max_ms": float(lat.max()), "wall_s": wall, "cg_iters_max": int(iters.max()),
                    "cg_iters_mean": float(iters.mean()), "true_relres_max_host": worst,
@@ -394,6 +396,8 @@ def main():
                     help="0: FP64 factor+apply; 1: FP32 factor+apply (PCG stays FP64)")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip timing the other precision")
+    ap.add_argument("--serve-rate", type=float, default=5.0,
+                    help="serve workload: request arrivals per second (Poisson process)")
     ap.add_argument("--plain-launches", action="store_true",
                     help="no CUDA graphs: every kernel launched on its own (for profilers)")
     ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512, 1024],

@@ -157,9 +157,9 @@ class StageClusters:
     level: dict  # key -> level of its node
 
 
-def stage_clusters(tree: NDTree, k: int) -> StageClusters:
+def stage_clusters(tree, k: int) -> StageClusters:
     """All live clusters at stage ``k``, in id (lexicographic key) order."""
-    live, rows = cluster_keys(tree, k)
+    live, rows = tree_cluster_keys(tree, k)
     uniq, inv = np.unique(rows, axis=0, return_inverse=True)
     inv = inv.reshape(-1)
     order = np.argsort(inv, kind="stable")
@@ -184,3 +184,161 @@ def greedy_colouring(order: list, adjacency: dict) -> dict:
             c += 1
         colour[p] = c
     return colour
+
+
+# ---------------------------------------------------------------------------
+# Algebraic nested dissection (general sparse SPD input, no coordinates).
+#
+# The node at depth d bisects its vertex set V by a breadth-first level
+# structure of the subgraph of A induced on V: starting from the smallest
+# vertex index, one sweep finds a far vertex (the smallest index at the
+# largest distance), and the levels are the BFS distances from it.  With the
+# vertices ordered by (distance, index) and unreached vertices (other
+# components) last, the level L* of the median (position floor(|V|/2)) is the
+# separator; smaller distances go to the lower child, larger distances and
+# unreached vertices to the upper child.  (No edge joins the two children:
+# BFS distances of adjacent vertices differ by at most one.)  If the median is
+# unreached, the separator is empty and the reached vertices form the lower
+# child.  Node numbering and levels are those of the geometric tree.
+#
+# Clusters.  Interfaces are keyed by the subdomains they touch: the reach
+# R(v) of a separator vertex v is the set of leaves connected to v through
+# vertices of strictly lower level (for a neighbour u of lower level, u's own
+# leaf if u is a leaf vertex, else R(u)).  At stage k, with subdomains the
+# subtrees of the depth ell-1-k nodes, an interface vertex v of node S has
+# key = the sorted set of depth-(ell-1-k) ancestors of the leaves in R(v);
+# its cluster is (S, key).  The key at stage k+1 is the set of parents of the
+# key at stage k, so stage k+1 clusters are unions of stage k clusters.
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class GraphNDTree:
+    """Algebraic nested-dissection tree to depth ``nlevels - 1``."""
+
+    nlevels: int
+    node_of: np.ndarray  # vertex -> node (separator node or leaf)
+    level_of: np.ndarray  # vertex -> level
+    reach: list  # vertex -> sorted tuple of leaf ids (separator vertices; () for leaves)
+    width: int  # largest reach set (>= 1): the padded key width
+
+    @property
+    def depth_max(self) -> int:
+        return self.nlevels - 1
+
+
+def bfs_levels(rowptr, colind, inset: np.ndarray, root: int) -> np.ndarray:
+    """BFS distance from ``root`` of every vertex in the subgraph induced on
+    ``inset`` (boolean mask); -1 for vertices not reached."""
+    lev = np.full(inset.size, -1, dtype=np.int64)
+    lev[root] = 0
+    front = np.array([root], dtype=np.int64)
+    d = 0
+    while front.size:
+        nb = np.concatenate([colind[rowptr[v]:rowptr[v + 1]] for v in front])
+        nb = np.unique(nb)
+        nb = nb[inset[nb] & (lev[nb] < 0)]
+        d += 1
+        lev[nb] = d
+        front = nb.astype(np.int64)
+    return lev
+
+
+def graph_bisect(rowptr, colind, verts: np.ndarray):
+    """(separator, lower, upper) of the ascending vertex array ``verts``."""
+    n = rowptr.size - 1
+    inset = np.zeros(n, dtype=bool)
+    inset[verts] = True
+    lev = bfs_levels(rowptr, colind, inset, int(verts[0]))
+    lv = lev[verts]
+    far = lv.max()
+    r1 = int(verts[lv == far].min())
+    lev = bfs_levels(rowptr, colind, inset, r1)
+    lv = lev[verts]
+    big = np.iinfo(np.int64).max
+    key = np.where(lv < 0, big, lv)
+    order = np.lexsort((verts, key))  # by (distance, index)
+    med = key[order[verts.size // 2]]
+    if med == big:
+        return verts[:0], verts[lv >= 0], verts[lv < 0]
+    return verts[key == med], verts[key < med], verts[key > med]
+
+
+def graph_nested_dissection(rowptr, colind, nlevels: int) -> GraphNDTree:
+    """Algebraic ND on the graph of a symmetric CSR pattern; raises ValueError
+    on an empty leaf or subdomain."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    colind = np.asarray(colind, dtype=np.int64)
+    n = rowptr.size - 1
+    if nlevels < 1:
+        raise ValueError("nlevels must be >= 1")
+    node_of = np.full(n, -1, dtype=np.int64)
+    level_of = np.full(n, -1, dtype=np.int64)
+    dmax = nlevels - 1
+    frontier = [(0, np.arange(n, dtype=np.int64))]
+    for depth in range(dmax + 1):
+        nxt = []
+        for node, verts in frontier:
+            if verts.size == 0:
+                raise ValueError(f"empty nested-dissection subdomain at node {node}")
+            if depth == dmax:
+                node_of[verts] = node
+                level_of[verts] = 0
+                continue
+            sep, lo, hi = graph_bisect(rowptr, colind, verts)
+            node_of[sep] = node
+            level_of[sep] = dmax - depth
+            nxt.append((2 * node + 1, lo))
+            nxt.append((2 * node + 2, hi))
+        frontier = nxt
+    reach = [()] * n
+    for lvl in range(1, nlevels):
+        for v in np.nonzero(level_of == lvl)[0]:
+            s = set()
+            for u in colind[rowptr[v]:rowptr[v + 1]]:
+                if level_of[u] == 0:
+                    s.add(int(node_of[u]))
+                elif level_of[u] < lvl:
+                    s.update(reach[u])
+            reach[v] = tuple(sorted(s))
+    width = max([1] + [len(r) for r in reach])
+    return GraphNDTree(nlevels=nlevels, node_of=node_of, level_of=level_of, reach=reach,
+                       width=width)
+
+
+def ancestor(i: int, depth: int) -> int:
+    """The ancestor at ``depth`` of heap-numbered node ``i`` (i itself if not deeper)."""
+    while node_depth(i) > depth:
+        i = (i - 1) // 2
+    return i
+
+
+def graph_cluster_keys(tree: GraphNDTree, k: int):
+    """Cluster key of every live vertex at stage ``k`` (algebraic tree): like
+    ``cluster_keys``, rows ``(node, key[0], ..., key[width-1])`` with the key's
+    sorted subdomain ids padded with -1."""
+    ell = tree.nlevels
+    dk = ell - 1 - k
+    live = np.nonzero(tree.level_of >= k)[0].astype(np.int64)
+    rows = np.full((live.size, 1 + tree.width), -1, dtype=np.int64)
+    rows[:, 0] = tree.node_of[live]
+    for i, v in enumerate(live):
+        if tree.level_of[v] > k:
+            key = sorted({ancestor(leaf, dk) for leaf in tree.reach[v]})
+            rows[i, 1:1 + len(key)] = key
+    return live, rows
+
+
+def build_tree(coords, nlevels: int, rowptr=None, colind=None):
+    """The multilevel tree: geometric with coordinates, algebraic (from the
+    CSR pattern) when ``coords`` is None."""
+    if coords is None:
+        return graph_nested_dissection(rowptr, colind, nlevels)
+    return nested_dissection(coords, nlevels)
+
+
+def tree_cluster_keys(tree, k: int):
+    """``cluster_keys`` for either kind of tree."""
+    if isinstance(tree, GraphNDTree):
+        return graph_cluster_keys(tree, k)
+    return cluster_keys(tree, k)

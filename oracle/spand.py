@@ -100,6 +100,9 @@ class Factor:
     stage_colours: list = field(default_factory=list)
     stage_flags: list = field(default_factory=list)  # {interface key: near-tie flags}
     stage_keys: list = field(default_factory=list)
+    # diagonal prescaling: the factorization is of S A S with S = D^{-1/2},
+    # D = diag(A), and M = S M~ S (None: no prescaling)
+    scale: np.ndarray | None = None
 
     def nnz_factor(self) -> int:
         """Stored entries of the factor operators (L_s, W_s, Z_p, Q_p, E-tilde)."""
@@ -143,11 +146,19 @@ def _blocks_from_csr(A, clusters: partition.StageClusters):
 
 
 def factor(A, coords, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
-           skip: int | None = None) -> Factor:
-    """spaND factorization (Algorithm 2) of the sparse SPD matrix A (scipy sparse)."""
+           skip: int | None = None, prescale: bool = False) -> Factor:
+    """spaND factorization (Algorithm 2) of the sparse SPD matrix A (scipy sparse).
+
+    coords None: the multilevel partition is the algebraic one of A's graph
+    (``partition.graph_nested_dissection``).  prescale: factor
+    D^{-1/2} A D^{-1/2} with D = diag(A), the diagonal prescaling for
+    general SPD input; the preconditioner of A is then D^{-1/2} M~ D^{-1/2}."""
+    import scipy.sparse as sp
+
     import spand_inputs
 
     A = A.tocsr()
+    A.sort_indices()
     n = A.shape[0]
     if not (0.0 <= eps <= 1.0):
         raise ValueError("eps must lie in [0, 1]")
@@ -155,8 +166,16 @@ def factor(A, coords, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
         raise ValueError("unknown scheme")
     if skip is None:
         skip = spand_inputs.default_skip(n, nlevels)
-    tree = partition.nested_dissection(coords, nlevels)
     F = Factor(n=n, nlevels=nlevels, eps=eps, scheme=scheme, skip=skip)
+    tree = partition.build_tree(coords, nlevels, A.indptr, A.indices)
+    if prescale:
+        d = A.diagonal()
+        if not (d > 0).all():
+            raise NotSPDError("a diagonal entry is not positive")
+        F.scale = 1.0 / np.sqrt(d)
+        S = sp.diags(F.scale)
+        A = (S @ A @ S).tocsr()
+        A.sort_indices()
 
     sc0 = partition.stage_clusters(tree, 0)
     B = _blocks_from_csr(A, sc0)
@@ -260,7 +279,7 @@ def factor(A, coords, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
             assert not keys, "the last stage must eliminate everything"
             break
         # 4. merge into the clusters of stage k+1
-        kv_live, kv_rows = partition.cluster_keys(tree, k + 1)
+        kv_live, kv_rows = partition.tree_cluster_keys(tree, k + 1)
         row_of = {int(v): i for i, v in enumerate(kv_live)}
         parent = {}
         for p in keys:
@@ -338,10 +357,15 @@ def _backward(F: Factor, z: np.ndarray) -> None:
 
 
 def apply(F: Factor, r: np.ndarray) -> np.ndarray:
-    """The preconditioner M r = L^{-T} L^{-1} r (Algorithm 2 caption)."""
+    """The preconditioner M r = L^{-T} L^{-1} r (Algorithm 2 caption); with
+    prescaling S L^{-T} L^{-1} S r."""
     z = np.array(r, dtype=np.float64, copy=True)
+    if F.scale is not None:
+        z *= F.scale
     _forward(F, z)
     _backward(F, z)
+    if F.scale is not None:
+        z *= F.scale
     return z
 
 
@@ -419,9 +443,10 @@ def pcg(matvec, precond, b: np.ndarray, tol: float, maxit: int = 500,
 
 
 def solve(A, coords, b, nlevels: int, eps: float, scheme: int = SECOND_ORDER_FULL,
-          skip: int | None = None, tol: float = 1e-12, maxit: int = 500):
+          skip: int | None = None, tol: float = 1e-12, maxit: int = 500,
+          prescale: bool = False):
     """Factor A with spaND and solve A x = b by PCG; returns (Factor, PCGResult)."""
     A = A.tocsr()
-    F = factor(A, coords, nlevels, eps, scheme, skip)
+    F = factor(A, coords, nlevels, eps, scheme, skip, prescale=prescale)
     res = pcg(lambda v: A @ v, lambda v: apply(F, v), b, tol, maxit)
     return F, res

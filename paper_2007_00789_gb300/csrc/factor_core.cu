@@ -917,7 +917,7 @@ int upload_apply_plan(Run& R, cudaStream_t s) {
     const void* base = ph.kind == PH_INTERIOR ? (const void*)((const ApInterior*)pa + ph.begin)
                        : ph.kind == PH_SCALE  ? (const void*)((const ApScale*)ps + ph.begin)
                                               : (const void*)((const ApQE*)pq + ph.begin);
-    items[i] = {base, 0, ph.end - ph.begin, 0};
+    items[i] = {base, 0, 0, ph.end - ph.begin, 0, 1, 0};
   }
   std::vector<ApInterior> vi(R.api.size());
   for (size_t i = 0; i < R.api.size(); ++i) {
@@ -1213,10 +1213,10 @@ int apply_launches(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
     const int kind = ph.kind == PH_INTERIOR ? KK_AP_INTERIOR : ph.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
     P.run(kind, s, ph.flops, ph.bytes, [&] {
       if (ph.kind == PH_INTERIOR)
-        launch_ap_interior(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, z, fwd, s);
+        launch_ap_interior(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, 1, z, fwd, s);
       else if (ph.kind == PH_SCALE)
-        launch_ap_scale(items + i, 1, nt, ph.K, ph.max_m, z, fwd, s);
-      else launch_ap_qe(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, z, fwd, s);
+        launch_ap_scale(items + i, 1, nt, ph.K, ph.max_m, 1, z, fwd, s);
+      else launch_ap_qe(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, 1, z, fwd, s);
     });
   };
   for (size_t i = 0; i < h->phases.size(); ++i) one(i, true);
@@ -1236,16 +1236,43 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
     M.drop();
     M.key.resize(nseg);
     M.layouts.resize(nseg);
-    struct Ent {
-      int stage, kind, colour, K, seg;
-      size_t phase;
+    // vectors of one problem at a constant stride form one run (an item with
+    // nvec vectors, whose operators are read once for several of them)
+    struct Run {
+      const spand_s* h;
+      int64_t zoff, ldz;
+      int nvec;
     };
-    std::vector<Ent> ents;
-    for (int i = 0; i < nseg; ++i) {
+    std::vector<int> order(nseg);
+    for (int i = 0; i < nseg; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      if (segs[a].h != segs[b].h) return segs[a].h < segs[b].h;
+      return segs[a].zoff < segs[b].zoff;
+    });
+    std::vector<Run> runs;
+    for (int i : order) {
       const spand_s* h = segs[i].h;
       if (!h->factored) return fail(SPAND_ESTATE, "apply before a successful factorization");
       M.key[i] = {h, segs[i].zoff};
       M.layouts[i] = h->layout_id;
+      if (!runs.empty()) {
+        Run& q = runs.back();
+        const int64_t d = segs[i].zoff - q.zoff;
+        if (q.h == h && ((q.nvec == 1 && d >= h->n) || (q.nvec > 1 && d == q.ldz * q.nvec))) {
+          if (q.nvec == 1) q.ldz = d;
+          ++q.nvec;
+          continue;
+        }
+      }
+      runs.push_back({h, segs[i].zoff, (int64_t)h->n, 1});
+    }
+    struct Ent {
+      int stage, kind, colour, K, run;
+      size_t phase;
+    };
+    std::vector<Ent> ents;
+    for (int i = 0; i < (int)runs.size(); ++i) {
+      const spand_s* h = runs[i].h;
       for (size_t j = 0; j < h->phases.size(); ++j) {
         const Phase& ph = h->phases[j];
         ents.push_back({ph.stage, ph.kind, ph.colour, ph.K, i, j});
@@ -1268,11 +1295,15 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
       for (; e < ents.size() && ents[e].stage == h0.stage && ents[e].kind == h0.kind &&
              ents[e].colour == h0.colour && ents[e].K == h0.K;
            ++e) {
-        const spand_s* h = segs[ents[e].seg].h;
+        const Run& ru = runs[ents[e].run];
+        const spand_s* h = ru.h;
         const Phase& ph = h->phases[ents[e].phase];
         ApItem item;
         item.ops = nullptr;
-        item.zoff = segs[ents[e].seg].zoff;
+        item.zoff = ru.zoff;
+        item.ldz = ru.ldz;
+        item.nvec = ru.nvec;
+        item.pad = 0;
         item.count = ph.end - ph.begin;
         item.first = L.ntasks;
         // the descriptor base is the handle's table for the phase's kind
@@ -1287,8 +1318,9 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
         L.ntasks += item.count;
         L.max_m = std::max(L.max_m, ph.max_m);
         L.max_cols = std::max(L.max_cols, ph.max_cols);
-        L.flops += ph.flops;
-        L.bytes += ph.bytes;
+        L.max_nvec = std::max(L.max_nvec, ru.nvec);
+        L.flops += ph.flops * ru.nvec;
+        L.bytes += ph.bytes * ((ru.nvec + 3) / 4);  // operators read once per four vectors (at most)
       }
       L.nitems = (int)(items.size() - L.item0);
       M.launches.push_back(L);
@@ -1306,10 +1338,10 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
       P.run(kind, cs, L.flops, L.bytes, [&] {
         const ApItem* it = items + L.item0;
         if (L.kind == PH_INTERIOR)
-          launch_ap_interior(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, z, fwd, cs);
+          launch_ap_interior(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
         else if (L.kind == PH_SCALE)
-          launch_ap_scale(it, L.nitems, L.ntasks, L.K, L.max_m, z, fwd, cs);
-        else launch_ap_qe(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, z, fwd, cs);
+          launch_ap_scale(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_nvec, z, fwd, cs);
+        else launch_ap_qe(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
       });
     };
     for (const auto& L : M.launches) one(L, true);

@@ -312,7 +312,7 @@ struct MultiApply {
   std::vector<std::pair<const spand_s*, int64_t>> key;
   std::vector<uint64_t> layouts;
   struct Launch {
-    int kind, K, max_m, max_cols, nitems, ntasks;
+    int kind, K, max_m, max_cols, max_nvec, nitems, ntasks;
     size_t item0;
     double flops, bytes;
   };

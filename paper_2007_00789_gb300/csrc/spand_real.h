@@ -123,13 +123,14 @@ struct ApQE {
 };
 
 // A run of `count` operators of one problem (descriptors at ops, of the
-// launch's kind) applied to the vector z + zoff; in a launch the items are
-// sorted by `first`, the launch-wide index of their first operator.  One
-// launch can so cover the operators of several problems.
+// launch's kind) applied to the nvec vectors z + zoff + j * ldz; in a launch
+// the items are sorted by `first`, the launch-wide index of their first
+// operator.  One launch can so cover the operators of several problems and
+// several right-hand sides of each.
 struct ApItem {
   const void* ops;
-  int64_t zoff;
-  int count, first;
+  int64_t zoff, ldz;
+  int count, first, nvec, pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -157,13 +158,13 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, 
                  int max_segs, cudaStream_t s);
 
 // K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
-// over all nitems items (device array).
+// over all nitems items (device array); max_nvec: the most vectors of an item.
 void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,
-                        int max_cols, real_t* z, bool forward, cudaStream_t s);
-void launch_ap_scale(const ApItem* items, int nitems, int ntasks, int K, int max_m, real_t* z,
-                     bool forward, cudaStream_t s);
+                        int max_cols, int max_nvec, real_t* z, bool forward, cudaStream_t s);
+void launch_ap_scale(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_nvec,
+                     real_t* z, bool forward, cudaStream_t s);
 void launch_ap_qe(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_cols,
-                  real_t* z, bool forward, cudaStream_t s);
+                  int max_nvec, real_t* z, bool forward, cudaStream_t s);
 
 
 }  // namespace SPAND_NS

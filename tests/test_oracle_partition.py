@@ -101,3 +101,85 @@ def test_greedy_colouring_is_proper():
     col = P.greedy_colouring(list(range(prob.n)), adj)
     assert all(col[i] != col[j] for i in adj for j in adj[i])
     assert col[0] == 0 and col[1] == 1
+
+
+# ---- algebraic partition (no coordinates) ----
+
+def _path_graph(n):
+    rows, cols = [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+    rowptr = np.searchsorted(np.array(rows), np.arange(n + 1)).astype(np.int32)
+    return rowptr, np.array(cols, dtype=np.int32)
+
+
+def test_golden_graph_partition(golden_dir):
+    want = _read_golden(os.path.join(golden_dir, "partition_graph_path7_l3.txt"))
+    rowptr, colind = _path_graph(7)
+    tree = P.graph_nested_dissection(rowptr, colind, 3)
+    assert list(tree.node_of) == [6, 2, 5, 0, 4, 1, 3]
+    assert tree.reach[3] == (4, 5) and tree.reach[5] == (3, 4) and tree.reach[1] == (5, 6)
+    for k in range(3):
+        sc = P.stage_clusters(tree, k)
+        got = [(sc.level[key], sorted(int(v) for v in sc.members[key])) for key in sc.keys]
+        assert got == [(lv, sorted(vs)) for lv, vs in want[k]], (k, got)
+
+
+def _permuted(prob, seed):
+    """The same matrix with its vertices relabelled at random (coordinates dropped)."""
+    import scipy.sparse as sp
+    perm = np.random.default_rng(seed).permutation(prob.n)
+    A = prob.to_scipy()[perm][:, perm].tocsr()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("make,ell,seed", [
+    (lambda: si.laplacian_2d(20), 5, 0),
+    (lambda: si.laplacian_grid((9, 7, 6)), 5, 1),
+    (lambda: si.diffusion_grid((30, 11), seed=2), 6, 2),
+])
+def test_graph_partition_invariants(make, ell, seed):
+    A = _permuted(make(), seed)
+    rowptr, colind = A.indptr, A.indices
+    tree = P.graph_nested_dissection(rowptr, colind, ell)
+    n = A.shape[0]
+    assert (tree.node_of >= 0).all() and (tree.level_of >= 0).all()
+    # separators separate: no edge joins the two children's subtrees of any node
+    dmax = ell - 1
+
+    def under(i, node):
+        while P.node_depth(i) > P.node_depth(node):
+            i = (i - 1) // 2
+        return i == node
+    for node in range(2 ** dmax - 1):
+        lo, hi = 2 * node + 1, 2 * node + 2
+        in_lo = np.array([under(int(x), lo) for x in tree.node_of])
+        in_hi = np.array([under(int(x), hi) for x in tree.node_of])
+        for v in np.nonzero(in_lo)[0]:
+            assert not in_hi[colind[rowptr[v]:rowptr[v + 1]]].any()
+    # clusters: each live vertex once; stage k+1 clusters are unions of stage k ones;
+    # interiors of a stage are never adjacent
+    for k in range(ell):
+        sc = P.stage_clusters(tree, k)
+        cl = np.full(n, -1)
+        for ci, key in enumerate(sc.keys):
+            assert (cl[sc.members[key]] == -1).all()
+            cl[sc.members[key]] = ci
+        assert ((cl >= 0) == (tree.level_of >= k)).all()
+        inter = np.array([sc.level[key] == k for key in sc.keys])
+        for v in np.nonzero((cl >= 0) & inter[np.maximum(cl, 0)])[0]:
+            nb = colind[rowptr[v]:rowptr[v + 1]]
+            nb = nb[cl[nb] >= 0]
+            assert (~inter[cl[nb]] | (cl[nb] == cl[v])).all()
+        if k + 1 < ell:
+            nx = P.stage_clusters(tree, k + 1)
+            cl1 = np.full(n, -1)
+            for ci, key in enumerate(nx.keys):
+                cl1[nx.members[key]] = ci
+            for key in sc.keys:
+                if sc.level[key] > k:
+                    assert np.unique(cl1[sc.members[key]]).size == 1
