@@ -79,6 +79,13 @@ typedef struct {
                              results; meant for profilers that cannot replay graph nodes. */
   int32_t rrqr_threads;   /* threads per CTA of the on-chip RRQR: 256, 512 or 1024; 0 = the
                              library's choice.  Changes only the order of some FP sums. */
+  int32_t partition;      /* 0 = geometric nested dissection of the coordinates (algebraic when
+                             coords is NULL or dim is 0); 1 = algebraic nested dissection of the
+                             graph of A: breadth-first bisection, interfaces keyed by the
+                             subdomains their vertices reach (for general SPD input) */
+  int32_t prescale;       /* 1 = factor D^{-1/2} A D^{-1/2} (D = diag(A)) and precondition with
+                             D^{-1/2} M~ D^{-1/2}; SPAND_ENOTSPD at analyze if a diagonal entry is
+                             not positive; 0 = no prescaling (the default) */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */

@@ -32,6 +32,14 @@ int spand::ensure_device(spand_s* h) {
   CK(cudaMemcpy(h->d_colind, h->h_colind.data(), (size_t)h->nnz * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->d_val, h->h_val.data(), (size_t)h->nnz * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->d_pack, h->h_pack.data(), (size_t)h->nnz * 8, cudaMemcpyHostToDevice));
+  if (h->prescale) {
+    CK(cudaMalloc(&h->d_fval, nnz * 8));
+    CK(cudaMalloc(&h->d_scale, n * 8));
+    CK(cudaMemcpy(h->d_fval, h->h_fval.data(), (size_t)h->nnz * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_scale, h->h_scale.data(), n * 8, cudaMemcpyHostToDevice));
+  } else {
+    h->d_fval = h->d_val;
+  }
   return SPAND_OK;
 }
 
@@ -42,13 +50,22 @@ int factor_impl(spand_s* h, cudaStream_t s) {
 }
 
 // z = M r on FP64 vectors; an FP32 preconditioner is applied to an FP32 copy.
+// With diagonal prescaling z = S M~ S r, S = D^{-1/2}.
 int apply_any(spand_s* h, const double* r, double* z, cudaStream_t s) {
   if (!h->factored) return fail(SPAND_ESTATE, "spand_apply before a successful spand_factor");
-  if (h->precision == 0) return f64::apply(h, r, z, s);
+  if (h->precision == 0) {
+    if (!h->prescale) return f64::apply(h, r, z, s);
+    launch_scale(h->n, h->d_scale, r, z, s);
+    RET(f64::apply(h, z, z, s));
+    launch_scale(h->n, h->d_scale, z, z, s);
+    return SPAND_OK;
+  }
   if (!h->d_rf) CK(cudaMalloc(&h->d_rf, (size_t)h->n * sizeof(float)));
-  launch_d2f(h->n, r, h->d_rf, s);
+  if (h->prescale) launch_d2f_scaled(h->n, h->d_scale, r, h->d_rf, s);
+  else launch_d2f(h->n, r, h->d_rf, s);
   RET(f32::apply(h, h->d_rf, h->d_rf, s));
-  launch_f2d(h->n, h->d_rf, z, s);
+  if (h->prescale) launch_f2d_scaled(h->n, h->d_scale, h->d_rf, z, s);
+  else launch_f2d(h->n, h->d_rf, z, s);
   return SPAND_OK;
 }
 
@@ -186,6 +203,8 @@ void free_handle(spand_s* h) {
   cudaFree(h->d_colind);
   cudaFree(h->d_val);
   cudaFree(h->d_pack);
+  if (h->d_fval != h->d_val) cudaFree(h->d_fval);
+  cudaFree(h->d_scale);
   cudaFree(h->d_err);
   cudaFree(h->d_r);
   cudaFree(h->d_z);
@@ -211,8 +230,10 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   *out = nullptr;
   std::string err;
   if (validate_csr(A, err) != SPAND_OK) return fail(SPAND_EINVAL, err);
-  if (!coords) return fail(SPAND_EINVAL, "coords is NULL");
-  if (dim < 1 || dim > 3) return fail(SPAND_EINVAL, "dim must be 1, 2 or 3");
+  const bool algebraic = !coords || dim == 0 || (opts && opts->partition == 1);
+  if (opts && (opts->partition < 0 || opts->partition > 1))
+    return fail(SPAND_EINVAL, "partition must be 0 or 1");
+  if (!algebraic && (dim < 1 || dim > 3)) return fail(SPAND_EINVAL, "dim must be 1, 2 or 3");
   if (!(eps >= 0.0 && eps <= 1.0)) return fail(SPAND_EINVAL, "eps must lie in [0, 1]");
   if (nlevels < 1 || nlevels > 30) return fail(SPAND_EINVAL, "nlevels must be in [1, 30]");
   if (scheme < 0 || scheme > 2) return fail(SPAND_EINVAL, "unknown scheme");
@@ -246,7 +267,11 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
       return fail(SPAND_EINVAL, "rrqr_threads must be 0, 256, 512 or 1024");
     h->rrqr_threads = opts->rrqr_threads;
   }
-  int rc = build_tree(coords, A->n, dim, nlevels, h->tree, err);
+  if (opts && (opts->prescale < 0 || opts->prescale > 1)) return fail(SPAND_EINVAL, "prescale must be 0 or 1");
+  h->prescale = opts && opts->prescale == 1;
+  if (algebraic) h->dim = 0;
+  int rc = algebraic ? build_tree_graph(A->rowptr, A->colind, A->n, nlevels, h->tree, err)
+                     : build_tree(coords, A->n, dim, nlevels, h->tree, err);
   if (rc != SPAND_OK) return fail(rc, err);
   rc = build_stages(h->tree, A->rowptr, A->colind, h->skip, h->st, err);
   if (rc != SPAND_OK) return fail(rc, err);
@@ -296,6 +321,21 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   h->h_rowptr.assign(A->rowptr, A->rowptr + n + 1);
   h->h_colind.assign(A->colind, A->colind + A->nnz);
   h->h_val.assign(A->val, A->val + A->nnz);
+  if (h->prescale) {
+    // S = D^{-1/2}, D = diag(A); the factorization sees S A S
+    h->h_scale.assign(n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
+        if (A->colind[e] == i) {
+          if (!(A->val[e] > 0.0))
+            return fail(SPAND_ENOTSPD, "non-positive diagonal entry in row " + std::to_string(i));
+          h->h_scale[i] = 1.0 / std::sqrt(A->val[e]);
+        }
+    h->h_fval.resize(A->nnz);
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
+        h->h_fval[e] = h->h_scale[i] * A->val[e] * h->h_scale[A->colind[e]];
+  }
   *out = h.release();
   return SPAND_OK;
 }

@@ -134,6 +134,7 @@ struct Engine {
     v.rowptr = h->d_rowptr;
     v.colind = h->d_colind;
     v.val = h->d_val;
+    v.scale = h->prescale ? h->d_scale : nullptr;
     v.off = off;
     v.n = h->n;
     v.pad = 0;
@@ -215,14 +216,23 @@ struct Engine {
     as.reserve(L.refs.size());
     for (const auto& r : L.refs) as.push_back({segs[r.seg].h, segs[r.seg].off});
     const bool graph = !P.on;
+    const VSeg* vs = (const VSeg*)vseg.p;
+    bool scaled = false;
+    for (const auto& r : L.refs) scaled = scaled || segs[r.seg].h->prescale;
     if (precision == 0) {
-      P.run(KK_VEC, s, 0.0, 16.0 * entries(L), [&] { launch_seg_copy(chunks(L), L.nch(), R(), Z(), s); });
+      P.run(KK_VEC, s, 0.0, 16.0 * entries(L),
+            [&] { launch_seg_copy(chunks(L), L.nch(), vs, R(), Z(), s); });
       RET(f64::apply_multi(as.data(), (int)as.size(), Z(), ma, P, graph, s));
+      if (scaled)
+        P.run(KK_VEC, s, 0.0, 16.0 * entries(L),
+              [&] { launch_seg_rescale(chunks(L), L.nch(), vs, Z(), s); });
     } else {
       float* zf = (float*)vzf.p;
-      P.run(KK_VEC, s, 0.0, 12.0 * entries(L), [&] { launch_seg_d2f(chunks(L), L.nch(), R(), zf, s); });
+      P.run(KK_VEC, s, 0.0, 12.0 * entries(L),
+            [&] { launch_seg_d2f(chunks(L), L.nch(), vs, R(), zf, s); });
       RET(f32::apply_multi(as.data(), (int)as.size(), zf, ma, P, graph, s));
-      P.run(KK_VEC, s, 0.0, 12.0 * entries(L), [&] { launch_seg_f2d(chunks(L), L.nch(), zf, Z(), s); });
+      P.run(KK_VEC, s, 0.0, 12.0 * entries(L),
+            [&] { launch_seg_f2d(chunks(L), L.nch(), vs, zf, Z(), s); });
     }
     return SPAND_OK;
   }
@@ -810,18 +820,32 @@ int spand_apply_many(spand_t h, const double* r, double* z, int32_t nrhs, int64_
   std::vector<ApSeg> as(nrhs);
   for (int j = 0; j < nrhs; ++j) as[j] = {h, (int64_t)j * ld};
   const bool graph = !h->prof.on && !h->no_graph;
+  const double* sc = h->prescale ? h->d_scale : nullptr;  // z = S M~ S r when prescaled
   if (h->precision == 0) {
-    if (r != z)
+    if (sc) {
+      for (int j = 0; j < nrhs; ++j) launch_scale(h->n, sc, r + (size_t)j * ld, z + (size_t)j * ld, s);
+    } else if (r != z) {
       CK(cudaMemcpy2DAsync(z, (size_t)ld * 8, r, (size_t)ld * 8, (size_t)h->n * 8, nrhs,
                            cudaMemcpyDeviceToDevice, s));
-    return f64::apply_multi(as.data(), nrhs, z, E->ma, h->prof, graph, s);
+    }
+    RET(f64::apply_multi(as.data(), nrhs, z, E->ma, h->prof, graph, s));
+    if (sc)
+      for (int j = 0; j < nrhs; ++j) launch_scale(h->n, sc, z + (size_t)j * ld, z + (size_t)j * ld, s);
+    CK(cudaGetLastError());
+    return SPAND_OK;
   }
   // FP32 preconditioner: an FP32 copy of the columns (the padding rows are not touched)
   RET(E->vzf.ensure((size_t)nrhs * ld * sizeof(float)));
   float* zf = (float*)E->vzf.p;
-  for (int j = 0; j < nrhs; ++j) launch_d2f(h->n, r + (size_t)j * ld, zf + (size_t)j * ld, s);
+  for (int j = 0; j < nrhs; ++j) {
+    if (sc) launch_d2f_scaled(h->n, sc, r + (size_t)j * ld, zf + (size_t)j * ld, s);
+    else launch_d2f(h->n, r + (size_t)j * ld, zf + (size_t)j * ld, s);
+  }
   RET(f32::apply_multi(as.data(), nrhs, zf, E->ma, h->prof, graph, s));
-  for (int j = 0; j < nrhs; ++j) launch_f2d(h->n, zf + (size_t)j * ld, z + (size_t)j * ld, s);
+  for (int j = 0; j < nrhs; ++j) {
+    if (sc) launch_f2d_scaled(h->n, sc, zf + (size_t)j * ld, z + (size_t)j * ld, s);
+    else launch_f2d(h->n, zf + (size_t)j * ld, z + (size_t)j * ld, s);
+  }
   CK(cudaGetLastError());
   return SPAND_OK;
 }

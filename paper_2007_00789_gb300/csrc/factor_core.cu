@@ -401,7 +401,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
   if (fbytes) W.zero.push_back({fptr, fbytes});
   if (sbytes) W.zero.push_back({scr.p, sbytes});
   if (k == 0)
-    W.packs.push_back({h->d_val, h->d_pack, (real_t*)fptr, (real_t*)scr.p, h->pack_split, h->nnz});
+    W.packs.push_back({h->d_fval, h->d_pack, (real_t*)fptr, (real_t*)scr.p, h->pack_split, h->nnz});
   auto segc = [&](int c, int d) { return segcol_of(S.rowsegs[c], Ly.segcol[c], d); };
   int* d_err = d_cnt + 4 * ncl;
 

@@ -25,121 +25,130 @@ constexpr int kApWarps = kApThreads / 32;
 
 namespace cg = cooperative_groups;
 
-// Tiled matrix-vector products for NV vectors at once.  A CTA works on 32
-// outputs at a time (lane = output); its warps split the reduction dimension
-// and warp 0 adds the warps' partial sums from shared memory.  Each matrix
-// element loaded feeds NV FMAs (one per vector); with one vector, four
-// partial sums keep the FMA chain short.  The vectors sit in shared memory,
-// vector v at x + v * xs.
+// Matrix-vector products for NV vectors at once, written for memory-level
+// parallelism: the operators are read once from HBM, so each warp keeps many
+// independent coalesced loads in flight.  Each matrix element loaded feeds NV
+// FMAs (one per vector).  The vectors sit in shared memory, vector v at
+// x + v * xs.
 
 // out(r, v, sum_{c < C(rt)} M[r + c*ld] x_v[c]) for rows r in [r0, r1); ccap(rt)
-// bounds the columns a 32-row tile starting at rt needs (C for a full matrix,
-// rt + 32 for a lower-triangular one whose strict upper part is zero).
+// bounds the columns a 64-row tile starting at rt needs (C for a full matrix,
+// rt + 64 for a lower-triangular one whose strict upper part is zero).  A
+// warp reads columns of a 64-row tile (lane = rows rt+lane and rt+32+lane,
+// four columns per step: eight 128-byte loads in flight per lane pair), the
+// warps split the columns, and warp 0 and 1 add the warps' partial sums.
 template <int NV, class Cap, class Out>
 __device__ void gemv_n(const real_t* __restrict__ M, size_t ld, int r0, int r1, Cap ccap,
                        const real_t* __restrict__ x, int xs, real_t* red, Out out) {
-  constexpr int U = NV >= 4 ? 1 : 4 / NV;  // partial sums per vector
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int rt = r0; rt < r1; rt += 32) {
-    const int r = rt + lane;
+  for (int rt = r0; rt < r1; rt += 64) {
+    const int ra = rt + lane, rb = rt + 32 + lane;
+    const bool va = ra < r1, vb = rb < r1;
     const int C = ccap(rt);
-    const int per = (C + kApWarps - 1) / kApWarps;
+    const int per = (((C + kApWarps - 1) / kApWarps) + 3) & ~3;
     const int cb = warp * per, ce = min(C, cb + per);
-    real_t s[NV][U];
+    real_t sa[NV], sb[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
+    for (int v = 0; v < NV; ++v) sa[v] = sb[v] = 0.0;
+    const real_t* Ma = M + (va ? ra : r0);
+    const real_t* Mb = M + (vb ? rb : r0);
+    int c = cb;
+    for (; c + 3 < ce; c += 4) {
+      real_t a[4], b[4];
 #pragma unroll
-      for (int u = 0; u < U; ++u) s[v][u] = 0.0;
-    if (r < r1) {
-      const real_t* Mr = M + r;
-      int c = cb;
-      for (; c + U - 1 < ce; c += U) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const real_t a = Mr[(size_t)(c + u) * ld];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) s[v][u] = fma(a, x[v * xs + c + u], s[v][u]);
-        }
+      for (int u = 0; u < 4; ++u) {
+        a[u] = va ? Ma[(size_t)(c + u) * ld] : (real_t)0.0;
+        b[u] = vb ? Mb[(size_t)(c + u) * ld] : (real_t)0.0;
       }
-      for (; c < ce; ++c) {
-        const real_t a = Mr[(size_t)c * ld];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s[v][0] = fma(a, x[v * xs + c], s[v][0]);
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const real_t xv = x[v * xs + c + u];
+          sa[v] = fma(a[u], xv, sa[v]);
+          sb[v] = fma(b[u], xv, sb[v]);
+        }
+    }
+    for (; c < ce; ++c) {
+      const real_t a = va ? Ma[(size_t)c * ld] : (real_t)0.0;
+      const real_t b = vb ? Mb[(size_t)c * ld] : (real_t)0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        sa[v] = fma(a, x[v * xs + c], sa[v]);
+        sb[v] = fma(b, x[v * xs + c], sb[v]);
       }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      real_t t = s[v][0];
-#pragma unroll
-      for (int u = 1; u < U; ++u) t += s[v][u];
-      red[(v * kApWarps + warp) * 32 + lane] = t;
+      red[(v * kApWarps + warp) * 64 + lane] = sa[v];
+      red[(v * kApWarps + warp) * 64 + 32 + lane] = sb[v];
     }
     __syncthreads();
-    if (warp == 0 && r < r1) {
+    if (warp < 2) {
+      const int r = rt + warp * 32 + lane;
+      if (r < r1) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        real_t t = 0.0;
-        for (int w = 0; w < kApWarps; ++w) t += red[(v * kApWarps + w) * 32 + lane];
-        out(r, v, t);
+        for (int v = 0; v < NV; ++v) {
+          real_t t = 0.0;
+          for (int w = 0; w < kApWarps; ++w) t += red[(v * kApWarps + w) * 64 + warp * 32 + lane];
+          out(r, v, t);
+        }
       }
     }
     __syncthreads();
   }
 }
 
-// out(c, v, sum_{r in [rlo(ct), R)} M[r + c*ld] x_v[r]) for columns c in [c0, c1);
-// rlo(ct) is the first row a 32-column tile starting at ct needs (0 for a full
-// matrix, ct for the transpose of a lower-triangular one).
+// out(c, v, sum_{r in [rlo(c), R)} M[r + c*ld] x_v[r]) for columns c in [c0, c1);
+// rlo(c) is the first row column c needs (0 for a full matrix, c for the
+// transpose of a lower-triangular one).  A warp reduces four columns at a
+// time: its lanes read consecutive rows of each (coalesced, four loads in
+// flight per lane), then the partial sums are added across the warp.
 template <int NV, class Lo, class Out>
 __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
                        const real_t* __restrict__ x, int xs, real_t* red, Out out) {
-  constexpr int U = NV >= 4 ? 1 : 4 / NV;
+  (void)red;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int ct = c0; ct < c1; ct += 32) {
-    const int c = ct + lane;
-    const int rb0 = rlo(ct);
-    const int per = (R - rb0 + kApWarps - 1) / kApWarps;
-    const int rb = rb0 + warp * per, re = min(R, rb + per);
-    real_t s[NV][U];
+  for (int cq = c0 + 4 * warp; cq < c1; cq += 4 * kApWarps) {
+    real_t s[4][NV];
+    int lo4[4];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
+    for (int u = 0; u < 4; ++u) {
+      lo4[u] = cq + u < c1 ? rlo(cq + u) : R;
 #pragma unroll
-      for (int u = 0; u < U; ++u) s[v][u] = 0.0;
-    if (c < c1) {
-      const real_t* col = M + (size_t)c * ld;
-      int r = rb;
-      for (; r + U - 1 < re; r += U) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const real_t a = col[r + u];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) s[v][u] = fma(a, x[v * xs + r + u], s[v][u]);
-        }
-      }
-      for (; r < re; ++r) {
-        const real_t a = col[r];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s[v][0] = fma(a, x[v * xs + r], s[v][0]);
-      }
+      for (int v = 0; v < NV; ++v) s[u][v] = 0.0;
     }
+    const int rs = min(min(lo4[0], lo4[1]), min(lo4[2], lo4[3]));
+    for (int r = rs + lane; r < R; r += 32) {
+      real_t a[4];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      real_t t = s[v][0];
-#pragma unroll
-      for (int u = 1; u < U; ++u) t += s[v][u];
-      red[(v * kApWarps + warp) * 32 + lane] = t;
-    }
-    __syncthreads();
-    if (warp == 0 && c < c1) {
+      for (int u = 0; u < 4; ++u)
+        a[u] = (r >= lo4[u]) ? M[(size_t)(cq + u) * ld + r] : (real_t)0.0;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        real_t t = 0.0;
-        for (int w = 0; w < kApWarps; ++w) t += red[(v * kApWarps + w) * 32 + lane];
-        out(c, v, t);
+        const real_t xv = x[v * xs + r];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u][v] = fma(a[u], xv, s[u][v]);
       }
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real_t t = s[u][v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        s[u][v] = t;
+      }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cq + u < c1)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) out(cq + u, v, s[u][v]);
+    }
   }
+  __syncthreads();
 }
 
 // Every operator is applied by a thread-block cluster of K CTAs (K from the
@@ -171,7 +180,7 @@ __global__ void __launch_bounds__(kApThreads)
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
-  __shared__ real_t red[kApThreads * NV];
+  __shared__ real_t red[2 * kApThreads * NV];
   const int task = (int)(blockIdx.x / K);
   const ApItem it = find_item(items, nitems, task);
   const ApInterior t = ((const ApInterior*)it.ops)[task - it.first];
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(kApThreads)
     __syncthreads();
     if (forward) {
       // y = L_s^{-1} x, then z_s = y and z_w -= W_s y (column c of the panel row is W_s^T[:, c])
-      gemv_n<NV>(t.Linv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, m, red,
+      gemv_n<NV>(t.Linv, m, lo, hi, [&](int rt) { return min(m, rt + 64); }, xs, m, red,
                  [&](int r, int v, real_t val) { share(cl, K, ys + v * m, r, val); });
       cl.sync();
       for (int e = threadIdx.x; e < nv * (hi - lo); e += blockDim.x) {
@@ -230,7 +239,7 @@ __global__ void __launch_bounds__(kApThreads)
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
-  __shared__ real_t red[kApThreads * NV];
+  __shared__ real_t red[2 * kApThreads * NV];
   const int task = (int)(blockIdx.x / K);
   const ApItem it = find_item(items, nitems, task);
   const ApScale t = ((const ApScale*)it.ops)[task - it.first];
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(kApThreads)
     }
     cl.sync();  // every CTA has read z_p before any CTA overwrites part of it
     if (forward)
-      gemv_n<NV>(t.Zinv, m, lo, hi, [&](int rt) { return min(m, rt + 32); }, xs, m, red,
+      gemv_n<NV>(t.Zinv, m, lo, hi, [&](int rt) { return min(m, rt + 64); }, xs, m, red,
                  [&](int r, int v, real_t val) {
                    if (v < nv) zb[v * ldz + t.slots[r]] = val;
                  });
@@ -266,7 +275,7 @@ __global__ void __launch_bounds__(kApThreads)
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
   extern __shared__ real_t sh[];
-  __shared__ real_t red[kApThreads * NV];
+  __shared__ real_t red[2 * kApThreads * NV];
   const int task = (int)(blockIdx.x / K);
   const ApItem it = find_item(items, nitems, task);
   const ApQE t = ((const ApQE*)it.ops)[task - it.first];
@@ -329,8 +338,11 @@ __global__ void __launch_bounds__(kApThreads)
 
 }  // namespace
 
+// The dynamic shared memory a launch may use beyond the 48 KB default must be
+// granted per kernel; the static part (the partial-sum buffer) counts too, so
+// the grant is made for any dynamic size above 16 KB.
 static void smem_attr(const void* fn, int bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (bytes > 16 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 __global__ void k_copy_real(int n, const real_t* __restrict__ s, real_t* __restrict__ d) {
@@ -364,10 +376,12 @@ static void launch_ap(ApKernel kern, const ApItem* items, int nitems, int ntasks
 }
 
 // Vectors per pass for a launch whose items carry up to max_nvec vectors and
-// whose shared memory is per_vec bytes per vector: 1, 2 or 4.
+// whose shared memory is per_vec bytes per vector: 1, 2 or 4.  Several
+// vectors only while the CTA's shared memory stays under 96 KB, so that the
+// thread-block clusters of the single-vector launch shape stay schedulable.
 static int ap_vectors(int max_nvec, int per_vec) {
   int nv = max_nvec >= 4 ? 4 : (max_nvec >= 2 ? 2 : 1);
-  while (nv > 1 && (size_t)nv * per_vec > (size_t)200 * 1024) nv >>= 1;
+  while (nv > 1 && (size_t)nv * per_vec > (size_t)96 * 1024) nv >>= 1;
   return nv;
 }
 

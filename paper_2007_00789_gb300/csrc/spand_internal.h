@@ -20,11 +20,17 @@ namespace spand {
 // (coordinate below the cut) and 2i+2 (above); internal nodes are i < nint.
 struct Tree {
   int n = 0, dim = 0, nlevels = 0;
-  std::vector<double> coords;   // n x dim
-  std::vector<int> cut_dim;     // per internal node
-  std::vector<double> cut_val;  // per internal node
+  int algebraic = 0;            // 0: geometric bisection of coordinates; 1: of the graph of A
+  std::vector<double> coords;   // n x dim (geometric)
+  std::vector<int> cut_dim;     // per internal node (geometric)
+  std::vector<double> cut_val;  // per internal node (geometric)
   std::vector<int> node_of;     // vertex -> separator node or leaf
   std::vector<int> level_of;    // vertex -> level (leaves 0, root nlevels-1)
+  // algebraic: the reach of every vertex (leaves connected to it through
+  // vertices of lower level), CSR over vertices, ascending; width = the
+  // largest reach (>= 1)
+  std::vector<int> reach_ptr, reach;
+  int width = 1;
 };
 
 // Structure of one stage that does not depend on numerical ranks.
@@ -52,6 +58,9 @@ struct StageSym {
 
 int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err);
 // Cluster ids of every vertex at stage k (-1 if eliminated); returns #clusters.
+// Algebraic nested dissection of the (symmetric) CSR pattern.
+int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nlevels, Tree& t,
+                     std::string& err);
 int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster);
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
                  std::vector<StageSym>& st, std::string& err);
@@ -92,6 +101,7 @@ struct VSeg {
   const int32_t* rowptr;  // the segment's matrix (CSR, device)
   const int32_t* colind;
   const double* val;
+  const double* scale;    // D^{-1/2} of a prescaled problem (n entries), else null
   int64_t off;            // first entry of the segment in the concatenated vectors
   int n, pad;
 };
@@ -115,8 +125,17 @@ void launch_seg_step_p(const VChunk* ch, int nch, const VSegRef* refs, int nref,
                        const double* z, double* p, cudaStream_t s);
 void launch_seg_residual(const VChunk* ch, int nch, const double* b, const double* ax, double* r,
                          cudaStream_t s);
-void launch_seg_copy(const VChunk* ch, int nch, const double* src, double* dst, cudaStream_t s);
-void launch_seg_d2f(const VChunk* ch, int nch, const double* src, float* dst, cudaStream_t s);
-void launch_seg_f2d(const VChunk* ch, int nch, const float* src, double* dst, cudaStream_t s);
+// copies around an apply, scaled by the segment's D^{-1/2} where it has one
+void launch_seg_copy(const VChunk* ch, int nch, const VSeg* segs, const double* src, double* dst,
+                     cudaStream_t s);
+void launch_seg_rescale(const VChunk* ch, int nch, const VSeg* segs, double* dst, cudaStream_t s);
+void launch_seg_d2f(const VChunk* ch, int nch, const VSeg* segs, const double* src, float* dst,
+                    cudaStream_t s);
+void launch_seg_f2d(const VChunk* ch, int nch, const VSeg* segs, const float* src, double* dst,
+                    cudaStream_t s);
+// dst = sc .* src (and with an FP32 side), for the prescaled apply
+void launch_scale(int n, const double* sc, const double* src, double* dst, cudaStream_t s);
+void launch_d2f_scaled(int n, const double* sc, const double* src, float* dst, cudaStream_t s);
+void launch_f2d_scaled(int n, const double* sc, const float* src, double* dst, cudaStream_t s);
 
 }  // namespace spand

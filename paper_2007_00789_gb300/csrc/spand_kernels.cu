@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
 constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory per CTA we allow
 
 static void set_smem(const void* fn, int bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (bytes > 16 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s) {

@@ -98,6 +98,24 @@ __global__ void k_copy_vec(int n, const double* __restrict__ s, double* __restri
 inline int vec_blocks(int n) { return std::max(1, std::min((n + 255) / 256, 152 * 16)); }
 
 
+// dst = sc .* src (the diagonal prescaling of the preconditioner apply)
+__global__ void k_scale(int n, const double* __restrict__ sc, const double* __restrict__ s,
+                        double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = sc[i] * s[i];
+}
+
+__global__ void k_d2f_scaled(int n, const double* __restrict__ sc, const double* __restrict__ s,
+                             float* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = (float)(sc[i] * s[i]);
+}
+
+__global__ void k_f2d_scaled(int n, const double* __restrict__ sc, const float* __restrict__ s,
+                             double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = sc[i] * (double)s[i];
+}
+
 __global__ void k_d2f(int n, const double* __restrict__ s, float* __restrict__ d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = (float)s[i];
 }
@@ -196,22 +214,45 @@ __global__ void __launch_bounds__(kSegThreads)
   for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) r[i] = b[i] - ax[i];
 }
 
+// The copies around a preconditioner apply; a segment whose problem is
+// prescaled multiplies by its D^{-1/2} (g.scale) on the way.
 __global__ void __launch_bounds__(kSegThreads)
-    k_seg_copy(const VChunk* __restrict__ ch, const double* __restrict__ s, double* __restrict__ d) {
+    k_seg_copy(const VChunk* __restrict__ ch, const VSeg* __restrict__ segs,
+               const double* __restrict__ s, double* __restrict__ d) {
   const VChunk c = ch[blockIdx.x];
-  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = s[i];
+  const double* sc = segs[c.seg].scale;
+  const int64_t off = segs[c.seg].off;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x)
+    d[i] = sc ? sc[i - off] * s[i] : s[i];
 }
 
 __global__ void __launch_bounds__(kSegThreads)
-    k_seg_d2f(const VChunk* __restrict__ ch, const double* __restrict__ s, float* __restrict__ d) {
+    k_seg_rescale(const VChunk* __restrict__ ch, const VSeg* __restrict__ segs, double* __restrict__ d) {
   const VChunk c = ch[blockIdx.x];
-  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = (float)s[i];
+  const double* sc = segs[c.seg].scale;
+  if (!sc) return;
+  const int64_t off = segs[c.seg].off;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] *= sc[i - off];
 }
 
 __global__ void __launch_bounds__(kSegThreads)
-    k_seg_f2d(const VChunk* __restrict__ ch, const float* __restrict__ s, double* __restrict__ d) {
+    k_seg_d2f(const VChunk* __restrict__ ch, const VSeg* __restrict__ segs,
+              const double* __restrict__ s, float* __restrict__ d) {
   const VChunk c = ch[blockIdx.x];
-  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) d[i] = (double)s[i];
+  const double* sc = segs[c.seg].scale;
+  const int64_t off = segs[c.seg].off;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x)
+    d[i] = (float)(sc ? sc[i - off] * s[i] : s[i]);
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+    k_seg_f2d(const VChunk* __restrict__ ch, const VSeg* __restrict__ segs,
+              const float* __restrict__ s, double* __restrict__ d) {
+  const VChunk c = ch[blockIdx.x];
+  const double* sc = segs[c.seg].scale;
+  const int64_t off = segs[c.seg].off;
+  for (int64_t i = c.begin + threadIdx.x; i < c.end; i += blockDim.x)
+    d[i] = sc ? sc[i - off] * (double)s[i] : (double)s[i];
 }
 
 }  // namespace
@@ -287,14 +328,29 @@ void launch_seg_residual(const VChunk* ch, int nch, const double* b, const doubl
                          cudaStream_t s) {
   if (nch > 0) k_seg_residual<<<nch, kSegThreads, 0, s>>>(ch, b, ax, r);
 }
-void launch_seg_copy(const VChunk* ch, int nch, const double* src, double* dst, cudaStream_t s) {
-  if (nch > 0) k_seg_copy<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
+void launch_seg_copy(const VChunk* ch, int nch, const VSeg* segs, const double* src, double* dst,
+                     cudaStream_t s) {
+  if (nch > 0) k_seg_copy<<<nch, kSegThreads, 0, s>>>(ch, segs, src, dst);
 }
-void launch_seg_d2f(const VChunk* ch, int nch, const double* src, float* dst, cudaStream_t s) {
-  if (nch > 0) k_seg_d2f<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
+void launch_seg_rescale(const VChunk* ch, int nch, const VSeg* segs, double* dst, cudaStream_t s) {
+  if (nch > 0) k_seg_rescale<<<nch, kSegThreads, 0, s>>>(ch, segs, dst);
 }
-void launch_seg_f2d(const VChunk* ch, int nch, const float* src, double* dst, cudaStream_t s) {
-  if (nch > 0) k_seg_f2d<<<nch, kSegThreads, 0, s>>>(ch, src, dst);
+void launch_seg_d2f(const VChunk* ch, int nch, const VSeg* segs, const double* src, float* dst,
+                    cudaStream_t s) {
+  if (nch > 0) k_seg_d2f<<<nch, kSegThreads, 0, s>>>(ch, segs, src, dst);
+}
+void launch_seg_f2d(const VChunk* ch, int nch, const VSeg* segs, const float* src, double* dst,
+                    cudaStream_t s) {
+  if (nch > 0) k_seg_f2d<<<nch, kSegThreads, 0, s>>>(ch, segs, src, dst);
+}
+void launch_scale(int n, const double* sc, const double* src, double* dst, cudaStream_t s) {
+  k_scale<<<vec_blocks(n), 256, 0, s>>>(n, sc, src, dst);
+}
+void launch_d2f_scaled(int n, const double* sc, const double* src, float* dst, cudaStream_t s) {
+  k_d2f_scaled<<<vec_blocks(n), 256, 0, s>>>(n, sc, src, dst);
+}
+void launch_f2d_scaled(int n, const double* sc, const float* src, double* dst, cudaStream_t s) {
+  k_f2d_scaled<<<vec_blocks(n), 256, 0, s>>>(n, sc, src, dst);
 }
 
 }  // namespace spand

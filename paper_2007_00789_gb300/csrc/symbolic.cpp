@@ -123,7 +123,210 @@ static uint64_t vertex_key(const Tree& t, int v, int k) {
   return key;
 }
 
+// ---------------------------------------------------------------------------
+// Algebraic partition (input without coordinates).  The node at depth d
+// bisects its vertex set V by breadth-first distances in the subgraph induced
+// on V: a first sweep from the smallest vertex finds the far vertex (smallest
+// index at the largest distance), the second sweep's distances from it order
+// V by (distance, index) with unreached vertices last; the distance of the
+// median (position |V|/2) is the separator, smaller distances the lower child,
+// larger ones and unreached vertices the upper child (an unreached median:
+// empty separator, the reached vertices form the lower child).  Interfaces
+// are keyed by reach: the leaves connected to a separator vertex through
+// vertices of lower level; at stage k the key is the set of depth
+// nlevels-1-k ancestors of those leaves.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GraphBisector {
+  const int32_t* rowptr;
+  const int32_t* colind;
+  std::vector<int> stamp, dist;
+  std::vector<int> front, next;
+  int cur = 0;
+
+  // distances from root within the vertices stamped `cur` (-1: not reached)
+  void bfs(int root) {
+    dist[root] = 0;
+    front.assign(1, root);
+    int d = 0;
+    while (!front.empty()) {
+      next.clear();
+      ++d;
+      for (int v : front)
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+          const int u = colind[e];
+          if (stamp[u] == cur && dist[u] < 0) {
+            dist[u] = d;
+            next.push_back(u);
+          }
+        }
+      front.swap(next);
+    }
+  }
+
+  void bisect(const std::vector<int>& verts, std::vector<int>& sep, std::vector<int>& lo,
+              std::vector<int>& hi) {
+    ++cur;
+    for (int v : verts) {
+      stamp[v] = cur;
+      dist[v] = -1;
+    }
+    bfs(verts[0]);
+    int far = -1, r1 = -1;
+    for (int v : verts)
+      if (dist[v] > far) {
+        far = dist[v];
+        r1 = v;
+      }
+    for (int v : verts) dist[v] = -1;
+    bfs(r1);
+    const long big = 1L << 40;
+    std::vector<std::pair<long, int>> ord;
+    ord.reserve(verts.size());
+    for (int v : verts) ord.push_back({dist[v] < 0 ? big : (long)dist[v], v});
+    std::nth_element(ord.begin(), ord.begin() + verts.size() / 2, ord.end());
+    const long med = ord[verts.size() / 2].first;
+    sep.clear();
+    lo.clear();
+    hi.clear();
+    for (int v : verts) {
+      const long key = dist[v] < 0 ? big : (long)dist[v];
+      if (med == big) {
+        (key < big ? lo : hi).push_back(v);
+      } else if (key == med) {
+        sep.push_back(v);
+      } else {
+        (key < med ? lo : hi).push_back(v);
+      }
+    }
+  }
+};
+
+inline int ancestor_at(int i, int depth) {
+  while (node_depth(i) > depth) i = (i - 1) / 2;
+  return i;
+}
+
+}  // namespace
+
+int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nlevels, Tree& t,
+                     std::string& err) {
+  t.n = n;
+  t.dim = 0;
+  t.nlevels = nlevels;
+  t.algebraic = 1;
+  t.coords.clear();
+  t.node_of.assign(n, -1);
+  t.level_of.assign(n, -1);
+  const int dmax = nlevels - 1;
+  GraphBisector gb{rowptr, colind, std::vector<int>(n, 0), std::vector<int>(n, -1), {}, {}, 0};
+  struct Part { int node; std::vector<int> verts; };
+  std::vector<Part> frontier, next;
+  frontier.push_back({0, {}});
+  frontier[0].verts.resize(n);
+  std::iota(frontier[0].verts.begin(), frontier[0].verts.end(), 0);
+  std::vector<int> sep, lo, hi;
+  for (int depth = 0; depth <= dmax; ++depth) {
+    next.clear();
+    for (Part& pt : frontier) {
+      if (pt.verts.empty()) {
+        err = "empty nested-dissection subdomain at node " + std::to_string(pt.node);
+        return SPAND_EINVAL;
+      }
+      if (depth == dmax) {
+        for (int v : pt.verts) {
+          t.node_of[v] = pt.node;
+          t.level_of[v] = 0;
+        }
+        continue;
+      }
+      gb.bisect(pt.verts, sep, lo, hi);
+      for (int v : sep) {
+        t.node_of[v] = pt.node;
+        t.level_of[v] = dmax - depth;
+      }
+      next.push_back({2 * pt.node + 1, lo});
+      next.push_back({2 * pt.node + 2, hi});
+    }
+    frontier.swap(next);
+  }
+  // reach sets, by increasing level
+  std::vector<std::vector<int>> R(n);
+  for (int lvl = 1; lvl <= dmax; ++lvl)
+    for (int v = 0; v < n; ++v) {
+      if (t.level_of[v] != lvl) continue;
+      auto& s = R[v];
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        const int u = colind[e];
+        if (t.level_of[u] == 0) s.push_back(t.node_of[u]);
+        else if (t.level_of[u] < lvl) s.insert(s.end(), R[u].begin(), R[u].end());
+      }
+      std::sort(s.begin(), s.end());
+      s.erase(std::unique(s.begin(), s.end()), s.end());
+    }
+  t.reach_ptr.assign(n + 1, 0);
+  t.width = 1;
+  for (int v = 0; v < n; ++v) {
+    t.reach_ptr[v + 1] = t.reach_ptr[v] + (int)R[v].size();
+    t.width = std::max(t.width, (int)R[v].size());
+  }
+  t.reach.resize(t.reach_ptr[n]);
+  for (int v = 0; v < n; ++v) std::copy(R[v].begin(), R[v].end(), t.reach.begin() + t.reach_ptr[v]);
+  return SPAND_OK;
+}
+
+// Stage-k clusters of an algebraic tree: (node, sorted ancestor set padded
+// with -1) in lexicographic order.
+static int cluster_map_graph(const Tree& t, int k, std::vector<int>& cl,
+                             std::vector<int>* level_of_cluster) {
+  const int n = t.n, W = t.width;
+  const int dk = t.nlevels - 1 - k;
+  std::vector<int> live;
+  for (int v = 0; v < n; ++v)
+    if (t.level_of[v] >= k) live.push_back(v);
+  std::vector<int> keys((size_t)live.size() * (W + 1), -1);
+  std::vector<int> tmp;
+  for (size_t i = 0; i < live.size(); ++i) {
+    const int v = live[i];
+    int* row = &keys[i * (W + 1)];
+    row[0] = t.node_of[v];
+    if (t.level_of[v] > k) {
+      tmp.clear();
+      for (int e = t.reach_ptr[v]; e < t.reach_ptr[v + 1]; ++e) tmp.push_back(ancestor_at(t.reach[e], dk));
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      for (size_t j = 0; j < tmp.size(); ++j) row[1 + j] = tmp[j];
+    }
+  }
+  std::vector<int> order(live.size());
+  std::iota(order.begin(), order.end(), 0);
+  auto less = [&](int a, int b) {
+    const int* ra = &keys[(size_t)a * (W + 1)];
+    const int* rb = &keys[(size_t)b * (W + 1)];
+    for (int j = 0; j <= W; ++j)
+      if (ra[j] != rb[j]) return ra[j] < rb[j];
+    return live[a] < live[b];
+  };
+  std::sort(order.begin(), order.end(), less);
+  cl.assign(n, -1);
+  int ncl = -1;
+  if (level_of_cluster) level_of_cluster->clear();
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int a = order[i];
+    const bool same = i > 0 && std::equal(&keys[(size_t)a * (W + 1)], &keys[(size_t)a * (W + 1)] + W + 1,
+                                          &keys[(size_t)order[i - 1] * (W + 1)]);
+    if (!same) {
+      ++ncl;
+      if (level_of_cluster) level_of_cluster->push_back(t.level_of[live[a]]);
+    }
+    cl[live[a]] = ncl;
+  }
+  return ncl + 1;
+}
+
 int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
+  if (t.algebraic) return cluster_map_graph(t, k, cl, level_of_cluster);
   const int n = t.n;
   std::vector<std::pair<std::pair<int, uint64_t>, int>> items;
   items.reserve(n);

@@ -53,7 +53,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("skip", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("plain_launches", ctypes.c_int32), ("rrqr_threads", ctypes.c_int32)]
+                ("plain_launches", ctypes.c_int32), ("rrqr_threads", ctypes.c_int32),
+                ("partition", ctypes.c_int32), ("prescale", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -173,15 +174,19 @@ class Spand:
     def __init__(self, rowptr, colind, val, coords, nlevels: int, eps: float, scheme: int = 1,
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
                  max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0,
-                 plain_launches: bool = False, rrqr_threads: int = 0):
+                 plain_launches: bool = False, rrqr_threads: int = 0, partition: int = 0,
+                 prescale: bool = False):
+        """coords None (or partition=1): algebraic nested dissection of A's graph;
+        prescale: factor D^{-1/2} A D^{-1/2} and precondition with D^{-1/2} M~ D^{-1/2}."""
         L = load_library()
         self._lib = L
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         self._colind = np.ascontiguousarray(colind, dtype=np.int32)
         self._val = np.ascontiguousarray(val, dtype=np.float64)
-        coords = np.ascontiguousarray(coords, dtype=np.float64)
-        if coords.ndim == 1:
-            coords = coords[:, None]
+        if coords is not None:
+            coords = np.ascontiguousarray(coords, dtype=np.float64)
+            if coords.ndim == 1:
+                coords = coords[:, None]
         self.n = int(self._rowptr.size - 1)
         self.nnz = int(self._rowptr[-1])
         csr = _CSR(self.n, self.nnz, self._rowptr.ctypes.data, self._colind.ctypes.data,
@@ -189,10 +194,13 @@ class Spand:
         opts = _Opts(-1 if skip is None else int(skip), 0 if maxit is None else int(maxit),
                      0 if true_res_every is None else int(true_res_every),
                      -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
-                     int(precision), 1 if plain_launches else 0, int(rrqr_threads))
+                     int(precision), 1 if plain_launches else 0, int(rrqr_threads),
+                     int(partition), 1 if prescale else 0)
         h = ctypes.c_void_p()
-        _check(L.spand_analyze(ctypes.byref(csr), coords.ctypes.data, coords.shape[1], int(nlevels),
-                               float(eps), int(scheme), ctypes.byref(opts), ctypes.byref(h)))
+        cptr = None if coords is None else coords.ctypes.data
+        cdim = 0 if coords is None else coords.shape[1]
+        _check(L.spand_analyze(ctypes.byref(csr), cptr, cdim, int(nlevels), float(eps), int(scheme),
+                               ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
         self.nlevels = int(nlevels)
 

@@ -113,3 +113,36 @@ def test_batch_arguments_checked_without_gpu():
     batch.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("make,ell,seed", [
+    (lambda: si.laplacian_2d(20), 5, 1),
+    (lambda: si.laplacian_grid((9, 7, 6)), 5, 2),
+    (lambda: si.diffusion_grid((30, 11), seed=2), 6, 3),
+])
+def test_algebraic_partition_matches_oracle(make, ell, seed):
+    """Without coordinates the library partitions A's graph; cluster maps equal the oracle's."""
+    from paper_2007_00789_gb300 import spand as S
+    prob = make()
+    perm = np.random.default_rng(seed).permutation(prob.n)
+    A = prob.to_scipy()[perm][:, perm].tocsr()
+    A.sort_indices()
+    h = S.Spand(A.indptr, A.indices, A.data, None, ell, 1e-2, 1)
+    tree = P.graph_nested_dissection(A.indptr, A.indices, ell)
+    for k in range(ell):
+        sc = P.stage_clusters(tree, k)
+        want = np.full(prob.n, -1)
+        for ci, key in enumerate(sc.keys):
+            want[sc.members[key]] = ci
+        assert np.array_equal(h.cluster_map(k), want), k
+    h.close()
+
+
+def test_prescale_rejects_nonpositive_diagonal():
+    from paper_2007_00789_gb300 import spand as S
+    p = si.laplacian_2d(8)
+    val = p.val.copy()
+    val[np.nonzero(p.colind == 0)[0][0]] = 0.0
+    with pytest.raises(S.SpandError) as e:
+        S.Spand(p.rowptr, p.colind, val, p.coords, 3, 1e-2, 1, prescale=True)
+    assert e.value.code == S.SPAND_ENOTSPD

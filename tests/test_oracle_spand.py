@@ -13,7 +13,10 @@
   in eqs. trailing-1/2/3);
 * the Dirichlet Laplacian eigenpairs of §4.1.1 pin the input stencil, and the
   second-order forward error on them is below the first-order one;
-* PCG iteration counts are about halved (§4.1.2).
+* PCG iteration counts are about halved (§4.1.2);
+* general SPD input: with the algebraic partition, eps = 0 is still exact;
+  diagonal prescaling makes the factorization invariant to a diagonal
+  rescaling T A T and changes nothing on a constant diagonal.
 """
 import numpy as np
 import pytest
@@ -135,3 +138,55 @@ def test_bad_inputs():
     bad[5, 5] = -4.0
     with pytest.raises(S.NotSPDError):
         S.factor(bad.tocsr(), prob.coords, 3, 0.1)
+
+
+# ---- general SPD input: algebraic partition and diagonal prescaling ----
+
+def _relabel(prob, seed):
+    perm = np.random.default_rng(seed).permutation(prob.n)
+    A = prob.to_scipy()[perm][:, perm].tocsr()
+    A.sort_indices()
+    return A
+
+
+def test_algebraic_partition_exact_at_eps0():
+    """With eps = 0 the factorization is exact for any partition: M = A^{-1}, one PCG step."""
+    A = _relabel(si.diffusion_grid((11, 9), seed=4), 0)
+    F = S.factor(A, None, 4, 0.0, S.SECOND_ORDER_FULL)
+    Ad = A.toarray()
+    M = np.column_stack([S.apply(F, e) for e in np.eye(A.shape[0])])
+    assert np.abs(M @ Ad - np.eye(A.shape[0])).max() < 1e-10
+    b = si.rhs_normal(A.shape[0], seed=1)
+    res = S.pcg(lambda v: A @ v, lambda v: S.apply(F, v), b, 1e-12)
+    assert res.iters == 1
+
+
+def test_prescaling_removes_diagonal_scaling():
+    """Prescaled factorizations of A and of T A T (T diagonal, positive) coincide:
+    both factor the same matrix D^{-1/2} A D^{-1/2}, so ranks are identical and
+    M_{TAT} = T^{-1} M_A T^{-1}."""
+    import scipy.sparse as sp
+    prob = si.diffusion_3d(8, seed=5)
+    A = prob.to_scipy()
+    t = 10.0 ** np.random.default_rng(2).uniform(-3, 3, prob.n)
+    T = sp.diags(t)
+    B = (T @ A @ T).tocsr()
+    FA = S.factor(A, prob.coords, 5, 1e-2, S.SECOND_ORDER_FULL, prescale=True)
+    FB = S.factor(B, prob.coords, 5, 1e-2, S.SECOND_ORDER_FULL, prescale=True)
+    assert FA.stage_ranks == FB.stage_ranks
+    r = si.rhs_normal(prob.n, seed=3)
+    za = S.apply(FA, r / t) / t
+    zb = S.apply(FB, r)
+    assert np.abs(za - zb).max() <= 1e-10 * np.abs(zb).max()
+
+
+def test_prescaling_constant_diagonal_is_neutral():
+    """With a constant diagonal (the Poisson matrix) prescaling changes nothing but rounding."""
+    prob = si.laplacian_2d(16)
+    A = prob.to_scipy()
+    F0 = S.factor(A, prob.coords, 5, 1e-2, S.SECOND_ORDER_FULL)
+    F1 = S.factor(A, prob.coords, 5, 1e-2, S.SECOND_ORDER_FULL, prescale=True)
+    assert F0.stage_ranks == F1.stage_ranks
+    r = si.rhs_normal(prob.n, seed=0)
+    z0, z1 = S.apply(F0, r), S.apply(F1, r)
+    assert np.abs(z0 - z1).max() <= 1e-12 * np.abs(z0).max()
