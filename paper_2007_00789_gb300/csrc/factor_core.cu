@@ -24,6 +24,8 @@
 namespace spand {
 namespace SPAND_NS {
 
+int plan_multi(const ApSeg* segs, int nseg, MultiApply& M, cudaStream_t s);
+
 namespace {
 
 struct ApInteriorP {
@@ -908,17 +910,7 @@ int upload_apply_plan(Run& R, cudaStream_t s) {
   RET(h->farena.alloc(std::max<size_t>(R.api.size() * sizeof(ApInterior), 16), &pa));
   RET(h->farena.alloc(std::max<size_t>(R.aps.size() * sizeof(ApScale), 16), &ps));
   RET(h->farena.alloc(std::max<size_t>(R.apq.size() * sizeof(ApQE), 16), &pq));
-  void* pit = nullptr;
-  RET(h->farena.alloc(std::max<size_t>(R.phases.size() * sizeof(ApItem), 16), &pit));
   const int* dpool = (const int*)pp;
-  std::vector<ApItem> items(R.phases.size());
-  for (size_t i = 0; i < R.phases.size(); ++i) {
-    const Phase& ph = R.phases[i];
-    const void* base = ph.kind == PH_INTERIOR ? (const void*)((const ApInterior*)pa + ph.begin)
-                       : ph.kind == PH_SCALE  ? (const void*)((const ApScale*)ps + ph.begin)
-                                              : (const void*)((const ApQE*)pq + ph.begin);
-    items[i] = {base, 0, 0, ph.end - ph.begin, 0, 1, 0};
-  }
   std::vector<ApInterior> vi(R.api.size());
   for (size_t i = 0; i < R.api.size(); ++i) {
     const auto& a = R.api[i];
@@ -937,10 +929,7 @@ int upload_apply_plan(Run& R, cudaStream_t s) {
   if (!vi.empty()) CK(cudaMemcpyAsync(pa, vi.data(), vi.size() * sizeof(ApInterior), cudaMemcpyHostToDevice, s));
   if (!vs.empty()) CK(cudaMemcpyAsync(ps, vs.data(), vs.size() * sizeof(ApScale), cudaMemcpyHostToDevice, s));
   if (!vq.empty()) CK(cudaMemcpyAsync(pq, vq.data(), vq.size() * sizeof(ApQE), cudaMemcpyHostToDevice, s));
-  if (!items.empty())
-    CK(cudaMemcpyAsync(pit, items.data(), items.size() * sizeof(ApItem), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
-  h->d_items = pit;
   h->d_api = pa;
   h->d_aps = ps;
   h->d_apq = pq;
@@ -1161,6 +1150,9 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     RET(upload_apply_plan(runs[i], s));
     hs[i]->launches = launches;
     hs[i]->factored = true;
+    // the plan of the problem's own apply, so that applying allocates nothing
+    ApSeg seg{hs[i], 0};
+    RET(plan_multi(&seg, 1, hs[i]->self_ma, s));
   }
   CK(cudaGetLastError());
   G.valid = capture;
@@ -1176,58 +1168,19 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
 
 int factor(spand_s* h, cudaStream_t s) { return factor_group(&h, 1, h->fg, h->prof, s); }
 
-int apply_launches(spand_s* h, const real_t* r, real_t* z, cudaStream_t s);
-
-// The whole apply as one CUDA graph (built on first use for these vectors),
-// or as plain launches while profiling.
+// The apply of one problem: the merged apply over that problem alone (one
+// launch per phase; with graphs, the cluster-size groups of a phase run as
+// parallel graph branches).
 int apply(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
-  if (h->prof.on || h->no_graph) return apply_launches(h, r, z, s);
-  if (!(h->apply_exec && h->apply_r == (const void*)r && h->apply_z == (void*)z)) {
-    if (h->apply_exec) cudaGraphExecDestroy(h->apply_exec);
-    h->apply_exec = nullptr;
-    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = apply_launches(h, r, z, h->cap_stream);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
-    RET(rc);
-    CK(ce);
-    const cudaError_t ie = cudaGraphInstantiate(&h->apply_exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ie);
-    h->apply_r = r;
-    h->apply_z = z;
-  }
-  CK(cudaGraphLaunch(h->apply_exec, s));
-  return SPAND_OK;
+  if (r != z)
+    h->prof.run(KK_VEC, s, 0.0, 2.0 * sizeof(real_t) * h->n, [&] { launch_copy_real(h->n, r, z, s); });
+  ApSeg seg{h, 0};
+  return apply_multi(&seg, 1, z, h->self_ma, h->prof, !h->no_graph, s);
 }
 
-int apply_launches(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
-  Prof& P = h->prof;
-  const int n = h->n;
-  if (r != z) P.run(KK_VEC, s, 0.0, 2.0 * sizeof(real_t) * n, [&] { launch_copy_real(n, r, z, s); });
-  const ApItem* items = (const ApItem*)h->d_items;
-  auto one = [&](size_t i, bool fwd) {
-    const Phase& ph = h->phases[i];
-    const int nt = ph.end - ph.begin;
-    const int kind = ph.kind == PH_INTERIOR ? KK_AP_INTERIOR : ph.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
-    P.run(kind, s, ph.flops, ph.bytes, [&] {
-      if (ph.kind == PH_INTERIOR)
-        launch_ap_interior(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, 1, z, fwd, s);
-      else if (ph.kind == PH_SCALE)
-        launch_ap_scale(items + i, 1, nt, ph.K, ph.max_m, 1, z, fwd, s);
-      else launch_ap_qe(items + i, 1, nt, ph.K, ph.max_m, ph.max_cols, 1, z, fwd, s);
-    });
-  };
-  for (size_t i = 0; i < h->phases.size(); ++i) one(i, true);
-  for (size_t i = h->phases.size(); i-- > 0;) one(i, false);
-  CK(cudaGetLastError());
-  return SPAND_OK;
-}
-
-// Merged apply over several problems (see apply_multi in spand_handle.h).
-int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, bool graph,
-                cudaStream_t s) {
+// The launch plan of a merged apply (rebuilt when the problems, their
+// offsets or their factorizations changed).
+int plan_multi(const ApSeg* segs, int nseg, MultiApply& M, cudaStream_t s) {
   bool same = (int)M.key.size() == nseg;
   for (int i = 0; same && i < nseg; ++i)
     same = M.key[i].first == segs[i].h && M.key[i].second == segs[i].zoff &&
@@ -1291,6 +1244,8 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
       const Ent& h0 = ents[e];
       L.kind = h0.kind;
       L.K = h0.K;
+      L.stage = h0.stage;
+      L.colour = h0.colour;
       L.item0 = items.size();
       for (; e < ents.size() && ents[e].stage == h0.stage && ents[e].kind == h0.kind &&
              ents[e].colour == h0.colour && ents[e].K == h0.K;
@@ -1331,33 +1286,72 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
                          cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // the host table must outlive the copy
   }
+  return SPAND_OK;
+}
+
+// Merged apply over several problems (see apply_multi in spand_handle.h).
+int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, bool graph,
+                cudaStream_t s) {
+  RET(plan_multi(segs, nseg, M, s));
   const ApItem* items = (const ApItem*)M.items.p;
-  auto launch_all = [&](cudaStream_t cs) {
-    auto one = [&](const MultiApply::Launch& L, bool fwd) {
-      const int kind = L.kind == PH_INTERIOR ? KK_AP_INTERIOR : L.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
-      P.run(kind, cs, L.flops, L.bytes, [&] {
-        const ApItem* it = items + L.item0;
-        if (L.kind == PH_INTERIOR)
-          launch_ap_interior(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
-        else if (L.kind == PH_SCALE)
-          launch_ap_scale(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_nvec, z, fwd, cs);
-        else launch_ap_qe(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
-      });
+  auto one = [&](const MultiApply::Launch& L, bool fwd, cudaStream_t cs) {
+    const int kind = L.kind == PH_INTERIOR ? KK_AP_INTERIOR : L.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
+    P.run(kind, cs, L.flops, L.bytes, [&] {
+      const ApItem* it = items + L.item0;
+      if (L.kind == PH_INTERIOR)
+        launch_ap_interior(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
+      else if (L.kind == PH_SCALE)
+        launch_ap_scale(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_nvec, z, fwd, cs);
+      else launch_ap_qe(it, L.nitems, L.ntasks, L.K, L.max_m, L.max_cols, L.max_nvec, z, fwd, cs);
+    });
+  };
+  // groups of consecutive launches with equal (stage, kind, colour): independent
+  std::vector<std::pair<size_t, size_t>> groups;
+  for (size_t i = 0; i < M.launches.size();) {
+    size_t j = i + 1;
+    const auto& a = M.launches[i];
+    while (j < M.launches.size() && M.launches[j].stage == a.stage && M.launches[j].kind == a.kind &&
+           M.launches[j].colour == a.colour)
+      ++j;
+    groups.push_back({i, j});
+    i = j;
+  }
+  auto launch_all = [&](cudaStream_t cs, bool forked) {
+    auto group = [&](size_t b, size_t e, bool fwd) {
+      if (!forked || e - b == 1) {
+        for (size_t i = b; i < e; ++i) one(M.launches[i], fwd, cs);
+        return;
+      }
+      cudaEventRecord(M.fork, cs);
+      const int nb = (int)std::min<size_t>(e - b, MultiApply::kSide);
+      for (int q = 0; q < nb; ++q) cudaStreamWaitEvent(M.side[q], M.fork, 0);
+      for (size_t i = b; i < e; ++i) one(M.launches[i], fwd, M.side[(i - b) % MultiApply::kSide]);
+      for (int q = 0; q < nb; ++q) {
+        cudaEventRecord(M.join[q], M.side[q]);
+        cudaStreamWaitEvent(cs, M.join[q], 0);
+      }
     };
-    for (const auto& L : M.launches) one(L, true);
-    for (auto it = M.launches.rbegin(); it != M.launches.rend(); ++it) one(*it, false);
+    for (const auto& g : groups) group(g.first, g.second, true);
+    for (auto it = groups.rbegin(); it != groups.rend(); ++it) group(it->first, it->second, false);
   };
   if (!graph || P.on) {
-    launch_all(s);
+    launch_all(s, false);
     CK(cudaGetLastError());
     return SPAND_OK;
+  }
+  if (!M.fork) {
+    CK(cudaEventCreateWithFlags(&M.fork, cudaEventDisableTiming));
+    for (int q = 0; q < MultiApply::kSide; ++q) {
+      CK(cudaStreamCreateWithFlags(&M.side[q], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&M.join[q], cudaEventDisableTiming));
+    }
   }
   if (!(M.exec && M.gz == (const void*)z)) {
     if (M.exec) cudaGraphExecDestroy(M.exec);
     M.exec = nullptr;
     if (!M.cap_stream) CK(cudaStreamCreateWithFlags(&M.cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(M.cap_stream, cudaStreamCaptureModeThreadLocal));
-    launch_all(M.cap_stream);
+    launch_all(M.cap_stream, true);
     cudaGraph_t g = nullptr;
     const cudaError_t le = cudaGetLastError();
     const cudaError_t ce = cudaStreamEndCapture(M.cap_stream, &g);

@@ -313,6 +313,7 @@ struct MultiApply {
   std::vector<uint64_t> layouts;
   struct Launch {
     int kind, K, max_m, max_cols, max_nvec, nitems, ntasks;
+    int stage, colour;  // launches of equal (stage, kind, colour) are independent
     size_t item0;
     double flops, bytes;
   };
@@ -321,6 +322,11 @@ struct MultiApply {
   cudaGraphExec_t exec = nullptr;
   const void* gz = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // side streams of the captured graph: the independent launches of one
+  // logical phase (its cluster-size groups) become parallel graph nodes
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
   void drop() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -334,6 +340,14 @@ struct MultiApply {
     items.release();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
+    for (int i = 0; i < kSide; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+      side[i] = nullptr;
+      join[i] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
   }
 };
 
@@ -375,7 +389,6 @@ struct spand_s {
   void* d_api = nullptr;  // apply descriptors of the handle's precision
   void* d_aps = nullptr;
   void* d_apq = nullptr;
-  void* d_items = nullptr;  // one apply item per phase (the handle's own apply)
   int precision = 0;      // 0: FP64 factor and apply; 1: FP32 factor and apply (PCG stays FP64)
   float* d_rf = nullptr;  // FP32 copy of the vector an FP32 apply works on
   int64_t nnz_factor = 0;
@@ -397,20 +410,16 @@ struct spand_s {
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own
   uint64_t layout_id = 0;     // new value at every full factorization (arena layout changes)
   cudaStream_t cap_stream = nullptr;  // capture needs a stream other than the legacy one
-  cudaGraphExec_t apply_exec = nullptr;
+  spand::MultiApply self_ma;  // the apply plan (and graph) of this problem alone
   bool no_graph = false;  // plain launches only (set by the allocation-free PCG)
-  const void* apply_r = nullptr;
-  void* apply_z = nullptr;
   void drop_graphs() {
     fg.drop();
-    if (apply_exec) cudaGraphExecDestroy(apply_exec);
-    apply_exec = nullptr;
-    apply_r = nullptr;
-    apply_z = nullptr;
+    self_ma.drop();
   }
   void free_graphs() {
     drop_graphs();
     fg.release();
+    self_ma.release();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
   }
