@@ -244,7 +244,7 @@ struct StageLayout {
 
 // Whether a cluster of cs CTAs with the largest shared-memory slice can be resident.
 bool cluster_ok(spand_s* h, int cs) {
-  if (h->rrqr_path == 1 || (h->rrqr_path == 2 && cs > 8)) return false;
+  if (h->rrqr_path == 1 || h->rrqr_path == 3 || (h->rrqr_path == 2 && cs > 8)) return false;
   int lc = 0;
   while ((1 << lc) < cs) ++lc;
   int& st = h->cluster_state[sizeof(real_t) == 4 ? 1 : 0][lc];
@@ -550,6 +550,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         t.rank = d_cnt + ncl;
         t.nref = d_cnt + 2 * ncl;
         t.flag = d_cnt + 3 * ncl;
+        t.err = d_err;
         t.eps = h->eps;
         t.scheme = h->scheme;
         t.id = p;
@@ -597,6 +598,9 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
           const int cs = 1 << (b - 1);
           if (rrqr_cluster_active(cs, bytes_b, thr) <= 0) thr = 256;
         }
+        // too wide for a cluster: spread over several CTAs of a cooperative
+        // launch (bucket 6), unless the single-CTA streamed kernel is asked for
+        if ((b == 0 && h->rrqr_path != 1) || h->rrqr_path == 3) b = 6;
         auto& g = W.qr[{col, b * 4096 + thr}];
         g.threads = thr;
         g.bucket = b;
@@ -607,6 +611,9 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         g.smem = std::max(g.smem, bytes_b);
         if (b == 0 && rrqr_smem_bytes(g.max_m, g.max_cols, g.max_segs) > 220 * 1024)
           return fail(SPAND_ENOMEM, "interface block too wide for the RRQR workspace (stage " +
+                                        std::to_string(k) + ")");
+        if (b == 6 && rrqr_grid_smem_bytes(m, 32, t.nseg_max) > 200 * 1024)
+          return fail(SPAND_ENOMEM, "interface too tall for the multi-CTA RRQR (stage " +
                                         std::to_string(k) + ")");
       }
     }
@@ -625,6 +632,16 @@ struct StageBlob {
   size_t e, inv, fq, merge, ti, tiles, contr, zc, lt, rt, mi, id, seg, ints;
   PotrfPlan pint, pz;
   std::vector<size_t> qr;
+  // multi-CTA QR launches: grid-task arrays (patched with workspace pointers
+  // once the blob's device address is known) and the zeroed workspace
+  struct GridLaunch {
+    size_t off;        // RRQRGridTask array in the blob
+    int ntasks, nctas, smem;
+    size_t group;      // index of the QrGroup
+  };
+  std::vector<GridLaunch> grid;
+  std::vector<std::vector<size_t>> grid_ws;  // per launch: workspace int offset of each task
+  size_t ws = 0, ws_ints = 0;
 };
 
 StageBlob pack_blob(StageWork& W, Blob& blob) {
@@ -645,10 +662,60 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
   o.rt = blob.add(W.rtrsm);
   o.mi = blob.add(W.mirror);
   o.id = blob.add(W.ident);
-  for (auto& kv : W.qr) o.qr.push_back(blob.add(kv.second.tasks));
+  size_t gi = 0;
+  for (auto& kv : W.qr) {
+    const auto& g = kv.second;
+    o.qr.push_back(blob.add(g.tasks));
+    if (g.bucket == 6) {
+      // at most one CTA per SM per launch; tasks share the SMs by their work m x ncols
+      for (size_t t0 = 0; t0 < g.tasks.size(); t0 += kNumSMs) {
+        const size_t t1 = std::min(g.tasks.size(), t0 + (size_t)kNumSMs);
+        double wsum = 0.0;
+        for (size_t i = t0; i < t1; ++i) wsum += (double)g.tasks[i].m * g.tasks[i].ncols_max;
+        const int spare = kNumSMs - (int)(t1 - t0);
+        std::vector<RRQRGridTask> gts;
+        std::vector<size_t> wsoff;
+        int cta = 0, smem = 0;
+        for (size_t i = t0; i < t1; ++i) {
+          const RRQRTask& t = g.tasks[i];
+          const double w = (double)t.m * t.ncols_max;
+          int nc = 1 + (wsum > 0.0 ? (int)(spare * w / wsum) : 0);
+          nc = std::max(1, std::min(nc, (t.ncols_max + 31) / 32));  // at least 32 columns per CTA
+          RRQRGridTask gt;
+          gt.t = t;
+          gt.ws = nullptr;
+          gt.cta0 = cta;
+          gt.ncta = nc;
+          gts.push_back(gt);
+          wsoff.push_back(o.ws_ints);
+          o.ws_ints += qr_grid_ws_ints(nc);
+          cta += nc;
+          smem = std::max(smem, rrqr_grid_smem_bytes(t.m, (t.ncols_max + nc - 1) / nc, t.nseg_max));
+        }
+        StageBlob::GridLaunch gl;
+        gl.off = blob.add(gts);
+        gl.ntasks = (int)gts.size();
+        gl.nctas = cta;
+        gl.smem = smem;
+        gl.group = gi;
+        o.grid.push_back(gl);
+        o.grid_ws.push_back(wsoff);
+      }
+    }
+    ++gi;
+  }
   o.seg = blob.add(W.qr_segs);
   o.ints = blob.add(W.ints);
+  o.ws = blob.add(std::vector<int>(std::max<size_t>(o.ws_ints, 4), 0));
   return o;
+}
+
+// The grid tasks' workspace pointers, once the blob sits at device address D.
+void patch_grid(const StageBlob& o, Blob& blob, char* D) {
+  for (size_t L = 0; L < o.grid.size(); ++L) {
+    RRQRGridTask* gt = (RRQRGridTask*)(blob.h.data() + o.grid[L].off);
+    for (int i = 0; i < o.grid[L].ntasks; ++i) gt[i].ws = (int*)(D + o.ws) + o.grid_ws[L][i];
+  }
 }
 
 // All launches of one stage on stream cs; D: the uploaded blob, cnt: the live
@@ -719,20 +786,36 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
       [&] { launch_copy((const CopyTask*)(D + O.mi), (int)W.mirror.size(), cs); });
   run(KK_SCALE_COPY, W.ident.size(), 0.0, potrf_bytes(W.ident) / 2,
       [&] { launch_set_identity((const PotrfTask*)(D + O.id), (int)W.ident.size(), cs); });
+  if (O.ws_ints) CK(cudaMemsetAsync(D + O.ws, 0, O.ws_ints * sizeof(int), cs));
   size_t gi = 0;
+  cudaError_t gerr = cudaSuccess;
   for (auto& kv : W.qr) {
     const auto& g = kv.second;
     const int b = g.bucket;
-    const size_t off = O.qr[gi++];
-    run(KK_RRQR, g.tasks.size(), 0.0, 0.0, [&] {
-      if (b == 0)
-        launch_rrqr((const RRQRTask*)(D + off), (int)g.tasks.size(), (const RRQRSeg*)(D + O.seg),
-                    g.max_m, g.max_cols, g.max_segs, cs);
-      else
-        launch_rrqr_cluster((const RRQRTask*)(D + off), (int)g.tasks.size(),
-                            (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, g.threads, cs);
-    });
+    const size_t off = O.qr[gi];
+    if (b == 6) {
+      for (const auto& gl : O.grid) {
+        if (gl.group != gi) continue;
+        run(KK_RRQR, (size_t)gl.ntasks, 0.0, 0.0, [&] {
+          const cudaError_t e = launch_rrqr_grid((const RRQRGridTask*)(D + gl.off), gl.ntasks,
+                                                 gl.nctas, (const RRQRSeg*)(D + O.seg), gl.smem, cs);
+          if (e != cudaSuccess && gerr == cudaSuccess) gerr = e;
+        });
+      }
+    } else {
+      run(KK_RRQR, g.tasks.size(), 0.0, 0.0, [&] {
+        if (b == 0)
+          launch_rrqr((const RRQRTask*)(D + off), (int)g.tasks.size(), (const RRQRSeg*)(D + O.seg),
+                      g.max_m, g.max_cols, g.max_segs, cs);
+        else
+          launch_rrqr_cluster((const RRQRTask*)(D + off), (int)g.tasks.size(),
+                              (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, g.threads, cs);
+      });
+    }
+    ++gi;
   }
+  if (gerr != cudaSuccess)
+    return fail(SPAND_ECUDA, std::string("multi-CTA RRQR launch: ") + cudaGetErrorString(gerr));
   CK(cudaGetLastError());
   return SPAND_OK;
 }
@@ -971,6 +1054,9 @@ int factor_replay(spand_s* const* hs, int count, FactorGroup& G, cudaStream_t s)
     for (size_t j = 0; j < g.who.size(); ++j) {
       const int ncl = g.ncl[j];
       const int* c = hp + g.ioff[j];
+      if (c[4 * ncl + 1] != 0)
+        return fail(SPAND_ECUDA, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
+                                     std::to_string(k) + ")");
       if (c[4 * ncl] != 0)
         return fail(SPAND_ENOTSPD, "non-positive Cholesky pivot in problem " +
                                        std::to_string(g.who[j]) + " at stage " + std::to_string(k) +
@@ -1089,6 +1175,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       RET(G.tables.ensure(blob.h.size() + 16));
       D = G.tables.p;
     }
+    patch_grid(O, blob, D);
     CK(cudaMemcpyAsync(D, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
     // launches go to the capture stream (recorded into the stage graph) or to s
     cudaStream_t cs = s;
@@ -1128,6 +1215,12 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     CK(cudaStreamSynchronize(s));
     for (size_t j = 0; j < who.size(); ++j) {
       const int* c = hp + ioffs[j];
+      if (c[4 * ncls[j] + 1] != 0) {
+        for (int i = 0; i < count; ++i) hs[i]->factored = false;
+        G.drop();
+        return fail(SPAND_ECUDA, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
+                                     std::to_string(k) + ")");
+      }
       if (c[4 * ncls[j]] != 0) {
         for (int i = 0; i < count; ++i) hs[i]->factored = false;
         G.drop();

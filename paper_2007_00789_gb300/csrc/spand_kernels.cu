@@ -579,6 +579,348 @@ __global__ void __launch_bounds__(kQrThreads)
 }
 
 // ---------------------------------------------------------------------------
+// The same QR spread over several CTAs that synchronise through global
+// memory (one cooperative launch, all CTAs resident): for interface blocks
+// too large for the shared memory of a thread-block cluster.  CTA k of a
+// task owns a contiguous slice of its columns; per step every CTA publishes
+// its best and second-best candidate, one barrier, every CTA merges the
+// candidates, reads the pivot column from global memory and forms v itself,
+// the owner records v and tau, and every CTA updates its own columns.  The
+// owner stores the R entries into the pivot column one barrier later, once
+// every CTA has read it.  Each column is processed by one warp exactly as in
+// k_rrqr, so the results equal k_rrqr's bit for bit.  Barrier waits are
+// bounded: a wait that runs out raises the task's abort flag and the
+// problem's error word, and every CTA of the task leaves.
+// ---------------------------------------------------------------------------
+constexpr long kQrGridSpin = 1L << 24;  // about a second of polling per barrier
+
+struct GridSlot {  // one CTA's candidates of one step (6 ints)
+  double best, second;
+  int idx, pad;
+};
+
+__device__ __forceinline__ bool qr_grid_barrier(int* ctr, int* abort, int target) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(ctr, 1);
+    int ok = 1;
+    long it = 0;
+    while (*(volatile int*)ctr < target) {
+      if (*(volatile int*)abort) {
+        ok = 0;
+        break;
+      }
+      if (++it > kQrGridSpin) {
+        atomicExch(abort, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+    k_rrqr_grid(const RRQRGridTask* __restrict__ tasks, int ntasks, const RRQRSeg* __restrict__ segs) {
+  extern __shared__ real_t sm[];
+  __shared__ double s_red[kQrThreads / kWarp], s_sec[kQrThreads / kWarp];
+  __shared__ int s_idx[kQrThreads / kWarp];
+  __shared__ double s_nu64;
+  // the task of this CTA
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].cta0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const RRQRGridTask gt = tasks[lo];
+  const RRQRTask& t = gt.t;
+  const int crank = (int)blockIdx.x - gt.cta0, G = gt.ncta;
+  int* ctr = gt.ws;
+  int* abort = gt.ws + 1;
+  GridSlot* slots = reinterpret_cast<GridSlot*>(gt.ws + 4);  // [2][G]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / kWarp;
+  const int m = t.m;
+  const size_t ld = t.ld;
+  const int nseg = t.seg_end - t.seg_begin;
+  const int cpb_max = (t.ncols_max + G - 1) / G;
+  real_t* v = sm;                                       // m
+  real_t* norms = v + m;                                // cpb_max
+  int* cols = reinterpret_cast<int*>(norms + cpb_max);  // cpb_max
+  int* segoff = cols + cpb_max;                         // nseg + 1
+  if (tid == 0) {
+    int acc = 0;
+    for (int s = 0; s < nseg; ++s) {
+      segoff[s] = acc;
+      acc += t.cur[segs[t.seg_begin + s].cl];
+    }
+    segoff[nseg] = acc;
+  }
+  __syncthreads();
+  const int N = segoff[nseg];
+  const int cpb = (N + G - 1) / G;
+  const int g0 = crank * cpb, nloc = max(0, min(N, g0 + cpb) - g0);
+  for (int l = tid; l < nloc; l += kQrThreads) {
+    const int g = g0 + l;
+    int a = 0, b = nseg - 1;  // last segment with segoff <= g
+    while (a < b) {
+      const int mid = (a + b + 1) >> 1;
+      if (segoff[mid] <= g) a = mid;
+      else b = mid - 1;
+    }
+    cols[l] = segs[t.seg_begin + a].col + (g - segoff[a]);
+  }
+  __syncthreads();
+  for (int l = warp; l < nloc; l += nw) {
+    const real_t* col = t.A + (size_t)cols[l] * ld;
+    real_t s = 0.0;
+    for (int i = lane; i < m; i += kWarp) s += col[i] * col[i];
+    s = warp_sum(s);
+    if (lane == 0) norms[l] = s;
+  }
+  __syncthreads();
+  const double eps = t.eps;
+  const int scheme = t.scheme;
+  const double thr1 = eps * eps;
+  const double thr2 = thr1 * thr1;
+  const int maxsteps = min(m, N);
+  int r = -1, nsteps = 0, flags = 0, nbar = 0;
+  bool ok = true;
+  double nu0sq = 0.0;
+  int pend_l = -1, pend_step = 0;  // own pivot column still to receive its R entries
+  double pend_beta = 0.0;
+  for (int step = 0; step < maxsteps; ++step) {
+    // local best (ties to the lowest column) and local second best
+    double bv = -1.0, sv = -1.0;
+    int bi = -1;
+    for (int l = tid; l < nloc; l += kQrThreads) {
+      const double x = (double)norms[l];
+      if (x < 0.0) continue;
+      if (x > bv || (x == bv && g0 + l < bi)) {
+        sv = fmax(sv, bv);
+        bv = x;
+        bi = g0 + l;
+      } else {
+        sv = fmax(sv, x);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const double os = __shfl_xor_sync(0xffffffffu, sv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+        sv = fmax(fmax(sv, os), bv);
+        bv = ov;
+        bi = oi;
+      } else {
+        sv = fmax(fmax(sv, os), ov);
+      }
+    }
+    if (lane == 0) {
+      s_red[warp] = bv;
+      s_sec[warp] = sv;
+      s_idx[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = s_red[0], s2 = s_sec[0];
+      int ix = s_idx[0];
+      for (int w = 1; w < nw; ++w) {
+        const double ov = s_red[w];
+        const int oi = s_idx[w];
+        if (ov > b || (ov == b && oi >= 0 && (ix < 0 || oi < ix))) {
+          s2 = fmax(fmax(s2, s_sec[w]), b);
+          b = ov;
+          ix = oi;
+        } else {
+          s2 = fmax(fmax(s2, s_sec[w]), ov);
+        }
+      }
+      GridSlot gs;
+      gs.best = b;
+      gs.second = s2;
+      gs.idx = ix;
+      gs.pad = 0;
+      slots[(step & 1) * G + crank] = gs;
+    }
+    ++nbar;
+    if (!qr_grid_barrier(ctr, abort, nbar * G)) {
+      ok = false;
+      break;
+    }
+    // the previous pivot column has been read by every CTA: store its R entries
+    if (pend_l >= 0) {
+      real_t* pc = t.A + (size_t)cols[pend_l] * ld;
+      for (int i = pend_step + tid; i < m; i += kQrThreads) pc[i] = (i == pend_step) ? (real_t)pend_beta : (real_t)0.0;
+      pend_l = -1;
+    }
+    // merge the CTAs' candidates (every thread, the same order everywhere)
+    double best = -1.0, sec = -1.0;
+    int bidx = -1;
+    for (int k = 0; k < G; ++k) {
+      const double kb = __ldcg(&slots[(step & 1) * G + k].best);
+      const double ks = __ldcg(&slots[(step & 1) * G + k].second);
+      const int ki = __ldcg(&slots[(step & 1) * G + k].idx);
+      if (ki < 0) continue;
+      if (kb > best || (kb == best && (bidx < 0 || ki < bidx))) {
+        sec = fmax(fmax(sec, ks), best);
+        best = kb;
+        bidx = ki;
+      } else {
+        sec = fmax(fmax(sec, ks), kb);
+      }
+    }
+    if (bidx < 0) break;  // no candidate left (cannot happen for step < min(m, N))
+    // the pivot column, in global memory (written by its owner before the barrier)
+    int pseg = 0;
+    {
+      int a = 0, b = nseg - 1;
+      while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (segoff[mid] <= bidx) a = mid;
+        else b = mid - 1;
+      }
+      pseg = a;
+    }
+    const real_t* pc = t.A + (size_t)(segs[t.seg_begin + pseg].col + (bidx - segoff[pseg])) * ld;
+    double nusq = best;
+    if (sizeof(real_t) < sizeof(double)) {
+      // FP32 storage: nu_0 and near-threshold decisions use the FP64 norm
+      const bool nearthr = step == 0 || fabs(nusq - thr1 * nu0sq) <= 1e-4 * thr1 * nu0sq ||
+                           (scheme == SPAND_SECOND_ORDER_SUPERFINE &&
+                            fabs(nusq - thr2 * nu0sq) <= 1e-4 * thr2 * nu0sq);
+      if (nearthr) {
+        if (warp == 0) {
+          double s64 = 0.0;
+          for (int i = step + lane; i < m; i += kWarp) {
+            const double a = (double)__ldcg(pc + i);
+            s64 = fma(a, a, s64);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          if (lane == 0) s_nu64 = s64;
+        }
+        __syncthreads();
+        nusq = s_nu64;
+        __syncthreads();
+      }
+    }
+    if (sec >= 0.0 && nusq > 0.0 && nusq - sec <= 1e-12 * nusq) flags |= 1;
+    if (step == 0) {
+      nu0sq = nusq;
+      if (nu0sq == 0.0) {
+        r = 0;
+        break;
+      }
+    }
+    if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
+    if (scheme == SPAND_SECOND_ORDER_SUPERFINE && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq)
+      flags |= 2;
+    if (r < 0 && nusq < thr1 * nu0sq) {
+      r = step;
+      if (scheme != SPAND_SECOND_ORDER_SUPERFINE) break;
+    }
+    if (scheme == SPAND_SECOND_ORDER_SUPERFINE && nusq < thr2 * nu0sq) break;
+    const double alpha = __ldcg(pc + step);
+    const double normx = sqrt(nusq);
+    double beta, tau;
+    if (normx == 0.0) {
+      beta = alpha;
+      tau = 0.0;
+    } else {
+      beta = alpha >= 0.0 ? -normx : normx;
+      tau = (beta - alpha) / beta;
+    }
+    const double den = alpha - beta;
+    const bool owner = bidx >= g0 && bidx < g0 + nloc;
+    for (int i = tid; i < m; i += kQrThreads) {
+      real_t vi;
+      if (i < step) vi = 0.0;
+      else if (i == step) vi = 1.0;
+      else vi = (normx == 0.0) ? 0.0 : (real_t)(__ldcg(pc + i) / den);
+      v[i] = vi;
+      if (owner) t.V[i + (size_t)step * m] = vi;
+    }
+    if (owner) {
+      if (tid == 0) {
+        t.tau[step] = tau;
+        norms[bidx - g0] = -1.0;
+      }
+      pend_l = bidx - g0;
+      pend_step = step;
+      pend_beta = beta;
+    }
+    __syncthreads();
+    // apply H_step to the other non-pivoted columns of this CTA; refresh their norms
+    for (int l = warp; l < nloc; l += nw) {
+      if (norms[l] < 0.0) continue;
+      real_t* col = t.A + (size_t)cols[l] * ld;
+      real_t d = 0.0;
+      for (int i = step + lane; i < m; i += kWarp) d += v[i] * col[i];
+      d = warp_sum(d);
+      const real_t f = tau * d;
+      real_t s = 0.0;
+      for (int i = step + lane; i < m; i += kWarp) {
+        const real_t a = col[i] - f * v[i];
+        col[i] = a;
+        if (i > step) s += a * a;
+      }
+      s = warp_sum(s);
+      if (lane == 0) norms[l] = s;
+    }
+    __syncthreads();
+    nsteps = step + 1;
+  }
+  // every CTA has read the last pivot column once all pass this barrier
+  if (ok) {
+    ++nbar;
+    ok = qr_grid_barrier(ctr, abort, nbar * G);
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(t.err + 1, 1);
+    return;
+  }
+  if (pend_l >= 0) {
+    real_t* pc = t.A + (size_t)cols[pend_l] * ld;
+    for (int i = pend_step + tid; i < m; i += kQrThreads) pc[i] = (i == pend_step) ? (real_t)pend_beta : (real_t)0.0;
+  }
+  __syncthreads();
+  if (r < 0) r = nsteps;
+  // coarse rows of this CTA's columns -> the neighbours' rows (transposed)
+  for (int e = tid; e < r * nloc; e += kQrThreads) {
+    const int i = e % r, l = e / r;
+    const int g = g0 + l;
+    int a = 0, b = nseg - 1;
+    while (a < b) {
+      const int mid = (a + b + 1) >> 1;
+      if (segoff[mid] <= g) a = mid;
+      else b = mid - 1;
+    }
+    const RRQRSeg sg = segs[t.seg_begin + a];
+    sg.mirror[(g - segoff[a]) + (size_t)i * sg.mirror_ld] = t.A[i + (size_t)cols[l] * ld];
+  }
+  if (crank == 0) {
+    for (int e = tid; e < r * r; e += kQrThreads) {
+      const int i = e % r, j = e / r;
+      t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid == 0) {
+      t.rank[t.id] = r;
+      t.nref[t.id] = nsteps;
+      t.flag[t.id] = flags;
+      t.cur[t.id] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The same QR with the block held on chip: a thread-block cluster of C CTAs
 // (C = 1, 2, 4, 8 or 16) per interface, each CTA keeping a contiguous slice of
 // the columns in its shared memory for the whole factorization.  Per step the
@@ -1006,6 +1348,29 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs,
   const int bytes = rrqr_smem_bytes(max_m, max_cols, max_segs);
   set_smem((const void*)k_rrqr, bytes);
   k_rrqr<<<ntasks, kQrThreads, bytes, s>>>(t, segs);
+}
+
+int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs) {
+  // v (real_t) + norms (real_t) + cols (int) + segoff (int)
+  return max_m * (int)sizeof(real_t) + max_cpb * (int)sizeof(real_t) + max_cpb * 4 +
+         (max_segs + 2) * 4 + 16;
+}
+
+cudaError_t launch_rrqr_grid(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
+                             int smem_bytes, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  set_smem((const void*)k_rrqr_grid, smem_bytes);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nctas);
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident, or the launch fails
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_rrqr_grid, t, ntasks, segs);
 }
 
 }  // namespace SPAND_NS

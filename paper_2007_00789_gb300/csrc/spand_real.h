@@ -94,10 +94,22 @@ struct RRQRTask {
   int* rank;       // outputs, indexed by cluster id: rank r, reflectors taken, near-tie flags
   int* nref;
   int* flag;
+  int* err;        // the problem's error words: err[1] = 1 if a multi-CTA QR lost synchronisation
   double eps;      // relative tolerance of the problem (Algorithm 1)
   int scheme;      // SPAND_FIRST_ORDER, SPAND_SECOND_ORDER_FULL or SPAND_SECOND_ORDER_SUPERFINE
   int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max, pad;
 };
+
+// An interface QR spread over ncta CTAs of one cooperative launch (CTAs
+// cta0 .. cta0+ncta-1), for blocks too large for a thread-block cluster's
+// shared memory.  ws: the task's workspace of kQrGridWs(ncta) ints, zero at
+// launch (barrier counter, abort flag, candidate slots).
+struct RRQRGridTask {
+  RRQRTask t;
+  int* ws;
+  int cta0, ncta;
+};
+inline size_t qr_grid_ws_ints(int ncta) { return 4 + 2 * (size_t)ncta * 6; }
 
 // Preconditioner apply descriptors.  The triangular factors and Q_p are
 // applied through explicit matrices formed at the end of each stage
@@ -156,6 +168,11 @@ void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int
                          int smem_bytes, int threads, cudaStream_t s);
 void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, int max_cols,
                  int max_segs, cudaStream_t s);
+// Cooperative multi-CTA QR: nctas CTAs in all (at most one per SM), each task
+// its range of them; returns a CUDA error code of the launch.
+int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs);
+cudaError_t launch_rrqr_grid(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
+                             int smem_bytes, cudaStream_t s);
 
 // K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
 // over all nitems items (device array); max_nvec: the most vectors of an item.

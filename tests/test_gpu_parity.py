@@ -185,6 +185,32 @@ def test_streamed_and_on_chip_rrqr_agree(d, ell, scheme):
     b.close()
 
 
+@pytest.mark.parametrize("make,ell,scheme,precision", [
+    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 0),
+    (lambda: si.laplacian_2d(64), 6, 2, 0),
+    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 1, 1),
+])
+def test_multi_cta_rrqr_equals_streamed(make, ell, scheme, precision):
+    """The multi-CTA QR (columns spread over several CTAs of a cooperative
+    launch) processes every column as the single-CTA streamed kernel does:
+    ranks, reflector counts and near-tie flags identical, M r equal up to the
+    apply's atomic accumulation order."""
+    from paper_2007_00789_gb300 import spand as S
+    prob = make()
+    a = S.Spand.from_problem(prob, ell, 1e-2, scheme, rrqr_kernel=1, precision=precision)
+    b = S.Spand.from_problem(prob, ell, 1e-2, scheme, rrqr_kernel=3, precision=precision)
+    a.factor()
+    b.factor()
+    assert np.array_equal(a.ranks(), b.ranks())
+    r = np.random.default_rng(4).standard_normal(prob.n)
+    za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
+    assert np.abs(za - zb).max() <= (1e-13 if precision == 0 else 1e-6) * np.abs(za).max()
+    b.factor()  # replayed from the stage graphs (the workspace is reset by the graph)
+    assert np.array_equal(a.ranks(), b.ranks())
+    a.close()
+    b.close()
+
+
 def test_not_spd_reported():
     _torch()
     from paper_2007_00789_gb300 import spand as S
