@@ -166,9 +166,10 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, rank, world, local, dist):
+def run_batch(args, rank, world, local, dist, emit=True):
     """64 independent problems (2D 128^2..512^2 and 3D 24^3..48^3 FV diffusion,
-    a = 10^U(-2,2)): one step = batch factorization + batch PCG of all of them."""
+    a = 10^U(-2,2)): one step = batch factorization + batch PCG of all of them.
+    Prints the JSON line (emit) or returns it."""
     import numpy as np
     import torch
 
@@ -286,36 +287,37 @@ def run_batch(args, rank, world, local, dist):
                                 "gflop_per_step": k["flops"] / args.steps / 1e9}
                     for k in kstats if k["launches"]},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     batch.close()
     for h in hs:
         h.close()
+    if not emit:
+        return line
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_serve(args, rank, world, local, dist):
-    """Serving trace: a resident 96^3 diffusion problem plus new problems of
-    n = 16k..500k arriving with a Poisson process of requests of 1..32
-    right-hand sides; PCG to 1e-10.  Reports solves/s and request latency."""
+def serve_trace(precision, eps, scheme, rate, local, requests=120, new_problems=12):
+    """Run one serving trace: a resident 96^3 diffusion problem plus new problems of
+    n = 16k..500k, requests of 1..32 right-hand sides arriving as a Poisson process
+    of the given rate, PCG to 1e-10.  Returns the measurements (a dict)."""
     import concurrent.futures as cf
 
     import numpy as np
-    import torch
 
     import spand_inputs as si
     from paper_2007_00789_gb300 import spand
 
     tol = 1e-10
-    probs, trace = si.serve_workload(rate=args.serve_rate)
+    probs, trace = si.serve_workload(requests=requests, rate=rate, new_problems=new_problems)
     max_n = max(p.n for p, _ in probs)
-    srv = spand.SpandServer(precision=args.precision, tol=tol, max_segments=512,
+    srv = spand.SpandServer(precision=precision, tol=tol, max_segments=512,
                             max_entries=6 * 32 * ((max_n + 31) // 32 * 32))
     # analysis (host) of every problem happens before the trace starts
     with cf.ThreadPoolExecutor(16) as ex:
-        hs = list(ex.map(lambda pe: spand.Spand.from_problem(pe[0], pe[1], args.eps, args.scheme,
-                                                             precision=args.precision), probs))
+        hs = list(ex.map(lambda pe: spand.Spand.from_problem(pe[0], pe[1], eps, scheme,
+                                                             precision=precision), probs))
     mids = [srv.add(h, pinned=(i == 0)) for i, h in enumerate(hs)]
     # warm-up: the resident problem is factored and one request solved
     rng0 = np.random.default_rng(1)
@@ -341,7 +343,7 @@ def run_serve(args, rank, world, local, dist):
     st = srv.stats()
     worst = 0.0
     for k, (_, pi, nr, _) in enumerate(trace):
-        x, it, rel, lat = results[k]
+        x = results[k][0]
         A = probs[pi][0].to_scipy()
         b = rhs[k]
         worst = max(worst, max(np.linalg.norm(b[j] - A @ x[j]) / np.linalg.norm(b[j])
@@ -350,32 +352,39 @@ def run_serve(args, rank, world, local, dist):
     solves = sum(nr for _, _, nr, _ in trace)
     iters = np.concatenate([results[k][1] for k in range(len(trace))])
     h2d = sum(8 * nr * probs[pi][0].n for _, pi, nr, _ in trace)
+    srv.close()
+    for h in hs:
+        h.close()
+    return {"solves_per_s": solves / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "wall_s": wall,
+            "requests": len(trace), "solves": solves, "new_problems": len(probs) - 1,
+            "arrival_rate_per_s": rate, "tol": tol, "cg_iters_max": int(iters.max()),
+            "cg_iters_mean": float(iters.mean()), "true_relres_max_host": worst,
+            "server": {k: st[k] for k in ("ticks", "max_inflight", "resident_problems",
+                                          "resident_bytes", "solves_per_s")},
+            "h2d_bytes": h2d, "clocks": clk.summary()}
+
+
+def run_serve(args, rank, world, local, dist):
+    """The serving workload as its own JSON line (value = served solves/s)."""
+    r = serve_trace(args.precision, args.eps, args.scheme, args.serve_rate, local)
+    cfg = {"workload": "serve", "resident": "diffusion_3d(96), a=10^U(-3,3)", "nrhs": "1..32",
+           "timing": "host wall clock from first submission (requests' b and x in host memory,"
+                     " copies and factorizations of new problems included)"}
+    cfg.update({k: v for k, v in r.items() if k not in ("clocks", "h2d_bytes")})
     line = {
-        "metric": METRIC, "value": solves / wall, "unit": "solves/s", "n_gpus": world,
-        "steps": len(trace), "warmup": 1, "ms_per_step": wall * 1e3 / len(trace),
+        "metric": METRIC, "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": r["requests"], "warmup": 1, "ms_per_step": r["wall_s"] * 1e3 / r["requests"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == 0 else "f32 factor/apply + f64 pcg",
-        "data": "synthetic",
-        "config": {"workload": "serve", "resident": "diffusion_3d(96), a=10^U(-3,3)",
-                   "new_problems": len(probs) - 1, "requests": len(trace), "solves": solves,
-                   "arrival_rate_per_s": args.serve_rate, "nrhs": "1..32", "tol": tol,
-                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                   "max_ms": float(lat.max()), "wall_s": wall, "cg_iters_max": int(iters.max()),
-                   "cg_iters_mean": float(iters.mean()), "true_relres_max_host": worst,
-                   "server": {k: st[k] for k in ("ticks", "max_inflight", "resident_problems",
-                                                 "resident_bytes", "solves_per_s")},
-                   "timing": "host wall clock from first submission (requests' b and x in host"
-                             " memory, copies and factorizations of new problems included)"},
-        "clocks": clk.summary(),
-        "e2e": {"value": solves / wall, "unit": "solves/s", "h2d_bytes_per_step": h2d // len(trace),
-                "d2h_bytes_per_step": h2d // len(trace)},
+        "data": "synthetic", "config": cfg, "clocks": r["clocks"],
+        "e2e": {"value": r["solves_per_s"], "unit": "solves/s",
+                "h2d_bytes_per_step": r["h2d_bytes"] // r["requests"],
+                "d2h_bytes_per_step": r["h2d_bytes"] // r["requests"]},
         "gpu_launches": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    srv.close()
-    for h in hs:
-        h.close()
 
 
 def main():
@@ -396,6 +405,8 @@ def main():
                     help="0: FP64 factor+apply; 1: FP32 factor+apply (PCG stays FP64)")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip timing the other precision")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served measurements beside the headline line")
     ap.add_argument("--serve-rate", type=float, default=5.0,
                     help="serve workload: request arrivals per second (Poisson process)")
     ap.add_argument("--plain-launches", action="store_true",
@@ -578,9 +589,35 @@ def main():
         except Exception as exc:  # the baseline must not sink the GPU line
             line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {exc}"[:300]}
+    # the metric's other parts, measured beside the headline: batched problems and
+    # served solves (rank 0 at N=1; a failure here is reported, not fatal)
+    h.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        import copy
+        try:
+            ab = copy.copy(args)
+            ab.precision, ab.steps, ab.warmup, ab.no_e2e = 1, 2, 3, True
+            bl = run_batch(ab, rank, world, local, None, emit=False)
+            line["batched"] = {"workload": "batch64: 64 FV diffusion problems, 2D 128^2..512^2 and"
+                                           " 3D 24^3..48^3, a=10^U(-2,2), FP32 factor / FP64 PCG",
+                               "s_per_step": bl["value"],
+                               **{k: bl["config"][k] for k in ("problems", "n_total", "solves_per_s",
+                                                               "cg_iters_max", "relres_max",
+                                                               "true_relres_max_host",
+                                                               "factor_ms")}}
+        except Exception as exc:
+            line["batched"] = {"error": str(exc)[:300]}
+        try:
+            sv = serve_trace(1, args.eps, args.scheme, 5.0, local, requests=60, new_problems=6)
+            line["served"] = {"workload": "resident 96^3 diffusion + 6 new 3D problems, 60 requests"
+                                          " of 1..32 RHS arriving at 5/s, tol 1e-10, FP32 factor",
+                              **{k: sv[k] for k in ("solves_per_s", "p50_ms", "p99_ms", "max_ms",
+                                                    "requests", "solves", "cg_iters_max",
+                                                    "true_relres_max_host", "wall_s")}}
+        except Exception as exc:
+            line["served"] = {"error": str(exc)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -1368,7 +1368,7 @@ int plan_multi(const ApSeg* segs, int nseg, MultiApply& M, cudaStream_t s) {
         L.max_cols = std::max(L.max_cols, ph.max_cols);
         L.max_nvec = std::max(L.max_nvec, ru.nvec);
         L.flops += ph.flops * ru.nvec;
-        L.bytes += ph.bytes * ((ru.nvec + 3) / 4);  // operators read once per four vectors (at most)
+        L.bytes += ph.bytes * ((ru.nvec + 3) / 4);  // operators read once per pass of <= 4 vectors
       }
       L.nitems = (int)(items.size() - L.item0);
       M.launches.push_back(L);

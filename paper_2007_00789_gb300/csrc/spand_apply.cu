@@ -379,34 +379,49 @@ static void launch_ap(ApKernel kern, const ApItem* items, int nitems, int ntasks
 // whose shared memory is per_vec bytes per vector: 1, 2 or 4.  Several
 // vectors only while the CTA's shared memory stays under 96 KB, so that the
 // thread-block clusters of the single-vector launch shape stay schedulable.
+// Up to 4 vectors per pass: wider passes (8, 16 in FP32) measured slower, the
+// extra registers and shared memory costing more resident warps than the
+// fewer operator reads save.
+constexpr int kApMaxVectors = 4;
+
 static int ap_vectors(int max_nvec, int per_vec) {
-  int nv = max_nvec >= 4 ? 4 : (max_nvec >= 2 ? 2 : 1);
+  int nv = 1;
+  while (nv * 2 <= std::min(max_nvec, kApMaxVectors)) nv *= 2;
   while (nv > 1 && (size_t)nv * per_vec > (size_t)96 * 1024) nv >>= 1;
   return nv;
 }
+
+template <template <int> class Pick>
+static ApKernel pick(int nv) {
+  if constexpr (kApMaxVectors >= 16) {
+    if (nv == 16) return Pick<16>::k;
+    if (nv == 8) return Pick<8>::k;
+  }
+  return nv == 4 ? Pick<4>::k : nv == 2 ? Pick<2>::k : Pick<1>::k;
+}
+template <int NV> struct PickInterior { static constexpr ApKernel k = k_ap_interior<NV>; };
+template <int NV> struct PickScale { static constexpr ApKernel k = k_ap_scale<NV>; };
+template <int NV> struct PickQE { static constexpr ApKernel k = k_ap_qe<NV>; };
 
 void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,
                         int max_cols, int max_nvec, real_t* z, bool forward, cudaStream_t s) {
   const int per = std::max(2 * max_m + max_cols, 1) * (int)sizeof(real_t);
   const int nv = ap_vectors(max_nvec, per);
-  ApKernel kern = nv == 4 ? k_ap_interior<4> : nv == 2 ? k_ap_interior<2> : k_ap_interior<1>;
-  launch_ap(kern, items, nitems, ntasks, K, nv * per, z, forward, s);
+  launch_ap(pick<PickInterior>(nv), items, nitems, ntasks, K, nv * per, z, forward, s);
 }
 
 void launch_ap_scale(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_nvec,
                      real_t* z, bool forward, cudaStream_t s) {
   const int per = std::max(max_m, 1) * (int)sizeof(real_t);
   const int nv = ap_vectors(max_nvec, per);
-  ApKernel kern = nv == 4 ? k_ap_scale<4> : nv == 2 ? k_ap_scale<2> : k_ap_scale<1>;
-  launch_ap(kern, items, nitems, ntasks, K, nv * per, z, forward, s);
+  launch_ap(pick<PickScale>(nv), items, nitems, ntasks, K, nv * per, z, forward, s);
 }
 
 void launch_ap_qe(const ApItem* items, int nitems, int ntasks, int K, int max_m, int max_cols,
                   int max_nvec, real_t* z, bool forward, cudaStream_t s) {
   const int per = std::max(2 * max_m + max_cols, 1) * (int)sizeof(real_t);
   const int nv = ap_vectors(max_nvec, per);
-  ApKernel kern = nv == 4 ? k_ap_qe<4> : nv == 2 ? k_ap_qe<2> : k_ap_qe<1>;
-  launch_ap(kern, items, nitems, ntasks, K, nv * per, z, forward, s);
+  launch_ap(pick<PickQE>(nv), items, nitems, ntasks, K, nv * per, z, forward, s);
 }
 
 }  // namespace SPAND_NS

@@ -160,15 +160,16 @@ def test_batch_not_spd_names_problem():
     batch.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_many_rhs_match_single(precision):
-    """spand_apply_many / spand_pcg_many (padded leading dimension) against the single-column calls."""
+@pytest.mark.parametrize("precision,nrhs", [(0, 5), (1, 5), (1, 21)])
+def test_many_rhs_match_single(precision, nrhs):
+    """spand_apply_many / spand_pcg_many (padded leading dimension) against the
+    single-column calls; 21 columns run five passes of 4 vectors plus one."""
     torch = _torch()
     from paper_2007_00789_gb300 import spand as S
     p = si.diffusion_3d(20, seed=9, lo=-2, hi=2)
     h = S.Spand.from_problem(p, 8, 1e-2, 1, precision=precision)
     h.factor()
-    nrhs, ld = 5, p.n + 5
+    ld = p.n + 5
     rng = np.random.default_rng(4)
     R = torch.zeros((nrhs, ld), dtype=torch.float64, device="cuda")
     R[:, :p.n] = torch.from_numpy(rng.standard_normal((nrhs, p.n))).cuda()
