@@ -1161,22 +1161,36 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < 0.0) continue;  // the same l for the whole group
       real_t* a = A + l;
-      real_t d0 = 0.0, d1 = 0.0;
+      // four independent partial dot products, two for the new norm: the
+      // per-thread chains are what bounds the latency of a step
+      real_t d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
       int i = step + sl;
-      for (; i + tpc < m; i += 2 * tpc) {
+      for (; i + 3 * tpc < m; i += 4 * tpc) {
         d0 = fma(v[i], a[(size_t)i * ncl], d0);
         d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
+        d2 = fma(v[i + 2 * tpc], a[(size_t)(i + 2 * tpc) * ncl], d2);
+        d3 = fma(v[i + 3 * tpc], a[(size_t)(i + 3 * tpc) * ncl], d3);
       }
-      if (i < m) d0 = fma(v[i], a[(size_t)i * ncl], d0);
-      real_t d = d0 + d1;
+      for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+      real_t d = (d0 + d1) + (d2 + d3);
       for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
       const real_t f = tau * d;
-      real_t s2 = 0.0;
-      for (i = step + sl; i < m; i += tpc) {
-        const real_t x = fma(-f, v[i], a[(size_t)i * ncl]);
-        a[(size_t)i * ncl] = x;
-        if (i > step) s2 = fma(x, x, s2);
+      real_t s2a = 0.0, s2b = 0.0;
+      i = step + sl;
+      for (; i + tpc < m; i += 2 * tpc) {
+        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
+        const real_t x1 = fma(-f, v[i + tpc], a[(size_t)(i + tpc) * ncl]);
+        a[(size_t)i * ncl] = x0;
+        a[(size_t)(i + tpc) * ncl] = x1;
+        if (i > step) s2a = fma(x0, x0, s2a);
+        s2b = fma(x1, x1, s2b);  // row i + tpc > step
       }
+      if (i < m) {
+        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
+        a[(size_t)i * ncl] = x0;
+        if (i > step) s2a = fma(x0, x0, s2a);
+      }
+      real_t s2 = s2a + s2b;
       for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
       __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
       if (sl == 0) {
