@@ -931,14 +931,46 @@ __global__ void __launch_bounds__(kQrThreads)
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-// Candidate exchange of one step: the largest squared norm (as the int64 bit
-// pattern of a non-negative real_t, which orders like the value; pivoted
-// columns hold -1.0 and sort below every candidate), its column, and the second
-// largest.  Integer compares keep the pivot search off the FP64 pipe.
+// Candidate keys.  The bit pattern of a non-negative real_t, read as a signed
+// integer of the same width, orders like the value; the pivot search and the
+// threshold tests of the step therefore compare integers.  (GB300's FP64 pipe
+// is narrow: a warp-wide FP64 instruction costs tens of cycles, which the
+// per-step decisions would otherwise pay in every warp, and FP32 storage needs
+// no FP64 at all there.)  No candidate: the most negative integer.
+template <typename R>
+struct QrKeyOf;
+template <>
+struct QrKeyOf<double> {
+  typedef long long key;
+  typedef unsigned long long ukey;
+  static __device__ __forceinline__ key of(double x) { return __double_as_longlong(x); }
+  static __device__ __forceinline__ double val(key k) { return __longlong_as_double(k); }
+  static __device__ __forceinline__ double rval(key k) { return __longlong_as_double(k); }
+  // for x >= 0: value < x  <=>  key < above(x);  value <= x  <=>  key <= below(x)
+  static __device__ __forceinline__ key above(double x) { return __double_as_longlong(x); }
+  static __device__ __forceinline__ key below(double x) { return __double_as_longlong(x); }
+};
+template <>
+struct QrKeyOf<float> {
+  typedef int key;
+  typedef unsigned ukey;
+  static __device__ __forceinline__ key of(float x) { return __float_as_int(x); }
+  static __device__ __forceinline__ double val(key k) { return (double)__int_as_float(k); }
+  static __device__ __forceinline__ float rval(key k) { return __int_as_float(k); }
+  static __device__ __forceinline__ key above(double x) { return __float_as_int(__double2float_ru(x)); }
+  static __device__ __forceinline__ key below(double x) { return __float_as_int(__double2float_rd(x)); }
+};
+typedef QrKeyOf<real_t> QK;
+typedef QK::key qkey_t;
+typedef QK::ukey qukey_t;
+constexpr qkey_t kNoKey = (qkey_t)(1ull << (8 * sizeof(qkey_t) - 1));
+
+// Candidate exchange of one step: the largest squared norm's key, its column,
+// its entry in the pivot row (the reflector's alpha), and the second largest key.
 struct QrSlot {
-  long long best, second;
-  double alpha;  // the candidate column's entry in the pivot row (the reflector's alpha)
-  int idx, pad;
+  qkey_t best, second;
+  real_t alpha;
+  int idx;
 };
 
 __device__ __forceinline__ void slot_merge(QrSlot& a, const QrSlot& b) {
@@ -953,30 +985,83 @@ __device__ __forceinline__ void slot_merge(QrSlot& a, const QrSlot& b) {
   }
 }
 
-constexpr long long kNoKey = (long long)0x8000000000000000ULL;
+// keys shifted to unsigned (no candidate -> 0) for the warp reductions
+__device__ __forceinline__ qukey_t qk_up(qkey_t k) { return k < 0 ? (qukey_t)0 : (qukey_t)k + 1u; }
+__device__ __forceinline__ qkey_t qk_down(qukey_t u) { return u == 0 ? kNoKey : (qkey_t)(u - 1u); }
 
-__device__ __forceinline__ QrSlot warp_merge(QrSlot mine) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    QrSlot other;
-    other.best = __shfl_xor_sync(0xffffffffu, mine.best, o);
-    other.second = __shfl_xor_sync(0xffffffffu, mine.second, o);
-    other.idx = __shfl_xor_sync(0xffffffffu, mine.idx, o);
-    other.alpha = __shfl_xor_sync(0xffffffffu, mine.alpha, o);
-    other.pad = 0;
-    slot_merge(mine, other);
-  }
-  return mine;
+__device__ __forceinline__ unsigned warp_max(unsigned x) { return __reduce_max_sync(0xffffffffu, x); }
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long x) {
+  const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(x >> 32));
+  const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(x >> 32) == hi ? (unsigned)x : 0u);
+  return ((unsigned long long)hi << 32) | lo;
 }
 
-// One thread per column: the dot product v^T a, the update a -= tau (v^T a) v
-// and the new trailing norm are plain FMA chains in each thread, with no
-// cross-lane reductions; each thread also keeps the best candidate among its
-// columns for the next step.  The block is stored row-major (row i of the
-// local columns contiguous) so that a warp reads consecutive addresses.  Per
-// step: one block barrier and two cluster barriers; every warp reads the
-// CTAs' candidates itself, and the owner of the pivot column pushes v and tau
-// into every CTA's shared memory.
+// The merge of the 32 lanes' slots, with the rules of slot_merge (largest key,
+// ties to the lowest column; second = the largest key but the winner's),
+// through warp-wide integer reductions instead of a shuffle tree.
+__device__ __forceinline__ QrSlot warp_merge(const QrSlot& s) {
+  const int lane = threadIdx.x & 31;
+  const qukey_t ub = qk_up(s.best);
+  const qukey_t mb = warp_max(ub);
+  const bool top = ub == mb;
+  const unsigned mi = __reduce_min_sync(0xffffffffu, top ? (unsigned)s.idx : 0xffffffffu);
+  const int win = __ffs(__ballot_sync(0xffffffffu, top && (unsigned)s.idx == mi)) - 1;
+  const qukey_t ms = warp_max(lane == win ? qk_up(s.second) : ub);
+  QrSlot o;
+  o.best = qk_down(mb);
+  o.second = qk_down(ms);
+  o.alpha = __shfl_sync(0xffffffffu, s.alpha, win);
+  o.idx = (int)mi;
+  return o;
+}
+
+// beta, tau and 1/(alpha - beta) of the Householder reflector that maps a
+// column with pivot-row entry alpha and squared norm nsq (pivot row and below)
+// onto beta e_1; called by a whole warp, the result lands in out[0..2].  FP32
+// storage computes them in FP32; FP64 takes the square root once and the two
+// quotients in two lanes of the same instructions (IEEE division: the values
+// are those of separate computations).
+__device__ __forceinline__ void reflector_scalars(real_t alpha, real_t nsq, int lane, real_t* out) {
+  if constexpr (sizeof(real_t) < sizeof(double)) {
+    if (lane == 0) {
+      const float nx = sqrtf(nsq);
+      float beta = alpha, tau = 0.f, inv = 0.f;
+      if (nx != 0.f) {
+        beta = alpha >= 0.f ? -nx : nx;
+        tau = (beta - alpha) / beta;
+        inv = 1.f / (alpha - beta);
+      }
+      out[0] = beta;
+      out[1] = tau;
+      out[2] = inv;
+    }
+  } else {
+    if (lane < 2) {
+      const double nx = sqrt((double)nsq);
+      const double beta = (nx == 0.0) ? (double)alpha : (alpha >= 0.0 ? -nx : nx);
+      const double num = lane == 0 ? beta - alpha : 1.0;
+      const double den = lane == 0 ? beta : alpha - beta;
+      const double q = (nx == 0.0) ? 0.0 : num / den;
+      if (lane == 0) {
+        out[0] = beta;
+        out[1] = q;
+      } else {
+        out[2] = q;
+      }
+    }
+  }
+}
+
+// One thread per column (or a few, rows split among them): the dot product
+// v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
+// in each thread; each thread also keeps the best candidate among its columns
+// for the next step.  The block is stored row-major (row i of the local
+// columns contiguous) so that a warp reads consecutive addresses.  Per step:
+// one block barrier and two cluster barriers.  The first cluster barrier is
+// split: between its arrive and its wait, warp 0 forms the reflector scalars of
+// its CTA's best candidate, so that the CTA that owns the pivot has them ready
+// when the exchange completes; every warp then reads the CTAs' candidates
+// itself, and the owner pushes v and tau into every CTA's shared memory.
 __global__ void __launch_bounds__(kQrcMaxThreads)
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int csize) {
@@ -986,9 +1071,10 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   extern __shared__ real_t sm[];
   __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
-  __shared__ double s_tau;   // tau of the current step, written by the owner
-  __shared__ double s_nu64;  // FP64 norm of the pivot column (FP32 storage only)
-  __shared__ int s_N;
+  __shared__ real_t s_refl[3];  // beta, tau, 1/(alpha - beta) for this CTA's best candidate
+  __shared__ real_t s_tau;      // tau of the current step, written by the owner
+  __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
+  __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256, 512 or 1024
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
   const int m = t.m;
@@ -1011,6 +1097,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     }
     segoff[nseg] = acc;
     s_N = acc;
+    s_flags = 0;
   }
   __syncthreads();
   const int N = s_N;
@@ -1040,9 +1127,9 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     A[(size_t)i * ncl + l] = t.A[i + (size_t)pcol[l] * ld];
   }
   __syncthreads();
-  QrSlot mine{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
+  QrSlot mine{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
   for (int l = grp; l < nloc; l += ngrp) {
-    real_t s2 = 0.0;
+    real_t s2 = 0;
     for (int i = sl; i < m; i += tpc) {
       const real_t a = A[(size_t)i * ncl + l];
       s2 = fma(a, a, s2);
@@ -1050,40 +1137,49 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
     if (sl == 0) {
       norms[l] = s2;
-      QrSlot c{__double_as_longlong(s2), kNoKey, m > 0 ? A[l] : 0.0, g0 + l, 0};
+      QrSlot c{QK::of(s2), kNoKey, m > 0 ? A[l] : (real_t)0, g0 + l};
       slot_merge(mine, c);
     }
   }
   const double eps = t.eps;
   const int scheme = t.scheme;
+  const bool superfine = scheme == SPAND_SECOND_ORDER_SUPERFINE;
   const double thr1 = eps * eps;
   const double thr2 = thr1 * thr1;
   const int maxsteps = min(m, N);
   int r = -1, nsteps = 0, flags = 0;
-  double nu0sq = 0.0;
+  // thresholds, fixed once nu_0 is known: as doubles, as keys (value < T <=>
+  // key < K), the FP32 windows in which the norm is recomputed in FP64, and the
+  // near-threshold flag margins
+  double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
+  qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
   for (int step = 0; step < maxsteps; ++step) {
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
+    QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     if (warp == 0) {
-      QrSlot a{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
-      if (lane < nw) a = s_warp[lane];
-      a = warp_merge(a);
-      if (lane == 0) s_slot = a;
+      if (lane < nw) cta = s_warp[lane];
+      cta = warp_merge(cta);
+      if (lane == 0) s_slot = cta;
     }
-    cluster.sync();
-    QrSlot gb{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
+    cluster.barrier_arrive();
+    if (warp == 0 && cta.best != kNoKey) reflector_scalars(cta.alpha, QK::rval(cta.best), lane, s_refl);
+    cluster.barrier_wait();
+    QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     if (lane < csize) gb = *cluster.map_shared_rank(&s_slot, lane);
     gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
-    double nusq = __longlong_as_double(gb.best);
-    if (sizeof(real_t) < sizeof(double)) {
-      // FP32 storage: the decisions that set the rank (nu_0 and any step close
-      // to the threshold) use the pivot column's norm recomputed in FP64
-      const bool nearthr = step == 0 || fabs(nusq - thr1 * nu0sq) <= 1e-4 * thr1 * nu0sq ||
-                           (scheme == SPAND_SECOND_ORDER_SUPERFINE &&
-                            fabs(nusq - thr2 * nu0sq) <= 1e-4 * thr2 * nu0sq);
-      if (nearthr && gb.idx >= 0 && gb.idx < N) {
-        if (crank == gb.idx / cpb && warp == 0) {
+    const qkey_t bk = gb.best;
+    const int owner = gb.idx / cpb;
+    // FP32 storage: the decisions that set the rank (nu_0 and any step close to
+    // a threshold) use the pivot column's norm recomputed in FP64
+    bool near = false;
+    double nu64 = 0.0;
+    if constexpr (sizeof(real_t) < sizeof(double)) {
+      near = (step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2)) &&
+             gb.idx >= 0 && gb.idx < N;
+      if (near) {
+        if (crank == owner && warp == 0) {
           const int l = gb.idx - g0;
           double s64 = 0.0;
           for (int i = step + lane; i < m; i += kWarp) {
@@ -1096,74 +1192,76 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
             for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_nu64, c) = s64;
         }
         cluster.sync();
-        nusq = s_nu64;
+        nu64 = s_nu64;
       }
     }
-    if (tid == 0 && gb.second >= 0 && nusq > 0.0) {
-      const double sec = __longlong_as_double(gb.second);
-      if (nusq - sec <= 1e-12 * nusq) flags |= 1;
-    }
     if (step == 0) {
-      nu0sq = nusq;
+      nu0sq = near ? nu64 : QK::val(bk);
       if (!(nu0sq > 0.0)) {
         r = 0;
         break;
       }
+      T1 = thr1 * nu0sq;
+      T2 = thr2 * nu0sq;
+      K1 = QK::above(T1);
+      K2 = QK::above(T2);
+      F1 = 1e-10 * thr1 * nu0sq;
+      F2 = 1e-10 * thr2 * nu0sq;
+      if constexpr (sizeof(real_t) < sizeof(double)) {
+        const double w1 = 1e-4 * thr1 * nu0sq, w2 = 1e-4 * thr2 * nu0sq;
+        lo1 = QK::above(T1 - w1);
+        hi1 = QK::below(T1 + w1);
+        lo2 = QK::above(T2 - w2);
+        hi2 = QK::below(T2 + w2);
+      }
     }
-    if (tid == 0) {
-      if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
-      if (scheme == SPAND_SECOND_ORDER_SUPERFINE && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq)
-        flags |= 2;
+    // flags (a near tie of the two largest norms; a norm within 1e-10 of a
+    // threshold) in one CTA other than the owner, off the pivot's path; the
+    // CTAs' flags are OR-ed at the end
+    if (tid == 0 && crank == (owner + 1) % csize) {
+      const double nusq = near ? nu64 : QK::val(bk);
+      if (gb.second >= 0 && nusq > 0.0) {
+        const double sec = QK::val(gb.second);
+        if (nusq - sec <= 1e-12 * nusq) flags |= 1;
+      }
+      if (fabs(nusq - T1) <= F1) flags |= 2;
+      if (superfine && fabs(nusq - T2) <= F2) flags |= 2;
     }
-    if (r < 0 && nusq < thr1 * nu0sq) {
+    const bool lt1 = near ? nu64 < T1 : bk < K1;
+    const bool lt2 = near ? nu64 < T2 : bk < K2;
+    if (r < 0 && lt1) {
       r = step;
-      if (scheme != SPAND_SECOND_ORDER_SUPERFINE) break;
+      if (!superfine) break;
     }
-    if (scheme == SPAND_SECOND_ORDER_SUPERFINE && nusq < thr2 * nu0sq) break;
-    const int owner = gb.idx / cpb;
+    if (superfine && lt2) break;
     if (crank == owner) {
       const int l = gb.idx - g0;
-      double beta = 0.0, tau = 0.0, inv = 0.0;
-      if (lane == 0) {
-        // alpha travels with the candidate: reading it from A here would race
-        // with the threads of other warps that overwrite the pivot column below
-        const double alpha = gb.alpha;
-        const double normx = sqrt(nusq);
-        if (normx == 0.0) {
-          beta = alpha;
-          tau = 0.0;
-        } else {
-          beta = alpha >= 0.0 ? -normx : normx;
-          tau = (beta - alpha) / beta;
-          inv = 1.0 / (alpha - beta);
-        }
-      }
-      beta = __shfl_sync(0xffffffffu, beta, 0);
-      tau = __shfl_sync(0xffffffffu, tau, 0);
-      inv = __shfl_sync(0xffffffffu, inv, 0);
+      if (near && warp == 0) reflector_scalars(gb.alpha, (real_t)nu64, lane, s_refl);
+      __syncthreads();  // s_refl, written by warp 0
+      const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
       for (int i = step + tid; i < m; i += nthr) {
         real_t* ai = A + (size_t)i * ncl + l;
-        const real_t vi = (i == step) ? 1.0 : (*ai) * inv;
-        *ai = (i == step) ? beta : 0.0;
+        const real_t vi = (i == step) ? (real_t)1 : (*ai) * inv;
+        *ai = (i == step) ? beta : (real_t)0;
         t.V[i + (size_t)step * m] = vi;
         for (int c = 0; c < csize; ++c) cluster.map_shared_rank(v, c)[i] = vi;
       }
-      for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0.0;
+      for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
       if (tid == 0) {
         t.tau[step] = tau;
-        norms[l] = -1.0;
+        norms[l] = -1;
         for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_tau, c) = tau;
       }
     }
     cluster.sync();
-    const real_t tau = (real_t)s_tau;
-    mine = QrSlot{kNoKey, kNoKey, 0.0, 0x7fffffff, 0};
+    const real_t tau = s_tau;
+    mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     for (int l = grp; l < nloc; l += ngrp) {
-      if (norms[l] < 0.0) continue;  // the same l for the whole group
+      if (norms[l] < (real_t)0) continue;  // the same l for the whole group
       real_t* a = A + l;
       // four independent partial dot products, two for the new norm: the
       // per-thread chains are what bounds the latency of a step
-      real_t d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+      real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
       int i = step + sl;
       for (; i + 3 * tpc < m; i += 4 * tpc) {
         d0 = fma(v[i], a[(size_t)i * ncl], d0);
@@ -1175,7 +1273,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       real_t d = (d0 + d1) + (d2 + d3);
       for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
       const real_t f = tau * d;
-      real_t s2a = 0.0, s2b = 0.0;
+      real_t s2a = 0, s2b = 0;
       i = step + sl;
       for (; i + tpc < m; i += 2 * tpc) {
         const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
@@ -1195,15 +1293,15 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
       if (sl == 0) {
         norms[l] = s2;
-        QrSlot c{__double_as_longlong(s2), kNoKey,
-                 step + 1 < m ? a[(size_t)(step + 1) * ncl] : 0.0, g0 + l, 0};
+        QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? a[(size_t)(step + 1) * ncl] : (real_t)0, g0 + l};
         slot_merge(mine, c);
       }
     }
     nsteps = step + 1;
   }
   if (r < 0) r = nsteps;
-  __syncthreads();
+  if (tid == 0 && flags) atomicOr(cluster.map_shared_rank(&s_flags, 0), flags);
+  cluster.sync();
   // write the columns back, mirror the coarse rows into the neighbours' rows
   for (int e = tid; e < m * nloc; e += nthr) {
     const int i = e % m, l = e / m;
@@ -1224,7 +1322,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       t.rank[t.id] = r;
       t.nref[t.id] = nsteps;
       t.cur[t.id] = r;
-      t.flag[t.id] = flags;
+      t.flag[t.id] = s_flags;
     }
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
