@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   // key < K), the FP32 windows in which the norm is recomputed in FP64, and the
   // near-threshold flag margins
   double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
-  qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
+  qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0, f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;
   for (int step = 0; step < maxsteps; ++step) {
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
@@ -1213,19 +1213,35 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
         hi1 = QK::below(T1 + w1);
         lo2 = QK::above(T2 - w2);
         hi2 = QK::below(T2 + w2);
+        f1lo = QK::above(T1 - F1);
+        f1hi = QK::below(T1 + F1);
+        f2lo = QK::above(T2 - F2);
+        f2hi = QK::below(T2 + F2);
       }
     }
     // flags (a near tie of the two largest norms; a norm within 1e-10 of a
     // threshold) in one CTA other than the owner, off the pivot's path; the
     // CTAs' flags are OR-ed at the end
     if (tid == 0 && crank == (owner + 1) % csize) {
-      const double nusq = near ? nu64 : QK::val(bk);
-      if (gb.second >= 0 && nusq > 0.0) {
-        const double sec = QK::val(gb.second);
-        if (nusq - sec <= 1e-12 * nusq) flags |= 1;
+      if (sizeof(real_t) < sizeof(double) && !near) {
+        // an FP32 norm: FP32 spacing (6e-8 relative) is far wider than either
+        // margin, so a near tie is equality and the threshold margins hold at
+        // most one value, tested by key
+        if (bk > 0 && gb.second == bk) flags |= 1;
+        if ((bk >= f1lo && bk <= f1hi) || (superfine && bk >= f2lo && bk <= f2hi)) flags |= 2;
+      } else {
+        // the FP64 tests, reached only when the keys are close: a relative gap
+        // of 1e-12 spans fewer than 2^14 doubles, one of 1e-10 fewer than 2^22
+        const double nusq = near ? nu64 : QK::val(bk);
+        const long long k = __double_as_longlong(nusq);
+        if (gb.second >= 0 && nusq > 0.0) {
+          const double sec = QK::val(gb.second);
+          if (k - __double_as_longlong(sec) <= (1ll << 14) && nusq - sec <= 1e-12 * nusq) flags |= 1;
+        }
+        if (llabs(k - __double_as_longlong(T1)) <= (1ll << 22) && fabs(nusq - T1) <= F1) flags |= 2;
+        if (superfine && llabs(k - __double_as_longlong(T2)) <= (1ll << 22) && fabs(nusq - T2) <= F2)
+          flags |= 2;
       }
-      if (fabs(nusq - T1) <= F1) flags |= 2;
-      if (superfine && fabs(nusq - T2) <= F2) flags |= 2;
     }
     const bool lt1 = near ? nu64 < T1 : bk < K1;
     const bool lt2 = near ? nu64 < T2 : bk < K2;
@@ -1263,6 +1279,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       // per-thread chains are what bounds the latency of a step
       real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
       int i = step + sl;
+#pragma unroll 2
       for (; i + 3 * tpc < m; i += 4 * tpc) {
         d0 = fma(v[i], a[(size_t)i * ncl], d0);
         d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
@@ -1273,22 +1290,32 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       real_t d = (d0 + d1) + (d2 + d3);
       for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
       const real_t f = tau * d;
-      real_t s2a = 0, s2b = 0;
+      // four rows per pass, all loads ahead of the stores (a store to the
+      // block could alias the next loads of v, which would serialise them)
+      real_t s2a = 0, s2b = 0, s2c = 0, s2d = 0;
       i = step + sl;
-      for (; i + tpc < m; i += 2 * tpc) {
-        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
-        const real_t x1 = fma(-f, v[i + tpc], a[(size_t)(i + tpc) * ncl]);
-        a[(size_t)i * ncl] = x0;
-        a[(size_t)(i + tpc) * ncl] = x1;
-        if (i > step) s2a = fma(x0, x0, s2a);
-        s2b = fma(x1, x1, s2b);  // row i + tpc > step
+      const size_t rs = (size_t)tpc * ncl;
+      for (; i + 3 * tpc < m; i += 4 * tpc) {
+        real_t* p0 = a + (size_t)i * ncl;
+        const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
+        const real_t a0 = p0[0], a1 = p0[rs], a2 = p0[2 * rs], a3 = p0[3 * rs];
+        const real_t x0 = fma(-f, v0, a0), x1 = fma(-f, v1, a1);
+        const real_t x2 = fma(-f, v2, a2), x3 = fma(-f, v3, a3);
+        p0[0] = x0;
+        p0[rs] = x1;
+        p0[2 * rs] = x2;
+        p0[3 * rs] = x3;
+        if (i > step) s2a = fma(x0, x0, s2a);  // rows i + tpc, ... are below the pivot row
+        s2b = fma(x1, x1, s2b);
+        s2c = fma(x2, x2, s2c);
+        s2d = fma(x3, x3, s2d);
       }
-      if (i < m) {
+      for (; i < m; i += tpc) {
         const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
         a[(size_t)i * ncl] = x0;
         if (i > step) s2a = fma(x0, x0, s2a);
       }
-      real_t s2 = s2a + s2b;
+      real_t s2 = (s2a + s2b) + (s2c + s2d);
       for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
       __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
       if (sl == 0) {
