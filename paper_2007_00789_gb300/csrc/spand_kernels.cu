@@ -924,10 +924,9 @@ __global__ void __launch_bounds__(kQrThreads)
 // The same QR with the block held on chip: a thread-block cluster of C CTAs
 // (C = 1, 2, 4, 8 or 16) per interface, each CTA keeping a contiguous slice of
 // the columns in its shared memory for the whole factorization.  Per step the
-// CTAs exchange their local (largest, second largest) squared norms through
-// distributed shared memory, the CTA that owns the pivot column builds the
-// Householder vector, and the others copy it from the owner's shared memory.
-// Two cluster barriers per step; results are identical to k_rrqr's rules.
+// CTAs push their best candidates into each other's shared memory, one cluster
+// barrier, then every CTA reads the pivot column from its owner's shared
+// memory and forms the Householder vector itself.  The pivot rules are k_rrqr's.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
@@ -1052,16 +1051,58 @@ __device__ __forceinline__ void reflector_scalars(real_t alpha, real_t nsq, int 
   }
 }
 
+// The same scalars formed by every thread (FP32 storage: a few FP32 instructions).
+__device__ __forceinline__ void reflector_scalars_r(real_t alpha, real_t nsq, real_t* beta,
+                                                    real_t* tau, real_t* inv) {
+  const real_t nx = sqrt(nsq);
+  *beta = alpha;
+  *tau = 0;
+  *inv = 0;
+  if (nx != (real_t)0) {
+    *beta = alpha >= (real_t)0 ? -nx : nx;
+    *tau = (*beta - alpha) / *beta;
+    *inv = (real_t)1 / (alpha - *beta);
+  }
+}
+
+// Flags of one step: bit 0 a near tie of the two largest squared norms
+// (relative gap <= 1e-12), bit 1 the pivot's squared norm within 1e-10 of a
+// threshold.  FP32 norms: FP32 spacing (6e-8 relative) is far wider than either
+// margin, so a near tie is equality and a margin holds at most one value,
+// tested by key.  FP64 norms: the FP64 tests, reached only when the keys are
+// close (a relative gap of 1e-12 spans fewer than 2^14 doubles, one of 1e-10
+// fewer than 2^22).
+__device__ __forceinline__ int qr_step_flags(bool near, qkey_t bk, qkey_t second, double nu64,
+                                             double T1, double T2, double F1, double F2,
+                                             qkey_t f1lo, qkey_t f1hi, qkey_t f2lo, qkey_t f2hi,
+                                             bool superfine) {
+  int fl = 0;
+  if (sizeof(real_t) < sizeof(double) && !near) {
+    if (bk > 0 && second == bk) fl |= 1;
+    if ((bk >= f1lo && bk <= f1hi) || (superfine && bk >= f2lo && bk <= f2hi)) fl |= 2;
+    return fl;
+  }
+  const double nusq = near ? nu64 : QK::val(bk);
+  const long long k = __double_as_longlong(nusq);
+  if (second >= 0 && nusq > 0.0) {
+    const double sec = QK::val(second);
+    if (k - __double_as_longlong(sec) <= (1ll << 14) && nusq - sec <= 1e-12 * nusq) fl |= 1;
+  }
+  if (llabs(k - __double_as_longlong(T1)) <= (1ll << 22) && fabs(nusq - T1) <= F1) fl |= 2;
+  if (superfine && llabs(k - __double_as_longlong(T2)) <= (1ll << 22) && fabs(nusq - T2) <= F2)
+    fl |= 2;
+  return fl;
+}
+
 // One thread per column (or a few, rows split among them): the dot product
 // v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
 // in each thread; each thread also keeps the best candidate among its columns
 // for the next step.  The block is stored row-major (row i of the local
 // columns contiguous) so that a warp reads consecutive addresses.  Per step:
-// one block barrier and two cluster barriers.  The first cluster barrier is
-// split: between its arrive and its wait, warp 0 forms the reflector scalars of
-// its CTA's best candidate, so that the CTA that owns the pivot has them ready
-// when the exchange completes; every warp then reads the CTAs' candidates
-// itself, and the owner pushes v and tau into every CTA's shared memory.
+// two block barriers (three for FP64, whose reflector scalars one warp forms)
+// and one cluster barrier.  The owner keeps the pivot column intact until the
+// next step's barrier, when every CTA has read it, and only then writes its R
+// entries.
 __global__ void __launch_bounds__(kQrcMaxThreads)
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int csize) {
@@ -1069,10 +1110,9 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   const int crank = (int)cluster.block_rank();
   const RRQRTask t = tasks[blockIdx.x / csize];
   extern __shared__ real_t sm[];
-  __shared__ QrSlot s_slot;  // this CTA's candidates, read by the cluster
+  __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
-  __shared__ real_t s_refl[3];  // beta, tau, 1/(alpha - beta) for this CTA's best candidate
-  __shared__ real_t s_tau;      // tau of the current step, written by the owner
+  __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
   __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256, 512 or 1024
@@ -1153,45 +1193,61 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   // near-threshold flag margins
   double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
   qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0, f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;
+  // deferred R entries of the last pivot column (owner CTA only): other CTAs
+  // read that column one step later, so it is overwritten after the next
+  // exchange barrier
+  int pend_l = -1, pend_step = 0;
+  real_t pend_beta = 0;
   for (int step = 0; step < maxsteps; ++step) {
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+    QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
     if (warp == 0) {
+      QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
       if (lane < nw) cta = s_warp[lane];
       cta = warp_merge(cta);
-      if (lane == 0) s_slot = cta;
+      if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
     }
-    cluster.barrier_arrive();
-    if (warp == 0 && cta.best != kNoKey) reflector_scalars(cta.alpha, QK::rval(cta.best), lane, s_refl);
-    cluster.barrier_wait();
+    cluster.sync();
     QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    if (lane < csize) gb = *cluster.map_shared_rank(&s_slot, lane);
+    if (lane < csize) gb = in[lane];
     gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    if (pend_l >= 0) {
+      for (int i = pend_step + tid; i < m; i += nthr)
+        A[(size_t)i * ncl + pend_l] = (i == pend_step) ? pend_beta : (real_t)0;
+      pend_l = -1;
+    }
+    if (!(gb.idx >= 0 && gb.idx < N)) {  // no candidate left (N - step > 0 columns remain: not reached)
+      if (r < 0) r = step;
+      break;
+    }
     const qkey_t bk = gb.best;
     const int owner = gb.idx / cpb;
+    const int lp = gb.idx - owner * cpb;  // the pivot's column in the owner's slice
+    const real_t* pc = cluster.map_shared_rank(A, owner) + lp;
+    bool pulled = false;
     // FP32 storage: the decisions that set the rank (nu_0 and any step close to
     // a threshold) use the pivot column's norm recomputed in FP64
     bool near = false;
     double nu64 = 0.0;
     if constexpr (sizeof(real_t) < sizeof(double)) {
-      near = (step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2)) &&
-             gb.idx >= 0 && gb.idx < N;
+      near = step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2);
       if (near) {
-        if (crank == owner && warp == 0) {
-          const int l = gb.idx - g0;
+        for (int i = step + tid; i < m; i += nthr) v[i] = pc[(size_t)i * ncl];
+        pulled = true;
+        __syncthreads();
+        if (warp == 0) {
           double s64 = 0.0;
           for (int i = step + lane; i < m; i += kWarp) {
-            const double a = (double)A[(size_t)i * ncl + l];
+            const double a = (double)v[i];
             s64 = fma(a, a, s64);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
-          if (lane == 0)
-            for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_nu64, c) = s64;
+          if (lane == 0) s_nu64 = s64;
         }
-        cluster.sync();
+        __syncthreads();
         nu64 = s_nu64;
       }
     }
@@ -1219,58 +1275,54 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
         f2hi = QK::below(T2 + F2);
       }
     }
-    // flags (a near tie of the two largest norms; a norm within 1e-10 of a
-    // threshold) in one CTA other than the owner, off the pivot's path; the
-    // CTAs' flags are OR-ed at the end
-    if (tid == 0 && crank == (owner + 1) % csize) {
-      if (sizeof(real_t) < sizeof(double) && !near) {
-        // an FP32 norm: FP32 spacing (6e-8 relative) is far wider than either
-        // margin, so a near tie is equality and the threshold margins hold at
-        // most one value, tested by key
-        if (bk > 0 && gb.second == bk) flags |= 1;
-        if ((bk >= f1lo && bk <= f1hi) || (superfine && bk >= f2lo && bk <= f2hi)) flags |= 2;
-      } else {
-        // the FP64 tests, reached only when the keys are close: a relative gap
-        // of 1e-12 spans fewer than 2^14 doubles, one of 1e-10 fewer than 2^22
-        const double nusq = near ? nu64 : QK::val(bk);
-        const long long k = __double_as_longlong(nusq);
-        if (gb.second >= 0 && nusq > 0.0) {
-          const double sec = QK::val(gb.second);
-          if (k - __double_as_longlong(sec) <= (1ll << 14) && nusq - sec <= 1e-12 * nusq) flags |= 1;
-        }
-        if (llabs(k - __double_as_longlong(T1)) <= (1ll << 22) && fabs(nusq - T1) <= F1) flags |= 2;
-        if (superfine && llabs(k - __double_as_longlong(T2)) <= (1ll << 22) && fabs(nusq - T2) <= F2)
-          flags |= 2;
-      }
-    }
     const bool lt1 = near ? nu64 < T1 : bk < K1;
     const bool lt2 = near ? nu64 < T2 : bk < K2;
     if (r < 0 && lt1) {
       r = step;
-      if (!superfine) break;
-    }
-    if (superfine && lt2) break;
-    if (crank == owner) {
-      const int l = gb.idx - g0;
-      if (near && warp == 0) reflector_scalars(gb.alpha, (real_t)nu64, lane, s_refl);
-      __syncthreads();  // s_refl, written by warp 0
-      const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
-      for (int i = step + tid; i < m; i += nthr) {
-        real_t* ai = A + (size_t)i * ncl + l;
-        const real_t vi = (i == step) ? (real_t)1 : (*ai) * inv;
-        *ai = (i == step) ? beta : (real_t)0;
-        t.V[i + (size_t)step * m] = vi;
-        for (int c = 0; c < csize; ++c) cluster.map_shared_rank(v, c)[i] = vi;
+      if (!superfine) {
+        if (tid == 0 && crank == 0) flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2,
+                                                         f1lo, f1hi, f2lo, f2hi, superfine);
+        break;
       }
+    }
+    // the pivot column, read from its owner's shared memory (its rows at and
+    // below the pivot row), becomes v in every CTA
+    if (!pulled)
+      for (int i = step + tid; i < m; i += nthr) v[i] = pc[(size_t)i * ncl];
+    // flags (a near tie of the two largest norms; a norm within 1e-10 of a
+    // threshold), kept in CTA 0 while the column is in flight
+    if (tid == 0 && crank == 0)
+      flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2, f1lo, f1hi, f2lo, f2hi, superfine);
+    if (superfine && lt2) break;
+    const real_t nsq = near ? (real_t)nu64 : QK::rval(bk);
+    real_t beta, tau, inv;
+    if constexpr (sizeof(real_t) < sizeof(double)) {
+      // FP32: every warp forms the scalars itself
+      reflector_scalars_r(gb.alpha, nsq, &beta, &tau, &inv);
+    } else {
+      if (warp == 0) reflector_scalars(gb.alpha, nsq, lane, s_refl);
+      __syncthreads();  // s_refl, written by warp 0
+      beta = s_refl[0];
+      tau = s_refl[1];
+      inv = s_refl[2];
+    }
+    const bool own = crank == owner;
+    for (int i = step + tid; i < m; i += nthr) {  // the rows this thread read
+      const real_t vi = (i == step) ? (real_t)1 : v[i] * inv;
+      v[i] = vi;
+      if (own) t.V[i + (size_t)step * m] = vi;
+    }
+    if (own) {
       for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
       if (tid == 0) {
         t.tau[step] = tau;
-        norms[l] = -1;
-        for (int c = 0; c < csize; ++c) *cluster.map_shared_rank(&s_tau, c) = tau;
+        norms[lp] = -1;
       }
+      pend_l = lp;
+      pend_step = step;
+      pend_beta = beta;
     }
-    cluster.sync();
-    const real_t tau = s_tau;
+    __syncthreads();
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
@@ -1328,7 +1380,11 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   }
   if (r < 0) r = nsteps;
   if (tid == 0 && flags) atomicOr(cluster.map_shared_rank(&s_flags, 0), flags);
-  cluster.sync();
+  cluster.sync();  // every CTA has also read the last pivot column
+  if (pend_l >= 0)
+    for (int i = pend_step + tid; i < m; i += nthr)
+      A[(size_t)i * ncl + pend_l] = (i == pend_step) ? pend_beta : (real_t)0;
+  __syncthreads();
   // write the columns back, mirror the coarse rows into the neighbours' rows
   for (int e = tid; e < m * nloc; e += nthr) {
     const int i = e % m, l = e / m;
