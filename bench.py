@@ -411,7 +411,7 @@ def main():
                     help="serve workload: request arrivals per second (Poisson process)")
     ap.add_argument("--plain-launches", action="store_true",
                     help="no CUDA graphs: every kernel launched on its own (for profilers)")
-    ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512, 1024],
+    ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512],
                     help="threads per CTA of the on-chip RRQR (0: the library's choice)")
     ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: on-chip RRQR in clusters of up to 16 CTAs; 1: global-memory RRQR;"

@@ -79,7 +79,7 @@ typedef struct {
   int32_t plain_launches; /* 0 = replay refactorizations and applies from CUDA graphs (the
                              default); 1 = plain kernel launches only.  Same kernels, same
                              results; meant for profilers that cannot replay graph nodes. */
-  int32_t rrqr_threads;   /* threads per CTA of the on-chip RRQR: 256, 512 or 1024; 0 = the
+  int32_t rrqr_threads;   /* threads per CTA of the on-chip RRQR: 256 or 512; 0 = the
                              library's choice.  Changes only the order of some FP sums. */
   int32_t partition;      /* 0 = geometric nested dissection of the coordinates (algebraic when
                              coords is NULL or dim is 0); 1 = algebraic nested dissection of the

@@ -263,9 +263,8 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     if (opts->plain_launches < 0 || opts->plain_launches > 1)
       return fail(SPAND_EINVAL, "plain_launches must be 0 or 1");
     h->no_graph = opts->plain_launches == 1;
-    if (opts->rrqr_threads != 0 && opts->rrqr_threads != 256 && opts->rrqr_threads != 512 &&
-        opts->rrqr_threads != 1024)
-      return fail(SPAND_EINVAL, "rrqr_threads must be 0, 256, 512 or 1024");
+    if (opts->rrqr_threads != 0 && opts->rrqr_threads != 256 && opts->rrqr_threads != 512)
+      return fail(SPAND_EINVAL, "rrqr_threads must be 0, 256 or 512");
     h->rrqr_threads = opts->rrqr_threads;
   }
   if (opts && (opts->prescale < 0 || opts->prescale > 1)) return fail(SPAND_EINVAL, "prescale must be 0 or 1");

@@ -404,7 +404,7 @@ struct spand_s {
   int pcg_iters = 0;
   spand::Prof prof;
   int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel; 2: clusters <= 8
-  int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512, 1024); 0 = automatic
+  int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512); 0 = automatic
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
   spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own

@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
 // diagonal block becomes I_r and t.cur[p] = r.
 // ---------------------------------------------------------------------------
 constexpr int kQrThreads = 256;
-constexpr int kQrcMaxThreads = 1024;  // the cluster RRQR runs 256, 512 or 1024 threads per CTA
+constexpr int kQrcMaxThreads = 512;  // the cluster RRQR runs 256 or 512 threads per CTA
 
 struct ArgMax {
   real_t v;
@@ -1094,6 +1094,158 @@ __device__ __forceinline__ int qr_step_flags(bool near, qkey_t bk, qkey_t second
   return fl;
 }
 
+// One column's part of a step (a thread of the tpc that share the column):
+// the dot product v^T a over four partial sums, the update a -= tau (v^T a) v
+// four rows per pass with all loads ahead of the stores (a store to the block
+// could alias the next loads of v, which would serialise them), and the new
+// trailing norm over four partial sums.  The group's first thread records the
+// norm and offers the column as a candidate.
+__device__ __forceinline__ void qr_update_one(real_t* a, const real_t* v, int ncl, int step, int m,
+                                              int sl, int tpc, unsigned gmask, real_t tau, int gidx,
+                                              real_t* norm, QrSlot& mine) {
+  real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+  int i = step + sl;
+#pragma unroll 2
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    d0 = fma(v[i], a[(size_t)i * ncl], d0);
+    d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
+    d2 = fma(v[i + 2 * tpc], a[(size_t)(i + 2 * tpc) * ncl], d2);
+    d3 = fma(v[i + 3 * tpc], a[(size_t)(i + 3 * tpc) * ncl], d3);
+  }
+  for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+  real_t d = (d0 + d1) + (d2 + d3);
+  for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
+  const real_t f = tau * d;
+  real_t s2a = 0, s2b = 0, s2c = 0, s2d = 0;
+  i = step + sl;
+  const size_t rs = (size_t)tpc * ncl;
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    real_t* p0 = a + (size_t)i * ncl;
+    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
+    const real_t a0 = p0[0], a1 = p0[rs], a2 = p0[2 * rs], a3 = p0[3 * rs];
+    const real_t x0 = fma(-f, v0, a0), x1 = fma(-f, v1, a1);
+    const real_t x2 = fma(-f, v2, a2), x3 = fma(-f, v3, a3);
+    p0[0] = x0;
+    p0[rs] = x1;
+    p0[2 * rs] = x2;
+    p0[3 * rs] = x3;
+    if (i > step) s2a = fma(x0, x0, s2a);  // rows i + tpc, ... are below the pivot row
+    s2b = fma(x1, x1, s2b);
+    s2c = fma(x2, x2, s2c);
+    s2d = fma(x3, x3, s2d);
+  }
+  for (; i < m; i += tpc) {
+    const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
+    a[(size_t)i * ncl] = x0;
+    if (i > step) s2a = fma(x0, x0, s2a);
+  }
+  real_t s2 = (s2a + s2b) + (s2c + s2d);
+  for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
+  __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
+  if (sl == 0) {
+    *norm = s2;
+    QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? a[(size_t)(step + 1) * ncl] : (real_t)0, gidx};
+    slot_merge(mine, c);
+  }
+}
+
+// Two columns in one pass, each with exactly qr_update_one's arithmetic; a
+// column that is not live (pivoted) is read but neither written nor offered.
+__device__ __forceinline__ void qr_update_pair(real_t* a, real_t* b, bool ha, bool hb,
+                                               const real_t* v, int ncl, int step, int m, int sl,
+                                               int tpc, unsigned gmask, real_t tau, int ia, int ib,
+                                               real_t* na, real_t* nb, QrSlot& mine) {
+  real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+  int i = step + sl;
+  const size_t rs = (size_t)tpc * ncl;
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    const size_t o = (size_t)i * ncl;
+    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
+    d0 = fma(v0, a[o], d0);
+    e0 = fma(v0, b[o], e0);
+    d1 = fma(v1, a[o + rs], d1);
+    e1 = fma(v1, b[o + rs], e1);
+    d2 = fma(v2, a[o + 2 * rs], d2);
+    e2 = fma(v2, b[o + 2 * rs], e2);
+    d3 = fma(v3, a[o + 3 * rs], d3);
+    e3 = fma(v3, b[o + 3 * rs], e3);
+  }
+  for (; i < m; i += tpc) {
+    d0 = fma(v[i], a[(size_t)i * ncl], d0);
+    e0 = fma(v[i], b[(size_t)i * ncl], e0);
+  }
+  real_t d = (d0 + d1) + (d2 + d3), e = (e0 + e1) + (e2 + e3);
+  for (int o = tpc >> 1; o > 0; o >>= 1) {
+    d += __shfl_xor_sync(gmask, d, o);
+    e += __shfl_xor_sync(gmask, e, o);
+  }
+  const real_t f = tau * d, g = tau * e;
+  real_t s2a = 0, s2b = 0, s2c = 0, s2d = 0, t2a = 0, t2b = 0, t2c = 0, t2d = 0;
+  i = step + sl;
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    const size_t o = (size_t)i * ncl;
+    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
+    const real_t a0 = a[o], a1 = a[o + rs], a2 = a[o + 2 * rs], a3 = a[o + 3 * rs];
+    const real_t b0 = b[o], b1 = b[o + rs], b2 = b[o + 2 * rs], b3 = b[o + 3 * rs];
+    const real_t x0 = fma(-f, v0, a0), x1 = fma(-f, v1, a1);
+    const real_t x2 = fma(-f, v2, a2), x3 = fma(-f, v3, a3);
+    const real_t y0 = fma(-g, v0, b0), y1 = fma(-g, v1, b1);
+    const real_t y2 = fma(-g, v2, b2), y3 = fma(-g, v3, b3);
+    if (ha) {
+      a[o] = x0;
+      a[o + rs] = x1;
+      a[o + 2 * rs] = x2;
+      a[o + 3 * rs] = x3;
+    }
+    if (hb) {
+      b[o] = y0;
+      b[o + rs] = y1;
+      b[o + 2 * rs] = y2;
+      b[o + 3 * rs] = y3;
+    }
+    if (i > step) {
+      s2a = fma(x0, x0, s2a);
+      t2a = fma(y0, y0, t2a);
+    }
+    s2b = fma(x1, x1, s2b);
+    t2b = fma(y1, y1, t2b);
+    s2c = fma(x2, x2, s2c);
+    t2c = fma(y2, y2, t2c);
+    s2d = fma(x3, x3, s2d);
+    t2d = fma(y3, y3, t2d);
+  }
+  for (; i < m; i += tpc) {
+    const size_t o = (size_t)i * ncl;
+    const real_t x0 = fma(-f, v[i], a[o]);
+    const real_t y0 = fma(-g, v[i], b[o]);
+    if (ha) a[o] = x0;
+    if (hb) b[o] = y0;
+    if (i > step) {
+      s2a = fma(x0, x0, s2a);
+      t2a = fma(y0, y0, t2a);
+    }
+  }
+  real_t s2 = (s2a + s2b) + (s2c + s2d), t2 = (t2a + t2b) + (t2c + t2d);
+  for (int o = tpc >> 1; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(gmask, s2, o);
+    t2 += __shfl_xor_sync(gmask, t2, o);
+  }
+  __syncwarp(gmask);  // the row step+1 entries were written by another thread of the group
+  if (sl == 0) {
+    const bool nxt = step + 1 < m;
+    if (ha) {
+      *na = s2;
+      QrSlot c{QK::of(s2), kNoKey, nxt ? a[(size_t)(step + 1) * ncl] : (real_t)0, ia};
+      slot_merge(mine, c);
+    }
+    if (hb) {
+      *nb = t2;
+      QrSlot c{QK::of(t2), kNoKey, nxt ? b[(size_t)(step + 1) * ncl] : (real_t)0, ib};
+      slot_merge(mine, c);
+    }
+  }
+}
+
 // One thread per column (or a few, rows split among them): the dot product
 // v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
 // in each thread; each thread also keeps the best candidate among its columns
@@ -1115,7 +1267,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
   __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N, s_flags;
-  const int nthr = (int)blockDim.x;  // 256, 512 or 1024
+  const int nthr = (int)blockDim.x;  // 256 or 512
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
   const int m = t.m;
   const size_t ld = t.ld;
@@ -1324,57 +1476,20 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     }
     __syncthreads();
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    for (int l = grp; l < nloc; l += ngrp) {
+    // FP32: a thread with two columns (l, l + ngrp) updates both in one pass,
+    // which doubles its independent chains; every column sees the same
+    // arithmetic (four partial sums over the same rows) on either path
+    constexpr bool kPairs = sizeof(real_t) < sizeof(double);
+    for (int l = grp; l < nloc; l += (kPairs ? 2 : 1) * ngrp) {
+      const int l2 = l + ngrp;
+      if (kPairs && l2 < nloc) {
+        const bool h1 = norms[l] >= (real_t)0, h2 = norms[l2] >= (real_t)0;
+        if (h1 || h2) qr_update_pair(A + l, A + l2, h1, h2, v, ncl, step, m, sl, tpc, gmask, tau,
+                                     g0 + l, g0 + l2, norms + l, norms + l2, mine);
+        continue;
+      }
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
-      real_t* a = A + l;
-      // four independent partial dot products, two for the new norm: the
-      // per-thread chains are what bounds the latency of a step
-      real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-      int i = step + sl;
-#pragma unroll 2
-      for (; i + 3 * tpc < m; i += 4 * tpc) {
-        d0 = fma(v[i], a[(size_t)i * ncl], d0);
-        d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
-        d2 = fma(v[i + 2 * tpc], a[(size_t)(i + 2 * tpc) * ncl], d2);
-        d3 = fma(v[i + 3 * tpc], a[(size_t)(i + 3 * tpc) * ncl], d3);
-      }
-      for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
-      real_t d = (d0 + d1) + (d2 + d3);
-      for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(gmask, d, o);
-      const real_t f = tau * d;
-      // four rows per pass, all loads ahead of the stores (a store to the
-      // block could alias the next loads of v, which would serialise them)
-      real_t s2a = 0, s2b = 0, s2c = 0, s2d = 0;
-      i = step + sl;
-      const size_t rs = (size_t)tpc * ncl;
-      for (; i + 3 * tpc < m; i += 4 * tpc) {
-        real_t* p0 = a + (size_t)i * ncl;
-        const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
-        const real_t a0 = p0[0], a1 = p0[rs], a2 = p0[2 * rs], a3 = p0[3 * rs];
-        const real_t x0 = fma(-f, v0, a0), x1 = fma(-f, v1, a1);
-        const real_t x2 = fma(-f, v2, a2), x3 = fma(-f, v3, a3);
-        p0[0] = x0;
-        p0[rs] = x1;
-        p0[2 * rs] = x2;
-        p0[3 * rs] = x3;
-        if (i > step) s2a = fma(x0, x0, s2a);  // rows i + tpc, ... are below the pivot row
-        s2b = fma(x1, x1, s2b);
-        s2c = fma(x2, x2, s2c);
-        s2d = fma(x3, x3, s2d);
-      }
-      for (; i < m; i += tpc) {
-        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
-        a[(size_t)i * ncl] = x0;
-        if (i > step) s2a = fma(x0, x0, s2a);
-      }
-      real_t s2 = (s2a + s2b) + (s2c + s2d);
-      for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
-      __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
-      if (sl == 0) {
-        norms[l] = s2;
-        QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? a[(size_t)(step + 1) * ncl] : (real_t)0, g0 + l};
-        slot_merge(mine, c);
-      }
+      qr_update_one(A + l, v, ncl, step, m, sl, tpc, gmask, tau, g0 + l, norms + l, mine);
     }
     nsteps = step + 1;
   }
