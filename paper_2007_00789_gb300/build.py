@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspand.so")
 
 # (source, extra flags): the factor/apply translation units are compiled once per precision
-_F32 = ["-DSPAND_REAL=float", "-DSPAND_NS=f32"]
+_F32 = ["-DSPAND_REAL=float", "-DSPAND_NS=f32", "-DSPAND_SINGLE=1"]
 _F64 = ["-DSPAND_REAL=double", "-DSPAND_NS=f64"]
 SOURCES = [
     ("symbolic.cpp", []), ("api.cu", []), ("spand_pcg.cu", []), ("engine.cu", []),

@@ -197,7 +197,7 @@ struct Prof {
   }
 };
 
-constexpr int kQrClusterSmem = 200 * 1024;  // shared-memory slice per CTA of the on-chip RRQR
+constexpr int kQrClusterSmem = 224 * 1024;  // shared-memory slice per CTA of the on-chip RRQR
 constexpr int kNumSMs = 152;                 // GB300
 
 enum PhaseKind { PH_INTERIOR = 0, PH_SCALE = 1, PH_QE = 2 };

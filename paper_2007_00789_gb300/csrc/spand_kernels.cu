@@ -1094,6 +1094,473 @@ __device__ __forceinline__ int qr_step_flags(bool near, qkey_t bk, qkey_t second
   return fl;
 }
 
+// Two layouts of the on-chip block, one per storage precision.  FP32: column-
+// major in 16-byte vectors (the update is bound by issue and shared-memory
+// latency, which 128-bit accesses cut, and the pivot column is read in
+// vectors).  FP64: row-major with scalar accesses (the update is bound by the
+// FP64 pipe, and this layout measured faster there).
+#ifdef SPAND_SINGLE
+// The block on chip is column-major: each local column holds ldm = nch x kv
+// entries (kv = 16 / sizeof(real_t), nch odd), so that a column is a run of
+// 16-byte vectors and the lanes of a warp, on different columns, hit different
+// 16-byte bank groups.  A thread of the tpc that share a column takes its
+// vectors c0 + sl, c0 + sl + tpc, ... (c0: the vector holding the pivot row),
+// four rows per pass, with four partial sums for the dot product v^T a and for
+// the new trailing norm, over the nv = ceil(m / kv) vectors that hold rows; v is
+// zero above the pivot row and below row m (so are the padding rows of the
+// block), and entries above the pivot row are kept.
+constexpr int kQv = 16 / (int)sizeof(real_t);  // entries per 16-byte vector
+constexpr int kQu = 4 / kQv;                    // vectors per pass (four rows)
+struct alignas(16) QVec {
+  real_t x[kQv];
+};
+
+// the column's local layout: an odd number of vectors per column
+__host__ __device__ inline int qr_cm_nvec(int m) {
+  const int n = (m + kQv - 1) / kQv;
+  return (n & 1) ? n : n + 1;
+}
+
+__device__ __forceinline__ real_t qr_dot(const QVec* a, const QVec* w, int c0, int nv, int sl,
+                                         int tpc, unsigned gmask) {
+  real_t d[4] = {0, 0, 0, 0};
+  for (int c = c0 + sl; c < nv; c += kQu * tpc) {
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int cc = c + u * tpc;
+      if (kQu == 1 || cc < nv) {
+        const QVec x = a[cc], y = w[cc];
+#pragma unroll
+        for (int j = 0; j < kQv; ++j) d[u * kQv + j] = fma(y.x[j], x.x[j], d[u * kQv + j]);
+      }
+    }
+  }
+  real_t s = (d[0] + d[1]) + (d[2] + d[3]);
+  for (int o = tpc >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+  return s;
+}
+
+// a -= f w on the thread's vectors (entries above the pivot row kept); returns
+// the thread's part of the squared norm below the pivot row, reduced over the group
+__device__ __forceinline__ real_t qr_axpy_norm(QVec* a, const QVec* w, real_t f, bool store, int c0,
+                                               int nv, int step, int sl, int tpc, unsigned gmask) {
+  real_t s[4] = {0, 0, 0, 0};
+  for (int c = c0 + sl; c < nv; c += kQu * tpc) {
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int cc = c + u * tpc;
+      if (kQu == 1 || cc < nv) {
+        const QVec x = a[cc], y = w[cc];
+        QVec z;
+#pragma unroll
+        for (int j = 0; j < kQv; ++j) {
+          const int i = cc * kQv + j;
+          z.x[j] = (i < step) ? x.x[j] : fma(-f, y.x[j], x.x[j]);
+          if (i > step) s[u * kQv + j] = fma(z.x[j], z.x[j], s[u * kQv + j]);
+        }
+        if (store) a[cc] = z;
+      }
+    }
+  }
+  real_t t = (s[0] + s[1]) + (s[2] + s[3]);
+  for (int o = tpc >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(gmask, t, o);
+  return t;
+}
+
+// One column's part of a step; the group's first thread records the new norm
+// and offers the column as a candidate.
+__device__ __forceinline__ void qr_update_one(real_t* col, const real_t* v, int c0, int nv, int step,
+                                              int m, int sl, int tpc, unsigned gmask, real_t tau,
+                                              int gidx, real_t* norm, QrSlot& mine) {
+  QVec* a = reinterpret_cast<QVec*>(col);
+  const QVec* w = reinterpret_cast<const QVec*>(v);
+  const real_t f = tau * qr_dot(a, w, c0, nv, sl, tpc, gmask);
+  const real_t s2 = qr_axpy_norm(a, w, f, true, c0, nv, step, sl, tpc, gmask);
+  __syncwarp(gmask);  // the row step+1 entry was written by another thread of the group
+  if (sl == 0) {
+    *norm = s2;
+    QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? col[step + 1] : (real_t)0, gidx};
+    slot_merge(mine, c);
+  }
+}
+
+// Two columns in one pass (FP32: twice the independent chains per thread),
+// each with exactly qr_update_one's arithmetic; a column that is not live
+// (pivoted) is read but neither written nor offered.
+__device__ __forceinline__ void qr_update_pair(real_t* ca, real_t* cb, bool ha, bool hb,
+                                               const real_t* v, int c0, int nv, int step, int m,
+                                               int sl, int tpc, unsigned gmask, real_t tau, int ia,
+                                               int ib, real_t* na, real_t* nb, QrSlot& mine) {
+  QVec* a = reinterpret_cast<QVec*>(ca);
+  QVec* b = reinterpret_cast<QVec*>(cb);
+  const QVec* w = reinterpret_cast<const QVec*>(v);
+  real_t d[4] = {0, 0, 0, 0}, e[4] = {0, 0, 0, 0};
+  for (int c = c0 + sl; c < nv; c += kQu * tpc) {
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int cc = c + u * tpc;
+      if (kQu == 1 || cc < nv) {
+        const QVec x = a[cc], y = b[cc], z = w[cc];
+#pragma unroll
+        for (int j = 0; j < kQv; ++j) {
+          d[u * kQv + j] = fma(z.x[j], x.x[j], d[u * kQv + j]);
+          e[u * kQv + j] = fma(z.x[j], y.x[j], e[u * kQv + j]);
+        }
+      }
+    }
+  }
+  real_t sd = (d[0] + d[1]) + (d[2] + d[3]), se = (e[0] + e[1]) + (e[2] + e[3]);
+  for (int o = tpc >> 1; o > 0; o >>= 1) {
+    sd += __shfl_xor_sync(gmask, sd, o);
+    se += __shfl_xor_sync(gmask, se, o);
+  }
+  const real_t f = tau * sd, g = tau * se;
+  real_t s[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0};
+  for (int c = c0 + sl; c < nv; c += kQu * tpc) {
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int cc = c + u * tpc;
+      if (kQu == 1 || cc < nv) {
+        const QVec x = a[cc], y = b[cc], z = w[cc];
+        QVec p, q;
+#pragma unroll
+        for (int j = 0; j < kQv; ++j) {
+          const int i = cc * kQv + j;
+          p.x[j] = (i < step) ? x.x[j] : fma(-f, z.x[j], x.x[j]);
+          q.x[j] = (i < step) ? y.x[j] : fma(-g, z.x[j], y.x[j]);
+          if (i > step) {
+            s[u * kQv + j] = fma(p.x[j], p.x[j], s[u * kQv + j]);
+            r[u * kQv + j] = fma(q.x[j], q.x[j], r[u * kQv + j]);
+          }
+        }
+        if (ha) a[cc] = p;
+        if (hb) b[cc] = q;
+      }
+    }
+  }
+  real_t s2 = (s[0] + s[1]) + (s[2] + s[3]), t2 = (r[0] + r[1]) + (r[2] + r[3]);
+  for (int o = tpc >> 1; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(gmask, s2, o);
+    t2 += __shfl_xor_sync(gmask, t2, o);
+  }
+  __syncwarp(gmask);  // the row step+1 entries were written by another thread of the group
+  if (sl == 0) {
+    const bool nxt = step + 1 < m;
+    if (ha) {
+      *na = s2;
+      QrSlot c{QK::of(s2), kNoKey, nxt ? ca[step + 1] : (real_t)0, ia};
+      slot_merge(mine, c);
+    }
+    if (hb) {
+      *nb = t2;
+      QrSlot c{QK::of(t2), kNoKey, nxt ? cb[step + 1] : (real_t)0, ib};
+      slot_merge(mine, c);
+    }
+  }
+}
+
+// the squared norm of a whole column, with the partial sums of qr_axpy_norm
+__device__ __forceinline__ real_t qr_sumsq(const real_t* col, int nv, int sl, int tpc, unsigned gmask) {
+  const QVec* a = reinterpret_cast<const QVec*>(col);
+  real_t s[4] = {0, 0, 0, 0};
+  for (int c = sl; c < nv; c += kQu * tpc) {
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int cc = c + u * tpc;
+      if (kQu == 1 || cc < nv) {
+        const QVec x = a[cc];
+#pragma unroll
+        for (int j = 0; j < kQv; ++j) s[u * kQv + j] = fma(x.x[j], x.x[j], s[u * kQv + j]);
+      }
+    }
+  }
+  real_t t = (s[0] + s[1]) + (s[2] + s[3]);
+  for (int o = tpc >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(gmask, t, o);
+  return t;
+}
+
+// One thread per column (or a few, rows split among them): the dot product
+// v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
+// in each thread; each thread also keeps the best candidate among its columns
+// for the next step.  Per step: two block barriers (three for FP64, whose
+// reflector scalars one warp forms) and one cluster barrier.  The owner keeps
+// the pivot column intact until the next step's barrier, when every CTA has
+// read it, and only then writes its R entries.
+__global__ void __launch_bounds__(kQrcMaxThreads)
+    k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
+                   int csize) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const RRQRTask t = tasks[blockIdx.x / csize];
+  extern __shared__ real_t sm[];
+  __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
+  __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
+  __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
+  __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
+  __shared__ int s_N, s_flags;
+  const int nthr = (int)blockDim.x;  // 256 or 512
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
+  const int m = t.m;
+  const size_t ld = t.ld;
+  const int nseg = t.seg_end - t.seg_begin;
+  const int ncl = (t.ncols_max + csize - 1) / csize;  // local column capacity
+  // column stride: an odd number of vectors (bank spread); the arithmetic runs
+  // over the nc vectors that hold rows
+  const int nch = qr_cm_nvec(m), ldm = nch * kQv, nc = (m + kQv - 1) / kQv;
+  real_t* v = reinterpret_cast<real_t*>((reinterpret_cast<uintptr_t>(sm) + 15) & ~(uintptr_t)15);
+  real_t* A = v + ldm;                                 // ncl columns of ldm entries
+  real_t* norms = A + (size_t)ncl * ldm;               // ncl
+  int* pcol = reinterpret_cast<int*>(norms + ncl);     // ncl: column in the panel row
+  int* segid = pcol + ncl;                             // ncl: segment of the column
+  int* segoff = segid + ncl;                           // nseg + 1
+  if (tid == 0) {
+    int acc = 0;
+    for (int g = 0; g < nseg; ++g) {
+      segoff[g] = acc;
+      acc += t.cur[segs[t.seg_begin + g].cl];
+    }
+    segoff[nseg] = acc;
+    s_N = acc;
+    s_flags = 0;
+  }
+  __syncthreads();
+  const int N = s_N;
+  const int cpb = (N + csize - 1) / csize;
+  const int g0 = crank * cpb;
+  const int nloc = max(0, min(N, g0 + cpb) - g0);
+  // tpc threads share a column (its rows split among them), enough to keep all
+  // warps busy when the CTA holds few columns
+  int tpc = 1;
+  while (tpc < 8 && nloc * tpc * 2 <= nthr) tpc *= 2;
+  const int ngrp = nthr / tpc, grp = tid / tpc, sl = tid % tpc;
+  const unsigned gmask = (tpc == 32) ? 0xffffffffu : (((1u << tpc) - 1u) << (lane & ~(tpc - 1)));
+  for (int l = tid; l < nloc; l += nthr) {
+    const int g = g0 + l;
+    int lo = 0, hi = nseg - 1;  // last segment with segoff <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segoff[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    segid[l] = lo;
+    pcol[l] = segs[t.seg_begin + lo].col + (g - segoff[lo]);
+  }
+  __syncthreads();
+  for (int e = tid; e < ldm * nloc; e += nthr) {
+    const int i = e % ldm, l = e / ldm;
+    A[(size_t)l * ldm + i] = (i < m) ? t.A[i + (size_t)pcol[l] * ld] : (real_t)0;
+  }
+  __syncthreads();
+  QrSlot mine{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+  for (int l = grp; l < nloc; l += ngrp) {
+    const real_t s2 = qr_sumsq(A + (size_t)l * ldm, nc, sl, tpc, gmask);
+    if (sl == 0) {
+      norms[l] = s2;
+      QrSlot c{QK::of(s2), kNoKey, m > 0 ? A[(size_t)l * ldm] : (real_t)0, g0 + l};
+      slot_merge(mine, c);
+    }
+  }
+  const double eps = t.eps;
+  const int scheme = t.scheme;
+  const bool superfine = scheme == SPAND_SECOND_ORDER_SUPERFINE;
+  const double thr1 = eps * eps;
+  const double thr2 = thr1 * thr1;
+  const int maxsteps = min(m, N);
+  int r = -1, nsteps = 0, flags = 0;
+  // thresholds, fixed once nu_0 is known: as doubles, as keys (value < T <=>
+  // key < K), the FP32 windows in which the norm is recomputed in FP64, and the
+  // near-threshold flag margins
+  double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
+  qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0, f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;
+  // deferred R entries of the last pivot column (owner CTA only): other CTAs
+  // read that column one step later, so it is overwritten after the next
+  // exchange barrier
+  int pend_l = -1, pend_step = 0;
+  real_t pend_beta = 0;
+  for (int step = 0; step < maxsteps; ++step) {
+    mine = warp_merge(mine);
+    if (lane == 0) s_warp[warp] = mine;
+    __syncthreads();
+    QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
+    if (warp == 0) {
+      QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+      if (lane < nw) cta = s_warp[lane];
+      cta = warp_merge(cta);
+      if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
+    }
+    cluster.sync();
+    QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+    if (lane < csize) gb = in[lane];
+    gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    if (pend_l >= 0) {
+      for (int i = pend_step + tid; i < m; i += nthr)
+        A[(size_t)pend_l * ldm + i] = (i == pend_step) ? pend_beta : (real_t)0;
+      pend_l = -1;
+    }
+    if (!(gb.idx >= 0 && gb.idx < N)) {  // no candidate left (N - step > 0 columns remain: not reached)
+      if (r < 0) r = step;
+      break;
+    }
+    const qkey_t bk = gb.best;
+    const int owner = gb.idx / cpb;
+    const int lp = gb.idx - owner * cpb;  // the pivot's column in the owner's slice
+    // the pivot column in the owner's shared memory, read in 16-byte vectors
+    // from the one holding the pivot row
+    const QVec* pcv = reinterpret_cast<const QVec*>(cluster.map_shared_rank(A, owner) + (size_t)lp * ldm);
+    QVec* vv = reinterpret_cast<QVec*>(v);
+    const int c0 = step / kQv;
+    bool pulled = false;
+    // FP32 storage: the decisions that set the rank (nu_0 and any step close to
+    // a threshold) use the pivot column's norm recomputed in FP64
+    bool near = false;
+    double nu64 = 0.0;
+    if constexpr (sizeof(real_t) < sizeof(double)) {
+      near = step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2);
+      if (near) {
+        for (int c = c0 + tid; c < nc; c += nthr) vv[c] = pcv[c];
+        pulled = true;
+        __syncthreads();
+        if (warp == 0) {
+          double s64 = 0.0;
+          for (int i = step + lane; i < m; i += kWarp) {
+            const double a = (double)v[i];
+            s64 = fma(a, a, s64);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          if (lane == 0) s_nu64 = s64;
+        }
+        __syncthreads();
+        nu64 = s_nu64;
+      }
+    }
+    if (step == 0) {
+      nu0sq = near ? nu64 : QK::val(bk);
+      if (!(nu0sq > 0.0)) {
+        r = 0;
+        break;
+      }
+      T1 = thr1 * nu0sq;
+      T2 = thr2 * nu0sq;
+      K1 = QK::above(T1);
+      K2 = QK::above(T2);
+      F1 = 1e-10 * thr1 * nu0sq;
+      F2 = 1e-10 * thr2 * nu0sq;
+      if constexpr (sizeof(real_t) < sizeof(double)) {
+        const double w1 = 1e-4 * thr1 * nu0sq, w2 = 1e-4 * thr2 * nu0sq;
+        lo1 = QK::above(T1 - w1);
+        hi1 = QK::below(T1 + w1);
+        lo2 = QK::above(T2 - w2);
+        hi2 = QK::below(T2 + w2);
+        f1lo = QK::above(T1 - F1);
+        f1hi = QK::below(T1 + F1);
+        f2lo = QK::above(T2 - F2);
+        f2hi = QK::below(T2 + F2);
+      }
+    }
+    const bool lt1 = near ? nu64 < T1 : bk < K1;
+    const bool lt2 = near ? nu64 < T2 : bk < K2;
+    if (r < 0 && lt1) {
+      r = step;
+      if (!superfine) {
+        if (tid == 0 && crank == 0) flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2,
+                                                         f1lo, f1hi, f2lo, f2hi, superfine);
+        break;
+      }
+    }
+    // the pivot column, read from its owner's shared memory (its rows at and
+    // below the pivot row), becomes v in every CTA
+    if (!pulled)
+      for (int c = c0 + tid; c < nc; c += nthr) vv[c] = pcv[c];
+    // flags (a near tie of the two largest norms; a norm within 1e-10 of a
+    // threshold), kept in CTA 0 while the column is in flight
+    if (tid == 0 && crank == 0)
+      flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2, f1lo, f1hi, f2lo, f2hi, superfine);
+    if (superfine && lt2) break;
+    const real_t nsq = near ? (real_t)nu64 : QK::rval(bk);
+    real_t beta, tau, inv;
+    if constexpr (sizeof(real_t) < sizeof(double)) {
+      // FP32: every warp forms the scalars itself
+      reflector_scalars_r(gb.alpha, nsq, &beta, &tau, &inv);
+    } else {
+      if (warp == 0) reflector_scalars(gb.alpha, nsq, lane, s_refl);
+      __syncthreads();  // s_refl, written by warp 0
+      beta = s_refl[0];
+      tau = s_refl[1];
+      inv = s_refl[2];
+    }
+    const bool own = crank == owner;
+    for (int c = c0 + tid; c < nc; c += nthr) {  // the vectors this thread read
+#pragma unroll
+      for (int j = 0; j < kQv; ++j) {
+        const int i = c * kQv + j;
+        const real_t vi = (i < step || i >= m) ? (real_t)0 : (i == step) ? (real_t)1 : v[i] * inv;
+        v[i] = vi;
+        if (own && i >= step && i < m) t.V[i + (size_t)step * m] = vi;
+      }
+    }
+    if (own) {
+      for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
+      if (tid == 0) {
+        t.tau[step] = tau;
+        norms[lp] = -1;
+      }
+      pend_l = lp;
+      pend_step = step;
+      pend_beta = beta;
+    }
+    __syncthreads();
+    mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+    // FP32: a thread with two columns (l, l + ngrp) updates both in one pass,
+    // which doubles its independent chains; every column sees the same
+    // arithmetic (four partial sums over the same rows) on either path
+    constexpr bool kPairs = sizeof(real_t) < sizeof(double);
+    for (int l = grp; l < nloc; l += (kPairs ? 2 : 1) * ngrp) {
+      const int l2 = l + ngrp;
+      if (kPairs && l2 < nloc) {
+        const bool h1 = norms[l] >= (real_t)0, h2 = norms[l2] >= (real_t)0;
+        if (h1 || h2) qr_update_pair(A + (size_t)l * ldm, A + (size_t)l2 * ldm, h1, h2, v, c0, nc, step, m, sl, tpc, gmask, tau,
+                                     g0 + l, g0 + l2, norms + l, norms + l2, mine);
+        continue;
+      }
+      if (norms[l] < (real_t)0) continue;  // the same l for the whole group
+      qr_update_one(A + (size_t)l * ldm, v, c0, nc, step, m, sl, tpc, gmask, tau, g0 + l, norms + l, mine);
+    }
+    nsteps = step + 1;
+  }
+  if (r < 0) r = nsteps;
+  if (tid == 0 && flags) atomicOr(cluster.map_shared_rank(&s_flags, 0), flags);
+  cluster.sync();  // every CTA has also read the last pivot column
+  if (pend_l >= 0)
+    for (int i = pend_step + tid; i < m; i += nthr)
+      A[(size_t)pend_l * ldm + i] = (i == pend_step) ? pend_beta : (real_t)0;
+  __syncthreads();
+  // write the columns back, mirror the coarse rows into the neighbours' rows
+  for (int e = tid; e < m * nloc; e += nthr) {
+    const int i = e % m, l = e / m;
+    t.A[i + (size_t)pcol[l] * ld] = A[(size_t)l * ldm + i];
+  }
+  for (int e = tid; e < r * nloc; e += nthr) {
+    const int i = e % r, l = e / r;
+    const RRQRSeg g = segs[t.seg_begin + segid[l]];
+    const int c = g0 + l - segoff[segid[l]];
+    g.mirror[c + (size_t)i * g.mirror_ld] = A[(size_t)l * ldm + i];
+  }
+  if (crank == 0) {
+    for (int e = tid; e < r * r; e += nthr) {
+      const int i = e % r, j = e / r;
+      t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid == 0) {
+      t.rank[t.id] = r;
+      t.nref[t.id] = nsteps;
+      t.cur[t.id] = r;
+      t.flag[t.id] = s_flags;
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+#else  // FP64 storage: row-major block
 // One column's part of a step (a thread of the tpc that share the column):
 // the dot product v^T a over four partial sums, the update a -= tau (v^T a) v
 // four rows per pass with all loads ahead of the stores (a store to the block
@@ -1525,6 +1992,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
+#endif
 
 }  // namespace
 
@@ -1594,9 +2062,15 @@ void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cud
 }
 
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
-  const long ncl = ((ncols_max + csize - 1) / csize) | 1;
   const long e = (long)sizeof(real_t);
+#ifdef SPAND_SINGLE
+  const long ncl = (ncols_max + csize - 1) / csize;
+  const long ldm = (long)qr_cm_nvec(m) * kQv;
+  const long b = 16 + e * ldm * (ncl + 1) + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
+#else
+  const long ncl = ((ncols_max + csize - 1) / csize) | 1;
   const long b = e * m * ncl + e * m + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
+#endif
   return (int)std::min<long>(b, 1L << 30);
 }
 
