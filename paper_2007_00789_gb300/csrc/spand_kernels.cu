@@ -1388,10 +1388,16 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       cta = warp_merge(cta);
       if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
     }
-    cluster.sync();
-    QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    if (lane < csize) gb = in[lane];
-    gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    QrSlot gb;
+    if (csize == 1) {  // a lone CTA: its own best is the pivot
+      __syncthreads();
+      gb = in[0];
+    } else {
+      cluster.sync();
+      gb = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+      if (lane < csize) gb = in[lane];
+      gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    }
     if (pend_l >= 0) {
       for (int i = pend_step + tid; i < m; i += nthr)
         A[(size_t)pend_l * ldm + i] = (i == pend_step) ? pend_beta : (real_t)0;
@@ -1409,6 +1415,12 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     const QVec* pcv = reinterpret_cast<const QVec*>(cluster.map_shared_rank(A, owner) + (size_t)lp * ldm);
     QVec* vv = reinterpret_cast<QVec*>(v);
     const int c0 = step / kQv;
+    // each thread's first vector of the column stays in registers from here to
+    // the scaling below, the load in flight through the decisions; further
+    // vectors (columns of more than nthr vectors) go through shared memory
+    const int cme = c0 + tid;
+    QVec pv;
+    if (cme < nc) pv = pcv[cme];
     bool pulled = false;
     // FP32 storage: the decisions that set the rank (nu_0 and any step close to
     // a threshold) use the pivot column's norm recomputed in FP64
@@ -1417,7 +1429,8 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     if constexpr (sizeof(real_t) < sizeof(double)) {
       near = step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2);
       if (near) {
-        for (int c = c0 + tid; c < nc; c += nthr) vv[c] = pcv[c];
+        if (cme < nc) vv[cme] = pv;
+        for (int c = cme + nthr; c < nc; c += nthr) vv[c] = pcv[c];
         pulled = true;
         __syncthreads();
         if (warp == 0) {
@@ -1471,7 +1484,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     // the pivot column, read from its owner's shared memory (its rows at and
     // below the pivot row), becomes v in every CTA
     if (!pulled)
-      for (int c = c0 + tid; c < nc; c += nthr) vv[c] = pcv[c];
+      for (int c = cme + nthr; c < nc; c += nthr) vv[c] = pcv[c];
     // flags (a near tie of the two largest norms; a norm within 1e-10 of a
     // threshold), kept in CTA 0 while the column is in flight
     if (tid == 0 && crank == 0)
@@ -1490,15 +1503,17 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       inv = s_refl[2];
     }
     const bool own = crank == owner;
-    for (int c = c0 + tid; c < nc; c += nthr) {  // the vectors this thread read
+    auto scale = [&](QVec x, int c) {
 #pragma unroll
       for (int j = 0; j < kQv; ++j) {
         const int i = c * kQv + j;
-        const real_t vi = (i < step || i >= m) ? (real_t)0 : (i == step) ? (real_t)1 : v[i] * inv;
-        v[i] = vi;
-        if (own && i >= step && i < m) t.V[i + (size_t)step * m] = vi;
+        x.x[j] = (i < step || i >= m) ? (real_t)0 : (i == step) ? (real_t)1 : x.x[j] * inv;
+        if (own && i >= step && i < m) t.V[i + (size_t)step * m] = x.x[j];
       }
-    }
+      vv[c] = x;
+    };
+    if (cme < nc) scale(pv, cme);
+    for (int c = cme + nthr; c < nc; c += nthr) scale(vv[c], c);  // the vectors this thread read
     if (own) {
       for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
       if (tid == 0) {
