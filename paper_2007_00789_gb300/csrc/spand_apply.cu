@@ -22,6 +22,13 @@ namespace {
 
 constexpr int kApThreads = 256;
 constexpr int kApWarps = kApThreads / 32;
+// FP64: at most 128 registers (two CTAs per SM) stated, which the compiler
+// otherwise undercuts with spills; FP32: the compiler's own choice measured best
+#ifdef SPAND_SINGLE
+#define AP_BOUNDS __launch_bounds__(kApThreads)
+#else
+#define AP_BOUNDS __launch_bounds__(kApThreads, 2)
+#endif
 
 namespace cg = cooperative_groups;
 
@@ -30,6 +37,70 @@ namespace cg = cooperative_groups;
 // independent coalesced loads in flight.  Each matrix element loaded feeds NV
 // FMAs (one per vector).  The vectors sit in shared memory, vector v at
 // x + v * xs.
+
+// One 64-row tile starting at rt of gemv_n below; TWO = false when the tile's
+// second half holds no row, so that no instruction is spent on it (an FP64
+// instruction costs its full warp width on the narrow FP64 pipe whatever the
+// active lanes).
+template <int NV, bool TWO, class Out>
+__device__ __forceinline__ void gemv_n_tile(const real_t* __restrict__ M, size_t ld, int r0, int r1,
+                                            int rt, int C, const real_t* __restrict__ x, int xs,
+                                            real_t* red, Out& out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ra = rt + lane, rb = rt + 32 + lane;
+  const bool va = ra < r1, vb = TWO && rb < r1;
+  const int per = (((C + kApWarps - 1) / kApWarps) + 3) & ~3;
+  const int cb = warp * per, ce = min(C, cb + per);
+  real_t sa[NV], sb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sa[v] = sb[v] = 0.0;
+  const real_t* Ma = M + (va ? ra : r0);
+  const real_t* Mb = M + (vb ? rb : r0);
+  int c = cb;
+  for (; c + 3 < ce; c += 4) {
+    real_t a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = va ? Ma[(size_t)(c + u) * ld] : (real_t)0.0;
+      if (TWO) b[u] = vb ? Mb[(size_t)(c + u) * ld] : (real_t)0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const real_t xv = x[v * xs + c + u];
+        sa[v] = fma(a[u], xv, sa[v]);
+        if (TWO) sb[v] = fma(b[u], xv, sb[v]);
+      }
+  }
+  for (; c < ce; ++c) {
+    const real_t a = va ? Ma[(size_t)c * ld] : (real_t)0.0;
+    const real_t b = vb ? Mb[(size_t)c * ld] : (real_t)0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sa[v] = fma(a, x[v * xs + c], sa[v]);
+      if (TWO) sb[v] = fma(b, x[v * xs + c], sb[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    red[(v * kApWarps + warp) * 64 + lane] = sa[v];
+    if (TWO) red[(v * kApWarps + warp) * 64 + 32 + lane] = sb[v];
+  }
+  __syncthreads();
+  if (warp < (TWO ? 2 : 1)) {
+    const int r = rt + warp * 32 + lane;
+    if (r < r1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real_t t = 0.0;
+        for (int w = 0; w < kApWarps; ++w) t += red[(v * kApWarps + w) * 64 + warp * 32 + lane];
+        out(r, v, t);
+      }
+    }
+  }
+  __syncthreads();
+}
 
 // out(r, v, sum_{c < C(rt)} M[r + c*ld] x_v[c]) for rows r in [r0, r1); ccap(rt)
 // bounds the columns a 64-row tile starting at rt needs (C for a full matrix,
@@ -40,62 +111,12 @@ namespace cg = cooperative_groups;
 template <int NV, class Cap, class Out>
 __device__ void gemv_n(const real_t* __restrict__ M, size_t ld, int r0, int r1, Cap ccap,
                        const real_t* __restrict__ x, int xs, real_t* red, Out out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int rt = r0; rt < r1; rt += 64) {
-    const int ra = rt + lane, rb = rt + 32 + lane;
-    const bool va = ra < r1, vb = rb < r1;
-    const int C = ccap(rt);
-    const int per = (((C + kApWarps - 1) / kApWarps) + 3) & ~3;
-    const int cb = warp * per, ce = min(C, cb + per);
-    real_t sa[NV], sb[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sa[v] = sb[v] = 0.0;
-    const real_t* Ma = M + (va ? ra : r0);
-    const real_t* Mb = M + (vb ? rb : r0);
-    int c = cb;
-    for (; c + 3 < ce; c += 4) {
-      real_t a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = va ? Ma[(size_t)(c + u) * ld] : (real_t)0.0;
-        b[u] = vb ? Mb[(size_t)(c + u) * ld] : (real_t)0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const real_t xv = x[v * xs + c + u];
-          sa[v] = fma(a[u], xv, sa[v]);
-          sb[v] = fma(b[u], xv, sb[v]);
-        }
-    }
-    for (; c < ce; ++c) {
-      const real_t a = va ? Ma[(size_t)c * ld] : (real_t)0.0;
-      const real_t b = vb ? Mb[(size_t)c * ld] : (real_t)0.0;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        sa[v] = fma(a, x[v * xs + c], sa[v]);
-        sb[v] = fma(b, x[v * xs + c], sb[v]);
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      red[(v * kApWarps + warp) * 64 + lane] = sa[v];
-      red[(v * kApWarps + warp) * 64 + 32 + lane] = sb[v];
-    }
-    __syncthreads();
-    if (warp < 2) {
-      const int r = rt + warp * 32 + lane;
-      if (r < r1) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          real_t t = 0.0;
-          for (int w = 0; w < kApWarps; ++w) t += red[(v * kApWarps + w) * 64 + warp * 32 + lane];
-          out(r, v, t);
-        }
-      }
-    }
-    __syncthreads();
+    // FP32 keeps one code path (the skipped half costs little on the FP32 pipe)
+    if (sizeof(real_t) == sizeof(float) || rt + 32 < r1)
+      gemv_n_tile<NV, true>(M, ld, r0, r1, rt, ccap(rt), x, xs, red, out);
+    else
+      gemv_n_tile<NV, false>(M, ld, r0, r1, rt, ccap(rt), x, xs, red, out);
   }
 }
 
@@ -103,7 +124,8 @@ __device__ void gemv_n(const real_t* __restrict__ M, size_t ld, int r0, int r1, 
 // rlo(c) is the first row column c needs (0 for a full matrix, c for the
 // transpose of a lower-triangular one).  A warp reduces four columns at a
 // time: its lanes read consecutive rows of each (coalesced, four loads in
-// flight per lane), then the partial sums are added across the warp.
+// flight per lane), then the partial sums are added across the warp; lanes 0,
+// 8, 16 and 24 write the four results.
 template <int NV, class Lo, class Out>
 __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
                        const real_t* __restrict__ x, int xs, real_t* red, Out out) {
@@ -131,21 +153,23 @@ __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, 
         for (int u = 0; u < 4; ++u) s[u][v] = fma(a[u], xv, s[u][v]);
       }
     }
+    // the four columns' sums across the warp, transposed as they are reduced:
+    // after the xor-16 and xor-8 exchanges each lane carries one column
+    // (u = 2 * bit 4 + bit 3 of the lane), so 6 additions replace 20
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const int uq = (h16 ? 2 : 0) + (h8 ? 1 : 0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        real_t t = s[u][v];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        s[u][v] = t;
-      }
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cq + u < c1)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) out(cq + u, v, s[u][v]);
+    for (int v = 0; v < NV; ++v) {
+      real_t k0 = h16 ? s[2][v] : s[0][v], k1 = h16 ? s[3][v] : s[1][v];
+      const real_t g0 = h16 ? s[0][v] : s[2][v], g1 = h16 ? s[1][v] : s[3][v];
+      k0 += __shfl_xor_sync(0xffffffffu, g0, 16);
+      k1 += __shfl_xor_sync(0xffffffffu, g1, 16);
+      real_t t = h8 ? k1 : k0;
+      t += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+      t += __shfl_xor_sync(0xffffffffu, t, 4);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      if ((lane & 7) == 0 && cq + uq < c1) out(cq + uq, v, t);
     }
   }
   __syncthreads();
@@ -175,7 +199,7 @@ __device__ __forceinline__ ApItem find_item(const ApItem* __restrict__ items, in
 }
 
 template <int NV>
-__global__ void __launch_bounds__(kApThreads)
+__global__ void AP_BOUNDS
     k_ap_interior(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(kApThreads)
 }
 
 template <int NV>
-__global__ void __launch_bounds__(kApThreads)
+__global__ void AP_BOUNDS
     k_ap_scale(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
@@ -270,7 +294,7 @@ __global__ void __launch_bounds__(kApThreads)
 }
 
 template <int NV>
-__global__ void __launch_bounds__(kApThreads)
+__global__ void AP_BOUNDS
     k_ap_qe(const ApItem* __restrict__ items, int nitems, real_t* __restrict__ z, int forward) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = (int)cl.num_blocks(), k = (int)cl.block_rank();
