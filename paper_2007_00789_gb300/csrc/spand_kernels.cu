@@ -81,9 +81,11 @@ __device__ void potrf_body(real_t* a, int m, int ld, int id, int* err, real_t* s
         *s_fail = 1;
         if (err) atomicCAS(err, 0, id + 1);
       } else {
-        const real_t sq = sqrt(d);
-        a[j + (size_t)j * ld] = sq;
-        *s_inv = 1.0 / sq;
+        // one reciprocal square root instead of a square root and a division
+        // (each a long sequence of warp-wide instructions on the FP64 pipe)
+        const real_t inv = rsqrt(d);
+        a[j + (size_t)j * ld] = d * inv;
+        *s_inv = inv;
       }
     }
     __syncthreads();
@@ -138,28 +140,39 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int smem_cap) {
 // ---------------------------------------------------------------------------
 // Batched triangular solve with a lower factor, 32 right-hand sides per CTA.
 // The right-hand sides are staged in shared memory (row-major, 32 wide) and
-// solved by 32-row blocks: warp 0 solves the 32 x 32 diagonal block (lane =
-// right-hand side, dot-product form), then all warps update the rows below
-// with the block's solution (4 partial sums per row).  Rows of an identity
-// right-hand side above its unit entry stay zero and are skipped.
+// solved by 32-row blocks.  The diagonal block is solved column by column by
+// all warps: after x_j is final, every warp subtracts L_ij x_j from its rows i
+// of the block (independent FMAs), and warp 0, which holds row j+1, finishes
+// it with the reciprocal pivot (one division per block, across the lanes: on
+// GB300's narrow FP64 pipe a division costs tens of warp-wide instructions).
+// Then all warps update the rows below with the block's solution (4 partial
+// sums per row).  Rows of an identity right-hand side above its unit entry
+// stay zero and are skipped.
 // ---------------------------------------------------------------------------
 constexpr int kTrsmNC = 32;
 constexpr int kTrsmThreads = 128;
 
 __device__ void trsm_blocked(const real_t* __restrict__ L, size_t ldl, int m, real_t* xs,
-                             int row0, int nc) {
+                             int row0, int nc, real_t* rd) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int rb = row0; rb < m; rb += 32) {
     const int re = min(m, rb + 32);
-    if (warp == 0 && lane < nc) {
-      for (int i = rb; i < re; ++i) {
-        real_t s = xs[i * kTrsmNC + lane];
-        const real_t* Li = L + i;
-        for (int j = rb; j < i; ++j) s = fma(-Li[j * ldl], xs[j * kTrsmNC + lane], s);
-        xs[i * kTrsmNC + lane] = s / Li[i * ldl];
-      }
-    }
+    if (warp == 0 && rb + lane < re) rd[lane] = (real_t)1 / L[(size_t)(rb + lane) * (ldl + 1)];
     __syncthreads();
+    if (warp == 0 && lane < nc) xs[rb * kTrsmNC + lane] *= rd[0];
+    __syncthreads();
+    for (int j = rb; j + 1 < re; ++j) {
+      if (lane < nc) {
+        const real_t xj = xs[j * kTrsmNC + lane];
+        const real_t* Lj = L + (size_t)j * ldl;
+        for (int i = j + 1 + warp; i < re; i += nw) {
+          real_t xi = fma(-Lj[i], xj, xs[i * kTrsmNC + lane]);
+          if (i == j + 1) xi *= rd[i - rb];
+          xs[i * kTrsmNC + lane] = xi;
+        }
+      }
+      __syncthreads();
+    }
     if (lane < nc) {
       for (int i = re + warp; i < m; i += nw) {
         const real_t* Li = L + i;
@@ -182,6 +195,7 @@ __device__ void trsm_blocked(const real_t* __restrict__ L, size_t ldl, int m, re
 __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restrict__ tasks,
                                                        int smem_rows) {
   extern __shared__ real_t sm[];  // smem_rows x kTrsmNC
+  __shared__ real_t s_rd[32];     // reciprocal pivots of a diagonal block
   const TrsmTask t = tasks[blockIdx.x];
   const int m = t.m, nc = t.ncols;
   if (m == 0 || nc == 0) return;
@@ -209,7 +223,7 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restric
       }
     }
     __syncthreads();
-    trsm_blocked(L, ldl, m, sm, row0, nc);
+    trsm_blocked(L, ldl, m, sm, row0, nc, s_rd);
     if (!t.trans || t.pad >= 0) {
       for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
         const int i = e % m, cc = e / m;
