@@ -1485,8 +1485,19 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
         f2hi = QK::below(T2 + F2);
       }
     }
-    const bool lt1 = near ? nu64 < T1 : bk < K1;
-    const bool lt2 = near ? nu64 < T2 : bk < K2;
+    // the FP64 compares only on the rare near-threshold steps (a select would
+    // run them, and the conversion below, in every thread of every step)
+    bool lt1, lt2;
+    real_t nsq;
+    if (__builtin_expect(near, 0)) {
+      lt1 = nu64 < T1;
+      lt2 = nu64 < T2;
+      nsq = (real_t)nu64;
+    } else {
+      lt1 = bk < K1;
+      lt2 = bk < K2;
+      nsq = QK::rval(bk);
+    }
     if (r < 0 && lt1) {
       r = step;
       if (!superfine) {
@@ -1504,7 +1515,6 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     if (tid == 0 && crank == 0)
       flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2, f1lo, f1hi, f2lo, f2hi, superfine);
     if (superfine && lt2) break;
-    const real_t nsq = near ? (real_t)nu64 : QK::rval(bk);
     real_t beta, tau, inv;
     if constexpr (sizeof(real_t) < sizeof(double)) {
       // FP32: every warp forms the scalars itself
