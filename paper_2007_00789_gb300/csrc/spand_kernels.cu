@@ -146,7 +146,7 @@ __global__ void k_potrf(const PotrfTask* __restrict__ tasks, int smem_cap) {
 // it with the reciprocal pivot (one division per block, across the lanes: on
 // GB300's narrow FP64 pipe a division costs tens of warp-wide instructions).
 // Then all warps update the rows below with the block's solution (4 partial
-// sums per row).  Rows of an identity right-hand side above its unit entry
+// sums per row, the row of L read by the lanes at once and shuffled).  Rows of an identity right-hand side above its unit entry
 // stay zero and are skipped.
 // ---------------------------------------------------------------------------
 constexpr int kTrsmNC = 32;
@@ -173,20 +173,27 @@ __device__ void trsm_blocked(const real_t* __restrict__ L, size_t ldl, int m, re
       }
       __syncthreads();
     }
-    if (lane < nc) {
-      for (int i = re + warp; i < m; i += nw) {
-        const real_t* Li = L + i;
-        real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int j = rb;
-        for (; j + 3 < re; j += 4) {
-          s0 = fma(Li[j * ldl], xs[j * kTrsmNC + lane], s0);
-          s1 = fma(Li[(j + 1) * ldl], xs[(j + 1) * kTrsmNC + lane], s1);
-          s2 = fma(Li[(j + 2) * ldl], xs[(j + 2) * kTrsmNC + lane], s2);
-          s3 = fma(Li[(j + 3) * ldl], xs[(j + 3) * kTrsmNC + lane], s3);
-        }
-        for (; j < re; ++j) s0 = fma(Li[j * ldl], xs[j * kTrsmNC + lane], s0);
-        xs[i * kTrsmNC + lane] -= (s0 + s1) + (s2 + s3);
+    // rows below the block: lane j loads L(i, rb + j) (the row's 32 entries in
+    // flight at once, the next row's while this one is summed) and the lanes
+    // take them by shuffle
+    const int w = re - rb;
+    auto lrow = [&](int i) {
+      return (i < m && lane < w) ? L[i + (size_t)(rb + lane) * ldl] : (real_t)0.0;
+    };
+    real_t lnext = lrow(re + warp);
+    for (int i = re + warp; i < m; i += nw) {
+      const real_t lv = lnext;
+      lnext = lrow(i + nw);
+      real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < w; j += 4) {
+        s0 = fma(__shfl_sync(0xffffffffu, lv, j), xs[(rb + j) * kTrsmNC + lane], s0);
+        s1 = fma(__shfl_sync(0xffffffffu, lv, j + 1), xs[(rb + j + 1) * kTrsmNC + lane], s1);
+        s2 = fma(__shfl_sync(0xffffffffu, lv, j + 2), xs[(rb + j + 2) * kTrsmNC + lane], s2);
+        s3 = fma(__shfl_sync(0xffffffffu, lv, j + 3), xs[(rb + j + 3) * kTrsmNC + lane], s3);
       }
+      for (; j < w; ++j) s0 = fma(__shfl_sync(0xffffffffu, lv, j), xs[(rb + j) * kTrsmNC + lane], s0);
+      if (lane < nc) xs[i * kTrsmNC + lane] -= (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
   }
@@ -264,8 +271,8 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(const TrsmTask* __restric
 // Explicit Q^T = H_{nref-1} ... H_0 of an interface (for the apply), 32
 // columns per CTA: lane c follows column c0+c from the unit vector through
 // the reflectors; the 4 warps share the rows of every dot product and update
-// (so that all four FP64 units of the SM work), combining partial sums in
-// shared memory.
+// (so that all four FP64 units of the SM work), 32-row chunks each, combining
+// partial sums in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kFqThreads = 128;
 
@@ -300,14 +307,34 @@ __global__ void __launch_bounds__(kFqThreads) k_form_qt(const FormQtTask* __rest
   __syncthreads();
   for (int s = 0; s < t.nref; ++s) {
     const real_t* v = t.V + (size_t)s * m;
-    real_t d = 0.0;
-    for (int i = s + warp; i < m; i += nw) d = fma(v[i], sm[i * kTrsmNC + lane], d);
-    part[warp * kTrsmNC + lane] = d;
+    // warp w takes the 32-row chunks s + 32 (w + k nw): the lanes load the
+    // chunk of v at once (coalesced) and take its entries by shuffle; four
+    // partial sums per lane
+    real_t d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    for (int i0 = s + 32 * warp; i0 < m; i0 += 32 * nw) {
+      const int w = min(32, m - i0);
+      const real_t vv = lane < w ? v[i0 + lane] : (real_t)0.0;
+      const real_t* q = sm + (size_t)i0 * kTrsmNC + lane;
+      int j = 0;
+      for (; j + 3 < w; j += 4) {
+        d0 = fma(__shfl_sync(0xffffffffu, vv, j), q[j * kTrsmNC], d0);
+        d1 = fma(__shfl_sync(0xffffffffu, vv, j + 1), q[(j + 1) * kTrsmNC], d1);
+        d2 = fma(__shfl_sync(0xffffffffu, vv, j + 2), q[(j + 2) * kTrsmNC], d2);
+        d3 = fma(__shfl_sync(0xffffffffu, vv, j + 3), q[(j + 3) * kTrsmNC], d3);
+      }
+      for (; j < w; ++j) d0 = fma(__shfl_sync(0xffffffffu, vv, j), q[j * kTrsmNC], d0);
+    }
+    part[warp * kTrsmNC + lane] = (d0 + d1) + (d2 + d3);
     __syncthreads();
     real_t dt = 0.0;
     for (int w = 0; w < nw; ++w) dt += part[w * kTrsmNC + lane];
     const real_t f = t.tau[s] * dt;
-    for (int i = s + warp; i < m; i += nw) sm[i * kTrsmNC + lane] = fma(-f, v[i], sm[i * kTrsmNC + lane]);
+    for (int i0 = s + 32 * warp; i0 < m; i0 += 32 * nw) {
+      const int w = min(32, m - i0);
+      const real_t vv = lane < w ? v[i0 + lane] : (real_t)0.0;
+      real_t* q = sm + (size_t)i0 * kTrsmNC + lane;
+      for (int j = 0; j < w; ++j) q[j * kTrsmNC] = fma(-f, __shfl_sync(0xffffffffu, vv, j), q[j * kTrsmNC]);
+    }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
