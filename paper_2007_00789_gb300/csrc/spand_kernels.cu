@@ -382,11 +382,15 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
         }
       }
       __syncthreads();
-#pragma unroll 8
-      for (int k = 0; k < kKc; ++k) {
-        const real_t a = As[k][ti];
+      // only the chunk's kk rows, and only warps with a column in the tile (the
+      // zero padding would add exact zeros at the full FP64 instruction cost)
+      if (tj < t.cols) {
+#pragma unroll 4
+        for (int k = 0; k < kk; ++k) {
+          const real_t a = As[k][ti];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += a * Bs[k][tj + q];
+          for (int q = 0; q < 4; ++q) acc[q] += a * Bs[k][tj + q];
+        }
       }
       __syncthreads();
     }
