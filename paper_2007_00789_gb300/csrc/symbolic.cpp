@@ -20,8 +20,10 @@
 // The key is packed two bits per depth, most significant first, so that
 // numeric order of (S, packed key) is that lexicographic order.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include "spand_internal.h"
@@ -29,6 +31,26 @@
 namespace spand {
 
 static inline int node_depth(int i) { return 31 - __builtin_clz((unsigned)(i + 1)); }
+
+// fn(i, w) for i in [0, n) on up to 16 host threads; w is the worker index
+// (for per-worker scratch).  The items must be independent.
+template <class F>
+static void parallel_for(int n, F&& fn) {
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nth = std::max(1, std::min(n, std::min(16, hw)));
+  if (nth <= 1) {
+    for (int i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  std::atomic<int> next(0);
+  auto work = [&](int w) {
+    for (int i; (i = next.fetch_add(1)) < n;) fn(i, w);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& x : th) x.join();
+}
 
 int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err) {
   t.n = n;
@@ -43,25 +65,33 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
   t.level_of.assign(n, -1);
   std::vector<int> verts(n);
   std::iota(verts.begin(), verts.end(), 0);
-  // frontier of (node, [begin, end) in a vertex buffer)
+  // frontier of (node, [begin, end) in a vertex buffer); the boxes of a depth
+  // are independent (disjoint vertex slices, their own nodes) and are cut in
+  // parallel, each box's children stored at 2i, 2i + 1 as in a serial sweep
   struct Box { int node, b, e; };
+  struct Scratch { std::vector<int> lo, hi; std::vector<double> vals; };
   std::vector<Box> frontier{{0, 0, n}}, next;
-  std::vector<int> buf(n), lo, eq, hi;
-  std::vector<double> vals;
+  std::vector<Scratch> scratch(16);
+  std::vector<int> buf, eq;
   for (int depth = 0; depth <= dmax; ++depth) {
-    next.clear();
-    for (const Box& bx : frontier) {
+    next.assign(2 * frontier.size(), Box{0, 0, 0});
+    std::atomic<int> empty_node(-1);
+    parallel_for((int)frontier.size(), [&](int bi, int w) {
+      const Box bx = frontier[bi];
       if (bx.e <= bx.b) {
-        err = "empty nested-dissection box at node " + std::to_string(bx.node);
-        return SPAND_EINVAL;
+        empty_node.store(bx.node);
+        return;
       }
       if (depth == dmax) {
         for (int i = bx.b; i < bx.e; ++i) {
           t.node_of[verts[i]] = bx.node;
           t.level_of[verts[i]] = 0;
         }
-        continue;
+        return;
       }
+      std::vector<int>& lo = scratch[w].lo;
+      std::vector<int>& hi = scratch[w].hi;
+      std::vector<double>& vals = scratch[w].vals;
       const int c = depth % dim;
       vals.clear();
       for (int i = bx.b; i < bx.e; ++i) vals.push_back(coords[(size_t)verts[i] * dim + c]);
@@ -87,8 +117,12 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
       for (int v : lo) verts[p++] = v;
       const int mid = p;
       for (int v : hi) verts[p++] = v;
-      next.push_back({2 * bx.node + 1, bx.b, mid});
-      next.push_back({2 * bx.node + 2, mid, p});
+      next[2 * bi] = {2 * bx.node + 1, bx.b, mid};
+      next[2 * bi + 1] = {2 * bx.node + 2, mid, p};
+    });
+    if (empty_node.load() >= 0) {
+      err = "empty nested-dissection box at node " + std::to_string(empty_node.load());
+      return SPAND_EINVAL;
     }
     frontier.swap(next);
   }
@@ -364,10 +398,15 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
   const int ell = t.nlevels;
   const int n = t.n;
   st.assign(ell, StageSym());
-  std::vector<int> cl_prev, cl;
+  // the cluster maps of all stages depend on the tree only: made in parallel;
+  // stage k uses its own map and, for the parents, stage k + 1's
+  std::vector<std::vector<int>> maps(ell);
+  std::vector<int> nmaps(ell, 0);
+  parallel_for(ell, [&](int k, int) { nmaps[k] = cluster_map(t, k, maps[k], &st[k].level); });
   for (int k = 0; k < ell; ++k) {
     StageSym& S = st[k];
-    S.ncl = cluster_map(t, k, cl, &S.level);
+    S.ncl = nmaps[k];
+    const std::vector<int>& cl = maps[k];
     S.interior.assign(S.ncl, 0);
     for (int c = 0; c < S.ncl; ++c) {
       if (S.level[c] == k) {
@@ -467,8 +506,7 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     // parents at stage k+1
     S.parent.assign(S.ncl, -1);
     if (k + 1 < ell) {
-      std::vector<int> cl_next;
-      cluster_map(t, k + 1, cl_next, nullptr);
+      const std::vector<int>& cl_next = maps[k + 1];
       std::vector<int> first(S.ncl, -1);
       for (int v = 0; v < n; ++v)
         if (cl[v] >= 0 && first[cl[v]] < 0) first[cl[v]] = v;
@@ -477,6 +515,7 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
       err = "interfaces left after the last stage";
       return SPAND_EINVAL;
     }
+    std::vector<int>().swap(maps[k]);  // no later stage reads it
   }
   return SPAND_OK;
 }
