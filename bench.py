@@ -41,10 +41,11 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (the profiling recipe's figure); n
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 152 SMs x 2070 MHz x 128 FP32 FMA/clk/SM
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
-# capture of this bench's command (profiles/launches_poisson3d_64_fp64.txt):
+# capture of this bench's command (profiles/launches_poisson3d_64_fp64.txt and
+# profiles/launches_poisson3d_64_fp32.txt):
 # (workload, precision, kernel kind) -> bytes per launch.  Only valid for the
 # kernel version that was captured; absent entries report null.
-TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 19.27e6}
+TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 19.27e6, ("poisson3d_64", 1, "rrqr"): 9.57e6}
 
 WORKLOADS = {
     # name: (factory, ell, rhs, rhs seed)
