@@ -1975,9 +1975,11 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       }
     }
     // the pivot column, read from its owner's shared memory (its rows at and
-    // below the pivot row), becomes v in every CTA
-    if (!pulled)
-      for (int i = step + tid; i < m; i += nthr) v[i] = pc[(size_t)i * ncl];
+    // below the pivot row) by warps 1.., becomes v in every CTA; warp 0 forms
+    // the reflector scalars meanwhile (a long dependent FP64 sequence)
+    const int pt = tid - kWarp, pn = nthr - kWarp;
+    if (!pulled && warp > 0)
+      for (int i = step + pt; i < m; i += pn) v[i] = pc[(size_t)i * ncl];
     // flags (a near tie of the two largest norms; a norm within 1e-10 of a
     // threshold), kept in CTA 0 while the column is in flight
     if (tid == 0 && crank == 0)
@@ -1996,11 +1998,12 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       inv = s_refl[2];
     }
     const bool own = crank == owner;
-    for (int i = step + tid; i < m; i += nthr) {  // the rows this thread read
-      const real_t vi = (i == step) ? (real_t)1 : v[i] * inv;
-      v[i] = vi;
-      if (own) t.V[i + (size_t)step * m] = vi;
-    }
+    if (warp > 0)
+      for (int i = step + pt; i < m; i += pn) {  // the rows this thread read
+        const real_t vi = (i == step) ? (real_t)1 : v[i] * inv;
+        v[i] = vi;
+        if (own) t.V[i + (size_t)step * m] = vi;
+      }
     if (own) {
       for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
       if (tid == 0) {
