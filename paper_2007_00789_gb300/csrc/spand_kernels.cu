@@ -1686,103 +1686,6 @@ __device__ __forceinline__ void qr_update_one(real_t* a, const real_t* v, int nc
   }
 }
 
-// Two columns in one pass, each with exactly qr_update_one's arithmetic; a
-// column that is not live (pivoted) is read but neither written nor offered.
-__device__ __forceinline__ void qr_update_pair(real_t* a, real_t* b, bool ha, bool hb,
-                                               const real_t* v, int ncl, int step, int m, int sl,
-                                               int tpc, unsigned gmask, real_t tau, int ia, int ib,
-                                               real_t* na, real_t* nb, QrSlot& mine) {
-  real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-  int i = step + sl;
-  const size_t rs = (size_t)tpc * ncl;
-  for (; i + 3 * tpc < m; i += 4 * tpc) {
-    const size_t o = (size_t)i * ncl;
-    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
-    d0 = fma(v0, a[o], d0);
-    e0 = fma(v0, b[o], e0);
-    d1 = fma(v1, a[o + rs], d1);
-    e1 = fma(v1, b[o + rs], e1);
-    d2 = fma(v2, a[o + 2 * rs], d2);
-    e2 = fma(v2, b[o + 2 * rs], e2);
-    d3 = fma(v3, a[o + 3 * rs], d3);
-    e3 = fma(v3, b[o + 3 * rs], e3);
-  }
-  for (; i < m; i += tpc) {
-    d0 = fma(v[i], a[(size_t)i * ncl], d0);
-    e0 = fma(v[i], b[(size_t)i * ncl], e0);
-  }
-  real_t d = (d0 + d1) + (d2 + d3), e = (e0 + e1) + (e2 + e3);
-  for (int o = tpc >> 1; o > 0; o >>= 1) {
-    d += __shfl_xor_sync(gmask, d, o);
-    e += __shfl_xor_sync(gmask, e, o);
-  }
-  const real_t f = tau * d, g = tau * e;
-  real_t s2a = 0, s2b = 0, s2c = 0, s2d = 0, t2a = 0, t2b = 0, t2c = 0, t2d = 0;
-  i = step + sl;
-  for (; i + 3 * tpc < m; i += 4 * tpc) {
-    const size_t o = (size_t)i * ncl;
-    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
-    const real_t a0 = a[o], a1 = a[o + rs], a2 = a[o + 2 * rs], a3 = a[o + 3 * rs];
-    const real_t b0 = b[o], b1 = b[o + rs], b2 = b[o + 2 * rs], b3 = b[o + 3 * rs];
-    const real_t x0 = fma(-f, v0, a0), x1 = fma(-f, v1, a1);
-    const real_t x2 = fma(-f, v2, a2), x3 = fma(-f, v3, a3);
-    const real_t y0 = fma(-g, v0, b0), y1 = fma(-g, v1, b1);
-    const real_t y2 = fma(-g, v2, b2), y3 = fma(-g, v3, b3);
-    if (ha) {
-      a[o] = x0;
-      a[o + rs] = x1;
-      a[o + 2 * rs] = x2;
-      a[o + 3 * rs] = x3;
-    }
-    if (hb) {
-      b[o] = y0;
-      b[o + rs] = y1;
-      b[o + 2 * rs] = y2;
-      b[o + 3 * rs] = y3;
-    }
-    if (i > step) {
-      s2a = fma(x0, x0, s2a);
-      t2a = fma(y0, y0, t2a);
-    }
-    s2b = fma(x1, x1, s2b);
-    t2b = fma(y1, y1, t2b);
-    s2c = fma(x2, x2, s2c);
-    t2c = fma(y2, y2, t2c);
-    s2d = fma(x3, x3, s2d);
-    t2d = fma(y3, y3, t2d);
-  }
-  for (; i < m; i += tpc) {
-    const size_t o = (size_t)i * ncl;
-    const real_t x0 = fma(-f, v[i], a[o]);
-    const real_t y0 = fma(-g, v[i], b[o]);
-    if (ha) a[o] = x0;
-    if (hb) b[o] = y0;
-    if (i > step) {
-      s2a = fma(x0, x0, s2a);
-      t2a = fma(y0, y0, t2a);
-    }
-  }
-  real_t s2 = (s2a + s2b) + (s2c + s2d), t2 = (t2a + t2b) + (t2c + t2d);
-  for (int o = tpc >> 1; o > 0; o >>= 1) {
-    s2 += __shfl_xor_sync(gmask, s2, o);
-    t2 += __shfl_xor_sync(gmask, t2, o);
-  }
-  __syncwarp(gmask);  // the row step+1 entries were written by another thread of the group
-  if (sl == 0) {
-    const bool nxt = step + 1 < m;
-    if (ha) {
-      *na = s2;
-      QrSlot c{QK::of(s2), kNoKey, nxt ? a[(size_t)(step + 1) * ncl] : (real_t)0, ia};
-      slot_merge(mine, c);
-    }
-    if (hb) {
-      *nb = t2;
-      QrSlot c{QK::of(t2), kNoKey, nxt ? b[(size_t)(step + 1) * ncl] : (real_t)0, ib};
-      slot_merge(mine, c);
-    }
-  }
-}
-
 // One thread per column (or a few, rows split among them): the dot product
 // v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
 // in each thread; each thread also keeps the best candidate among its columns
@@ -1802,7 +1705,6 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
   __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
-  __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256 or 512
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
@@ -1878,10 +1780,10 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   const int maxsteps = min(m, N);
   int r = -1, nsteps = 0, flags = 0;
   // thresholds, fixed once nu_0 is known: as doubles, as keys (value < T <=>
-  // key < K), the FP32 windows in which the norm is recomputed in FP64, and the
-  // near-threshold flag margins
+  // key < K), and the near-threshold flag margins
   double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
-  qkey_t K1 = 0, K2 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0, f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;
+  qkey_t K1 = 0, K2 = 0;
+  const qkey_t f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;  // margins of FP32 keys: not used here
   // deferred R entries of the last pivot column (owner CTA only): other CTAs
   // read that column one step later, so it is overwritten after the next
   // exchange barrier
@@ -1915,31 +1817,17 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     const int owner = gb.idx / cpb;
     const int lp = gb.idx - owner * cpb;  // the pivot's column in the owner's slice
     const real_t* pc = cluster.map_shared_rank(A, owner) + lp;
-    bool pulled = false;
-    // FP32 storage: the decisions that set the rank (nu_0 and any step close to
-    // a threshold) use the pivot column's norm recomputed in FP64
-    bool near = false;
-    double nu64 = 0.0;
-    if constexpr (sizeof(real_t) < sizeof(double)) {
-      near = step == 0 || (bk >= lo1 && bk <= hi1) || (superfine && bk >= lo2 && bk <= hi2);
-      if (near) {
-        for (int i = step + tid; i < m; i += nthr) v[i] = pc[(size_t)i * ncl];
-        pulled = true;
-        __syncthreads();
-        if (warp == 0) {
-          double s64 = 0.0;
-          for (int i = step + lane; i < m; i += kWarp) {
-            const double a = (double)v[i];
-            s64 = fma(a, a, s64);
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
-          if (lane == 0) s_nu64 = s64;
-        }
-        __syncthreads();
-        nu64 = s_nu64;
-      }
-    }
+    // the pivot column, read from its owner's shared memory (its rows at and
+    // below the pivot row) by warps 1.. from here on, through the decisions,
+    // becomes v in every CTA; warp 0 forms the reflector scalars meanwhile (a
+    // long dependent FP64 sequence).  v is not read before the next barrier.
+    const int pt = tid - kWarp, pn = nthr - kWarp;
+    if (warp > 0)
+      for (int i = step + pt; i < m; i += pn) v[i] = pc[(size_t)i * ncl];
+    // FP64 storage: the decisions take the norms as they are (the FP32
+    // kernel's FP64 recomputation near the thresholds has no counterpart here)
+    constexpr bool near = false;
+    const double nu64 = 0.0;
     if (step == 0) {
       nu0sq = near ? nu64 : QK::val(bk);
       if (!(nu0sq > 0.0)) {
@@ -1952,17 +1840,6 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       K2 = QK::above(T2);
       F1 = 1e-10 * thr1 * nu0sq;
       F2 = 1e-10 * thr2 * nu0sq;
-      if constexpr (sizeof(real_t) < sizeof(double)) {
-        const double w1 = 1e-4 * thr1 * nu0sq, w2 = 1e-4 * thr2 * nu0sq;
-        lo1 = QK::above(T1 - w1);
-        hi1 = QK::below(T1 + w1);
-        lo2 = QK::above(T2 - w2);
-        hi2 = QK::below(T2 + w2);
-        f1lo = QK::above(T1 - F1);
-        f1hi = QK::below(T1 + F1);
-        f2lo = QK::above(T2 - F2);
-        f2hi = QK::below(T2 + F2);
-      }
     }
     const bool lt1 = near ? nu64 < T1 : bk < K1;
     const bool lt2 = near ? nu64 < T2 : bk < K2;
@@ -1974,29 +1851,15 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
         break;
       }
     }
-    // the pivot column, read from its owner's shared memory (its rows at and
-    // below the pivot row) by warps 1.., becomes v in every CTA; warp 0 forms
-    // the reflector scalars meanwhile (a long dependent FP64 sequence)
-    const int pt = tid - kWarp, pn = nthr - kWarp;
-    if (!pulled && warp > 0)
-      for (int i = step + pt; i < m; i += pn) v[i] = pc[(size_t)i * ncl];
     // flags (a near tie of the two largest norms; a norm within 1e-10 of a
     // threshold), kept in CTA 0 while the column is in flight
     if (tid == 0 && crank == 0)
       flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2, f1lo, f1hi, f2lo, f2hi, superfine);
     if (superfine && lt2) break;
     const real_t nsq = near ? (real_t)nu64 : QK::rval(bk);
-    real_t beta, tau, inv;
-    if constexpr (sizeof(real_t) < sizeof(double)) {
-      // FP32: every warp forms the scalars itself
-      reflector_scalars_r(gb.alpha, nsq, &beta, &tau, &inv);
-    } else {
-      if (warp == 0) reflector_scalars(gb.alpha, nsq, lane, s_refl);
-      __syncthreads();  // s_refl, written by warp 0
-      beta = s_refl[0];
-      tau = s_refl[1];
-      inv = s_refl[2];
-    }
+    if (warp == 0) reflector_scalars(gb.alpha, nsq, lane, s_refl);
+    __syncthreads();  // s_refl, written by warp 0
+    const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
     const bool own = crank == owner;
     if (warp > 0)
       for (int i = step + pt; i < m; i += pn) {  // the rows this thread read
@@ -2016,18 +1879,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     }
     __syncthreads();
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    // FP32: a thread with two columns (l, l + ngrp) updates both in one pass,
-    // which doubles its independent chains; every column sees the same
-    // arithmetic (four partial sums over the same rows) on either path
-    constexpr bool kPairs = sizeof(real_t) < sizeof(double);
-    for (int l = grp; l < nloc; l += (kPairs ? 2 : 1) * ngrp) {
-      const int l2 = l + ngrp;
-      if (kPairs && l2 < nloc) {
-        const bool h1 = norms[l] >= (real_t)0, h2 = norms[l2] >= (real_t)0;
-        if (h1 || h2) qr_update_pair(A + l, A + l2, h1, h2, v, ncl, step, m, sl, tpc, gmask, tau,
-                                     g0 + l, g0 + l2, norms + l, norms + l2, mine);
-        continue;
-      }
+    for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
       qr_update_one(A + l, v, ncl, step, m, sl, tpc, gmask, tau, g0 + l, norms + l, mine);
     }
