@@ -45,7 +45,7 @@ FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 152 SMs x 2070 MHz x 128 FP3
 # profiles/launches_poisson3d_64_fp32.txt):
 # (workload, precision, kernel kind) -> bytes per launch.  Only valid for the
 # kernel version that was captured; absent entries report null.
-TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 19.27e6, ("poisson3d_64", 1, "rrqr"): 9.57e6}
+TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 19.30e6, ("poisson3d_64", 1, "rrqr"): 9.57e6}
 
 WORKLOADS = {
     # name: (factory, ell, rhs, rhs seed)
