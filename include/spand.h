@@ -36,6 +36,9 @@ extern "C" {
 #define SPAND_ECUDA (-4)    /* a CUDA runtime call failed */
 #define SPAND_ENOCONV (-5)  /* PCG reached maxit; x holds the last iterate */
 #define SPAND_ESTATE (-6)   /* call out of order (e.g. apply before factor) */
+#define SPAND_ETIMEOUT (-7) /* a bounded device-side wait ran out (the CTAs of a multi-CTA RRQR
+                               lost each other); the handle is left unfactored, the device
+                               stays usable, and the call may be retried */
 
 /* Sparsification schemes (Algorithm 1 / §2). */
 #define SPAND_FIRST_ORDER 0            /* eq. trailing-1: E dropped */
@@ -137,8 +140,21 @@ int spand_analyze(const spand_csr* A, const double* coords, int dim, int nlevels
  * factored by dense Cholesky.  May be called again (refactor) on the same
  * handle.  Synchronises the stream once per level to learn the ranks.
  * Errors: SPAND_ENOTSPD (the handle stays valid but unfactored),
- * SPAND_ENOMEM, SPAND_ECUDA. */
+ * SPAND_ENOMEM, SPAND_ECUDA, SPAND_ETIMEOUT (the barrier wait of a multi-CTA
+ * RRQR ran out; the handle stays valid but unfactored). */
 int spand_factor(spand_t h, void* stream);
+
+/* Testing hook for the one bounded device-side wait of the factorization:
+ * the barrier between the CTAs of a multi-CTA RRQR (Algorithm 1 on interface
+ * blocks too wide for a thread-block cluster; rrqr_kernel = 3 forces it for
+ * every interface).  limit: polls of the barrier counter before a wait gives
+ * up (<= 0 restores the default, about a second); unreachable != 0 raises the
+ * first barrier's target by one, so that it is never met and every wait of
+ * the task runs out after `limit` polls.  The next spand_factor then returns
+ * SPAND_ETIMEOUT and leaves the handle unfactored; no kernel is left
+ * running.  Takes effect at the next spand_factor (the handle's captured
+ * graphs are dropped).  Not meant for production use. */
+int spand_test_set_qr_wait(spand_t h, int64_t limit, int32_t unreachable);
 
 /* z = M r with M = L^{-T} L^{-1} (Algorithm 2 caption).  r and z are device
  * arrays of n doubles; they may alias.  Requires a successful spand_factor,
@@ -169,8 +185,12 @@ int spand_pcg_host(spand_t h, const double* b_host, double* x_host, double tol,
  *   - Limit: n <= 262144; larger systems return SPAND_EINVAL before any
  *     device work.  The handle must have been factored (SPAND_ESTATE).
  *   - The first call on a device looks up the array's device address for
- *     that device (cudaGetSymbolAddress); make that first call before any
- *     stream capture on that device.
+ *     that device (cudaGetSymbolAddress) and keeps it for the rest of the
+ *     process; make that first call before any stream capture on that
+ *     device.  The address belongs to the device's primary context: do not
+ *     call this after cudaDeviceReset (or from a non-primary driver context)
+ *     in the same process, since the kept address would then name memory of
+ *     a context that no longer exists.
  *   - Every call, from any handle, uses the same array, which keeps the
  *     previous call's contents (x is set to 0 and the scalars are cleared at
  *     the start, so stale data does not leak into a result).  Calls that
@@ -322,6 +342,15 @@ typedef struct {
   int32_t max_inflight;   /* most right-hand sides in flight at once */
   int32_t resident_problems;
   int64_t resident_bytes;
+  /* latency split of the completed requests: waiting for the problem's
+   * factorization (submission to the problem being ready), queued with the
+   * problem ready (for segment slots and vector space), and solving (admission
+   * to completion; includes the copies of b and x); p50 and p99 of each, and
+   * the three parts of the slowest request */
+  double factor_wait_p50_ms, factor_wait_p99_ms;
+  double queue_p50_ms, queue_p99_ms;
+  double solve_p50_ms, solve_p99_ms;
+  double max_split_ms[3];
 } spand_server_stats;
 
 int spand_server_create(const spand_server_opts* opts, spand_server_t* out);
@@ -341,6 +370,21 @@ int spand_server_get_stats(spand_server_t s, spand_server_stats* st);
 /* Stops the threads (requests still queued are abandoned) and frees the
  * server's memory; the handles stay with the caller. */
 void spand_server_destroy(spand_server_t s);
+
+/* ---------------------------------------------------------------------------
+ * Measurement aid (the paper has no counterpart).
+ *
+ * The factorization kernels are bound by the fused multiply-add pipe of their
+ * precision, and no measured FP64 rate of the GPU is published to divide by.
+ * spand_measure_fma_peak times independent FMA chains in every thread of a
+ * grid of 8 CTAs of 256 threads per SM on the current device (best of five
+ * launches after a warm-up, CUDA events on a stream of its own) and returns the
+ * achieved rate in TFLOP/s (2 flops per FMA) in *tflops and the best launch
+ * time in *ms (may be NULL).  precision: 0 = FP64, 1 = FP32.  Synchronises
+ * the device's work on its own stream only; allocates no device memory.
+ * Errors: SPAND_EINVAL (bad precision, null tflops), SPAND_ECUDA.
+ * --------------------------------------------------------------------------- */
+int spand_measure_fma_peak(int precision, double* tflops, double* ms);
 
 /* Frees every device and host resource of the handle.  NULL is ignored. */
 void spand_destroy(spand_t h);

@@ -488,6 +488,14 @@ int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count) {
   return SPAND_OK;
 }
 
+int spand_test_set_qr_wait(spand_t h, int64_t limit, int32_t unreachable) {
+  if (!h) return fail(SPAND_EINVAL, "null handle");
+  h->qr_wait_limit = limit > 0 ? (long long)limit : spand_s::kQrWaitDefault;
+  h->qr_wait_extra = unreachable ? 1 : 0;
+  h->drop_graphs();  // the captured task tables hold the previous values
+  return SPAND_OK;
+}
+
 void spand_destroy(spand_t h) { free_handle(h); }
 
 const char* spand_strerror(int code) {
@@ -499,6 +507,7 @@ const char* spand_strerror(int code) {
     case SPAND_ECUDA: return "CUDA error";
     case SPAND_ENOCONV: return "PCG did not converge within maxit";
     case SPAND_ESTATE: return "call out of order";
+    case SPAND_ETIMEOUT: return "a bounded device-side wait timed out";
     default: return "unknown error";
   }
 }
@@ -567,6 +576,7 @@ int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t
   if (dot_partials(n) > kNoAllocScalars - 16) return fail(SPAND_EINVAL, "internal: too many dot partials");
   // profiling would create CUDA events and a graph capture allocates: plain launches only
   const bool prof_on = h->prof.on;
+  const bool no_graph = h->no_graph;
   h->prof.on = false;
   h->no_graph = true;
   // scalars start from zero (the array keeps whatever the previous call left)
@@ -631,7 +641,7 @@ int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t
   };
   const int rc = body();
   h->prof.on = prof_on;
-  h->no_graph = false;
+  h->no_graph = no_graph;
   return rc;
 }
 

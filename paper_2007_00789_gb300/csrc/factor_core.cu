@@ -240,6 +240,7 @@ struct StageLayout {
   std::vector<int64_t> slot_off;           // offset of the cluster's slots in the pool
   std::vector<real_t*> Z, V, tau;
   std::vector<int> maxref, ncols_ub;       // interfaces: reflector capacity, sum of widths
+  std::vector<uint8_t> qr_grid;            // interfaces: 1 if the multi-CTA RRQR factors it
 };
 
 // Whether a cluster of cs CTAs with the largest shared-memory slice can be resident.
@@ -504,6 +505,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
   Ly.tau.assign(ncl, nullptr);
   Ly.maxref.assign(ncl, 0);
   Ly.ncols_ub.assign(ncl, 0);
+  Ly.qr_grid.assign(ncl, 0);
   if (S.sparsify) {
     for (int p : S.ifaces) {
       const int m = Ly.m[p];
@@ -556,7 +558,8 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         t.id = p;
         t.maxref = Ly.maxref[p];
         t.ncols_max = Ly.ncols_ub[p];
-        t.pad = 0;
+        t.wait_extra = h->qr_wait_extra;
+        t.wait_limit = h->qr_wait_limit;
         t.seg_begin = (int)W.qr_segs.size();
         const auto& rs = S.rowsegs[p];
         for (size_t i = 0; i < rs.size(); ++i) {
@@ -601,6 +604,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         // too wide for a cluster: spread over several CTAs of a cooperative
         // launch (bucket 6), unless the single-CTA streamed kernel is asked for
         if ((b == 0 && h->rrqr_path != 1) || h->rrqr_path == 3) b = 6;
+        Ly.qr_grid[p] = b == 6 ? 1 : 0;
         auto& g = W.qr[{col, b * 4096 + thr}];
         g.threads = thr;
         g.bucket = b;
@@ -796,7 +800,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
     if (b == 6) {
       for (const auto& gl : O.grid) {
         if (gl.group != gi) continue;
-        run(KK_RRQR, (size_t)gl.ntasks, 0.0, 0.0, [&] {
+        run(KK_RRQR_GRID, (size_t)gl.ntasks, 0.0, 0.0, [&] {
           const cudaError_t e = launch_rrqr_grid((const RRQRGridTask*)(D + gl.off), gl.ntasks,
                                                  gl.nctas, (const RRQRSeg*)(D + O.seg), gl.smem, cs);
           if (e != cudaSuccess && gerr == cudaSuccess) gerr = e;
@@ -807,15 +811,18 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
         if (b == 0)
           launch_rrqr((const RRQRTask*)(D + off), (int)g.tasks.size(), (const RRQRSeg*)(D + O.seg),
                       g.max_m, g.max_cols, g.max_segs, cs);
-        else
-          launch_rrqr_cluster((const RRQRTask*)(D + off), (int)g.tasks.size(),
-                              (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, g.threads, cs);
+        else {
+          const cudaError_t e =
+              launch_rrqr_cluster((const RRQRTask*)(D + off), (int)g.tasks.size(),
+                                  (const RRQRSeg*)(D + O.seg), 1 << (b - 1), g.smem, g.threads, cs);
+          if (e != cudaSuccess && gerr == cudaSuccess) gerr = e;
+        }
       });
     }
     ++gi;
   }
   if (gerr != cudaSuccess)
-    return fail(SPAND_ECUDA, std::string("multi-CTA RRQR launch: ") + cudaGetErrorString(gerr));
+    return fail(SPAND_ECUDA, std::string("RRQR launch: ") + cudaGetErrorString(gerr));
   CK(cudaGetLastError());
   return SPAND_OK;
 }
@@ -834,16 +841,19 @@ int finish_stage(Run& R, int k, const int* hp, Prof& P) {
   h->flags[k].assign(hp + 3 * ncl, hp + 4 * ncl);
   auto segc = [&](int c, int d) { return segcol_of(S.rowsegs[c], Ly.segcol[c], d); };
   if (P.on && S.sparsify) {
-    double fl = 0.0, by = 0.0;
+    double fl[2] = {0.0, 0.0}, by[2] = {0.0, 0.0};
     for (int p : S.ifaces) {
       const int m = Ly.m[p], nref = h->nrefs[k][p];
+      const int w = Ly.qr_grid[p];
       int N = 0;
       for (int q : S.adj1[p]) N += (S.colour[q] < S.colour[p]) ? h->ranks[k][q] : Ly.m[q];
-      for (int t = 0; t < nref; ++t) fl += 6.0 * (double)(m - t) * (double)(N - t);
-      by += 16.0 * (double)m * N;  // the block is read and written once
+      for (int t = 0; t < nref; ++t) fl[w] += 6.0 * (double)(m - t) * (double)(N - t);
+      by[w] += 16.0 * (double)m * N;  // the block is read and written once
     }
-    P.stat[KK_RRQR].flops += fl;
-    P.stat[KK_RRQR].bytes += by;
+    P.stat[KK_RRQR].flops += fl[0];
+    P.stat[KK_RRQR].bytes += by[0];
+    P.stat[KK_RRQR_GRID].flops += fl[1];
+    P.stat[KK_RRQR_GRID].bytes += by[1];
   }
   auto explicit_inverse = [&](const real_t* Lb, int m, real_t** out) -> int {
     void* ip = nullptr;
@@ -1055,7 +1065,7 @@ int factor_replay(spand_s* const* hs, int count, FactorGroup& G, cudaStream_t s)
       const int ncl = g.ncl[j];
       const int* c = hp + g.ioff[j];
       if (c[4 * ncl + 1] != 0)
-        return fail(SPAND_ECUDA, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
+        return fail(SPAND_ETIMEOUT, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
                                      std::to_string(k) + ")");
       if (c[4 * ncl] != 0)
         return fail(SPAND_ENOTSPD, "non-positive Cholesky pivot in problem " +
@@ -1218,7 +1228,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       if (c[4 * ncls[j] + 1] != 0) {
         for (int i = 0; i < count; ++i) hs[i]->factored = false;
         G.drop();
-        return fail(SPAND_ECUDA, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
+        return fail(SPAND_ETIMEOUT, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
                                      std::to_string(k) + ")");
       }
       if (c[4 * ncls[j]] != 0) {

@@ -364,10 +364,7 @@ __global__ void AP_BOUNDS
 
 // The dynamic shared memory a launch may use beyond the 48 KB default must be
 // granted per kernel; the static part (the partial-sum buffer) counts too, so
-// the grant is made for any dynamic size above 16 KB.
-static void smem_attr(const void* fn, int bytes) {
-  if (bytes > 16 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
+// the grant is made for any dynamic size above 16 KB (grant_smem only raises it).
 
 __global__ void k_copy_real(int n, const real_t* __restrict__ s, real_t* __restrict__ d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = s[i];
@@ -379,11 +376,13 @@ void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s) {
 
 typedef void (*ApKernel)(const ApItem*, int, real_t*, int);
 
+// Attribute and launch errors are left for cudaGetLastError, which the apply
+// checks after its launches.
 static void launch_ap(ApKernel kern, const ApItem* items, int nitems, int ntasks, int K, int bytes,
                       real_t* z, bool forward, cudaStream_t s) {
   if (ntasks <= 0) return;
-  smem_attr((const void*)kern, bytes);
-  if (K > 8) cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (grant_smem((const void*)kern, bytes) != cudaSuccess) return;
+  if (K > 8 && allow_wide_clusters((const void*)kern) != cudaSuccess) return;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ntasks * K));
   cfg.blockDim = dim3(kApThreads);

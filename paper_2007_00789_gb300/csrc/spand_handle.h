@@ -129,12 +129,12 @@ struct Blob {
 enum KernelKind {
   KK_PACK, KK_MERGE, KK_POTRF, KK_TRSM, KK_SCHUR, KK_SCALE_POTRF, KK_SCALE_TRSM, KK_SCALE_COPY,
   KK_RRQR, KK_ECOPY, KK_TRTRI, KK_FORMQ, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT,
-  KK_VEC, KK_COUNT
+  KK_VEC, KK_RRQR_GRID, KK_COUNT
 };
 static const char* const kKindName[KK_COUNT] = {
     "pack", "merge", "potrf", "trsm", "schur", "scale_potrf", "scale_trsm", "scale_copy",
     "rrqr", "e_copy", "trtri", "form_qt", "apply_interior", "apply_scale", "apply_qe", "spmv",
-    "dot", "vector"};
+    "dot", "vector", "rrqr_grid"};
 
 struct Prof {
   bool on = false;
@@ -412,6 +412,11 @@ struct spand_s {
   cudaStream_t cap_stream = nullptr;  // capture needs a stream other than the legacy one
   spand::MultiApply self_ma;  // the apply plan (and graph) of this problem alone
   bool no_graph = false;  // plain launches only (set by the allocation-free PCG)
+  // bounded wait of the multi-CTA RRQR: polls per barrier before it gives up, and
+  // the testing hook that makes the first barrier unreachable (spand_test_set_qr_wait)
+  static constexpr long long kQrWaitDefault = 1LL << 24;  // about a second
+  long long qr_wait_limit = kQrWaitDefault;
+  int qr_wait_extra = 0;
   void drop_graphs() {
     fg.drop();
     self_ma.drop();

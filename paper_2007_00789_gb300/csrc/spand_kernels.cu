@@ -637,27 +637,27 @@ __global__ void __launch_bounds__(kQrThreads)
 // bounded: a wait that runs out raises the task's abort flag and the
 // problem's error word, and every CTA of the task leaves.
 // ---------------------------------------------------------------------------
-constexpr long kQrGridSpin = 1L << 24;  // about a second of polling per barrier
-
 struct GridSlot {  // one CTA's candidates of one step (6 ints)
   double best, second;
   int idx, pad;
 };
 
-__device__ __forceinline__ bool qr_grid_barrier(int* ctr, int* abort, int target) {
+// limit: polls of the counter before the wait gives up (the task's wait_limit,
+// about a second by default).
+__device__ __forceinline__ bool qr_grid_barrier(int* ctr, int* abort, int target, long long limit) {
   __shared__ int s_ok;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(ctr, 1);
     int ok = 1;
-    long it = 0;
+    long long it = 0;
     while (*(volatile int*)ctr < target) {
       if (*(volatile int*)abort) {
         ok = 0;
         break;
       }
-      if (++it > kQrGridSpin) {
+      if (++it > limit) {
         atomicExch(abort, 1);
         ok = 0;
         break;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kQrThreads)
       slots[(step & 1) * G + crank] = gs;
     }
     ++nbar;
-    if (!qr_grid_barrier(ctr, abort, nbar * G)) {
+    if (!qr_grid_barrier(ctr, abort, nbar * G + (nbar == 1 ? t.wait_extra : 0), t.wait_limit)) {
       ok = false;
       break;
     }
@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(kQrThreads)
   // every CTA has read the last pivot column once all pass this barrier
   if (ok) {
     ++nbar;
-    ok = qr_grid_barrier(ctr, abort, nbar * G);
+    ok = qr_grid_barrier(ctr, abort, nbar * G + (nbar == 1 ? t.wait_extra : 0), t.wait_limit);
   }
   if (!ok) {
     if (tid == 0) atomicExch(t.err + 1, 1);
@@ -1926,9 +1926,9 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
 // ---------------------------------------------------------------------------
 constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory per CTA we allow
 
-static void set_smem(const void* fn, int bytes) {
-  if (bytes > 16 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
+// Errors of the grant surface through cudaGetLastError, which the callers check
+// after each stage's launches.
+static void set_smem(const void* fn, int bytes) { (void)grant_smem(fn, bytes); }
 
 void launch_copy(const CopyTask* t, int ntasks, cudaStream_t s) {
   if (ntasks > 0) k_copy<<<ntasks, 256, 0, s>>>(t);
@@ -1999,13 +1999,12 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
   return (int)std::min<long>(b, 1L << 30);
 }
 
-void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
-                         int smem_bytes, int threads, cudaStream_t s) {
-  if (ntasks <= 0) return;
-  cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem_bytes);
-  if (csize > 8)
-    cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+cudaError_t launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
+                                int smem_bytes, int threads, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  cudaError_t e = grant_smem((const void*)k_rrqr_cluster, smem_bytes);
+  if (e == cudaSuccess && csize > 8) e = allow_wide_clusters((const void*)k_rrqr_cluster);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ntasks * csize));
   cfg.blockDim = dim3((unsigned)threads);
@@ -2018,14 +2017,16 @@ void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, csize);
+  return cudaLaunchKernelEx(&cfg, k_rrqr_cluster, t, segs, csize);
 }
 
 int rrqr_cluster_active(int csize, int smem_bytes, int threads) {
-  cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem_bytes);
-  if (csize > 8)
-    cudaFuncSetAttribute((const void*)k_rrqr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = grant_smem((const void*)k_rrqr_cluster, smem_bytes);
+  if (e == cudaSuccess && csize > 8) e = allow_wide_clusters((const void*)k_rrqr_cluster);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)csize);
   cfg.blockDim = dim3((unsigned)threads);
@@ -2068,7 +2069,8 @@ int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs) {
 cudaError_t launch_rrqr_grid(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
                              int smem_bytes, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
-  set_smem((const void*)k_rrqr_grid, smem_bytes);
+  const cudaError_t e = grant_smem((const void*)k_rrqr_grid, smem_bytes);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nctas);
   cfg.blockDim = dim3(kQrThreads);

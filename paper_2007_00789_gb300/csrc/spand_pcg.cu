@@ -1,9 +1,44 @@
 // FP64 vector kernels of PCG (§4): CSR SpMV, deterministic two-pass dot
 // products, the CG vector updates with device-resident scalars, and the
 // FP64 <-> FP32 conversions around an FP32 preconditioner apply.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "spand_internal.h"
 
 namespace spand {
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void*>, int> g_smem_granted;  // (device, kernel) -> bytes
+std::map<std::pair<int, const void*>, int> g_wide_clusters;
+}  // namespace
+
+cudaError_t grant_smem(const void* fn, int bytes) {
+  if (bytes <= 16 * 1024) return cudaSuccess;  // the static part needs no grant below 48 KB in all
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  int& have = g_smem_granted[{dev, fn}];
+  if (bytes <= have) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
+cudaError_t allow_wide_clusters(const void* fn) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  int& done = g_wide_clusters[{dev, fn}];
+  if (done) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) done = 1;
+  return e;
+}
 
 namespace {
 

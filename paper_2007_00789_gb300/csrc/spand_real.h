@@ -17,6 +17,17 @@
 #endif
 
 namespace spand {
+
+// ---------------------------------------------------------------------------
+// Kernel attributes (spand_pcg.cu).  The dynamic shared memory a kernel may
+// use beyond 48 KB is a per-function limit on the current device; graphs
+// captured earlier can hold launches of the same kernel with more dynamic
+// shared memory than a later launch asks for, so the limit is only ever
+// raised, never lowered.  Both return the CUDA error of the attribute call.
+// ---------------------------------------------------------------------------
+cudaError_t grant_smem(const void* fn, int bytes);
+cudaError_t allow_wide_clusters(const void* fn);  // thread-block clusters of more than 8 CTAs
+
 namespace SPAND_NS {
 
 typedef SPAND_REAL real_t;
@@ -97,7 +108,9 @@ struct RRQRTask {
   int* err;        // the problem's error words: err[1] = 1 if a multi-CTA QR lost synchronisation
   double eps;      // relative tolerance of the problem (Algorithm 1)
   int scheme;      // SPAND_FIRST_ORDER, SPAND_SECOND_ORDER_FULL or SPAND_SECOND_ORDER_SUPERFINE
-  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max, pad;
+  int m, ld, seg_begin, seg_end, id, maxref, ncols_max, nseg_max;
+  int wait_extra;        // multi-CTA QR: added to the first barrier's target (testing hook, else 0)
+  long long wait_limit;  // multi-CTA QR: polls of a barrier counter before the wait gives up
 };
 
 // An interface QR spread over ncta CTAs of one cooperative launch (CTAs
@@ -164,8 +177,8 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize);
 // Clusters of this shape that can be resident at once (0: cannot be launched).
 int rrqr_cluster_active(int csize, int smem_bytes, int threads);
 // threads: CTA size, 256, 512 or 1024
-void launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
-                         int smem_bytes, int threads, cudaStream_t s);
+cudaError_t launch_rrqr_cluster(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int csize,
+                                int smem_bytes, int threads, cudaStream_t s);
 void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, int max_cols,
                  int max_segs, cudaStream_t s);
 // Cooperative multi-CTA QR: nctas CTAs in all (at most one per SM), each task

@@ -21,10 +21,12 @@ SPAND_ENOMEM = -3
 SPAND_ECUDA = -4
 SPAND_ENOCONV = -5
 SPAND_ESTATE = -6
+SPAND_ETIMEOUT = -7
 
 # Every entry point declared in include/spand.h.
 EXPORTS = [
-    "spand_analyze", "spand_factor", "spand_apply", "spand_pcg", "spand_pcg_host",
+    "spand_analyze", "spand_factor", "spand_test_set_qr_wait", "spand_apply", "spand_pcg",
+    "spand_pcg_host",
     "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
     "spand_pcg_noalloc", "spand_set_profiling", "spand_kernel_stats",
     "spand_apply_many", "spand_pcg_many",
@@ -32,7 +34,7 @@ EXPORTS = [
     "spand_batch_set_profiling", "spand_batch_kernel_stats", "spand_batch_destroy",
     "spand_server_create", "spand_server_add", "spand_server_submit", "spand_server_wait",
     "spand_server_get_stats", "spand_server_destroy",
-    "spand_destroy", "spand_strerror", "spand_last_error",
+    "spand_measure_fma_peak", "spand_destroy", "spand_strerror", "spand_last_error",
 ]
 _VOID = ("spand_destroy", "spand_batch_destroy", "spand_server_destroy", "spand_strerror",
          "spand_last_error")
@@ -78,7 +80,11 @@ class _ServerStats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("elapsed_s", ctypes.c_double), ("solves_per_s", ctypes.c_double),
                 ("ticks", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
-                ("resident_problems", ctypes.c_int32), ("resident_bytes", ctypes.c_int64)]
+                ("resident_problems", ctypes.c_int32), ("resident_bytes", ctypes.c_int64),
+                ("factor_wait_p50_ms", ctypes.c_double), ("factor_wait_p99_ms", ctypes.c_double),
+                ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("solve_p50_ms", ctypes.c_double), ("solve_p99_ms", ctypes.c_double),
+                ("max_split_ms", ctypes.c_double * 3)]
 
 
 class _KStat(ctypes.Structure):
@@ -102,6 +108,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_analyze.argtypes = [ctypes.POINTER(_CSR), vp, ctypes.c_int, ctypes.c_int, f64,
                                 ctypes.c_int, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
     L.spand_factor.argtypes = [vp, vp]
+    L.spand_test_set_qr_wait.argtypes = [vp, i64, i32]
     L.spand_apply.argtypes = [vp, vp, vp, vp]
     L.spand_pcg.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_pcg_host.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
@@ -132,6 +139,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.spand_server_get_stats.argtypes = [vp, ctypes.POINTER(_ServerStats)]
     L.spand_server_destroy.argtypes = [vp]
     L.spand_server_destroy.restype = None
+    L.spand_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     L.spand_destroy.argtypes = [vp]
     L.spand_destroy.restype = None
     L.spand_strerror.argtypes = [ctypes.c_int]
@@ -222,6 +230,10 @@ class Spand:
     def factor(self, stream=None):
         _check(self._lib.spand_factor(self._h, _stream_ptr(stream)))
 
+    def test_set_qr_wait(self, limit: int = 0, unreachable: bool = False):
+        """Testing hook of the multi-CTA RRQR's bounded barrier wait (spand_test_set_qr_wait)."""
+        _check(self._lib.spand_test_set_qr_wait(self._h, int(limit), 1 if unreachable else 0))
+
     def apply(self, r, z, stream=None):
         _check(self._lib.spand_apply(self._h, _dptr(r), _dptr(z), _stream_ptr(stream)))
 
@@ -307,6 +319,15 @@ class Spand:
         out = np.empty(self.n, dtype=np.int32)
         _check(self._lib.spand_cluster_map(self._h, int(stage), out.ctypes.data))
         return out
+
+
+def measure_fma_peak(precision: int = 0) -> tuple[float, float]:
+    """(TFLOP/s, best launch ms) of FMA chains on the current device (spand_measure_fma_peak)."""
+    L = load_library()
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(L.spand_measure_fma_peak(int(precision), ctypes.byref(tf), ctypes.byref(ms)))
+    return float(tf.value), float(ms.value)
 
 
 def _kstats(fn, h) -> list[dict]:
@@ -428,7 +449,9 @@ class SpandServer:
     def stats(self) -> dict:
         s = _ServerStats()
         _check(self._lib.spand_server_get_stats(self._h, ctypes.byref(s)))
-        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+        out = {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+        out["max_split_ms"] = list(out["max_split_ms"])
+        return out
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -53,6 +53,40 @@ def test_noalloc_matches_pcg_twice(make, ell, scheme):
     h.close()
 
 
+def test_noalloc_allocates_nothing():
+    """On a handle that has only been factored, the no-alloc solve leaves the
+    device's free memory unchanged; spand_pcg (which allocates its work
+    vectors) runs only afterwards, for the comparison."""
+    torch = _torch()
+    from paper_2007_00789_gb300 import spand as S
+    prob = si.diffusion_3d(20, seed=5)
+    ell, scheme = 7, 1
+    b = torch.from_numpy(si.rhs_normal(prob.n, seed=8)).cuda()
+    # the same problem shape solved once first: CUDA loads the kernels a call
+    # launches on their first use, and that load takes device memory of its own
+    warm = S.Spand.from_problem(prob, ell, 1e-2, scheme)
+    warm.factor()
+    xw = torch.zeros_like(b)
+    warm.pcg_noalloc(b, xw, 1e-12)
+    warm.close()
+    h = S.Spand.from_problem(prob, ell, 1e-2, scheme)
+    h.factor()
+    x = torch.zeros_like(b)
+    x_ref = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    it, rel = h.pcg_noalloc(b, x, 1e-12)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert rel <= 1e-12
+    it_ref, rel_ref = h.pcg(b, x_ref, 1e-12)
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    err = float((x - x_ref).abs().max() / x_ref.abs().max())
+    assert err <= TOL_X, err
+    h.close()
+
+
 def test_noalloc_rejects_too_large_system():
     torch = _torch()
     from paper_2007_00789_gb300 import spand as S
