@@ -386,6 +386,7 @@ struct Server {
     size_t bytes = 0;  // device bytes held by its factorization
     int users = 0;     // queued or running requests
     int64_t last_use = 0;
+    std::chrono::steady_clock::time_point t_ready;  // when its factorization last completed
   };
   struct Req {
     int64_t id = 0;
@@ -399,7 +400,9 @@ struct Server {
     int status = SPAND_OK;
     std::vector<int32_t> iters;
     std::vector<double> relres;
-    std::chrono::steady_clock::time_point t_submit, t_done;
+    // submission, admission to the solve engine, completion; the wait for the
+    // problem's factorization ends at max(t_submit, the problem's t_ready)
+    std::chrono::steady_clock::time_point t_submit, t_ready, t_admit, t_done;
   };
 
   spand_server_opts opts{};
@@ -420,6 +423,9 @@ struct Server {
   int error = SPAND_OK;
   std::string error_msg;
   std::vector<double> lat_ms;
+  // per completed request: waiting for the factorization, queued with the
+  // problem ready (slots, vector space), and solving (admission to completion)
+  std::vector<double> wait_factor_ms, wait_queue_ms, solve_ms;
   int64_t solves = 0;
   std::chrono::steady_clock::time_point t_first, t_last;
   bool any = false;
@@ -491,6 +497,7 @@ struct Server {
         const size_t el = h->precision == 1 ? 4 : 8;
         mu_estimate = (double)m.bytes / ((double)h->nnz * el);  // the latest problem's ratio
         m.state = 2;
+        m.t_ready = std::chrono::steady_clock::now();
       } else {
         m.state = 3;
         m.status = rc;
@@ -561,6 +568,8 @@ struct Server {
         RET(eng.add(m.h, off + j * q.stride, opts.tol, q.b + (size_t)j * m.h->n,
                     cudaMemcpyHostToDevice, s_solve, &q.seg[j]));
       q.done = 1;
+      q.t_admit = std::chrono::steady_clock::now();
+      q.t_ready = std::max(q.t_submit, m.t_ready);
       free_slots -= q.nrhs;
       m.last_use = tick_count;
       qi = queue.erase(qi);
@@ -593,6 +602,9 @@ struct Server {
       q.done = 2;
       q.t_done = std::chrono::steady_clock::now();
       lat_ms.push_back(std::chrono::duration<double, std::milli>(q.t_done - q.t_submit).count());
+      wait_factor_ms.push_back(std::chrono::duration<double, std::milli>(q.t_ready - q.t_submit).count());
+      wait_queue_ms.push_back(std::chrono::duration<double, std::milli>(q.t_admit - q.t_ready).count());
+      solve_ms.push_back(std::chrono::duration<double, std::milli>(q.t_done - q.t_admit).count());
       solves += q.nrhs;
       t_last = q.t_done;
       m.users -= 1;
@@ -990,18 +1002,32 @@ int spand_server_get_stats(spand_server_t s, spand_server_stats* st) {
   Server& S = s->srv;
   std::lock_guard<std::mutex> lk(S.mu);
   memset(st, 0, sizeof(*st));
-  std::vector<double> l = S.lat_ms;
-  std::sort(l.begin(), l.end());
-  auto pct = [&](double p) {
+  auto pct = [](std::vector<double> l, double p) {
     if (l.empty()) return 0.0;
+    std::sort(l.begin(), l.end());
     const size_t i = std::min(l.size() - 1, (size_t)std::ceil(p * (double)l.size()) - (p > 0 ? 1 : 0));
     return l[i];
   };
-  st->requests = (int64_t)l.size();
+  st->requests = (int64_t)S.lat_ms.size();
   st->solves = S.solves;
-  st->p50_ms = pct(0.50);
-  st->p99_ms = pct(0.99);
-  st->max_ms = l.empty() ? 0.0 : l.back();
+  st->p50_ms = pct(S.lat_ms, 0.50);
+  st->p99_ms = pct(S.lat_ms, 0.99);
+  st->max_ms = pct(S.lat_ms, 1.0);
+  st->factor_wait_p50_ms = pct(S.wait_factor_ms, 0.50);
+  st->factor_wait_p99_ms = pct(S.wait_factor_ms, 0.99);
+  st->queue_p50_ms = pct(S.wait_queue_ms, 0.50);
+  st->queue_p99_ms = pct(S.wait_queue_ms, 0.99);
+  st->solve_p50_ms = pct(S.solve_ms, 0.50);
+  st->solve_p99_ms = pct(S.solve_ms, 0.99);
+  // the slowest request's parts
+  size_t w = 0;
+  for (size_t i = 1; i < S.lat_ms.size(); ++i)
+    if (S.lat_ms[i] > S.lat_ms[w]) w = i;
+  if (!S.lat_ms.empty()) {
+    st->max_split_ms[0] = S.wait_factor_ms[w];
+    st->max_split_ms[1] = S.wait_queue_ms[w];
+    st->max_split_ms[2] = S.solve_ms[w];
+  }
   st->elapsed_s = S.any ? std::chrono::duration<double>(S.t_last - S.t_first).count() : 0.0;
   st->solves_per_s = st->elapsed_s > 0 ? (double)S.solves / st->elapsed_s : 0.0;
   st->ticks = S.tick_count;
