@@ -518,9 +518,12 @@ def main():
                     help="no CUDA graphs: every kernel launched on its own (for profilers)")
     ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512],
                     help="threads per CTA of the on-chip RRQR (0: the library's choice)")
-    ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="0: on-chip RRQR in clusters of up to 16 CTAs; 1: global-memory RRQR;"
-                         " 2: on-chip RRQR in clusters of up to 8 CTAs")
+    ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+                    help="0: on-chip RRQR in clusters of up to 16 CTAs, wider blocks over several"
+                         " CTAs with their slices in shared memory where they fit; 1: global-memory"
+                         " RRQR; 2: clusters of up to 8 CTAs; 3: always the streamed multi-CTA"
+                         " kernel; 4: always the on-chip multi-CTA kernel; 5: as 0 with the"
+                         " multi-CTA blocks streamed")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.precision is None:

@@ -70,11 +70,15 @@ typedef struct {
   int32_t max_restarts;   /* PCG restarts when the true residual misses tol; <0 = 2 */
   int32_t rrqr_kernel;    /* 0 = keep each interface block on chip (one CTA, or a thread-block
                              cluster of up to 16 CTAs) where it fits, else spread it over several
-                             CTAs of a cooperative launch that stream it from global memory;
+                             CTAs of a cooperative launch (at most one per SM) that keep their
+                             slices in shared memory where they fit, else stream them from
+                             global memory;
                              1 = always stream from global memory with one CTA per interface;
                              2 = as 0 with clusters of at most 8 CTAs (the portable cluster
-                             size); 3 = always the multi-CTA streamed kernel (equal to 1 bit for
-                             bit).  Same results up to the order of some FP sums. */
+                             size); 3 = always the multi-CTA streamed kernel; 4 = always the
+                             multi-CTA on-chip kernel where the block fits (else streamed);
+                             5 = as 0, but blocks too wide for a cluster always streamed.
+                             Same results up to the order of some FP sums. */
   int32_t precision;      /* 0 = FP64 factorization and apply (the default);
                              1 = FP32 factorization and apply, with the RRQR rank decisions
                              (nu_0 and every step within 1e-4 of the threshold) taken on norms

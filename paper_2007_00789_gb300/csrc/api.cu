@@ -255,8 +255,8 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     if (opts->maxit > 0) h->maxit = opts->maxit;
     if (opts->true_res_every > 0) h->true_every = opts->true_res_every;
     if (opts->max_restarts >= 0) h->max_restarts = opts->max_restarts;
-    if (opts->rrqr_kernel < 0 || opts->rrqr_kernel > 3)
-      return fail(SPAND_EINVAL, "rrqr_kernel must be 0, 1, 2 or 3");
+    if (opts->rrqr_kernel < 0 || opts->rrqr_kernel > 5)
+      return fail(SPAND_EINVAL, "rrqr_kernel must be 0 .. 5");
     h->rrqr_path = opts->rrqr_kernel;
     if (opts->precision < 0 || opts->precision > 1) return fail(SPAND_EINVAL, "precision must be 0 or 1");
     h->precision = opts->precision;

@@ -47,6 +47,16 @@ struct ApQEP {
 };
 
 
+// SPAND_DEBUG_PLAN=1 in the environment prints every interface's RRQR shape and
+// kernel choice to stderr while a stage is laid out (for tuning; off by default).
+bool debug_plan() {
+  static const bool on = [] {
+    const char* e = getenv("SPAND_DEBUG_PLAN");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 inline int segcol_of(const std::vector<int>& segs, const std::vector<int>& cols, int d) {
   auto it = std::lower_bound(segs.begin(), segs.end(), d);
   return cols[it - segs.begin()];
@@ -245,12 +255,27 @@ struct StageLayout {
 
 // Whether a cluster of cs CTAs with the largest shared-memory slice can be resident.
 bool cluster_ok(spand_s* h, int cs) {
-  if (h->rrqr_path == 1 || h->rrqr_path == 3 || (h->rrqr_path == 2 && cs > 8)) return false;
+  if (h->rrqr_path == 1 || h->rrqr_path == 3 || h->rrqr_path == 4 || (h->rrqr_path == 2 && cs > 8))
+    return false;
   int lc = 0;
   while ((1 << lc) < cs) ++lc;
   int& st = h->cluster_state[sizeof(real_t) == 4 ? 1 : 0][lc];
   if (st < 0) st = rrqr_cluster_active(cs, kQrClusterSmem, 256) > 0 ? 1 : 0;
   return st == 1;
+}
+
+// The multi-CTA RRQR keeps the block on chip when some number of CTAs, at
+// most one per SM, holds it in shared memory: the fewest CTAs that do (0 if
+// none).  kQrOnChip marks such tasks (a flag bit beside the testing hook in
+// wait_extra, cleared before the launch).
+constexpr int kGsmSmem = 220 * 1024;
+constexpr int kQrOnChip = 1 << 20;
+int gsm_need(int m, int ncols, int nseg) {
+  if (m <= 0 || ncols <= 0) return 1;
+  for (int nc = std::max(1, (int)(((int64_t)m * ncols * (int64_t)sizeof(real_t)) / kGsmSmem));
+       nc <= kNumSMs; ++nc)
+    if (rrqr_gsm_smem_bytes(m, (ncols + nc - 1) / nc, nseg) <= kGsmSmem) return nc;
+  return 0;
 }
 
 // Per-problem state of a factorization in progress.
@@ -603,8 +628,16 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         }
         // too wide for a cluster: spread over several CTAs of a cooperative
         // launch (bucket 6), unless the single-CTA streamed kernel is asked for
-        if ((b == 0 && h->rrqr_path != 1) || h->rrqr_path == 3) b = 6;
+        if ((b == 0 && h->rrqr_path != 1) || h->rrqr_path == 3 || h->rrqr_path == 4) b = 6;
         Ly.qr_grid[p] = b == 6 ? 1 : 0;
+        // multi-CTA: on chip where the block fits the shared memory of at most
+        // one CTA per SM, else streamed (rrqr_path 3: always streamed)
+        if (b == 6) t.wait_extra |= (h->rrqr_path != 3 && h->rrqr_path != 5 &&
+                                     gsm_need(m, t.ncols_max, t.nseg_max) > 0)
+                                        ? kQrOnChip : 0;
+        if (debug_plan())
+          fprintf(stderr, "spand plan: stage %d colour %d iface %d m %d ncols_ub %d nseg %d bucket %d thr %d\n",
+                  k, col, p, m, t.ncols_max, t.nseg_max, b, thr);
         auto& g = W.qr[{col, b * 4096 + thr}];
         g.threads = thr;
         g.bucket = b;
@@ -616,7 +649,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         if (b == 0 && rrqr_smem_bytes(g.max_m, g.max_cols, g.max_segs) > 220 * 1024)
           return fail(SPAND_ENOMEM, "interface block too wide for the RRQR workspace (stage " +
                                         std::to_string(k) + ")");
-        if (b == 6 && rrqr_grid_smem_bytes(m, 32, t.nseg_max) > 200 * 1024)
+        if (b == 6 && !(t.wait_extra & kQrOnChip) && rrqr_grid_smem_bytes(m, 32, t.nseg_max) > 200 * 1024)
           return fail(SPAND_ENOMEM, "interface too tall for the multi-CTA RRQR (stage " +
                                         std::to_string(k) + ")");
       }
@@ -642,10 +675,15 @@ struct StageBlob {
     size_t off;        // RRQRGridTask array in the blob
     int ntasks, nctas, smem;
     size_t group;      // index of the QrGroup
+    bool onchip;       // k_rrqr_gsm (the slices in shared memory) or k_rrqr_grid
   };
   std::vector<GridLaunch> grid;
   std::vector<std::vector<size_t>> grid_ws;  // per launch: workspace int offset of each task
+  std::vector<std::vector<size_t>> grid_stage;  // per launch: staging byte offset of each task
   size_t ws = 0, ws_ints = 0;
+  // staging of the on-chip multi-CTA QR: the blob's tail, never uploaded
+  // (always written before it is read)
+  size_t stage = 0, stage_bytes = 0, upload = 0;
 };
 
 StageBlob pack_blob(StageWork& W, Blob& blob) {
@@ -671,23 +709,79 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
     const auto& g = kv.second;
     o.qr.push_back(blob.add(g.tasks));
     if (g.bucket == 6) {
-      // at most one CTA per SM per launch; tasks share the SMs by their work m x ncols
-      for (size_t t0 = 0; t0 < g.tasks.size(); t0 += kNumSMs) {
-        const size_t t1 = std::min(g.tasks.size(), t0 + (size_t)kNumSMs);
+      std::vector<RRQRTask> onchip, streamed;
+      for (RRQRTask t : g.tasks) {
+        const bool oc = (t.wait_extra & kQrOnChip) != 0;
+        t.wait_extra &= ~kQrOnChip;
+        (oc ? onchip : streamed).push_back(t);
+      }
+      // on chip: launches of tasks whose fewest CTAs fit in one CTA per SM; the
+      // spare SMs go to the tasks by their work m x ncols
+      for (size_t t0 = 0; t0 < onchip.size();) {
+        size_t t1 = t0;
+        int used = 0;
+        while (t1 < onchip.size()) {
+          const RRQRTask& t = onchip[t1];
+          const int need = gsm_need(t.m, t.ncols_max, t.nseg_max);
+          if (t1 > t0 && used + need > kNumSMs) break;
+          used += need;
+          ++t1;
+        }
         double wsum = 0.0;
-        for (size_t i = t0; i < t1; ++i) wsum += (double)g.tasks[i].m * g.tasks[i].ncols_max;
+        for (size_t i = t0; i < t1; ++i) wsum += (double)onchip[i].m * onchip[i].ncols_max;
+        const int spare = std::max(0, kNumSMs - used);
+        std::vector<RRQRGridTask> gts;
+        std::vector<size_t> wsoff, stoff;
+        int cta = 0, smem = 0;
+        for (size_t i = t0; i < t1; ++i) {
+          const RRQRTask& t = onchip[i];
+          const double w = (double)t.m * t.ncols_max;
+          int nc = gsm_need(t.m, t.ncols_max, t.nseg_max) + (wsum > 0.0 ? (int)(spare * w / wsum) : 0);
+          nc = std::max(1, std::min(nc, std::max(1, t.ncols_max)));
+          RRQRGridTask gt;
+          gt.t = t;
+          gt.ws = nullptr;
+          gt.stage = nullptr;
+          gt.cta0 = cta;
+          gt.ncta = nc;
+          gts.push_back(gt);
+          wsoff.push_back(o.ws_ints);
+          o.ws_ints += qr_grid_ws_ints(nc);
+          stoff.push_back(o.stage_bytes);
+          o.stage_bytes += ((size_t)2 * nc * std::max(t.m, 1) * sizeof(real_t) + 255) & ~size_t(255);
+          cta += nc;
+          smem = std::max(smem, rrqr_gsm_smem_bytes(t.m, (t.ncols_max + nc - 1) / nc, t.nseg_max));
+        }
+        StageBlob::GridLaunch gl;
+        gl.off = blob.add(gts);
+        gl.ntasks = (int)gts.size();
+        gl.nctas = cta;
+        gl.smem = smem;
+        gl.group = gi;
+        gl.onchip = true;
+        o.grid.push_back(gl);
+        o.grid_ws.push_back(wsoff);
+        o.grid_stage.push_back(stoff);
+        t0 = t1;
+      }
+      // streamed: at most one CTA per SM per launch; tasks share the SMs by their work
+      for (size_t t0 = 0; t0 < streamed.size(); t0 += kNumSMs) {
+        const size_t t1 = std::min(streamed.size(), t0 + (size_t)kNumSMs);
+        double wsum = 0.0;
+        for (size_t i = t0; i < t1; ++i) wsum += (double)streamed[i].m * streamed[i].ncols_max;
         const int spare = kNumSMs - (int)(t1 - t0);
         std::vector<RRQRGridTask> gts;
         std::vector<size_t> wsoff;
         int cta = 0, smem = 0;
         for (size_t i = t0; i < t1; ++i) {
-          const RRQRTask& t = g.tasks[i];
+          const RRQRTask& t = streamed[i];
           const double w = (double)t.m * t.ncols_max;
           int nc = 1 + (wsum > 0.0 ? (int)(spare * w / wsum) : 0);
           nc = std::max(1, std::min(nc, (t.ncols_max + 31) / 32));  // at least 32 columns per CTA
           RRQRGridTask gt;
           gt.t = t;
           gt.ws = nullptr;
+          gt.stage = nullptr;
           gt.cta0 = cta;
           gt.ncta = nc;
           gts.push_back(gt);
@@ -702,8 +796,10 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
         gl.nctas = cta;
         gl.smem = smem;
         gl.group = gi;
+        gl.onchip = false;
         o.grid.push_back(gl);
         o.grid_ws.push_back(wsoff);
+        o.grid_stage.push_back({});
       }
     }
     ++gi;
@@ -711,6 +807,11 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
   o.seg = blob.add(W.qr_segs);
   o.ints = blob.add(W.ints);
   o.ws = blob.add(std::vector<int>(std::max<size_t>(o.ws_ints, 4), 0));
+  o.upload = blob.h.size();
+  if (o.stage_bytes) {
+    o.stage = (blob.h.size() + 255) & ~size_t(255);
+    blob.h.resize(o.stage + o.stage_bytes);
+  }
   return o;
 }
 
@@ -718,7 +819,10 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
 void patch_grid(const StageBlob& o, Blob& blob, char* D) {
   for (size_t L = 0; L < o.grid.size(); ++L) {
     RRQRGridTask* gt = (RRQRGridTask*)(blob.h.data() + o.grid[L].off);
-    for (int i = 0; i < o.grid[L].ntasks; ++i) gt[i].ws = (int*)(D + o.ws) + o.grid_ws[L][i];
+    for (int i = 0; i < o.grid[L].ntasks; ++i) {
+      gt[i].ws = (int*)(D + o.ws) + o.grid_ws[L][i];
+      gt[i].stage = o.grid[L].onchip ? (real_t*)(D + o.stage + o.grid_stage[L][i]) : nullptr;
+    }
   }
 }
 
@@ -801,8 +905,11 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
       for (const auto& gl : O.grid) {
         if (gl.group != gi) continue;
         run(KK_RRQR_GRID, (size_t)gl.ntasks, 0.0, 0.0, [&] {
-          const cudaError_t e = launch_rrqr_grid((const RRQRGridTask*)(D + gl.off), gl.ntasks,
-                                                 gl.nctas, (const RRQRSeg*)(D + O.seg), gl.smem, cs);
+          const cudaError_t e =
+              gl.onchip ? launch_rrqr_gsm((const RRQRGridTask*)(D + gl.off), gl.ntasks, gl.nctas,
+                                          (const RRQRSeg*)(D + O.seg), gl.smem, cs)
+                        : launch_rrqr_grid((const RRQRGridTask*)(D + gl.off), gl.ntasks, gl.nctas,
+                                           (const RRQRSeg*)(D + O.seg), gl.smem, cs);
           if (e != cudaSuccess && gerr == cudaSuccess) gerr = e;
         });
       }
@@ -1186,7 +1293,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       D = G.tables.p;
     }
     patch_grid(O, blob, D);
-    CK(cudaMemcpyAsync(D, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D, blob.h.data(), O.upload, cudaMemcpyHostToDevice, s));
     // launches go to the capture stream (recorded into the stage graph) or to s
     cudaStream_t cs = s;
     if (capture) {
@@ -1399,6 +1506,7 @@ int apply_multi(const ApSeg* segs, int nseg, real_t* z, MultiApply& M, Prof& P, 
   const ApItem* items = (const ApItem*)M.items.p;
   auto one = [&](const MultiApply::Launch& L, bool fwd, cudaStream_t cs) {
     const int kind = L.kind == PH_INTERIOR ? KK_AP_INTERIOR : L.kind == PH_SCALE ? KK_AP_SCALE : KK_AP_QE;
+    P.tag = (fwd ? 0 : 10000) + L.stage * 100 + L.K;
     P.run(kind, cs, L.flops, L.bytes, [&] {
       const ApItem* it = items + L.item0;
       if (L.kind == PH_INTERIOR)

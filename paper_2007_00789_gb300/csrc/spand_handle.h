@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -138,10 +139,12 @@ static const char* const kKindName[KK_COUNT] = {
 
 struct Prof {
   bool on = false;
+  int tag = -1;  // caller-set label of the next launches (e.g. the apply's stage), for the dump
   struct Pend {
     int kind;
     cudaEvent_t a, b;
     double flops, bytes;
+    int tag;
   };
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
@@ -168,7 +171,7 @@ struct Prof {
       launch();
       return;
     }
-    Pend p{kind, ev(), ev(), flops, bytes};
+    Pend p{kind, ev(), ev(), flops, bytes, tag};
     cudaEventRecord(p.a, s);
     launch();
     cudaEventRecord(p.b, s);
@@ -177,11 +180,19 @@ struct Prof {
   void add_flops(int kind, double flops) {
     if (on) stat[kind].flops += flops;
   }
-  // call after the stream has been synchronised
+  // call after the stream has been synchronised; SPAND_DEBUG_PROF=1 in the
+  // environment also prints every launch (kind, tag, ms, flops, bytes) to stderr
   void resolve() {
+    static const bool dump = [] {
+      const char* e = getenv("SPAND_DEBUG_PROF");
+      return e && e[0] == '1';
+    }();
     for (auto& p : pend) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, p.a, p.b);
+      if (dump)
+        fprintf(stderr, "spand launch: %s tag %d ms %.4f flops %.4g bytes %.4g\n", kKindName[p.kind],
+                p.tag, ms, p.flops, p.bytes);
       stat[p.kind].launches += 1;
       stat[p.kind].total_ms += ms;
       stat[p.kind].flops += p.flops;
@@ -403,7 +414,10 @@ struct spand_s {
   double pcg_ms = 0.0, pcg_relres = 0.0;
   int pcg_iters = 0;
   spand::Prof prof;
-  int rrqr_path = 0;  // 0: choose per interface; 1: always the global-memory kernel; 2: clusters <= 8
+  // 0: choose per interface; 1: always the global-memory kernel; 2: clusters <= 8;
+  // 3: always the streamed multi-CTA kernel; 4: always the on-chip multi-CTA kernel where it fits;
+  // 5: as 0 with the multi-CTA tasks streamed
+  int rrqr_path = 0;
   int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512); 0 = automatic
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
   spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)

@@ -671,6 +671,76 @@ __device__ __forceinline__ bool qr_grid_barrier(int* ctr, int* abort, int target
   return s_ok != 0;
 }
 
+// The merge of the G CTAs' candidates of a step (largest best, ties to the
+// lowest column; second = the largest of the others): thread k < G loads CTA
+// k's slot (all loads in flight at once), the warps reduce with shuffles and
+// thread 0 merges the warps.  Called by every thread of the CTA; the result
+// is returned to every thread.  red_*: shared scratch of kQrThreads / 32.
+__device__ __forceinline__ void grid_merge(const GridSlot* sl, int G, double* red_b, double* red_s,
+                                           int* red_i, double* out_best, double* out_sec,
+                                           int* out_idx) {
+  __shared__ double s_b, s_s;
+  __shared__ int s_i;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double b = -1.0, s2 = -1.0;
+  int ix = -1;
+  for (int k = tid; k < G; k += blockDim.x) {
+    const double kb = __ldcg(&sl[k].best);
+    const double ks = __ldcg(&sl[k].second);
+    const int ki = __ldcg(&sl[k].idx);
+    if (ki < 0) continue;
+    if (kb > b || (kb == b && (ix < 0 || ki < ix))) {
+      s2 = fmax(fmax(s2, ks), b);
+      b = kb;
+      ix = ki;
+    } else {
+      s2 = fmax(fmax(s2, ks), kb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+    const double os = __shfl_xor_sync(0xffffffffu, s2, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+    if (oi >= 0 && (ob > b || (ob == b && (ix < 0 || oi < ix)))) {
+      s2 = fmax(fmax(s2, os), b);
+      b = ob;
+      ix = oi;
+    } else {
+      s2 = fmax(fmax(s2, os), oi >= 0 ? ob : -1.0);
+    }
+  }
+  if (lane == 0) {
+    red_b[warp] = b;
+    red_s[warp] = s2;
+    red_i[warp] = ix;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double bb = -1.0, ss = -1.0;
+    int ii = -1;
+    for (int w = 0; w < nw; ++w) {
+      const double ob = red_b[w], os = red_s[w];
+      const int oi = red_i[w];
+      if (oi >= 0 && (ob > bb || (ob == bb && (ii < 0 || oi < ii)))) {
+        ss = fmax(fmax(ss, os), bb);
+        bb = ob;
+        ii = oi;
+      } else {
+        ss = fmax(fmax(ss, os), oi >= 0 ? ob : -1.0);
+      }
+    }
+    s_b = bb;
+    s_s = ss;
+    s_i = ii;
+  }
+  __syncthreads();
+  *out_best = s_b;
+  *out_sec = s_s;
+  *out_idx = s_i;
+  __syncthreads();  // the scratch and the result may be reused at once
+}
+
 __global__ void __launch_bounds__(kQrThreads)
     k_rrqr_grid(const RRQRGridTask* __restrict__ tasks, int ntasks, const RRQRSeg* __restrict__ segs) {
   extern __shared__ real_t sm[];
@@ -696,9 +766,19 @@ __global__ void __launch_bounds__(kQrThreads)
   const int nseg = t.seg_end - t.seg_begin;
   const int cpb_max = (t.ncols_max + G - 1) / G;
   real_t* v = sm;                                       // m
-  real_t* norms = v + m;                                // cpb_max
-  int* cols = reinterpret_cast<int*>(norms + cpb_max);  // cpb_max
-  int* segoff = cols + cpb_max;                         // nseg + 1
+  real_t* norms = v + m;                                // cpb_max: FP64 d (downdated), -1 once pivoted
+  real_t* errb = norms + cpb_max;                       // cpb_max: FP64 E (see k_rrqr_cluster)
+  real_t* cand = errb + cpb_max;                        // cpb_max: exact norms of the candidates
+  int* cols = reinterpret_cast<int*>(cand + cpb_max);   // cpb_max
+  int* memb = cols + cpb_max;                           // cpb_max
+  int* segoff = memb + cpb_max;                         // nseg + 1
+  // FP64 storage downdates the trailing norms (the scheme and its bounds are
+  // described at k_rrqr_cluster); FP32 storage recomputes them at every step
+  constexpr bool kDown = sizeof(real_t) == sizeof(double);
+  const double u64 = 1.1102230246251565e-16;
+  const double gam = 1.01 * (m + 2) * u64, cst = (8.0 * m + 64.0) * u64;
+  __shared__ double s_lbg[kQrThreads / kWarp];
+  __shared__ int s_nm;
   if (tid == 0) {
     int acc = 0;
     for (int s = 0; s < nseg; ++s) {
@@ -727,7 +807,11 @@ __global__ void __launch_bounds__(kQrThreads)
     real_t s = 0.0;
     for (int i = lane; i < m; i += kWarp) s += col[i] * col[i];
     s = warp_sum(s);
-    if (lane == 0) norms[l] = s;
+    if (lane == 0) {
+      norms[l] = s;
+      cand[l] = s;
+      errb[l] = gam * s;
+    }
   }
   __syncthreads();
   const double eps = t.eps;
@@ -745,7 +829,7 @@ __global__ void __launch_bounds__(kQrThreads)
     double bv = -1.0, sv = -1.0;
     int bi = -1;
     for (int l = tid; l < nloc; l += kQrThreads) {
-      const double x = (double)norms[l];
+      const double x = (double)cand[l];
       if (x < 0.0) continue;
       if (x > bv || (x == bv && g0 + l < bi)) {
         sv = fmax(sv, bv);
@@ -806,22 +890,10 @@ __global__ void __launch_bounds__(kQrThreads)
       for (int i = pend_step + tid; i < m; i += kQrThreads) pc[i] = (i == pend_step) ? (real_t)pend_beta : (real_t)0.0;
       pend_l = -1;
     }
-    // merge the CTAs' candidates (every thread, the same order everywhere)
+    // merge the CTAs' candidates
     double best = -1.0, sec = -1.0;
     int bidx = -1;
-    for (int k = 0; k < G; ++k) {
-      const double kb = __ldcg(&slots[(step & 1) * G + k].best);
-      const double ks = __ldcg(&slots[(step & 1) * G + k].second);
-      const int ki = __ldcg(&slots[(step & 1) * G + k].idx);
-      if (ki < 0) continue;
-      if (kb > best || (kb == best && (bidx < 0 || ki < bidx))) {
-        sec = fmax(fmax(sec, ks), best);
-        best = kb;
-        bidx = ki;
-      } else {
-        sec = fmax(fmax(sec, ks), kb);
-      }
-    }
+    grid_merge(slots + (step & 1) * G, G, s_red, s_sec, s_idx, &best, &sec, &bidx);
     if (bidx < 0) break;  // no candidate left (cannot happen for step < min(m, N))
     // the pivot column, in global memory (written by its owner before the barrier)
     int pseg = 0;
@@ -897,13 +969,16 @@ __global__ void __launch_bounds__(kQrThreads)
       if (tid == 0) {
         t.tau[step] = tau;
         norms[bidx - g0] = -1.0;
+        cand[bidx - g0] = -1.0;
       }
       pend_l = bidx - g0;
       pend_step = step;
       pend_beta = beta;
     }
+    if (tid == 0) s_nm = 0;
     __syncthreads();
-    // apply H_step to the other non-pivoted columns of this CTA; refresh their norms
+    // apply H_step to the other non-pivoted columns of this CTA; refresh their
+    // norms (FP32) or downdate them (FP64)
     for (int l = warp; l < nloc; l += nw) {
       if (norms[l] < 0.0) continue;
       real_t* col = t.A + (size_t)cols[l] * ld;
@@ -915,12 +990,65 @@ __global__ void __launch_bounds__(kQrThreads)
       for (int i = step + lane; i < m; i += kWarp) {
         const real_t a = col[i] - f * v[i];
         col[i] = a;
-        if (i > step) s += a * a;
+        if (!kDown && i > step) s += a * a;
       }
-      s = warp_sum(s);
-      if (lane == 0) norms[l] = s;
+      if constexpr (kDown) {
+        if (lane == 0) {  // lane 0 wrote the pivot-row entry itself
+          const double x = col[step];
+          const double dold = norms[l], eold = errb[l];
+          const double dn = fmax(fma(-x, x, dold), 0.0);
+          norms[l] = dn;
+          errb[l] = eold + cst * (dold + eold) + 1.01 * u64 * dn;
+          cand[l] = -1.0;
+        }
+      } else {
+        s = warp_sum(s);
+        if (lane == 0) {
+          norms[l] = s;
+          cand[l] = s;
+        }
+      }
     }
     __syncthreads();
+    if constexpr (kDown) {
+      // the columns whose exact norm may be the largest (or within 1e-12 of it)
+      // are recomputed exactly and become this CTA's candidates
+      double lbm = 0.0;
+      for (int l = tid; l < nloc; l += kQrThreads) {
+        const double dd = norms[l];
+        if (dd < 0.0) continue;
+        const double e = errb[l];
+        lbm = fmax(lbm, dd - (e + gam * (dd + e)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lbm = fmax(lbm, __shfl_xor_sync(0xffffffffu, lbm, o));
+      if (lane == 0) s_lbg[warp] = lbm;
+      __syncthreads();
+      double L = 0.0;
+      for (int w = 0; w < nw; ++w) L = fmax(L, s_lbg[w]);
+      const double Lthr = L * (1.0 - 4e-12);
+      for (int l = tid; l < nloc; l += kQrThreads) {
+        const double dd = norms[l];
+        if (dd < 0.0) continue;
+        const double e = errb[l];
+        if (dd + (e + gam * (dd + e)) >= Lthr) memb[atomicAdd(&s_nm, 1)] = l;
+      }
+      __syncthreads();
+      const int nm = s_nm;
+      for (int q = warp; q < nm; q += nw) {
+        const int l = memb[q];
+        const real_t* col = t.A + (size_t)cols[l] * ld;
+        real_t s2 = 0.0;
+        for (int i = step + 1 + lane; i < m; i += kWarp) s2 += col[i] * col[i];
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+          norms[l] = s2;
+          errb[l] = gam * s2;
+          cand[l] = s2;
+        }
+      }
+      __syncthreads();
+    }
     nsteps = step + 1;
   }
   // every CTA has read the last pivot column once all pass this barrier
@@ -1686,6 +1814,68 @@ __device__ __forceinline__ void qr_update_one(real_t* a, const real_t* v, int nc
   }
 }
 
+// Trailing norms by downdating.  Exact recomputation of every trailing column
+// norm at every step (the pivot rule) costs a third FMA per entry on the narrow
+// FP64 pipe.  Instead each live column carries d, its squared norm below the
+// pivot row downdated by the new pivot-row entry after each update
+// (||H x||^2 = ||x||^2 over the rows the reflector touches), and E, a bound on
+// |d - T| where T is the sum of squares of the column's stored entries:
+//   the initial sum of m squares:          E = gam d,  gam = 1.01 (m + 2) u;
+//   one reflector (rounding of v, tau, the dot product and the update, and
+//   the departure of the computed reflector from orthogonality, each a few m u
+//   relative to the column's squared norm before the step):
+//                                          E += cst (d_old + E),  cst = (8 m + 64) u;
+//   the downdate itself (one FMA):         E += 1.01 u |d|.
+// An exact recomputation of the sum of squares lies within gam T of T, so
+// |d - exact| <= B = E + gam (d + E).  Per step, L = the CTA's largest d - B
+// bounds the exact maximum from below; only the columns with d + B >= L (1 -
+// 4e-12) can hold the exact maximum or a value within 1e-12 of it, so only
+// they are recomputed exactly (and their d, E reset), and only they become
+// candidates.  The pivot chosen is therefore the one exact recomputation of
+// every norm would choose, with the same tie rule and the same near-tie flags.
+constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
+
+// One column's part of a step without the norm: the dot product and the
+// update of qr_update_one; the group's first thread (which holds the pivot row)
+// downdates d and grows E.
+__device__ __forceinline__ void qr_update_dd(real_t* a, const real_t* v, int ncl, int step, int m,
+                                             int sl, int tpc, unsigned gmask, real_t tau,
+                                             real_t* d, real_t* eb, double cst) {
+  real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+  int i = step + sl;
+#pragma unroll 2
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    d0 = fma(v[i], a[(size_t)i * ncl], d0);
+    d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
+    d2 = fma(v[i + 2 * tpc], a[(size_t)(i + 2 * tpc) * ncl], d2);
+    d3 = fma(v[i + 3 * tpc], a[(size_t)(i + 3 * tpc) * ncl], d3);
+  }
+  for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+  real_t dd = (d0 + d1) + (d2 + d3);
+  for (int o = tpc >> 1; o > 0; o >>= 1) dd += __shfl_xor_sync(gmask, dd, o);
+  const real_t f = tau * dd;
+  i = step + sl;
+  const size_t rs = (size_t)tpc * ncl;
+#pragma unroll 2
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    real_t* p0 = a + (size_t)i * ncl;
+    const real_t v0 = v[i], v1 = v[i + tpc], v2 = v[i + 2 * tpc], v3 = v[i + 3 * tpc];
+    const real_t a0 = p0[0], a1 = p0[rs], a2 = p0[2 * rs], a3 = p0[3 * rs];
+    p0[0] = fma(-f, v0, a0);
+    p0[rs] = fma(-f, v1, a1);
+    p0[2 * rs] = fma(-f, v2, a2);
+    p0[3 * rs] = fma(-f, v3, a3);
+  }
+  for (; i < m; i += tpc) a[(size_t)i * ncl] = fma(-f, v[i], a[(size_t)i * ncl]);
+  if (sl == 0) {
+    const real_t x = a[(size_t)step * ncl];  // written by this thread above
+    const real_t dold = *d, eold = *eb;
+    const real_t dn = fmax(fma(-x, x, dold), (real_t)0);  // T >= 0: clamping stays in the bound
+    *d = dn;
+    *eb = eold + cst * (dold + eold) + 1.01 * kU64 * dn;
+  }
+}
+
 // One thread per column (or a few, rows split among them): the dot product
 // v^T a, the update a -= tau (v^T a) v and the new trailing norm are FMA chains
 // in each thread; each thread also keeps the best candidate among its columns
@@ -1716,10 +1906,15 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   const int ncl = ((t.ncols_max + csize - 1) / csize) | 1;
   real_t* A = sm;                                      // m x ncl, row-major
   real_t* v = A + (size_t)m * ncl;                     // m
-  real_t* norms = v + m;                               // ncl
-  int* pcol = reinterpret_cast<int*>(norms + ncl);     // ncl: column in the panel row
+  real_t* norms = v + m;                               // ncl: d (downdated), -1 once pivoted
+  real_t* errb = norms + ncl;                          // ncl: E, the bound on d's error
+  int* pcol = reinterpret_cast<int*>(errb + ncl);      // ncl: column in the panel row
   int* segid = pcol + ncl;                             // ncl: segment of the column
-  int* segoff = segid + ncl;                           // nseg + 1
+  int* memb = segid + ncl;                             // ncl: columns recomputed this step
+  int* segoff = memb + ncl;                            // nseg + 1
+  __shared__ unsigned long long s_lb[kQrcMaxThreads / kWarp];
+  __shared__ int s_nmem;
+  const double gam = 1.01 * (m + 2) * kU64, cst = (8.0 * m + 64.0) * kU64;
   if (tid == 0) {
     int acc = 0;
     for (int g = 0; g < nseg; ++g) {
@@ -1768,6 +1963,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     for (int o = tpc >> 1; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o);
     if (sl == 0) {
       norms[l] = s2;
+      errb[l] = gam * s2;
       QrSlot c{QK::of(s2), kNoKey, m > 0 ? A[l] : (real_t)0, g0 + l};
       slot_merge(mine, c);
     }
@@ -1780,7 +1976,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   const int maxsteps = min(m, N);
   int r = -1, nsteps = 0, flags = 0;
   // thresholds, fixed once nu_0 is known: as doubles, as keys (value < T <=>
-  // key < K), and the near-threshold flag margins
+  // key < K), and the near-threshold flag margins (FP64 norms)
   double nu0sq = 0.0, T1 = 0.0, T2 = 0.0, F1 = 0.0, F2 = 0.0;
   qkey_t K1 = 0, K2 = 0;
   const qkey_t f1lo = 1, f1hi = 0, f2lo = 1, f2hi = 0;  // margins of FP32 keys: not used here
@@ -1877,13 +2073,60 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       pend_step = step;
       pend_beta = beta;
     }
+    if (tid == 0) s_nmem = 0;
     __syncthreads();
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
-      qr_update_one(A + l, v, ncl, step, m, sl, tpc, gmask, tau, g0 + l, norms + l, mine);
+      qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, tau, norms + l, errb + l, cst);
     }
     nsteps = step + 1;
+    __syncthreads();
+    // L: the largest lower bound d - B of the CTA's live columns
+    double lbm = 0.0;
+    for (int l = tid; l < nloc; l += nthr) {
+      const double d = norms[l];
+      if (d < 0.0) continue;
+      const double e = errb[l];
+      lbm = fmax(lbm, d - (e + gam * (d + e)));
+    }
+    const unsigned long long lbk = warp_max((unsigned long long)QK::of(lbm));
+    if (lane == 0) s_lb[warp] = lbk;
+    __syncthreads();
+    unsigned long long Lk = 0;
+    for (int w = 0; w < nw; ++w) Lk = max(Lk, s_lb[w]);
+    const double Lthr = QK::val((qkey_t)Lk) * (1.0 - 4e-12);
+    // the columns that may hold the exact maximum (or a value within 1e-12 of it)
+    for (int l = tid; l < nloc; l += nthr) {
+      const double d = norms[l];
+      if (d < 0.0) continue;
+      const double e = errb[l];
+      if (d + (e + gam * (d + e)) >= Lthr) memb[atomicAdd(&s_nmem, 1)] = l;
+    }
+    __syncthreads();
+    // their norms recomputed exactly, one warp per column; they are the candidates
+    const int nm = s_nmem;
+    for (int q = warp; q < nm; q += nw) {
+      const int l = memb[q];
+      real_t s0 = 0, s1 = 0;
+      int i = step + 1 + lane;
+      for (; i + kWarp < m; i += 2 * kWarp) {
+        const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
+        s0 = fma(x0, x0, s0);
+        s1 = fma(x1, x1, s1);
+      }
+      if (i < m) {
+        const real_t x0 = A[(size_t)i * ncl + l];
+        s0 = fma(x0, x0, s0);
+      }
+      const real_t s2 = warp_sum(s0 + s1);
+      if (lane == 0) {
+        norms[l] = s2;
+        errb[l] = gam * s2;
+        QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? A[(size_t)(step + 1) * ncl + l] : (real_t)0, g0 + l};
+        slot_merge(mine, c);
+      }
+    }
   }
   if (r < 0) r = nsteps;
   if (tid == 0 && flags) atomicOr(cluster.map_shared_rank(&s_flags, 0), flags);
@@ -1918,6 +2161,395 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 #endif
+
+// ---------------------------------------------------------------------------
+// The multi-CTA QR with the block on chip: for interface blocks too large for
+// the shared memory of one thread-block cluster but small enough for that of
+// several SMs.  One cooperative launch; CTA k of a task keeps a contiguous
+// slice of the block's columns in its shared memory for the whole
+// factorization (row-major, as the FP64 cluster kernel).  Per step each CTA
+// publishes its best candidate (exact squared norm, second best, column) and
+// a copy of that column's rows from the pivot row down into a staging area in
+// global memory (double-buffered by step parity), one bounded barrier, then
+// every CTA merges the candidates, reads the winner's staged column (from L2)
+// and forms v and the reflector scalars itself; the owner records v and tau and
+// writes the R entries into its own slice at once (the others use the staged
+// copy).  Pivot rule, ties, flags and thresholds are those of the other RRQR
+// kernels; FP64 storage downdates the trailing norms (see k_rrqr_cluster),
+// FP32 recomputes them.  A barrier wait that runs out raises the task's abort
+// flag and the problem's error word, and every CTA of the task leaves.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int gsm_ncl(int cpb) { return cpb | 1; }
+
+__global__ void __launch_bounds__(kQrThreads)
+    k_rrqr_gsm(const RRQRGridTask* __restrict__ tasks, int ntasks, const RRQRSeg* __restrict__ segs) {
+  extern __shared__ real_t sm[];
+  constexpr int nw = kQrThreads / kWarp;
+  __shared__ double s_bv[nw], s_sv[nw], s_lbg[nw];
+  __shared__ int s_bi[nw];
+  __shared__ double s_best, s_sec, s_nu64;
+  __shared__ int s_ix, s_nm, s_N;
+  __shared__ real_t s_refl[3];
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].cta0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const RRQRGridTask gt = tasks[lo];
+  const RRQRTask& t = gt.t;
+  const int crank = (int)blockIdx.x - gt.cta0, G = gt.ncta;
+  int* ctr = gt.ws;
+  int* abort = gt.ws + 1;
+  GridSlot* slots = reinterpret_cast<GridSlot*>(gt.ws + 4);  // [2][G]
+  real_t* stg = gt.stage;                                    // [2][G][m]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = t.m;
+  const size_t ld = t.ld;
+  const int nseg = t.seg_end - t.seg_begin;
+  const int ncl = gsm_ncl((t.ncols_max + G - 1) / G);  // the slice's row length
+  real_t* A = sm;                                     // m x ncl, row-major
+  real_t* v = A + (size_t)m * ncl;                    // m
+  real_t* norms = v + m;                              // ncl: d (FP64) or the norm (FP32); -1 once pivoted
+  real_t* errb = norms + ncl;                         // ncl: FP64 E
+  real_t* cand = errb + ncl;                          // ncl: exact norms of the candidates, else -1
+  int* pcol = reinterpret_cast<int*>(cand + ncl);     // ncl
+  int* segid = pcol + ncl;                            // ncl
+  int* memb = segid + ncl;                            // ncl
+  int* segoff = memb + ncl;                           // nseg + 1
+  constexpr bool kDown = sizeof(real_t) == sizeof(double);
+  const double u64 = 1.1102230246251565e-16;
+  const double gam = 1.01 * (m + 2) * u64, cst = (8.0 * m + 64.0) * u64;
+  if (tid == 0) {
+    int acc = 0;
+    for (int g = 0; g < nseg; ++g) {
+      segoff[g] = acc;
+      acc += t.cur[segs[t.seg_begin + g].cl];
+    }
+    segoff[nseg] = acc;
+    s_N = acc;
+  }
+  __syncthreads();
+  const int N = s_N;
+  const int cpb = (N + G - 1) / G;
+  const int g0 = crank * cpb, nloc = max(0, min(N, g0 + cpb) - g0);
+  int tpc = 1;
+  while (tpc < 32 && nloc * tpc * 2 <= kQrThreads) tpc *= 2;
+  const int ngrp = kQrThreads / tpc, grp = tid / tpc, sl = tid % tpc;
+  const unsigned gmask = (tpc == 32) ? 0xffffffffu : (((1u << tpc) - 1u) << (lane & ~(tpc - 1)));
+  for (int l = tid; l < nloc; l += kQrThreads) {
+    const int g = g0 + l;
+    int a = 0, b = nseg - 1;  // last segment with segoff <= g
+    while (a < b) {
+      const int mid = (a + b + 1) >> 1;
+      if (segoff[mid] <= g) a = mid;
+      else b = mid - 1;
+    }
+    segid[l] = a;
+    pcol[l] = segs[t.seg_begin + a].col + (g - segoff[a]);
+  }
+  __syncthreads();
+  for (int e = tid; e < m * nloc; e += kQrThreads) {
+    const int i = e % m, l = e / m;
+    A[(size_t)i * ncl + l] = t.A[i + (size_t)pcol[l] * ld];
+  }
+  __syncthreads();
+  for (int l = warp; l < nloc; l += nw) {
+    real_t s0 = 0, s1 = 0;
+    int i = lane;
+    for (; i + kWarp < m; i += 2 * kWarp) {
+      const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
+      s0 = fma(x0, x0, s0);
+      s1 = fma(x1, x1, s1);
+    }
+    if (i < m) s0 = fma(A[(size_t)i * ncl + l], A[(size_t)i * ncl + l], s0);
+    const real_t s2 = warp_sum(s0 + s1);
+    if (lane == 0) {
+      norms[l] = s2;
+      cand[l] = s2;
+      errb[l] = gam * s2;
+    }
+  }
+  __syncthreads();
+  const double eps = t.eps;
+  const int scheme = t.scheme;
+  const bool superfine = scheme == SPAND_SECOND_ORDER_SUPERFINE;
+  const double thr1 = eps * eps;
+  const double thr2 = thr1 * thr1;
+  const int maxsteps = min(m, N);
+  int r = -1, nsteps = 0, flags = 0, nbar = 0;
+  bool ok = true;
+  double nu0sq = 0.0;
+  for (int step = 0; step < maxsteps; ++step) {
+    // the CTA's best candidate (ties to the lowest column) and second best
+    double bv = -1.0, sv = -1.0;
+    int bi = -1;
+    for (int l = tid; l < nloc; l += kQrThreads) {
+      const double x = (double)cand[l];
+      if (x < 0.0) continue;
+      if (x > bv || (x == bv && g0 + l < bi)) {
+        sv = fmax(sv, bv);
+        bv = x;
+        bi = g0 + l;
+      } else {
+        sv = fmax(sv, x);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const double os = __shfl_xor_sync(0xffffffffu, sv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+        sv = fmax(fmax(sv, os), bv);
+        bv = ov;
+        bi = oi;
+      } else {
+        sv = fmax(fmax(sv, os), ov);
+      }
+    }
+    if (lane == 0) {
+      s_bv[warp] = bv;
+      s_sv[warp] = sv;
+      s_bi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = s_bv[0], s2 = s_sv[0];
+      int ix = s_bi[0];
+      for (int w = 1; w < nw; ++w) {
+        const double ov = s_bv[w];
+        const int oi = s_bi[w];
+        if (ov > b || (ov == b && oi >= 0 && (ix < 0 || oi < ix))) {
+          s2 = fmax(fmax(s2, s_sv[w]), b);
+          b = ov;
+          ix = oi;
+        } else {
+          s2 = fmax(fmax(s2, s_sv[w]), ov);
+        }
+      }
+      s_best = b;
+      s_sec = s2;
+      s_ix = ix;
+    }
+    __syncthreads();
+    // publish the candidate and a copy of its column (rows step .. m-1)
+    const int par = step & 1;
+    {
+      const int ix = s_ix;
+      real_t* dst = stg + ((size_t)par * G + crank) * m;
+      if (ix >= 0)
+        for (int i = step + tid; i < m; i += kQrThreads) dst[i] = A[(size_t)i * ncl + (ix - g0)];
+      if (tid == 0) {
+        GridSlot gs;
+        gs.best = s_best;
+        gs.second = s_sec;
+        gs.idx = ix;
+        gs.pad = 0;
+        slots[par * G + crank] = gs;
+      }
+    }
+    ++nbar;
+    if (!qr_grid_barrier(ctr, abort, nbar * G + (nbar == 1 ? t.wait_extra : 0), t.wait_limit)) {
+      ok = false;
+      break;
+    }
+    // merge the CTAs' candidates
+    double best = -1.0, sec = -1.0;
+    int bidx = -1;
+    grid_merge(slots + par * G, G, s_bv, s_sv, s_bi, &best, &sec, &bidx);
+    if (bidx < 0) break;  // no candidate left (cannot happen for step < min(m, N))
+    const int owner = bidx / cpb;
+    const real_t* pcs = stg + ((size_t)par * G + owner) * m;  // the pivot column, rows step..
+    double nusq = best;
+    if (sizeof(real_t) < sizeof(double)) {
+      // FP32 storage: nu_0 and near-threshold decisions use the FP64 norm
+      const bool nearthr = step == 0 || fabs(nusq - thr1 * nu0sq) <= 1e-4 * thr1 * nu0sq ||
+                           (superfine && fabs(nusq - thr2 * nu0sq) <= 1e-4 * thr2 * nu0sq);
+      if (nearthr) {
+        if (warp == 0) {
+          double s64 = 0.0;
+          for (int i = step + lane; i < m; i += kWarp) {
+            const double a = (double)__ldcg(pcs + i);
+            s64 = fma(a, a, s64);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          if (lane == 0) s_nu64 = s64;
+        }
+        __syncthreads();
+        nusq = s_nu64;
+        __syncthreads();
+      }
+    }
+    if (sec >= 0.0 && nusq > 0.0 && nusq - sec <= 1e-12 * nusq) flags |= 1;
+    if (step == 0) {
+      nu0sq = nusq;
+      if (nu0sq == 0.0) {
+        r = 0;
+        break;
+      }
+    }
+    if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
+    if (superfine && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq) flags |= 2;
+    if (r < 0 && nusq < thr1 * nu0sq) {
+      r = step;
+      if (!superfine) break;
+    }
+    if (superfine && nusq < thr2 * nu0sq) break;
+    // warp 0 forms the reflector scalars while the other warps read the pivot
+    // column (a long dependent FP64 sequence against an L2 read)
+    if (warp == 0) {
+      reflector_scalars(__ldcg(pcs + step), (real_t)nusq, lane, s_refl);
+    } else {
+      for (int i = step + 1 + tid - kWarp; i < m; i += kQrThreads - kWarp) v[i] = __ldcg(pcs + i);
+    }
+    __syncthreads();
+    const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
+    const bool own = crank == owner;
+    const int lp = bidx - g0;
+    for (int i = tid; i < m; i += kQrThreads) {
+      real_t vi;
+      if (i < step) vi = 0;
+      else if (i == step) vi = 1;
+      else vi = v[i] * inv;
+      v[i] = vi;
+      if (own) {
+        t.V[i + (size_t)step * m] = vi;
+        if (i >= step) A[(size_t)i * ncl + lp] = (i == step) ? beta : (real_t)0;  // R entries
+      }
+    }
+    if (own && tid == 0) {
+      t.tau[step] = tau;
+      norms[lp] = -1;
+      cand[lp] = -1;
+    }
+    if (tid == 0) s_nm = 0;
+    __syncthreads();
+    // apply H_step to the CTA's other live columns
+    for (int l = grp; l < nloc; l += ngrp) {
+      if (norms[l] < (real_t)0) continue;  // the same l for the whole group
+      real_t* a = A + l;
+      real_t d0 = 0, d1 = 0;
+      int i = step + sl;
+      for (; i + tpc < m; i += 2 * tpc) {
+        d0 = fma(v[i], a[(size_t)i * ncl], d0);
+        d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
+      }
+      if (i < m) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+      real_t dd = d0 + d1;
+      for (int o = tpc >> 1; o > 0; o >>= 1) dd += __shfl_xor_sync(gmask, dd, o);
+      const real_t f = tau * dd;
+      real_t q0 = 0, q1 = 0;
+      i = step + sl;
+      for (; i + tpc < m; i += 2 * tpc) {
+        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
+        const real_t x1 = fma(-f, v[i + tpc], a[(size_t)(i + tpc) * ncl]);
+        a[(size_t)i * ncl] = x0;
+        a[(size_t)(i + tpc) * ncl] = x1;
+        if (!kDown) {
+          if (i > step) q0 = fma(x0, x0, q0);
+          q1 = fma(x1, x1, q1);
+        }
+      }
+      if (i < m) {
+        const real_t x0 = fma(-f, v[i], a[(size_t)i * ncl]);
+        a[(size_t)i * ncl] = x0;
+        if (!kDown && i > step) q0 = fma(x0, x0, q0);
+      }
+      if constexpr (kDown) {
+        if (sl == 0) {  // this thread wrote the pivot-row entry
+          const double x = a[(size_t)step * ncl];
+          const double dold = norms[l], eold = errb[l];
+          const double dn = fmax(fma(-x, x, dold), 0.0);
+          norms[l] = dn;
+          errb[l] = eold + cst * (dold + eold) + 1.01 * u64 * dn;
+          cand[l] = -1;
+        }
+      } else {
+        real_t q = q0 + q1;
+        for (int o = tpc >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(gmask, q, o);
+        if (sl == 0) {
+          norms[l] = q;
+          cand[l] = q;
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (kDown) {
+      double lbm = 0.0;
+      for (int l = tid; l < nloc; l += kQrThreads) {
+        const double dd = norms[l];
+        if (dd < 0.0) continue;
+        const double e = errb[l];
+        lbm = fmax(lbm, dd - (e + gam * (dd + e)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lbm = fmax(lbm, __shfl_xor_sync(0xffffffffu, lbm, o));
+      if (lane == 0) s_lbg[warp] = lbm;
+      __syncthreads();
+      double L = 0.0;
+      for (int w = 0; w < nw; ++w) L = fmax(L, s_lbg[w]);
+      const double Lthr = L * (1.0 - 4e-12);
+      for (int l = tid; l < nloc; l += kQrThreads) {
+        const double dd = norms[l];
+        if (dd < 0.0) continue;
+        const double e = errb[l];
+        if (dd + (e + gam * (dd + e)) >= Lthr) memb[atomicAdd(&s_nm, 1)] = l;
+      }
+      __syncthreads();
+      const int nm = s_nm;
+      for (int q = warp; q < nm; q += nw) {
+        const int l = memb[q];
+        real_t s0 = 0, s1 = 0;
+        int i = step + 1 + lane;
+        for (; i + kWarp < m; i += 2 * kWarp) {
+          const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
+          s0 = fma(x0, x0, s0);
+          s1 = fma(x1, x1, s1);
+        }
+        if (i < m) s0 = fma(A[(size_t)i * ncl + l], A[(size_t)i * ncl + l], s0);
+        const real_t s2 = warp_sum(s0 + s1);
+        if (lane == 0) {
+          norms[l] = s2;
+          errb[l] = gam * s2;
+          cand[l] = s2;
+        }
+      }
+      __syncthreads();
+    }
+    nsteps = step + 1;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(t.err + 1, 1);
+    return;
+  }
+  if (r < 0) r = nsteps;
+  __syncthreads();
+  // write the slice back, mirror the coarse rows into the neighbours' rows
+  for (int e = tid; e < m * nloc; e += kQrThreads) {
+    const int i = e % m, l = e / m;
+    t.A[i + (size_t)pcol[l] * ld] = A[(size_t)i * ncl + l];
+  }
+  for (int e = tid; e < r * nloc; e += kQrThreads) {
+    const int i = e % r, l = e / r;
+    const RRQRSeg g = segs[t.seg_begin + segid[l]];
+    const int c = g0 + l - segoff[segid[l]];
+    g.mirror[c + (size_t)i * g.mirror_ld] = A[(size_t)i * ncl + l];
+  }
+  if (crank == 0) {
+    for (int e = tid; e < r * r; e += kQrThreads) {
+      const int i = e % r, j = e / r;
+      t.diag[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid == 0) {
+      t.rank[t.id] = r;
+      t.nref[t.id] = nsteps;
+      t.flag[t.id] = flags;
+      t.cur[t.id] = r;
+    }
+  }
+}
 
 }  // namespace
 
@@ -1994,7 +2626,7 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
   const long b = 16 + e * ldm * (ncl + 1) + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
 #else
   const long ncl = ((ncols_max + csize - 1) / csize) | 1;
-  const long b = e * m * ncl + e * m + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
+  const long b = e * m * ncl + e * m + 2 * e * ncl + 12L * ncl + 4L * (nseg + 2) + 16;
 #endif
   return (int)std::min<long>(b, 1L << 30);
 }
@@ -2061,9 +2693,33 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs,
 }
 
 int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs) {
-  // v (real_t) + norms (real_t) + cols (int) + segoff (int)
-  return max_m * (int)sizeof(real_t) + max_cpb * (int)sizeof(real_t) + max_cpb * 4 +
+  // v (real_t) + norms, bounds, candidates (real_t) + cols, members (int) + segoff (int)
+  return max_m * (int)sizeof(real_t) + 3 * max_cpb * (int)sizeof(real_t) + 2 * max_cpb * 4 +
          (max_segs + 2) * 4 + 16;
+}
+
+int rrqr_gsm_smem_bytes(int m, int cpb, int nseg) {
+  const long ncl = gsm_ncl(cpb), e = (long)sizeof(real_t);
+  const long b = e * m * ncl + e * m + 3 * e * ncl + 12L * ncl + 4L * (nseg + 2) + 16;
+  return (int)std::min<long>(b, 1L << 30);
+}
+
+cudaError_t launch_rrqr_gsm(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
+                            int smem_bytes, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  const cudaError_t e = grant_smem((const void*)k_rrqr_gsm, smem_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nctas);
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident, or the launch fails
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_rrqr_gsm, t, ntasks, segs);
 }
 
 cudaError_t launch_rrqr_grid(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,

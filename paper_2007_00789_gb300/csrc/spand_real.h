@@ -120,6 +120,7 @@ struct RRQRTask {
 struct RRQRGridTask {
   RRQRTask t;
   int* ws;
+  real_t* stage;  // on-chip variant: [2][ncta][m] staged candidate columns
   int cta0, ncta;
 };
 inline size_t qr_grid_ws_ints(int ncta) { return 4 + 2 * (size_t)ncta * 6; }
@@ -186,6 +187,12 @@ void launch_rrqr(const RRQRTask* t, int ntasks, const RRQRSeg* segs, int max_m, 
 int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs);
 cudaError_t launch_rrqr_grid(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
                              int smem_bytes, cudaStream_t s);
+// The same with every CTA's slice of columns in its shared memory (at most one
+// CTA per SM); rrqr_gsm_smem_bytes: the dynamic shared memory of a CTA holding
+// cpb columns of m rows.
+int rrqr_gsm_smem_bytes(int m, int cpb, int nseg);
+cudaError_t launch_rrqr_gsm(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
+                            int smem_bytes, cudaStream_t s);
 
 // K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
 // over all nitems items (device array); max_nvec: the most vectors of an item.

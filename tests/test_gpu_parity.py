@@ -93,10 +93,26 @@ CASES = [
 
 @pytest.mark.parametrize("name,make,ell,eps,scheme,skip,ties", CASES, ids=[c[0] for c in CASES])
 def test_parity_with_oracle(name, make, ell, eps, scheme, skip, ties):
-    prob = make()
+    _check_parity(make(), ell, eps, scheme, skip, ties, rrqr_kernel=0)
+
+
+# every interface through the multi-CTA QR that keeps the block in the shared
+# memory of several CTAs (the kernel of the widest 128^3 interfaces)
+ONCHIP_CASES = [c for c in CASES if c[0] in ("poisson2d_64_so", "diff3d_16_sf",
+                                             "diff3d_16_fo_eps1e-1", "diff_ragged_so",
+                                             "diff3d_32_so")]
+
+
+@pytest.mark.parametrize("name,make,ell,eps,scheme,skip,ties", ONCHIP_CASES,
+                         ids=[c[0] for c in ONCHIP_CASES])
+def test_on_chip_multi_cta_rrqr_parity(name, make, ell, eps, scheme, skip, ties):
+    _check_parity(make(), ell, eps, scheme, skip, ties, rrqr_kernel=4)
+
+
+def _check_parity(prob, ell, eps, scheme, skip, ties, rrqr_kernel):
     A = prob.to_scipy()
     F = OS.factor(A, prob.coords, ell, eps, scheme, skip=skip)
-    h = _gpu_handle(prob, ell, eps, scheme, skip)
+    h = _gpu_handle(prob, ell, eps, scheme, skip, rrqr_kernel=rrqr_kernel)
     want = _oracle_ranks(F)
     got = h.ranks()
     assert got.shape == want.shape
@@ -118,9 +134,23 @@ def test_parity_with_oracle(name, make, ell, eps, scheme, skip, ties):
             assert err <= TOL_APPLY, err
         assert h.info()["nnz_factor"] == F.nnz_factor()
     else:
+        # exact pivot ties (mirror-symmetric grids): either side's choice is a
+        # correct QR, so the two preconditioners must be equally good: the
+        # spectral radius of I - M A within 1 % and the same CG count to 1e-12
+        torch = _torch()
+        r = rng.standard_normal(prob.n)
+        err = np.abs(_gpu_apply(h, r) - OS.apply(F, r)).max() / np.abs(OS.apply(F, r)).max()
         rho_o = _rho(lambda v: OS.apply(F, v), A, prob.n)
         rho_g = _rho(lambda v: _gpu_apply(h, v), A, prob.n)
-        assert abs(rho_g - rho_o) <= 0.1 * rho_o, (rho_g, rho_o)
+        b = si.rhs_normal(prob.n, seed=5)
+        res = OS.pcg(lambda v: A @ v, lambda v: OS.apply(F, v), b, 1e-12)
+        bd = torch.from_numpy(b).cuda()
+        xd = torch.zeros_like(bd)
+        it, rel = h.pcg(bd, xd, 1e-12)
+        print(f"tied: M r err {err:.2e}, rho gpu {rho_g:.6f} oracle {rho_o:.6f}, "
+              f"CG {it} oracle {res.iters}")
+        assert abs(rho_g - rho_o) <= 0.01 * rho_o, (rho_g, rho_o)
+        assert it == res.iters and rel <= 1e-12
     h.close()
 
 
@@ -185,26 +215,29 @@ def test_streamed_and_on_chip_rrqr_agree(d, ell, scheme):
     b.close()
 
 
-@pytest.mark.parametrize("make,ell,scheme,precision", [
-    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 0),
-    (lambda: si.laplacian_2d(64), 6, 2, 0),
-    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 1, 1),
+@pytest.mark.parametrize("make,ell,scheme,precision,kernel", [
+    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 0, 3),
+    (lambda: si.laplacian_2d(64), 6, 2, 0, 3),
+    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 1, 1, 3),
+    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 0, 4),
+    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 1, 1, 4),
+    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 2, 1, 4),
 ])
-def test_multi_cta_rrqr_equals_streamed(make, ell, scheme, precision):
-    """The multi-CTA QR (columns spread over several CTAs of a cooperative
-    launch) processes every column as the single-CTA streamed kernel does:
-    ranks, reflector counts and near-tie flags identical, M r equal up to the
-    apply's atomic accumulation order."""
+def test_multi_cta_rrqr_equals_streamed(make, ell, scheme, precision, kernel):
+    """The multi-CTA QR kernels (columns spread over several CTAs of a
+    cooperative launch, streamed from global memory (3) or kept in shared
+    memory (4)) follow the single-CTA streamed kernel's rules: ranks, reflector
+    counts and near-tie flags identical, M r equal up to rounding order."""
     from paper_2007_00789_gb300 import spand as S
     prob = make()
     a = S.Spand.from_problem(prob, ell, 1e-2, scheme, rrqr_kernel=1, precision=precision)
-    b = S.Spand.from_problem(prob, ell, 1e-2, scheme, rrqr_kernel=3, precision=precision)
+    b = S.Spand.from_problem(prob, ell, 1e-2, scheme, rrqr_kernel=kernel, precision=precision)
     a.factor()
     b.factor()
     assert np.array_equal(a.ranks(), b.ranks())
     r = np.random.default_rng(4).standard_normal(prob.n)
     za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
-    assert np.abs(za - zb).max() <= (1e-13 if precision == 0 else 1e-6) * np.abs(za).max()
+    assert np.abs(za - zb).max() <= (1e-12 if precision == 0 else 1e-5) * np.abs(za).max()
     b.factor()  # replayed from the stage graphs (the workspace is reset by the graph)
     assert np.array_equal(a.ranks(), b.ranks())
     a.close()
