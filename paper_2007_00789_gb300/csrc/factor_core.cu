@@ -1155,10 +1155,202 @@ uint64_t next_layout_id() {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// The refactorization chain.  Check-table layout per stage (ints): for every
+// problem of the stage: counter offset, cluster count, offset of its expected
+// ranks and reflector counts (2 ncl ints) in the chain buffer, offset of its
+// flags there.  Status block (4 ints): kind (0 ok, 1 ranks differ, 2
+// non-positive Cholesky pivot, 3 a multi-CTA RRQR timed out), stage, problem
+// (index in the stage's list), cluster.
+// ---------------------------------------------------------------------------
+__global__ void k_stage_check(const int* __restrict__ cnt, const int* __restrict__ tab, int nprob,
+                              int* __restrict__ buf, int stage, cudaGraphConditionalHandle next,
+                              int has_next) {
+  __shared__ int s_bad;
+  int* status = buf;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const bool live = *(volatile int*)status == 0;  // an earlier stage failed: compare nothing
+  if (live) {
+    for (int j = 0; j < nprob; ++j) {
+      const int ioff = tab[4 * j], ncl = tab[4 * j + 1], eo = tab[4 * j + 2], fo = tab[4 * j + 3];
+      const int* c = cnt + ioff;
+      for (int i = threadIdx.x; i < 2 * ncl; i += blockDim.x)
+        if (c[ncl + i] != buf[eo + i]) s_bad = 1;
+      for (int i = threadIdx.x; i < ncl; i += blockDim.x) buf[fo + i] = c[3 * ncl + i];
+      if (threadIdx.x == 0 && status[0] == 0) {
+        if (c[4 * ncl + 1] != 0) {
+          status[0] = 3;
+          status[1] = stage;
+          status[2] = j;
+        } else if (c[4 * ncl] != 0) {
+          status[0] = 2;
+          status[1] = stage;
+          status[2] = j;
+          status[3] = c[4 * ncl] - 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (live && s_bad && status[0] == 0) {
+      status[0] = 1;
+      status[1] = stage;
+    }
+    if (has_next) cudaGraphSetConditional(next, status[0] == 0 ? 1u : 0u);
+  }
+}
+
+int build_chain(FactorGroup& G, cudaStream_t s) {
+  const size_t ns = G.sg.size();
+  // host image of the chain buffer: status, tables, expected ranks, flags
+  std::vector<int> img(4, 0);
+  std::vector<size_t> toff(ns);
+  std::vector<int> nprob(ns);
+  G.chain_foff.assign(ns, {});
+  std::vector<std::vector<size_t>> eoff(ns);
+  for (size_t k = 0; k < ns; ++k) {
+    const auto& g = G.sg[k];
+    nprob[k] = (int)g.who.size();
+    toff[k] = img.size();
+    img.resize(img.size() + 4 * g.who.size(), 0);
+  }
+  for (size_t k = 0; k < ns; ++k) {
+    const auto& g = G.sg[k];
+    size_t e = 0;
+    for (size_t j = 0; j < g.who.size(); ++j) {
+      const int ncl = g.ncl[j];
+      eoff[k].push_back(img.size());
+      img.insert(img.end(), g.expect.begin() + e, g.expect.begin() + e + 2 * (size_t)ncl);
+      e += 2 * (size_t)ncl;
+    }
+  }
+  G.chain_flags = img.size();
+  for (size_t k = 0; k < ns; ++k) {
+    const auto& g = G.sg[k];
+    for (size_t j = 0; j < g.who.size(); ++j) {
+      G.chain_foff[k].push_back(img.size());
+      img.resize(img.size() + g.ncl[j], 0);
+    }
+  }
+  for (size_t k = 0; k < ns; ++k)
+    for (size_t j = 0; j < G.sg[k].who.size(); ++j) {
+      int* t = img.data() + toff[k] + 4 * j;
+      t[0] = (int)G.sg[k].ioff[j];
+      t[1] = G.sg[k].ncl[j];
+      t[2] = (int)eoff[k][j];
+      t[3] = (int)G.chain_foff[k][j];
+    }
+  G.chain_ints = img.size();
+  RET(G.chain_buf.ensure(img.size() * sizeof(int)));
+  int* D = (int*)G.chain_buf.p;
+  CK(cudaMemcpyAsync(D, img.data(), img.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+
+  cudaGraph_t chain = nullptr;
+  CK(cudaGraphCreate(&chain, 0));
+  auto fail_out = [&](cudaError_t e) {
+    cudaGraphDestroy(chain);
+    return fail(SPAND_ECUDA, std::string("building the refactorization chain: ") + cudaGetErrorString(e));
+  };
+  cudaGraphNode_t prev = nullptr;
+  {
+    cudaMemsetParams mp = {};
+    mp.dst = D;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 4;
+    mp.height = 1;
+    const cudaError_t e = cudaGraphAddMemsetNode(&prev, chain, nullptr, 0, &mp);
+    if (e != cudaSuccess) return fail_out(e);
+  }
+  cudaGraphConditionalHandle next = 0;
+  for (size_t k = 0; k < ns; ++k) {
+    const auto& g = G.sg[k];
+    cudaGraph_t body = chain;
+    if (k > 0) {  // enabled by the previous stage's check
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = next;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cn = nullptr;
+      const cudaError_t e = cudaGraphAddNode(&cn, chain, &prev, nullptr, 1, &cp);
+      if (e != cudaSuccess) return fail_out(e);
+      body = cp.conditional.phGraph_out[0];
+      prev = cn;
+    }
+    if (g.graph) {
+      cudaGraphNode_t child = nullptr;
+      const cudaError_t e = cudaGraphAddChildGraphNode(&child, body, k > 0 ? nullptr : &prev,
+                                                       k > 0 ? 0 : 1, g.graph);
+      if (e != cudaSuccess) return fail_out(e);
+      if (k == 0) prev = child;
+    }
+    if (k + 1 < ns) {
+      cudaError_t e = cudaGraphConditionalHandleCreate(&next, chain, 0, cudaGraphCondAssignDefault);
+      if (e != cudaSuccess) return fail_out(e);
+      const int* cnt = (const int*)G.ints.p;
+      const int* tab = D + toff[k];
+      int np = nprob[k];
+      int* buf = D;
+      int stage = (int)k;
+      int has_next = 1;
+      void* args[] = {(void*)&cnt, (void*)&tab, (void*)&np, (void*)&buf, (void*)&stage, (void*)&next,
+                      (void*)&has_next};
+      cudaKernelNodeParams kp = {};
+      kp.func = (void*)k_stage_check;
+      kp.gridDim = dim3(1);
+      kp.blockDim = dim3(256);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = args;
+      cudaGraphNode_t kn = nullptr;
+      e = cudaGraphAddKernelNode(&kn, chain, &prev, 1, &kp);
+      if (e != cudaSuccess) return fail_out(e);
+      prev = kn;
+    }
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&G.chain, chain, 0);
+  cudaGraphDestroy(chain);
+  if (ie != cudaSuccess) {
+    G.chain = nullptr;
+    return fail(SPAND_ECUDA, std::string("instantiating the refactorization chain: ") + cudaGetErrorString(ie));
+  }
+  return SPAND_OK;
+}
+
+// One launch of the chain, one readback of its status and flags.
+int chain_replay(spand_s* const* hs, FactorGroup& G, cudaStream_t s) {
+  CK(cudaGraphLaunch(G.chain, s));
+  RET(ensure_pinned(G, G.chain_ints));
+  int* hp = G.h_ints;
+  CK(cudaMemcpyAsync(hp, G.chain_buf.p, G.chain_ints * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int kind = hp[0], stage = hp[1];
+  if (kind == 1) return 1;  // other ranks: the caller rebuilds
+  if (kind == 3)
+    return fail(SPAND_ETIMEOUT, "a multi-CTA RRQR timed out waiting for its CTAs (stage " +
+                                    std::to_string(stage) + ")");
+  if (kind == 2)
+    return fail(SPAND_ENOTSPD, "non-positive Cholesky pivot in problem " +
+                                   std::to_string(G.sg[stage].who[hp[2]]) + " at stage " +
+                                   std::to_string(stage) + ", cluster " + std::to_string(hp[3]));
+  for (size_t k = 0; k < G.sg.size(); ++k) {
+    const auto& g = G.sg[k];
+    for (size_t j = 0; j < g.who.size(); ++j) {
+      const int* f = hp + G.chain_foff[k][j];
+      hs[g.who[j]]->flags[k].assign(f, f + g.ncl[j]);
+    }
+  }
+  return SPAND_OK;
+}
+
 // Replays the stage graphs of the group's previous factorization; returns 1 if
 // a stage produced other ranks than the ones the graphs were built with (the
 // caller then rebuilds), SPAND_OK on success, or an error code.
 int factor_replay(spand_s* const* hs, int count, FactorGroup& G, cudaStream_t s) {
+  if (G.chain) return chain_replay(hs, G, s);
   for (size_t k = 0; k < G.sg.size(); ++k) {
     auto& g = G.sg[k];
     if (g.exec) CK(cudaGraphLaunch(g.exec, s));
@@ -1311,10 +1503,11 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       CK(ce);
       cudaGraphExec_t exec = nullptr;
       const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) cudaGraphDestroy(graph);
       CK(ie);
       auto& g = G.sg[k];
       g.exec = exec;
+      g.graph = graph;  // kept for the chain of the whole refactorization
       g.who = who;
       g.ncl = ncls;
       g.ioff = ioffs;
@@ -1371,6 +1564,12 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     G.layouts[i] = hs[i]->layout_id;
     for (const auto& g : runs[i].used_gen)
       if (g.first != hs[i]->scratch[0].gen || g.second != hs[i]->scratch[1].gen) G.valid = false;
+  }
+  // the stage graphs become one chain for the next refactorizations; if that
+  // fails, replay falls back to launching the stage graphs one by one
+  if (G.valid && !G.chain_failed && build_chain(G, s) != SPAND_OK) {
+    cudaGetLastError();
+    G.chain_failed = true;
   }
   stamp();
   return SPAND_OK;

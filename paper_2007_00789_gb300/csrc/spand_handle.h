@@ -270,6 +270,7 @@ struct FactorGroup {
   struct StageGraph {
     char* d_blob = nullptr;  // the stage's task tables (kept: the graph reads them)
     size_t cap = 0;
+    cudaGraph_t graph = nullptr;  // the captured stage (kept for the chain below)
     cudaGraphExec_t exec = nullptr;
     // counters of the stage: problem index, offset and cluster count per problem
     std::vector<int> who, ncl;
@@ -278,6 +279,16 @@ struct FactorGroup {
     std::vector<int> expect;  // per problem: ranks then reflector counts at capture
   };
   std::vector<StageGraph> sg;
+  // The whole refactorization as one graph: stage k+1 is the body of a
+  // conditional node that a check kernel after stage k enables only when the
+  // stage's ranks and reflector counts equal the ones the graphs were built
+  // with and no error word is set; the host reads one status block at the end.
+  cudaGraphExec_t chain = nullptr;
+  DevBuf chain_buf;             // status (4 ints), check tables, expected ranks, flags
+  size_t chain_flags = 0;       // int offset of the flags in chain_buf
+  size_t chain_ints = 0;        // ints of chain_buf read back after a launch
+  std::vector<std::vector<size_t>> chain_foff;  // per stage, per problem: flags offset
+  bool chain_failed = false;    // building it failed once: replay stage by stage
   bool valid = false;
   int prec = -1;
   std::vector<uint64_t> layouts;  // layout_id of every problem when the graphs were built
@@ -289,8 +300,13 @@ struct FactorGroup {
   void drop() {
     for (auto& g : sg) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
       g.exec = nullptr;
+      g.graph = nullptr;
     }
+    if (chain) cudaGraphExecDestroy(chain);
+    chain = nullptr;
+    chain_foff.clear();
     valid = false;
   }
   void release() {
@@ -300,6 +316,7 @@ struct FactorGroup {
     sg.clear();
     ints.release();
     tables.release();
+    chain_buf.release();
     if (h_ints) cudaFreeHost(h_ints);
     h_ints = nullptr;
     h_cap = 0;
