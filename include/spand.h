@@ -95,6 +95,11 @@ typedef struct {
   int32_t prescale;       /* 1 = factor D^{-1/2} A D^{-1/2} (D = diag(A)) and precondition with
                              D^{-1/2} M~ D^{-1/2}; SPAND_ENOTSPD at analyze if a diagonal entry is
                              not positive; 0 = no prescaling (the default) */
+  int32_t schur_simt;     /* precision = 1 only: 0 = the Schur updates of large blocks (both
+                             sides >= 64, contribution depth >= 96) run on the tensor cores in
+                             TF32 with a head/tail split of each operand (about FP32 accuracy),
+                             the others on the FP32 pipe (the default); 1 = all on the FP32
+                             pipe.  FP64 factorizations never use the tensor cores. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */

@@ -269,6 +269,8 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   }
   if (opts && (opts->prescale < 0 || opts->prescale > 1)) return fail(SPAND_EINVAL, "prescale must be 0 or 1");
   h->prescale = opts && opts->prescale == 1;
+  if (opts && (opts->schur_simt < 0 || opts->schur_simt > 1)) return fail(SPAND_EINVAL, "schur_simt must be 0 or 1");
+  h->schur_simt = opts && opts->schur_simt == 1;
   if (algebraic) h->dim = 0;
   int rc = algebraic ? build_tree_graph(A->rowptr, A->colind, A->n, nlevels, h->tree, err)
                      : build_tree(coords, A->n, dim, nlevels, h->tree, err);

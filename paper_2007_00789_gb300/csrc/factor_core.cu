@@ -140,10 +140,10 @@ double trsm_bytes(const std::vector<TrsmTask>& v) {
 // Algorithmic Schur work: 2 K rows cols per off-diagonal tile, K rows (rows+1)
 // for a tile on the diagonal of a diagonal block (only its lower half is needed).
 void schur_work(const std::vector<SchurTile>& tiles, const std::vector<SchurContrib>& c,
-                double* flops, double* bytes) {
+                double* flops, double* bytes, bool full_tiles = false) {
   double f = 0.0, b = 0.0;
   for (auto& t : tiles) {
-    const bool diag = (t.mirror == nullptr);
+    const bool diag = (t.mirror == nullptr) && !full_tiles;
     for (int i = t.cbegin; i < t.cend; ++i) {
       const double K = c[i].K;
       f += diag ? K * t.rows * (t.rows + 1) : 2.0 * K * t.rows * t.cols;
@@ -327,6 +327,8 @@ struct StageWork {
   std::vector<TrsmTask> trsm_int;
   int max_m_int = 0;
   std::vector<SchurTile> tiles;
+  std::vector<SchurTile> tiles_tc;  // 128 x 128 tiles for the tensor cores (FP32)
+  int* tc_err = nullptr;            // error word the tensor-core tiles report a timeout in
   std::vector<SchurContrib> contribs;
   std::vector<CopyTask> zcopy, mirror;
   std::vector<PotrfTask> zpotrf, ident;
@@ -499,14 +501,20 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
     if (ce == cb) continue;
     real_t* blk = Ly.row[q] + (size_t)segc(q, r) * mq;
     real_t* mir = (q != r) ? Ly.row[r] + (size_t)segc(r, q) * mr : nullptr;
-    for (int i0 = 0; i0 < mq; i0 += 32)
-      for (int j0 = 0; j0 < mr; j0 += 32) {
+    // FP32: large blocks with a deep contribution go to the tensor cores
+    int ksum = 0;
+    for (int e = cb; e < ce; ++e) ksum += W.contribs[e].K;
+    const bool tc = schur_tc_available() && !h->schur_simt && mq >= 64 && mr >= 64 && ksum >= 96;
+    const int tile = tc ? kSchurTcTile : 32;
+    if (tc) W.tc_err = d_err + 1;
+    for (int i0 = 0; i0 < mq; i0 += tile)
+      for (int j0 = 0; j0 < mr; j0 += tile) {
         if (q == r && j0 > i0) continue;  // diagonal block: lower tiles only, mirrored below
         SchurTile t;
         t.dst = blk + i0 + (size_t)j0 * mq;
         t.ld = mq;
-        t.rows = std::min(32, mq - i0);
-        t.cols = std::min(32, mr - j0);
+        t.rows = std::min(tile, mq - i0);
+        t.cols = std::min(tile, mr - j0);
         t.cbegin = cb;
         t.cend = ce;
         t.i0 = i0;
@@ -521,7 +529,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
           t.mirror = nullptr;
           t.ld_mirror = 0;
         }
-        W.tiles.push_back(t);
+        (tc ? W.tiles_tc : W.tiles).push_back(t);
       }
   }
   // ---- interfaces: scaling and sparsification
@@ -666,7 +674,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
 
 // Offsets of a stage's tables in its uploaded blob.
 struct StageBlob {
-  size_t e, inv, fq, merge, ti, tiles, contr, zc, lt, rt, mi, id, seg, ints;
+  size_t e, inv, fq, merge, ti, tiles, tiles_tc, contr, zc, lt, rt, mi, id, seg, ints;
   PotrfPlan pint, pz;
   std::vector<size_t> qr;
   // multi-CTA QR launches: grid-task arrays (patched with workspace pointers
@@ -698,6 +706,7 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
   plan_to_blob(o.pz, blob);
   o.ti = blob.add(W.trsm_int);
   o.tiles = blob.add(W.tiles);
+  o.tiles_tc = blob.add(W.tiles_tc);
   o.contr = blob.add(W.contribs);
   o.zc = blob.add(W.zcopy);
   o.lt = blob.add(W.ltrsm);
@@ -882,6 +891,13 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
       launch_schur((const SchurTile*)(D + O.tiles), (int)W.tiles.size(),
                    (const SchurContrib*)(D + O.contr), cs);
     });
+    schur_work(W.tiles_tc, W.contribs, &fl, &by, true);
+    cudaError_t te = cudaSuccess;
+    run(KK_SCHUR_TC, W.tiles_tc.size(), fl, by, [&] {
+      te = launch_schur_tc((const SchurTile*)(D + O.tiles_tc), (int)W.tiles_tc.size(),
+                           (const SchurContrib*)(D + O.contr), W.tc_err, cs);
+    });
+    if (te != cudaSuccess) return fail(SPAND_ECUDA, std::string("tensor-core Schur launch: ") + cudaGetErrorString(te));
   }
   run(KK_SCALE_COPY, W.zcopy.size(), 0.0, copy_bytes(W.zcopy),
       [&] { launch_copy((const CopyTask*)(D + O.zc), (int)W.zcopy.size(), cs); });

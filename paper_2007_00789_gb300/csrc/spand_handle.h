@@ -130,12 +130,12 @@ struct Blob {
 enum KernelKind {
   KK_PACK, KK_MERGE, KK_POTRF, KK_TRSM, KK_SCHUR, KK_SCALE_POTRF, KK_SCALE_TRSM, KK_SCALE_COPY,
   KK_RRQR, KK_ECOPY, KK_TRTRI, KK_FORMQ, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT,
-  KK_VEC, KK_RRQR_GRID, KK_COUNT
+  KK_VEC, KK_RRQR_GRID, KK_SCHUR_TC, KK_COUNT
 };
 static const char* const kKindName[KK_COUNT] = {
     "pack", "merge", "potrf", "trsm", "schur", "scale_potrf", "scale_trsm", "scale_copy",
     "rrqr", "e_copy", "trtri", "form_qt", "apply_interior", "apply_scale", "apply_qe", "spmv",
-    "dot", "vector", "rrqr_grid"};
+    "dot", "vector", "rrqr_grid", "schur_tc"};
 
 struct Prof {
   bool on = false;
@@ -436,6 +436,7 @@ struct spand_s {
   // 5: as 0 with the multi-CTA tasks streamed
   int rrqr_path = 0;
   int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512); 0 = automatic
+  bool schur_simt = false;  // FP32: keep every Schur tile on the SIMT path (no tensor cores)
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
   spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own

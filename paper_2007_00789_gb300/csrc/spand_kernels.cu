@@ -409,6 +409,199 @@ __global__ void __launch_bounds__(256) k_schur(const SchurTile* __restrict__ til
   }
 }
 
+#ifdef SPAND_SINGLE
+// ---------------------------------------------------------------------------
+// Schur tiles on the tensor cores (FP32 storage only): one 128 x 128 output
+// tile per CTA, T -= sum_c A_c^T B_c accumulated by tcgen05.mma (kind::tf32)
+// into tensor memory.  Each operand value x is split into a TF32 head and a
+// TF32 tail (hi = rn(x), lo = rn(x - hi), both rounded to nearest), and every
+// K-chunk issues hi*hi + hi*lo + lo*hi: the products of the heads and tails are
+// exact in the FP32 accumulator, and the dropped lo*lo term and the tail's own
+// rounding are below 2^-21 relative, close to FP32 arithmetic.
+//
+// Operands are staged by the CTA's threads (plain loads: the panel rows have
+// arbitrary leading dimensions, which the 16-byte stride rule of TMA tensor
+// copies does not allow) into shared memory in the K-major layout with the
+// 128-byte swizzle: row r of a 128 x 32 chunk is 128 bytes at r * 128, its
+// 16-byte piece q stored at piece q ^ (r & 7).  One thread issues the MMAs
+// (K = 8 per instruction, 4 per chunk and product) and commits them to an
+// mbarrier; the CTA waits on it (bounded) before restaging.  The accumulator
+// is read back with tcgen05.ld, warp w holding rows 32w .. 32w + 31.
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128, kTcN = 128, kTcK = 32, kTcThreads = 128;
+constexpr int kTcTileBytes = kTcM * kTcK * 4;             // one 128 x 32 FP32 chunk: 16 KB
+constexpr int kTcSmem = 4 * kTcTileBytes + 1024;          // A hi/lo, B hi/lo, 1024-byte alignment
+constexpr long long kTcWaitPolls = 1LL << 22;             // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t tc_smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of a K-major operand with the 128-byte
+// swizzle: start address, leading byte offset (unused by this layout), stride
+// byte offset 1024 (eight 128-byte rows), descriptor version 1, swizzle code 2.
+__device__ __forceinline__ unsigned long long tc_desc(uint32_t saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)1 << 16;
+  d |= (unsigned long long)(1024 >> 4) << 32;
+  d |= (unsigned long long)1 << 46;
+  d |= (unsigned long long)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N, M.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                              ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, unsigned long long da, unsigned long long db,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kTcWaitPolls; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// element (r, k) of a swizzled 128 x 32 chunk
+__device__ __forceinline__ int tc_sw(int r, int k) {
+  return r * kTcK + ((((k >> 2) ^ (r & 7)) << 2) | (k & 3));
+}
+
+__global__ void __launch_bounds__(kTcThreads)
+    k_schur_tc(const SchurTile* __restrict__ tiles, const SchurContrib* __restrict__ contribs,
+               int* __restrict__ err) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ uint32_t s_tmem;
+  const SchurTile t = tiles[blockIdx.x];
+  if (t.cend <= t.cbegin) return;  // no contribution (the same for the whole CTA)
+  float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+  float* Ah = base;
+  float* Al = base + kTcM * kTcK;
+  float* Bh = base + 2 * kTcM * kTcK;
+  float* Bl = base + 3 * kTcM * kTcK;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t bar = tc_smem_addr(&s_bar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem_addr(&s_tmem)),
+                 "r"(kTcN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = s_tmem;
+  uint32_t parity = 0;
+  bool ok = true, first = true;
+  for (int ci = t.cbegin; ci < t.cend && ok; ++ci) {
+    const SchurContrib c = contribs[ci];  // K-major: element (k, i) at k + i * ld
+    const float* ca = c.a + (size_t)t.i0 * c.lda;
+    const float* cb = c.b + (size_t)t.j0 * c.ldb;
+    for (int k0 = 0; k0 < c.K && ok; k0 += kTcK) {
+      const int k = lane;
+      const bool kin = k0 + k < c.K;
+#pragma unroll 4
+      for (int r = warp; r < kTcM; r += kTcThreads / 32) {
+        const float a = (kin && r < t.rows) ? ca[(size_t)(k0 + k) + (size_t)r * c.lda] : 0.f;
+        const float b = (kin && r < t.cols) ? cb[(size_t)(k0 + k) + (size_t)r * c.ldb] : 0.f;
+        const float ah = tf32_rn(a), bh = tf32_rn(b);
+        const int o = tc_sw(r, k);
+        Ah[o] = ah;
+        Al[o] = tf32_rn(a - ah);
+        Bh[o] = bh;
+        Bl[o] = tf32_rn(b - bh);
+      }
+      // the generic-proxy stores become visible to the tensor cores
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sah = tc_smem_addr(Ah), sal = tc_smem_addr(Al);
+        const uint32_t sbh = tc_smem_addr(Bh), sbl = tc_smem_addr(Bl);
+#pragma unroll
+        for (int kk = 0; kk < kTcK / 8; ++kk) {
+          const uint32_t off = kk * 32;  // 8 TF32 values along K
+          tc_mma(tmem, tc_desc(sah + off), tc_desc(sbh + off), (first && kk == 0) ? 0u : 1u);
+          tc_mma(tmem, tc_desc(sah + off), tc_desc(sbl + off), 1u);
+          tc_mma(tmem, tc_desc(sal + off), tc_desc(sbh + off), 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar)
+                     : "memory");
+      }
+      first = false;
+      ok = tc_wait(bar, parity);  // the MMAs have read the staged chunk
+      parity ^= 1u;
+      ok = __syncthreads_and(ok);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int row = warp * 32 + lane;
+#pragma unroll 1
+    for (int cb0 = 0; cb0 < kTcN; cb0 += 32) {
+      uint32_t v[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+          "%28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+            "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+            "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+            "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < t.rows) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = cb0 + j;
+          if (col < t.cols) {
+            float* d = t.dst + row + (size_t)col * t.ld;
+            const float val = *d - __uint_as_float(v[j]);
+            *d = val;
+            if (t.mirror) t.mirror[col + (size_t)row * t.ld_mirror] = val;
+          }
+        }
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(err, 1);
+    // MMAs possibly still in flight: give them a bounded wait before freeing
+    // the tensor memory they write
+    tc_wait(bar, parity ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Batched early-stopping column-pivoted Householder QR (Algorithm 1), one CTA
 // per interface, in place on the interface's panel row.  Columns are never
@@ -2616,6 +2809,32 @@ void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s) 
 
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s) {
   if (ntiles > 0) k_schur<<<ntiles, 256, 0, s>>>(tiles, c);
+}
+
+bool schur_tc_available() {
+#ifdef SPAND_SINGLE
+  return true;
+#else
+  return false;
+#endif
+}
+
+cudaError_t launch_schur_tc(const SchurTile* tiles, int ntiles, const SchurContrib* c, int* err,
+                            cudaStream_t s) {
+#ifdef SPAND_SINGLE
+  if (ntiles <= 0) return cudaSuccess;
+  const cudaError_t e = grant_smem((const void*)k_schur_tc, kTcSmem);
+  if (e != cudaSuccess) return e;
+  k_schur_tc<<<ntiles, kTcThreads, kTcSmem, s>>>(tiles, c, err);
+  return cudaGetLastError();
+#else
+  (void)tiles;
+  (void)ntiles;
+  (void)c;
+  (void)err;
+  (void)s;
+  return cudaErrorNotSupported;
+#endif
 }
 
 int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {

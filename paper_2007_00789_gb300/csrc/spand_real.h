@@ -169,6 +169,13 @@ void launch_scatter(const double* val, const int64_t* dst_index, real_t* base_lo
 void launch_potrf(const PotrfTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_trsm(const TrsmTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_schur(const SchurTile* tiles, int ntiles, const SchurContrib* c, cudaStream_t s);
+// Tensor-core Schur tiles of up to 128 x 128 (FP32 storage; contributions in the
+// K-major storage, pad = 0): available in the FP32 build only; err: set to 1 if
+// a bounded wait for the tensor cores ran out.
+bool schur_tc_available();
+constexpr int kSchurTcTile = 128;
+cudaError_t launch_schur_tc(const SchurTile* tiles, int ntiles, const SchurContrib* c, int* err,
+                            cudaStream_t s);
 void launch_copy_real(int n, const real_t* src, real_t* dst, cudaStream_t s);
 void launch_form_qt(const FormQtTask* t, int ntasks, int max_m, cudaStream_t s);
 void launch_set_identity(const PotrfTask* t, int ntasks, cudaStream_t s);

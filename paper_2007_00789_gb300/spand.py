@@ -56,7 +56,8 @@ class _Opts(ctypes.Structure):
                 ("true_res_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("plain_launches", ctypes.c_int32), ("rrqr_threads", ctypes.c_int32),
-                ("partition", ctypes.c_int32), ("prescale", ctypes.c_int32)]
+                ("partition", ctypes.c_int32), ("prescale", ctypes.c_int32),
+                ("schur_simt", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -183,7 +184,7 @@ class Spand:
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
                  max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0,
                  plain_launches: bool = False, rrqr_threads: int = 0, partition: int = 0,
-                 prescale: bool = False):
+                 prescale: bool = False, schur_simt: bool = False):
         """coords None (or partition=1): algebraic nested dissection of A's graph;
         prescale: factor D^{-1/2} A D^{-1/2} and precondition with D^{-1/2} M~ D^{-1/2}."""
         L = load_library()
@@ -203,7 +204,7 @@ class Spand:
                      0 if true_res_every is None else int(true_res_every),
                      -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
                      int(precision), 1 if plain_launches else 0, int(rrqr_threads),
-                     int(partition), 1 if prescale else 0)
+                     int(partition), 1 if prescale else 0, 1 if schur_simt else 0)
         h = ctypes.c_void_p()
         cptr = None if coords is None else coords.ctypes.data
         cdim = 0 if coords is None else coords.shape[1]

@@ -15,7 +15,11 @@ approximation.  What must hold, and is checked here:
   max|M r|, stays below 1e-3 on random-coefficient problems (measured values
   are printed), and the spectral radius of I - M A exceeds the FP64 oracle's
   by at most 1e-3 (FP32 rounding, amplified by the conditioning of the
-  blocks, adds an absolute floor of that order on high-contrast problems).
+  blocks, adds an absolute floor of that order on high-contrast problems);
+* the Schur updates of large blocks on the tensor cores (TF32 with a
+  head/tail split of each operand) give the preconditioner of the FP32-pipe
+  updates to within 1e-4 relative, the same CG iterations (+-1) and the same
+  ranks almost everywhere.
 """
 import numpy as np
 import pytest
@@ -95,6 +99,7 @@ def test_fp32_factor_reaches_fp64_accuracy(name, make, ell, scheme, ties):
 @pytest.mark.parametrize("make,ell", [
     (lambda: si.diffusion_3d(16, seed=2), 7),
     (lambda: si.diffusion_grid((45, 38), seed=9), 6),
+    (lambda: si.diffusion_3d(32, seed=6), 9),  # upper-level Schur blocks on the tensor cores
 ])
 def test_fp32_error_against_oracle(make, ell):
     from paper_2007_00789_gb300 import spand as S
@@ -116,3 +121,42 @@ def test_fp32_error_against_oracle(make, ell):
     print("spectral radius of I - M A: fp32", rho_32, "oracle", rho_o)
     assert rho_32 <= rho_o + 1e-3, (rho_32, rho_o)
     h32.close()
+
+
+@pytest.mark.parametrize("make,ell,scheme", [
+    (lambda: si.diffusion_3d(48, seed=1), 11, 1),
+    (lambda: si.diffusion_3d(40, seed=7), 10, 2),
+])
+def test_tensor_core_schur_matches_fp32_pipe(make, ell, scheme):
+    torch = _torch()
+    from paper_2007_00789_gb300 import spand as S
+    prob = make()
+    A = prob.to_scipy()
+    simt = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=1, schur_simt=True)
+    tc = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=1)
+    simt.factor()
+    tc.set_profiling(True)
+    tc.factor()
+    ks = {k["name"]: k for k in tc.kernel_stats()}
+    tc.set_profiling(False)
+    assert ks["schur_tc"]["launches"] > 0, "no Schur block reached the tensor cores"
+    tc.factor()  # graph-captured, as in production
+    ra, rb = simt.ranks(), tc.ranks()
+    live = ra[:, 1] >= 0
+    same = float(np.mean(ra[live, 1] == rb[live, 1]))
+    r = np.random.default_rng(9).standard_normal(prob.n)
+    za, zb = _apply(simt, r), _apply(tc, r)
+    err = np.abs(za - zb).max() / np.abs(za).max()
+    b = si.rhs_normal(prob.n, seed=3)
+    bd = torch.from_numpy(b).cuda()
+    xa, xb = torch.zeros_like(bd), torch.zeros_like(bd)
+    ita, _ = simt.pcg(bd, xa, 1e-12)
+    itb, relb = tc.pcg(bd, xb, 1e-12)
+    true_rel = np.linalg.norm(b - A @ xb.cpu().numpy()) / np.linalg.norm(b)
+    print(f"tensor-core Schur: {ks['schur_tc']['launches']} launches, {ks['schur_tc']['flops']/1e9:.2f} GFLOP;"
+          f" M r vs FP32 pipe {err:.2e}; identical ranks {same:.4f}; CG {itb} (FP32 pipe {ita})")
+    assert same >= 0.98
+    assert err <= 1e-4
+    assert abs(itb - ita) <= 1 and relb <= 1e-12 and true_rel <= 1e-12
+    simt.close()
+    tc.close()
