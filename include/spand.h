@@ -153,6 +153,21 @@ int spand_analyze(const spand_csr* A, const double* coords, int dim, int nlevels
  * RRQR ran out; the handle stays valid but unfactored). */
 int spand_factor(spand_t h, void* stream);
 
+/* Autotuner of the RRQR launch shapes (a launch-configuration search; the
+ * paper has no counterpart).  Interface blocks fall into size buckets 1..5,
+ * keyed by the smallest thread-block cluster (1, 2, 4, 8 or 16 CTAs) whose
+ * shared memory holds the block.  spand_tune factors the problem once per
+ * candidate shape -- 256 or 512 threads per CTA, times the cluster size of the
+ * default rule or twice it -- timing every RRQR launch with CUDA events on the
+ * stream, keeps the fastest shape of every bucket, and factors once more with
+ * it (graphs captured), leaving the handle factored as spand_factor does.  The
+ * handle keeps the choices for later factorizations (also inside a batch).
+ * The shapes change only the order of some floating-point sums.
+ *   choice -- host, may be NULL: 10 int32, the chosen CTA size and cluster
+ *             growth of buckets 1..5 (0 where no interface fell in a bucket).
+ * Costs five factorizations.  Errors: those of spand_factor. */
+int spand_tune(spand_t h, void* stream, int32_t* choice);
+
 /* Testing hook for the one bounded device-side wait of the factorization:
  * the barrier between the CTAs of a multi-CTA RRQR (Algorithm 1 on interface
  * blocks too wide for a thread-block cluster; rrqr_kernel = 3 forces it for

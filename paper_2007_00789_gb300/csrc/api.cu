@@ -370,6 +370,80 @@ int spand_factor(spand_t h, void* stream) {
   }
 }
 
+int spand_tune(spand_t h, void* stream, int32_t* choice) {
+  if (!h) return fail(SPAND_EINVAL, "null handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool prof_was = h->prof.on;
+  int saved_thr[6], saved_grow[6];
+  std::copy(h->tune_thr, h->tune_thr + 6, saved_thr);
+  std::copy(h->tune_grow, h->tune_grow + 6, saved_grow);
+  double best_ms[6];
+  int best_thr[6] = {0, 0, 0, 0, 0, 0}, best_grow[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < 6; ++b) best_ms[b] = 1e300;
+  auto restore = [&]() {
+    h->tuning = false;
+    std::copy(saved_thr, saved_thr + 6, h->tune_thr);
+    std::copy(saved_grow, saved_grow + 6, h->tune_grow);
+    h->prof.resolve();
+    h->prof.clear();
+    h->prof.on = prof_was;
+  };
+  try {
+    // every candidate shape for every bucket at once: while tuning, the buckets'
+    // RRQR launches are separate, so each bucket's time is read from its own launches
+    h->tuning = true;
+    for (int thr : {256, 512})
+      for (int grow : {1, 2}) {
+        for (int b = 1; b <= 5; ++b) {
+          h->tune_thr[b] = thr;
+          h->tune_grow[b] = grow;
+        }
+        h->drop_graphs();
+        h->prof.resolve();
+        h->prof.clear();
+        h->prof.on = true;  // per-launch events, plain launches
+        const int rc = factor_impl(h, s);
+        h->prof.resolve();
+        if (rc != SPAND_OK) {
+          restore();
+          h->factored = false;
+          return rc;
+        }
+        for (const auto& kv : h->prof.rrqr_tag_ms) {
+          const int b = kv.first;
+          if (b >= 1 && b <= 5 && kv.second < best_ms[b]) {
+            best_ms[b] = kv.second;
+            best_thr[b] = thr;
+            best_grow[b] = grow;
+          }
+        }
+      }
+    h->tuning = false;
+    h->prof.clear();
+    h->prof.on = prof_was;
+    for (int b = 1; b <= 5; ++b) {
+      h->tune_thr[b] = best_thr[b];
+      h->tune_grow[b] = best_grow[b];
+    }
+    h->drop_graphs();
+    const int rc = factor_impl(h, s);  // the tuned factorization (graphs captured)
+    if (rc != SPAND_OK) {
+      h->factored = false;
+      return rc;
+    }
+  } catch (const std::bad_alloc&) {
+    restore();
+    h->factored = false;
+    return fail(SPAND_ENOMEM, "host allocation failed");
+  }
+  if (choice)
+    for (int b = 1; b <= 5; ++b) {
+      choice[2 * (b - 1)] = best_thr[b];
+      choice[2 * (b - 1) + 1] = best_grow[b];
+    }
+  return SPAND_OK;
+}
+
 int spand_apply(spand_t h, const double* r, double* z, void* stream) {
   if (!h || !r || !z) return fail(SPAND_EINVAL, "null argument");
   return apply_any(h, r, z, (cudaStream_t)stream);

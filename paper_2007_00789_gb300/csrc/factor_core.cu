@@ -337,7 +337,7 @@ struct StageWork {
   struct QrGroup {
     std::vector<RRQRTask> tasks;
     int max_m = 0, max_cols = 0, max_segs = 0, smem = 0;
-    int bucket = 0, threads = 256;
+    int bucket = 0, threads = 256, base = 0;
   };
   // (colour, bucket * 4096 + CTA size) -> tasks; bucket b >= 1: thread-block
   // clusters of 2^(b-1) CTAs, bucket 0: the global-memory kernel
@@ -611,26 +611,32 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         // Cluster size: the smallest that fits shared memory, raised until the
         // colour's interfaces fill about two CTAs per SM, while keeping at least
         // 32 columns per CTA.
+        // The base bucket b0 (the smallest cluster whose shared memory holds the
+        // block) keys the tuned choices of spand_tune: a growth factor for the
+        // cluster size and the CTA size.
         const int ntask = (int)S.by_colour[col].size();
+        int b0 = 0;
+        for (int lc = 0; lc <= 4 && !b0; ++lc)
+          if (rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, 1 << lc) <= kQrClusterSmem &&
+              cluster_ok(h, 1 << lc))
+            b0 = lc + 1;
+        const int grow = b0 ? std::max(1, h->tune_grow[b0]) : 1;
         int want = 1;
         while (want < 16 && want * ntask < 2 * kNumSMs && (2 * want) * 32 <= t.ncols_max) want *= 2;
+        want = std::min(16, want * grow);
         int b = 0;
         int bytes_b = 0;
-        for (int lc = 0; lc <= 4; ++lc) {
-          const int cs = 1 << lc;
-          const int bytes = rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, cs);
-          if (bytes <= kQrClusterSmem && cluster_ok(h, cs)) {
-            int lw = lc;
-            while ((1 << lw) < want && lw < 4 && cluster_ok(h, 1 << (lw + 1))) ++lw;
-            b = lw + 1;
-            bytes_b = rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, 1 << lw);
-            break;
-          }
+        if (b0) {
+          int lw = b0 - 1;
+          while ((1 << lw) < want && lw < 4 && cluster_ok(h, 1 << (lw + 1))) ++lw;
+          b = lw + 1;
+          bytes_b = rrqr_cluster_smem_bytes(m, t.ncols_max, t.nseg_max, 1 << lw);
         }
-        // CTA size: the handle's choice, else 256 threads
+        // CTA size: the handle's choice, else the tuned one, else 256 threads
         int thr = 256;
-        if (b > 0 && h->rrqr_threads > 0) {
-          thr = h->rrqr_threads;
+        const int want_thr = h->rrqr_threads > 0 ? h->rrqr_threads : (b0 ? h->tune_thr[b0] : 0);
+        if (b > 0 && want_thr > 0) {
+          thr = want_thr;
           const int cs = 1 << (b - 1);
           if (rrqr_cluster_active(cs, bytes_b, thr) <= 0) thr = 256;
         }
@@ -646,9 +652,12 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
         if (debug_plan())
           fprintf(stderr, "spand plan: stage %d colour %d iface %d m %d ncols_ub %d nseg %d bucket %d thr %d\n",
                   k, col, p, m, t.ncols_max, t.nseg_max, b, thr);
-        auto& g = W.qr[{col, b * 4096 + thr}];
+        // while tuning, each base bucket launches on its own so that its time can
+        // be read from its launches; otherwise equal shapes share a launch
+        auto& g = W.qr[{col, ((h->tuning ? b0 : 0) * 8 + b) * 4096 + thr}];
         g.threads = thr;
         g.bucket = b;
+        g.base = b0;
         g.tasks.push_back(t);
         g.max_m = std::max(g.max_m, m);
         g.max_cols = std::max(g.max_cols, t.ncols_max);
@@ -839,7 +848,7 @@ void patch_grid(const StageBlob& o, Blob& blob, char* D) {
 // counters (reset from the blob's pristine copy first).  Returns the number of
 // kernel launches through *nl.
 int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, cudaStream_t cs,
-                 int* nl) {
+                 int* nl, FactorGroup& G) {
   auto run = [&](int kind, size_t ntasks, double flops, double bytes, auto&& launch) {
     if (ntasks == 0) return;
     ++*nl;
@@ -847,14 +856,32 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
   };
   if (!W.ints.empty())
     CK(cudaMemcpyAsync(cnt, D + O.ints, W.ints.size() * sizeof(int), cudaMemcpyDeviceToDevice, cs));
+  // The previous stage's apply operators read only that stage's data (its
+  // interface rows in the other scratch buffer, the factor arena), which this
+  // stage does not write: they run on a side branch (a parallel graph branch
+  // when captured) and fill the SMs this stage's latency-bound launches leave
+  // idle.  The branch joins at the end of the stage, before the next stage
+  // clears that scratch buffer.  With profiling, everything stays on cs.
+  const bool pend = !W.pend_e.empty() || !W.pend_inv.empty() || !W.pend_qt.empty();
+  cudaStream_t ps = cs;
+  if (pend && G.side && !P.on) {
+    CK(cudaEventRecord(G.ev_fork, cs));
+    CK(cudaStreamWaitEvent(G.side, G.ev_fork, 0));
+    ps = G.side;
+  }
   run(KK_ECOPY, W.pend_e.size(), 0.0, copy_bytes(W.pend_e),
-      [&] { launch_copy((const CopyTask*)(D + O.e), (int)W.pend_e.size(), cs); });
+      [&] { launch_copy((const CopyTask*)(D + O.e), (int)W.pend_e.size(), ps); });
   run(KK_TRTRI, W.pend_inv.size(), trtri_flops(W.pend_inv), trsm_bytes(W.pend_inv), [&] {
-    launch_trsm((const TrsmTask*)(D + O.inv), (int)W.pend_inv.size(), W.pend_inv_m, cs);
+    launch_trsm((const TrsmTask*)(D + O.inv), (int)W.pend_inv.size(), W.pend_inv_m, ps);
   });
   run(KK_FORMQ, W.pend_qt.size(), formqt_flops(W.pend_qt), 0.0, [&] {
-    launch_form_qt((const FormQtTask*)(D + O.fq), (int)W.pend_qt.size(), W.pend_qt_m, cs);
+    launch_form_qt((const FormQtTask*)(D + O.fq), (int)W.pend_qt.size(), W.pend_qt_m, ps);
   });
+  if (ps != cs) CK(cudaEventRecord(G.ev_join, ps));
+  auto join = [&]() -> int {
+    if (ps != cs) CK(cudaStreamWaitEvent(cs, G.ev_join, 0));
+    return SPAND_OK;
+  };
   for (auto& z : W.zero) CK(cudaMemsetAsync(z.first, 0, z.second, cs));
   for (auto& pk : W.packs)
     run(KK_PACK, 1, 0.0, 16.0 * pk.nnz,
@@ -897,7 +924,10 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
       te = launch_schur_tc((const SchurTile*)(D + O.tiles_tc), (int)W.tiles_tc.size(),
                            (const SchurContrib*)(D + O.contr), W.tc_err, cs);
     });
-    if (te != cudaSuccess) return fail(SPAND_ECUDA, std::string("tensor-core Schur launch: ") + cudaGetErrorString(te));
+    if (te != cudaSuccess) {
+      join();
+      return fail(SPAND_ECUDA, std::string("tensor-core Schur launch: ") + cudaGetErrorString(te));
+    }
   }
   run(KK_SCALE_COPY, W.zcopy.size(), 0.0, copy_bytes(W.zcopy),
       [&] { launch_copy((const CopyTask*)(D + O.zc), (int)W.zcopy.size(), cs); });
@@ -930,6 +960,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
         });
       }
     } else {
+      P.tag = g.base;  // the autotuner's key
       run(KK_RRQR, g.tasks.size(), 0.0, 0.0, [&] {
         if (b == 0)
           launch_rrqr((const RRQRTask*)(D + off), (int)g.tasks.size(), (const RRQRSeg*)(D + O.seg),
@@ -944,6 +975,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
     }
     ++gi;
   }
+  RET(join());
   if (gerr != cudaSuccess)
     return fail(SPAND_ECUDA, std::string("RRQR launch: ") + cudaGetErrorString(gerr));
   CK(cudaGetLastError());
@@ -1095,9 +1127,11 @@ int finish_stage(Run& R, int k, const int* hp, Prof& P) {
         real_t* Edst = (real_t*)ep;
         a.E = Edst;
         int acc = 0;
+        // E-tilde row-major (row i at i * ncols): rows r .. r + nE - 1 of each
+        // neighbour segment of the panel row, transposed into place
         for (auto& sw : segw) {
-          push_copy(R.pending_e, Ly.row[p] + r + (size_t)sw.first * m, Edst + (size_t)acc * nE, m,
-                    nE, nE, sw.second, 0);
+          push_copy(R.pending_e, Ly.row[p] + r + (size_t)sw.first * m, Edst + acc, m, ncols,
+                    sw.second, nE, 1);
           acc += sw.second;
         }
       } else {
@@ -1431,6 +1465,11 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
   G.drop();
   const bool capture = !P.on && !no_graph;
   if (capture && !G.cap_stream) CK(cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking));
+  if (!G.side) {
+    CK(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&G.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&G.ev_join, cudaEventDisableTiming));
+  }
   G.prec = precision;
   int maxell = 0;
   std::vector<Run> runs(count);
@@ -1511,7 +1550,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       cs = G.cap_stream;
     }
     int nl = 0;
-    const int lrc = launch_stage(W, O, D, dcnt, P, cs, &nl);
+    const int lrc = launch_stage(W, O, D, dcnt, P, cs, &nl, G);
     if (capture) {
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(G.cap_stream, &graph);

@@ -57,6 +57,7 @@ __device__ __forceinline__ void gemv_n_tile(const real_t* __restrict__ M, size_t
   const real_t* Ma = M + (va ? ra : r0);
   const real_t* Mb = M + (vb ? rb : r0);
   int c = cb;
+#pragma unroll 2
   for (; c + 3 < ce; c += 4) {
     real_t a[4], b[4];
 #pragma unroll
@@ -122,16 +123,28 @@ __device__ void gemv_n(const real_t* __restrict__ M, size_t ld, int r0, int r1, 
 
 // out(c, v, sum_{r in [rlo(c), R)} M[r + c*ld] x_v[r]) for columns c in [c0, c1);
 // rlo(c) is the first row column c needs (0 for a full matrix, c for the
-// transpose of a lower-triangular one).  A warp reduces four columns at a
-// time: its lanes read consecutive rows of each (coalesced, four loads in
-// flight per lane), then the partial sums are added across the warp; lanes 0,
-// 8, 16 and 24 write the four results.
+// transpose of a lower-triangular one).  A warp reduces four columns at a time
+// over a range of rows: its lanes read consecutive rows of each (coalesced, four
+// loads in flight per lane), then the partial sums are added across the warp.
+// When the columns are too few to give every warp four (a thin slice of a
+// large operator), the rows are split into chunks as well, so that all warps
+// work, and the chunks' partial sums are added in a fixed order in shared
+// memory (red: at least 32 * NV entries).
 template <int NV, class Lo, class Out>
 __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, int R, Lo rlo,
                        const real_t* __restrict__ x, int xs, real_t* red, Out out) {
-  (void)red;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cq = c0 + 4 * warp; cq < c1; cq += 4 * kApWarps) {
+  const int ncol = c1 - c0;
+  if (ncol <= 0) {
+    __syncthreads();
+    return;
+  }
+  const int ncg = (ncol + 3) / 4;                              // groups of four columns
+  const int nrc = ncg >= kApWarps ? 1 : (kApWarps + ncg - 1) / ncg;  // row chunks per group
+  const int chunk = nrc == 1 ? R : (((R + nrc - 1) / nrc) + 31) & ~31;
+  for (int item = warp; item < ncg * nrc; item += kApWarps) {
+    const int g = item % ncg, rc = item / ncg;
+    const int cq = c0 + 4 * g;
     real_t s[4][NV];
     int lo4[4];
 #pragma unroll
@@ -140,8 +153,10 @@ __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, 
 #pragma unroll
       for (int v = 0; v < NV; ++v) s[u][v] = 0.0;
     }
-    const int rs = min(min(lo4[0], lo4[1]), min(lo4[2], lo4[3]));
-    for (int r = rs + lane; r < R; r += 32) {
+    const int rb = rc * chunk, re = min(R, rb + chunk);
+    const int rs = max(rb, min(min(lo4[0], lo4[1]), min(lo4[2], lo4[3])));
+#pragma unroll 2
+    for (int r = rs + lane; r < re; r += 32) {
       real_t a[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -169,10 +184,45 @@ __device__ void gemv_t(const real_t* __restrict__ M, size_t ld, int c0, int c1, 
       t += __shfl_xor_sync(0xffffffffu, t, 4);
       t += __shfl_xor_sync(0xffffffffu, t, 2);
       t += __shfl_xor_sync(0xffffffffu, t, 1);
-      if ((lane & 7) == 0 && cq + uq < c1) out(cq + uq, v, t);
+      if ((lane & 7) == 0 && cq + uq < c1) {
+        if (nrc == 1) out(cq + uq, v, t);
+        else red[((rc * ncg + g) * 4 + uq) * NV + v] = t;
+      }
     }
   }
   __syncthreads();
+  if (nrc > 1) {
+    for (int e = threadIdx.x; e < ncol * NV; e += blockDim.x) {
+      const int c = e / NV, v = e - c * NV;
+      real_t t = 0.0;
+      for (int rc = 0; rc < nrc; ++rc) t += red[((rc * ncg + (c >> 2)) * 4 + (c & 3)) * NV + v];
+      out(c0 + c, v, t);
+    }
+    __syncthreads();
+  }
+}
+
+// out(r, v, sum_{c < C} M[r + c*ld] x_v[c]) for rows r in [r0, r1), one thread
+// per row: for a matrix of few columns (C up to a few dozen) whose rows are the
+// long dimension, every thread keeps C independent loads in flight, the warp's
+// loads of one column are consecutive, and no partial sums cross threads.
+template <int NV, class Out>
+__device__ void gemv_rows(const real_t* __restrict__ M, size_t ld, int r0, int r1, int C,
+                          const real_t* __restrict__ x, int xs, Out out) {
+  for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) {
+    real_t s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = 0.0;
+    const real_t* p = M + r;
+#pragma unroll 8
+    for (int c = 0; c < C; ++c) {
+      const real_t a = p[(size_t)c * ld];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] = fma(a, x[v * xs + c], s[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out(r, v, s[v]);
+  }
 }
 
 // Every operator is applied by a thread-block cluster of K CTAs (K from the
@@ -331,11 +381,13 @@ __global__ void AP_BOUNDS
         const int v = e / (hi - lo), i = lo + e - v * (hi - lo);
         zb[v * ldz + t.slots[i]] = ys[v * m + i];
       }
+      // (E-tilde is row-major: column c of E-tilde is row c of a column-major
+      // ncols x nE matrix with leading dimension ncols)
       if (nE > 0)
-        gemv_t<NV>(t.E, nE, part_lo(nc, k, K), part_lo(nc, k + 1, K), nE, [](int) { return 0; },
-                   ys + t.r, m, red, [&](int c, int v, real_t val) {
-                     if (v < nv) atomicAdd(zb + v * ldz + t.eslots[c], -val);
-                   });
+        gemv_rows<NV>(t.E, nc, part_lo(nc, k, K), part_lo(nc, k + 1, K), nE, ys + t.r, m,
+                      [&](int c, int v, real_t val) {
+                        if (v < nv) atomicAdd(zb + v * ldz + t.eslots[c], -val);
+                      });
     } else {
       // x_f -= E-tilde z_w, then z_p = Q x
       for (int e = threadIdx.x; e < NV * (hi - lo); e += blockDim.x) {
@@ -344,10 +396,11 @@ __global__ void AP_BOUNDS
       }
       if (nE > 0) {
         const int flo = max(lo, t.r) - t.r, fhi = min(hi, t.r + nE) - t.r;
+        // row i of E-tilde is contiguous: a warp reduces four rows at a time
         if (fhi > flo)
-          gemv_n<NV>(t.E, nE, flo, fhi, [&](int) { return nc; }, zw, nc, red,
-                     [&](int r, int v, real_t val) {
-                       share(cl, K, ys + v * m, t.r + r, xs[v * m + t.r + r] - val);
+          gemv_t<NV>(t.E, nc, flo, fhi, nc, [](int) { return 0; }, zw, nc, red,
+                     [&](int i, int v, real_t val) {
+                       share(cl, K, ys + v * m, t.r + i, xs[v * m + t.r + i] - val);
                      });
       }
       cl.sync();

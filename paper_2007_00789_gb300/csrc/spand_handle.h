@@ -150,8 +150,10 @@ struct Prof {
   size_t used = 0;
   std::vector<Pend> pend;
   spand_kernel_stat stat[KK_COUNT];
+  std::map<int, double> rrqr_tag_ms;  // cluster-RRQR launch time by tag (the autotuner's key)
   Prof() { clear(); }
   void clear() {
+    rrqr_tag_ms.clear();
     for (int k = 0; k < KK_COUNT; ++k) {
       memset(&stat[k], 0, sizeof(stat[k]));
       snprintf(stat[k].name, sizeof(stat[k].name), "%s", kKindName[k]);
@@ -195,6 +197,7 @@ struct Prof {
                 p.tag, ms, p.flops, p.bytes);
       stat[p.kind].launches += 1;
       stat[p.kind].total_ms += ms;
+      if (p.kind == KK_RRQR) rrqr_tag_ms[p.tag] += ms;
       stat[p.kind].flops += p.flops;
       stat[p.kind].bytes += p.bytes;
     }
@@ -297,6 +300,10 @@ struct FactorGroup {
   int* h_ints = nullptr;           // pinned readback of the counters
   size_t h_cap = 0;
   cudaStream_t cap_stream = nullptr;
+  // the previous stage's apply operators (explicit inverses, Q^T, E-tilde
+  // copies) are formed on a side branch beside the stage's own launches
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void drop() {
     for (auto& g : sg) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -322,6 +329,11 @@ struct FactorGroup {
     h_cap = 0;
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    side = nullptr;
+    ev_fork = ev_join = nullptr;
   }
 };
 
@@ -437,6 +449,12 @@ struct spand_s {
   int rrqr_path = 0;
   int rrqr_threads = 0;  // CTA size of the cluster RRQR (256, 512); 0 = automatic
   bool schur_simt = false;  // FP32: keep every Schur tile on the SIMT path (no tensor cores)
+  // spand_tune's choices per base bucket b0 = 1..5 (the smallest thread-block
+  // cluster, 2^(b0-1) CTAs, whose shared memory holds an interface's block):
+  // CTA size of the cluster RRQR (0 = 256) and growth factor of the cluster size
+  int tune_thr[6] = {0, 0, 0, 0, 0, 0};
+  int tune_grow[6] = {0, 0, 0, 0, 0, 0};
+  bool tuning = false;  // inside spand_tune: RRQR launches split by base bucket
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
   spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own

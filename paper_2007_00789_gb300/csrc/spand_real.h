@@ -142,7 +142,7 @@ struct ApScale {
 };
 struct ApQE {
   const real_t* Qt;   // m x m, Q_p^T, ld m
-  const real_t* E;    // nE x ncols, ld nE
+  const real_t* E;    // nE x ncols, row-major: E[i, c] at i * ncols + c
   const int* slots;   // m positions (before sparsification)
   const int* eslots;  // ncols positions
   int m, r, nE, ncols;

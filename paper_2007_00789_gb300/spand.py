@@ -25,7 +25,8 @@ SPAND_ETIMEOUT = -7
 
 # Every entry point declared in include/spand.h.
 EXPORTS = [
-    "spand_analyze", "spand_factor", "spand_test_set_qr_wait", "spand_apply", "spand_pcg",
+    "spand_analyze", "spand_factor", "spand_tune", "spand_test_set_qr_wait", "spand_apply",
+    "spand_pcg",
     "spand_pcg_host",
     "spand_matvec", "spand_info", "spand_ranks", "spand_cluster_map", "spand_num_clusters",
     "spand_pcg_noalloc", "spand_set_profiling", "spand_kernel_stats",
@@ -110,6 +111,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.c_int, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
     L.spand_factor.argtypes = [vp, vp]
     L.spand_test_set_qr_wait.argtypes = [vp, i64, i32]
+    L.spand_tune.argtypes = [vp, vp, vp]
     L.spand_apply.argtypes = [vp, vp, vp, vp]
     L.spand_pcg.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
     L.spand_pcg_host.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64), vp]
@@ -230,6 +232,13 @@ class Spand:
 
     def factor(self, stream=None):
         _check(self._lib.spand_factor(self._h, _stream_ptr(stream)))
+
+    def tune(self, stream=None) -> dict:
+        """spand_tune: the fastest RRQR launch shape per size bucket; leaves the handle factored.
+        Returns {bucket: (threads per CTA, cluster growth)} for the buckets that occurred."""
+        ch = np.zeros(10, dtype=np.int32)
+        _check(self._lib.spand_tune(self._h, _stream_ptr(stream), ch.ctypes.data))
+        return {b + 1: (int(ch[2 * b]), int(ch[2 * b + 1])) for b in range(5) if ch[2 * b]}
 
     def test_set_qr_wait(self, limit: int = 0, unreachable: bool = False):
         """Testing hook of the multi-CTA RRQR's bounded barrier wait (spand_test_set_qr_wait)."""
