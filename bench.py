@@ -76,6 +76,9 @@ WORKLOADS = {
     "poisson2d_64": ("laplacian_2d(64)", 6, "rhs_uniform", 0),
     "diffusion3d_64": ("diffusion_3d(64, seed=0)", 12, "rhs_normal", 0),
     "poisson3d_32": ("laplacian_3d(32)", 9, "rhs_normal", 0),
+    # smaller cases of the 128^3 family (same coefficient law, 128-vertex leaves), for profiling
+    "diffusion3d_48": ("diffusion_3d(48, seed=0)", 11, "rhs_normal", 1),
+    "diffusion3d_96": ("diffusion_3d(96, seed=0)", 14, "rhs_normal", 1),
     # 3D high-contrast diffusion, a = 10^U(-3,3) per cell (seed 0), b ~ N(0,1) from seed 1
     "diffusion3d_128": ("diffusion_3d(128, seed=0)", 15, "rhs_normal", 1),
 }
