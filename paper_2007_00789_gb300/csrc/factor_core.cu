@@ -848,7 +848,7 @@ void patch_grid(const StageBlob& o, Blob& blob, char* D) {
 // counters (reset from the blob's pristine copy first).  Returns the number of
 // kernel launches through *nl.
 int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, cudaStream_t cs,
-                 int* nl, FactorGroup& G) {
+                 int* nl, FactorGroup& G, int stage) {
   auto run = [&](int kind, size_t ntasks, double flops, double bytes, auto&& launch) {
     if (ntasks == 0) return;
     ++*nl;
@@ -950,6 +950,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
     if (b == 6) {
       for (const auto& gl : O.grid) {
         if (gl.group != gi) continue;
+        P.tag = stage * 100;
         run(KK_RRQR_GRID, (size_t)gl.ntasks, 0.0, 0.0, [&] {
           const cudaError_t e =
               gl.onchip ? launch_rrqr_gsm((const RRQRGridTask*)(D + gl.off), gl.ntasks, gl.nctas,
@@ -960,7 +961,7 @@ int launch_stage(StageWork& W, const StageBlob& O, char* D, int* cnt, Prof& P, c
         });
       }
     } else {
-      P.tag = g.base;  // the autotuner's key
+      P.tag = stage * 100 + g.base;  // the autotuner reads the base bucket (tag % 100)
       run(KK_RRQR, g.tasks.size(), 0.0, 0.0, [&] {
         if (b == 0)
           launch_rrqr((const RRQRTask*)(D + off), (int)g.tasks.size(), (const RRQRSeg*)(D + O.seg),
@@ -1367,6 +1368,7 @@ int build_chain(FactorGroup& G, cudaStream_t s) {
     G.chain = nullptr;
     return fail(SPAND_ECUDA, std::string("instantiating the refactorization chain: ") + cudaGetErrorString(ie));
   }
+  CK(cudaGraphUpload(G.chain, s));  // the device-side setup now, not in the first launch
   return SPAND_OK;
 }
 
@@ -1400,6 +1402,12 @@ int chain_replay(spand_s* const* hs, FactorGroup& G, cudaStream_t s) {
 // a stage produced other ranks than the ones the graphs were built with (the
 // caller then rebuilds), SPAND_OK on success, or an error code.
 int factor_replay(spand_s* const* hs, int count, FactorGroup& G, cudaStream_t s) {
+  // the stage graphs chained into one graph; if that fails, replay falls back
+  // to launching the stage graphs one by one
+  if (!G.chain && !G.chain_failed && build_chain(G, s) != SPAND_OK) {
+    cudaGetLastError();
+    G.chain_failed = true;
+  }
   if (G.chain) return chain_replay(hs, G, s);
   for (size_t k = 0; k < G.sg.size(); ++k) {
     auto& g = G.sg[k];
@@ -1550,7 +1558,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       cs = G.cap_stream;
     }
     int nl = 0;
-    const int lrc = launch_stage(W, O, D, dcnt, P, cs, &nl, G);
+    const int lrc = launch_stage(W, O, D, dcnt, P, cs, &nl, G, k);
     if (capture) {
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(G.cap_stream, &graph);
@@ -1620,12 +1628,8 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     for (const auto& g : runs[i].used_gen)
       if (g.first != hs[i]->scratch[0].gen || g.second != hs[i]->scratch[1].gen) G.valid = false;
   }
-  // the stage graphs become one chain for the next refactorizations; if that
-  // fails, replay falls back to launching the stage graphs one by one
-  if (G.valid && !G.chain_failed && build_chain(G, s) != SPAND_OK) {
-    cudaGetLastError();
-    G.chain_failed = true;
-  }
+  // the stage graphs become one chain at the first refactorization (a one-off
+  // factorization never pays for it)
   stamp();
   return SPAND_OK;
 }

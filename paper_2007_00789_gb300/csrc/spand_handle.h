@@ -197,7 +197,7 @@ struct Prof {
                 p.tag, ms, p.flops, p.bytes);
       stat[p.kind].launches += 1;
       stat[p.kind].total_ms += ms;
-      if (p.kind == KK_RRQR) rrqr_tag_ms[p.tag] += ms;
+      if (p.kind == KK_RRQR) rrqr_tag_ms[p.tag % 100] += ms;  // by base bucket
       stat[p.kind].flops += p.flops;
       stat[p.kind].bytes += p.bytes;
     }

@@ -1412,6 +1412,7 @@ __device__ __forceinline__ void reflector_scalars(real_t alpha, real_t nsq, int 
         out[1] = q;
       } else {
         out[2] = q;
+        out[3] = alpha - beta;  // the pivot-row entry of the unscaled reflector
       }
     }
   }
@@ -2087,7 +2088,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   extern __shared__ real_t sm[];
   __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
-  __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
+  __shared__ real_t s_refl[4];  // beta, tau, 1/(alpha - beta), alpha - beta, formed by warp 0
   __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256 or 512
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
@@ -2106,7 +2107,6 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   int* memb = segid + ncl;                             // ncl: columns recomputed this step
   int* segoff = memb + ncl;                            // nseg + 1
   __shared__ unsigned long long s_lb[kQrcMaxThreads / kWarp];
-  __shared__ int s_nmem;
   const double gam = 1.01 * (m + 2) * kU64, cst = (8.0 * m + 64.0) * kU64;
   if (tid == 0) {
     int acc = 0;
@@ -2210,9 +2210,12 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     // below the pivot row) by warps 1.. from here on, through the decisions,
     // becomes v in every CTA; warp 0 forms the reflector scalars meanwhile (a
     // long dependent FP64 sequence).  v is not read before the next barrier.
+    // v holds the reflector unscaled: x below the pivot row (read here) and
+    // alpha - beta at it (written by warp 0 with the scalars); the scale
+    // 1/(alpha - beta) enters the update's coefficient instead
     const int pt = tid - kWarp, pn = nthr - kWarp;
     if (warp > 0)
-      for (int i = step + pt; i < m; i += pn) v[i] = pc[(size_t)i * ncl];
+      for (int i = step + 1 + pt; i < m; i += pn) v[i] = pc[(size_t)i * ncl];
     // FP64 storage: the decisions take the norms as they are (the FP32
     // kernel's FP64 recomputation near the thresholds has no counterpart here)
     constexpr bool near = false;
@@ -2246,18 +2249,17 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       flags |= qr_step_flags(near, bk, gb.second, nu64, T1, T2, F1, F2, f1lo, f1hi, f2lo, f2hi, superfine);
     if (superfine && lt2) break;
     const real_t nsq = near ? (real_t)nu64 : QK::rval(bk);
-    if (warp == 0) reflector_scalars(gb.alpha, nsq, lane, s_refl);
-    __syncthreads();  // s_refl, written by warp 0
+    if (warp == 0) {
+      reflector_scalars(gb.alpha, nsq, lane, s_refl);
+      __syncwarp();
+      if (lane == 0) v[step] = s_refl[3];
+    }
+    __syncthreads();  // s_refl and v[step], written by warp 0; v below it by warps 1..
     const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
     const bool own = crank == owner;
-    if (warp > 0)
-      for (int i = step + pt; i < m; i += pn) {  // the rows this thread read
-        const real_t vi = (i == step) ? (real_t)1 : v[i] * inv;
-        v[i] = vi;
-        if (own) t.V[i + (size_t)step * m] = vi;
-      }
-    if (own) {
-      for (int i = tid; i < step; i += nthr) t.V[i + (size_t)step * m] = 0;
+    if (own) {  // the stored reflector, scaled: 1 at the pivot row, zero above
+      for (int i = tid; i < m; i += nthr)
+        t.V[i + (size_t)step * m] = i < step ? (real_t)0 : i == step ? (real_t)1 : v[i] * inv;
       if (tid == 0) {
         t.tau[step] = tau;
         norms[lp] = -1;
@@ -2265,59 +2267,62 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       pend_l = lp;
       pend_step = step;
       pend_beta = beta;
+      __syncthreads();  // norms[lp] (the whole CTA skips the pivot column)
     }
-    if (tid == 0) s_nmem = 0;
-    __syncthreads();
+    // the update with the unscaled v: tau (v^T a) v = (tau inv^2) (x^T a) x
+    const real_t coef = tau * inv * inv;
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+    double lbm = 0.0;  // L: the largest lower bound d - B of the CTA's live columns
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
-      qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, tau, norms + l, errb + l, cst);
+      qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, coef, norms + l, errb + l, cst);
+      if (sl == 0) {
+        const double d = norms[l], e = errb[l];
+        lbm = fmax(lbm, d - (e + gam * (d + e)));
+      }
     }
     nsteps = step + 1;
-    __syncthreads();
-    // L: the largest lower bound d - B of the CTA's live columns
-    double lbm = 0.0;
-    for (int l = tid; l < nloc; l += nthr) {
-      const double d = norms[l];
-      if (d < 0.0) continue;
-      const double e = errb[l];
-      lbm = fmax(lbm, d - (e + gam * (d + e)));
-    }
     const unsigned long long lbk = warp_max((unsigned long long)QK::of(lbm));
     if (lane == 0) s_lb[warp] = lbk;
-    __syncthreads();
+    __syncthreads();  // every column updated, every warp's bound published
     unsigned long long Lk = 0;
     for (int w = 0; w < nw; ++w) Lk = max(Lk, s_lb[w]);
     const double Lthr = QK::val((qkey_t)Lk) * (1.0 - 4e-12);
-    // the columns that may hold the exact maximum (or a value within 1e-12 of it)
-    for (int l = tid; l < nloc; l += nthr) {
-      const double d = norms[l];
-      if (d < 0.0) continue;
-      const double e = errb[l];
-      if (d + (e + gam * (d + e)) >= Lthr) memb[atomicAdd(&s_nmem, 1)] = l;
-    }
-    __syncthreads();
-    // their norms recomputed exactly, one warp per column; they are the candidates
-    const int nm = s_nmem;
-    for (int q = warp; q < nm; q += nw) {
-      const int l = memb[q];
-      real_t s0 = 0, s1 = 0;
-      int i = step + 1 + lane;
-      for (; i + kWarp < m; i += 2 * kWarp) {
-        const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
-        s0 = fma(x0, x0, s0);
-        s1 = fma(x1, x1, s1);
+    // the columns that may hold the exact maximum (or a value within 1e-12 of
+    // it): warp w tests columns 32 (w + nw j) + lane and recomputes its own
+    // members' norms exactly, all lanes on one column; they are the candidates
+    for (int c0 = warp * kWarp; c0 < nloc; c0 += nw * kWarp) {
+      const int lc = c0 + lane;
+      bool mem = false;
+      if (lc < nloc) {
+        const double d = norms[lc];
+        if (d >= 0.0) {
+          const double e = errb[lc];
+          mem = d + (e + gam * (d + e)) >= Lthr;
+        }
       }
-      if (i < m) {
-        const real_t x0 = A[(size_t)i * ncl + l];
-        s0 = fma(x0, x0, s0);
-      }
-      const real_t s2 = warp_sum(s0 + s1);
-      if (lane == 0) {
-        norms[l] = s2;
-        errb[l] = gam * s2;
-        QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? A[(size_t)(step + 1) * ncl + l] : (real_t)0, g0 + l};
-        slot_merge(mine, c);
+      unsigned bal = __ballot_sync(0xffffffffu, mem);
+      while (bal) {
+        const int l = c0 + __ffs(bal) - 1;
+        bal &= bal - 1;
+        real_t s0 = 0, s1 = 0;
+        int i = step + 1 + lane;
+        for (; i + kWarp < m; i += 2 * kWarp) {
+          const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
+          s0 = fma(x0, x0, s0);
+          s1 = fma(x1, x1, s1);
+        }
+        if (i < m) {
+          const real_t x0 = A[(size_t)i * ncl + l];
+          s0 = fma(x0, x0, s0);
+        }
+        const real_t s2 = warp_sum(s0 + s1);
+        if (lane == 0) {
+          norms[l] = s2;
+          errb[l] = gam * s2;
+          QrSlot c{QK::of(s2), kNoKey, step + 1 < m ? A[(size_t)(step + 1) * ncl + l] : (real_t)0, g0 + l};
+          slot_merge(mine, c);
+        }
       }
     }
   }
