@@ -686,7 +686,7 @@ def main():
                     "relres": rel, "mu": info["mu"], "skip": info["skip"],
                     "parallelism": f"replicas x{world}", "cuda_graphs": not args.plain_launches,
                     "rrqr_kernel": args.rrqr_kernel, "rrqr_threads": args.rrqr_threads,
-                    "rrqr_tuned": {str(k): v for k, v in tuned.items()} if tuned else None},
+                    "tuned": {str(k): v for k, v in tuned.items()} if tuned else None},
         "clocks": clk.summary(),
         "variant": variant,
         "e2e": e2e,

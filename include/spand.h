@@ -100,6 +100,9 @@ typedef struct {
                              TF32 with a head/tail split of each operand (about FP32 accuracy),
                              the others on the FP32 pipe (the default); 1 = all on the FP32
                              pipe.  FP64 factorizations never use the tensor cores. */
+  int32_t apply_kernels;  /* 0 = a single-vector apply (spand_apply, spand_pcg) is one persistent
+                             cooperative launch that walks every phase of the sweep (the
+                             default); 1 = one launch per phase, as the multi-vector forms. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */
@@ -162,10 +165,14 @@ int spand_factor(spand_t h, void* stream);
  * stream, keeps the fastest shape of every bucket, and factors once more with
  * it (graphs captured), leaving the handle factored as spand_factor does.  The
  * handle keeps the choices for later factorizations (also inside a batch).
- * The shapes change only the order of some floating-point sums.
- *   choice -- host, may be NULL: 10 int32, the chosen CTA size and cluster
- *             growth of buckets 1..5 (0 where no interface fell in a bucket).
- * Costs five factorizations.  Errors: those of spand_factor. */
+ * Then it times the two forms of the single-vector apply (spand_opts.
+ * apply_kernels: one persistent launch, or one launch per phase) and keeps the
+ * faster.  The choices change only the order of some floating-point sums.
+ *   choice -- host, may be NULL: 12 int32: the chosen CTA size and cluster
+ *             growth of buckets 1..5 (0 where no interface fell in a bucket),
+ *             then the apply form (0 persistent, 1 per phase) and a zero.
+ * Costs five factorizations and a few applies.  Errors: those of
+ * spand_factor. */
 int spand_tune(spand_t h, void* stream, int32_t* choice);
 
 /* Testing hook for the one bounded device-side wait of the factorization:

@@ -83,6 +83,18 @@ int ensure_pcg(spand_s* h) {
 }
 
 // scal slots: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
+// The abort word of the persistent apply (a grid barrier that ran out of
+// polls): reported as SPAND_ETIMEOUT by the next PCG, and cleared.
+int sweep_status(spand_s* h, cudaStream_t s) {
+  if (!h->sweep_valid || !h->sweep_ws) return SPAND_OK;
+  int ab = 0;
+  CK(cudaMemcpyAsync(&ab, h->sweep_ws + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!ab) return SPAND_OK;
+  CK(cudaMemsetAsync(h->sweep_ws + 1, 0, sizeof(int), s));
+  return fail(SPAND_ETIMEOUT, "a grid barrier of the preconditioner sweep timed out");
+}
+
 int pcg_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters, double* relres,
              cudaStream_t s) {
   if (!h->factored) return fail(SPAND_ESTATE, "spand_pcg before a successful spand_factor");
@@ -152,6 +164,7 @@ int pcg_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters,
   }
   CK(cudaGetLastError());
   if (rel >= tol && it >= h->maxit) rc = fail(SPAND_ENOCONV, "PCG reached maxit");
+  RET(sweep_status(h, s));
   if (iters) *iters = it;
   if (relres) *relres = rel;
   h->pcg_iters = it;
@@ -271,6 +284,9 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   h->prescale = opts && opts->prescale == 1;
   if (opts && (opts->schur_simt < 0 || opts->schur_simt > 1)) return fail(SPAND_EINVAL, "schur_simt must be 0 or 1");
   h->schur_simt = opts && opts->schur_simt == 1;
+  if (opts && (opts->apply_kernels < 0 || opts->apply_kernels > 1))
+    return fail(SPAND_EINVAL, "apply_kernels must be 0 or 1");
+  h->sweep_off = opts && opts->apply_kernels == 1;
   if (algebraic) h->dim = 0;
   int rc = algebraic ? build_tree_graph(A->rowptr, A->colind, A->n, nlevels, h->tree, err)
                      : build_tree(coords, A->n, dim, nlevels, h->tree, err);
@@ -436,11 +452,44 @@ int spand_tune(spand_t h, void* stream, int32_t* choice) {
     h->factored = false;
     return fail(SPAND_ENOMEM, "host allocation failed");
   }
-  if (choice)
+  // the single-vector apply: one persistent launch or one launch per phase,
+  // whichever is faster on this problem (timed on the handle's own vectors)
+  int apply_choice = h->sweep_valid ? 0 : 1;
+  if (h->sweep_valid) {
+    RET(ensure_pcg(h));
+    double* r = h->d_r;
+    double* z = h->d_z;
+    CK(cudaMemsetAsync(r, 0, (size_t)h->n * sizeof(double), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    int rc = SPAND_OK;
+    for (int v = 0; v < 2 && rc == SPAND_OK; ++v) {
+      h->sweep_valid = (v == 0);
+      for (int w = 0; w < 2 && rc == SPAND_OK; ++w) rc = apply_any(h, r, z, s);  // warm-up, graph capture
+      if (rc != SPAND_OK) break;
+      cudaEventRecord(e0, s);
+      for (int w = 0; w < 5 && rc == SPAND_OK; ++w) rc = apply_any(h, r, z, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(SPAND_ECUDA, "timing the apply forms");
+      cudaEventElapsedTime(&ms[v], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RET(rc);
+    apply_choice = ms[0] <= ms[1] ? 0 : 1;
+    h->sweep_valid = apply_choice == 0;
+    h->sweep_off = apply_choice == 1;  // later factorizations do not build the sweep
+  }
+  if (choice) {
     for (int b = 1; b <= 5; ++b) {
       choice[2 * (b - 1)] = best_thr[b];
       choice[2 * (b - 1) + 1] = best_grow[b];
     }
+    choice[10] = apply_choice;
+    choice[11] = 0;
+  }
   return SPAND_OK;
 }
 
@@ -713,6 +762,7 @@ int pcg_noalloc_impl(spand_s* h, const double* b, double* x, double tol, int32_t
     if (iters) *iters = it;
     if (relres) *relres = rel;
     if (rel >= tol && it >= h->maxit) return fail(SPAND_ENOCONV, "PCG reached maxit");
+    RET(sweep_status(h, s));
     return SPAND_OK;
   };
   const int rc = body();

@@ -33,6 +33,7 @@ struct ApInteriorP {
   const real_t* WT;
   int64_t slots, wslots;
   int m, ncols;
+  int dc;  // first column of the diagonal segment in the panel row
 };
 struct ApScaleP {
   const real_t* Zinv;
@@ -1034,6 +1035,7 @@ int finish_stage(Run& R, int k, const int* hp, Prof& P) {
       if (m > 0) RET(explicit_inverse(Ly.row[sidx] + (size_t)dc * m, m, &Linv));
       a.Linv = Linv;
       a.WT = Ly.row[sidx];
+      a.dc = dc;
       a.slots = Ly.slot_off[sidx];
       a.wslots = (int64_t)pool.size();
       for (int d : S.rowsegs[sidx]) {
@@ -1186,6 +1188,186 @@ int upload_apply_plan(Run& R, cudaStream_t s) {
   h->d_apq = pq;
   h->phases = R.phases;
   h->nnz_factor = R.nnzf;
+  return SPAND_OK;
+}
+
+// The program of the persistent single-vector sweep (k_ap_sweep), from the
+// problem's apply phases: per (stage, kind, colour) two sub-phases forward
+// and two backward (one for a scaling's copy back), items of about kSwItem
+// matrix entries.  Program, scratch vector and barrier words go into the
+// factor arena, so that applying allocates nothing.
+constexpr int kSwItem = 16384;
+
+int build_sweep(Run& R, cudaStream_t s) {
+  spand_s* h = R.h;
+  h->sweep_valid = false;
+  if (h->sweep_off) return SPAND_OK;
+  struct Grp {
+    int stage, kind, colour;
+    std::vector<std::pair<int, int>> ranges;
+  };
+  std::vector<Grp> groups;
+  for (const Phase& ph : R.phases) {
+    if (!groups.empty() && groups.back().stage == ph.stage && groups.back().kind == ph.kind &&
+        groups.back().colour == ph.colour)
+      groups.back().ranges.push_back({ph.begin, ph.end});
+    else
+      groups.push_back({ph.stage, ph.kind, ph.colour, {{ph.begin, ph.end}}});
+  }
+  std::vector<SwPhase> P;
+  std::vector<SwItem> I;
+  int max_vec = 1;
+  auto phase = [&](int kind, auto&& gen) {
+    SwPhase p{kind, (int)I.size(), 0, 0};
+    gen();
+    p.nitems = (int)I.size() - p.item0;
+    if (p.nitems) P.push_back(p);
+  };
+  // row blocks of a GEMV over C columns (multiples of 64 rows), column blocks
+  // of a transposed one over R rows (multiples of 4 columns)
+  auto rows = [&](int op, int m, int C, int aux) {
+    const int step = 64 * std::max(1, kSwItem / (64 * std::max(C, 1)));
+    for (int lo = 0; lo < m; lo += step) I.push_back({op, lo, std::min(m, lo + step), aux});
+  };
+  auto cols = [&](int op, int c0, int c1, int Rr, int& aux) {
+    const int step = 4 * std::max(1, kSwItem / (4 * std::max(Rr, 1)));
+    for (int lo = c0; lo < c1; lo += step) {
+      I.push_back({op, lo, std::min(c1, lo + step), aux});
+      aux = 0;
+    }
+  };
+  auto each = [&](const Grp& g, auto&& f) {
+    for (auto& rg : g.ranges)
+      for (int i = rg.first; i < rg.second; ++i) f(i);
+  };
+  for (const Grp& g : groups) {
+    if (g.kind == PH_INTERIOR) {
+      phase(SW_FI_A, [&] {
+        each(g, [&](int i) {
+          max_vec = std::max(max_vec, R.api[i].m);
+          if (R.api[i].m) rows(i, R.api[i].m, R.api[i].m / 2 + 1, 0);
+        });
+      });
+      phase(SW_FI_B, [&] {
+        each(g, [&](int i) {
+          const auto& a = R.api[i];
+          if (!a.m) return;
+          max_vec = std::max(max_vec, a.m);
+          int aux = 1;
+          cols(i, 0, a.dc, a.m, aux);
+          cols(i, a.dc + a.m, a.ncols, a.m, aux);
+          if (aux) I.push_back({i, 0, 0, 1});  // no neighbour: the copy alone
+        });
+      });
+    } else if (g.kind == PH_SCALE) {
+      phase(SW_FS_A, [&] {
+        each(g, [&](int i) {
+          max_vec = std::max(max_vec, R.aps[i].m);
+          if (R.aps[i].m) rows(i, R.aps[i].m, R.aps[i].m / 2 + 1, 0);
+        });
+      });
+      phase(SW_COPY, [&] {
+        each(g, [&](int i) {
+          for (int lo = 0; lo < R.aps[i].m; lo += 4096) I.push_back({i, lo, std::min(R.aps[i].m, lo + 4096), 0});
+        });
+      });
+    } else {
+      phase(SW_FQ_A, [&] {
+        each(g, [&](int i) {
+          max_vec = std::max(max_vec, R.apq[i].m);
+          if (R.apq[i].m) rows(i, R.apq[i].m, R.apq[i].m, 0);
+        });
+      });
+      phase(SW_FQ_B, [&] {
+        each(g, [&](int i) {
+          const auto& a = R.apq[i];
+          if (!a.m) return;
+          max_vec = std::max(max_vec, a.m);
+          if (a.nE > 0 && a.ncols > 0) {
+            const int step = 256 * std::max(1, kSwItem / (256 * a.nE));
+            for (int lo = 0; lo < a.ncols; lo += step) I.push_back({i, lo, std::min(a.ncols, lo + step), lo == 0});
+          } else {
+            I.push_back({i, 0, 0, 1});
+          }
+        });
+      });
+    }
+  }
+  for (auto gi = groups.rbegin(); gi != groups.rend(); ++gi) {
+    const Grp& g = *gi;
+    if (g.kind == PH_QE) {
+      phase(SW_BQ_A, [&] {
+        each(g, [&](int i) {
+          const auto& a = R.apq[i];
+          if (!a.m) return;
+          max_vec = std::max(max_vec, a.ncols);
+          int aux = 1;
+          if (a.nE > 0 && a.ncols > 0) cols(i, 0, a.nE, a.ncols, aux);
+          if (aux) I.push_back({i, 0, 0, 1});
+        });
+      });
+      phase(SW_BQ_B, [&] {
+        each(g, [&](int i) {
+          int aux = 0;
+          if (R.apq[i].m) cols(i, 0, R.apq[i].m, R.apq[i].m, aux);
+        });
+      });
+    } else if (g.kind == PH_SCALE) {
+      phase(SW_BS_A, [&] {
+        each(g, [&](int i) {
+          int aux = 0;
+          if (R.aps[i].m) cols(i, 0, R.aps[i].m, R.aps[i].m / 2 + 1, aux);
+        });
+      });
+      phase(SW_COPY, [&] {
+        each(g, [&](int i) {
+          for (int lo = 0; lo < R.aps[i].m; lo += 4096) I.push_back({i, lo, std::min(R.aps[i].m, lo + 4096), 0});
+        });
+      });
+    } else {
+      phase(SW_BI_A, [&] {
+        each(g, [&](int i) {
+          const auto& a = R.api[i];
+          if (!a.m) return;
+          max_vec = std::max(max_vec, a.ncols);
+          rows(i, a.m, std::max(a.ncols - a.m, 1), a.dc);
+        });
+      });
+      phase(SW_BI_B, [&] {
+        each(g, [&](int i) {
+          int aux = 0;
+          if (R.api[i].m) cols(i, 0, R.api[i].m, R.api[i].m / 2 + 1, aux);
+        });
+      });
+    }
+  }
+  const int smem = (max_vec + 16) * (int)sizeof(real_t);
+  const int nctas = sweep_ctas(smem);
+  if (nctas <= 0 || P.empty()) return SPAND_OK;  // the per-phase launches stay in use
+  void *pp = nullptr, *pi = nullptr, *py = nullptr, *pw = nullptr;
+  RET(h->farena.alloc(P.size() * sizeof(SwPhase), &pp));
+  RET(h->farena.alloc(std::max<size_t>(I.size(), 1) * sizeof(SwItem), &pi));
+  RET(h->farena.alloc(std::max<size_t>((size_t)h->n, 1) * sizeof(real_t), &py));
+  RET(h->farena.alloc(16, &pw));
+  CK(cudaMemcpyAsync(pp, P.data(), P.size() * sizeof(SwPhase), cudaMemcpyHostToDevice, s));
+  if (!I.empty()) CK(cudaMemcpyAsync(pi, I.data(), I.size() * sizeof(SwItem), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(pw, 0, 16, s));
+  CK(cudaStreamSynchronize(s));  // the host tables must outlive the copies
+  h->sweep_phases = pp;
+  h->sweep_items = pi;
+  h->sweep_y = py;
+  h->sweep_ws = (int*)pw;
+  h->sweep_nph = (int)P.size();
+  h->sweep_ctas = nctas;
+  h->sweep_smem = smem;
+  double fl = 0.0, by = 0.0;
+  for (const Phase& ph : R.phases) {
+    fl += 2.0 * ph.flops;
+    by += 2.0 * ph.bytes;
+  }
+  h->sweep_flops = fl;
+  h->sweep_bytes = by;
+  h->sweep_valid = true;
   return SPAND_OK;
 }
 
@@ -1614,6 +1796,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
   if (P.on) P.resolve();
   for (int i = 0; i < count; ++i) {
     RET(upload_apply_plan(runs[i], s));
+    RET(build_sweep(runs[i], s));
     hs[i]->launches = launches;
     hs[i]->factored = true;
     // the plan of the problem's own apply, so that applying allocates nothing
@@ -1642,6 +1825,17 @@ int factor(spand_s* h, cudaStream_t s) { return factor_group(&h, 1, h->fg, h->pr
 int apply(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
   if (r != z)
     h->prof.run(KK_VEC, s, 0.0, 2.0 * sizeof(real_t) * h->n, [&] { launch_copy_real(h->n, r, z, s); });
+  if (h->sweep_valid) {  // the whole sweep as one persistent launch
+    cudaError_t e = cudaSuccess;
+    h->prof.run(KK_AP_SWEEP, s, h->sweep_flops, h->sweep_bytes, [&] {
+      e = launch_ap_sweep((const SwPhase*)h->sweep_phases, h->sweep_nph,
+                          (const SwItem*)h->sweep_items, (const ApInterior*)h->d_api,
+                          (const ApScale*)h->d_aps, (const ApQE*)h->d_apq, z, (real_t*)h->sweep_y,
+                          h->sweep_ws, h->sweep_ctas, h->sweep_smem, spand_s::kSweepWait, s);
+    });
+    if (e != cudaSuccess) return fail(SPAND_ECUDA, std::string("apply sweep launch: ") + cudaGetErrorString(e));
+    return SPAND_OK;
+  }
   ApSeg seg{h, 0};
   return apply_multi(&seg, 1, z, h->self_ma, h->prof, !h->no_graph, s);
 }

@@ -413,6 +413,182 @@ __global__ void AP_BOUNDS
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole preconditioner sweep of one problem and one right-hand side as
+// one persistent cooperative launch.  The sweep is a list of sub-phases; a
+// sub-phase is a list of items -- one operator and a range of its rows or
+// columns -- that the CTAs take in turn, and a grid-wide barrier separates
+// dependent sub-phases.  An operator too large for one CTA is thereby spread
+// over as many CTAs as its size asks for (a thread-block cluster holds at most
+// 16), and a stage's few large operators no longer leave most SMs idle.  Where
+// an operator's product needs all of an intermediate vector (y = L^{-1} x
+// before the W_s update, y = Q^T x before the E-tilde one, ...), the
+// intermediate goes to the scratch vector Y at the operator's own slots (the
+// slots of the operators of one sub-phase are disjoint) and the next
+// sub-phase reads it there.  Reads of z and Y go through L2 (__ldcg): they
+// were written by other SMs before the barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool sweep_barrier(int* ctr, int* abort, int target, long long limit) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(ctr, 1);
+    int ok = 1;
+    long long it = 0;
+    while (*(volatile int*)ctr < target) {
+      if (*(volatile int*)abort) {
+        ok = 0;
+        break;
+      }
+      if (++it > limit) {
+        atomicExch(abort, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kApThreads, 2)
+    k_ap_sweep(const SwPhase* __restrict__ phases, int nph, const SwItem* __restrict__ items,
+               const ApInterior* __restrict__ api, const ApScale* __restrict__ aps,
+               const ApQE* __restrict__ apq, real_t* __restrict__ z, real_t* __restrict__ Y,
+               int* ctr, int* abort, long long limit) {
+  extern __shared__ real_t sh[];
+  __shared__ real_t red[2 * kApThreads];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto ld = [](const real_t* p) { return __ldcg(p); };
+  for (int ph = 0; ph < nph; ++ph) {
+    const SwPhase P = phases[ph];
+    for (int q = blockIdx.x; q < P.nitems; q += gridDim.x) {
+      const SwItem it = items[P.item0 + q];
+      switch (P.kind) {
+        case SW_FI_A: {  // rows of y = L_s^{-1} x_s into Y
+          const ApInterior t = api[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(z + t.slots[i]);
+          __syncthreads();
+          gemv_n<1>(t.Linv, m, it.lo, it.hi, [&](int rt) { return min(m, rt + 64); }, sh, m, red,
+                    [&](int r, int, real_t v) { Y[t.slots[r]] = v; });
+          break;
+        }
+        case SW_FI_B: {  // z_s = y; z_w -= W_s y over a range of neighbour columns
+          const ApInterior t = api[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(Y + t.slots[i]);
+          __syncthreads();
+          if (it.aux)
+            for (int i = tid; i < m; i += nt) z[t.slots[i]] = sh[i];
+          gemv_t<1>(t.WT, m, it.lo, it.hi, m, [](int) { return 0; }, sh, m, red,
+                    [&](int c, int, real_t v) {
+                      const int ws = t.wslots[c];
+                      if (ws >= 0) atomicAdd(z + ws, -v);
+                    });
+          break;
+        }
+        case SW_FS_A: {  // rows of Z_p^{-1} x_p into Y
+          const ApScale t = aps[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(z + t.slots[i]);
+          __syncthreads();
+          gemv_n<1>(t.Zinv, m, it.lo, it.hi, [&](int rt) { return min(m, rt + 64); }, sh, m, red,
+                    [&](int r, int, real_t v) { Y[t.slots[r]] = v; });
+          break;
+        }
+        case SW_COPY: {  // z = Y on a scaling's slots
+          const ApScale t = aps[it.op];
+          for (int i = it.lo + tid; i < it.hi; i += nt) z[t.slots[i]] = ld(Y + t.slots[i]);
+          break;
+        }
+        case SW_FQ_A: {  // rows of y = Q_p^T x_p into Y
+          const ApQE t = apq[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(z + t.slots[i]);
+          __syncthreads();
+          gemv_n<1>(t.Qt, m, it.lo, it.hi, [&](int) { return m; }, sh, m, red,
+                    [&](int r, int, real_t v) { Y[t.slots[r]] = v; });
+          break;
+        }
+        case SW_FQ_B: {  // z_p = y; z_w -= E-tilde^T y_f over a range of neighbour columns
+          const ApQE t = apq[it.op];
+          for (int i = tid; i < t.nE; i += nt) sh[i] = ld(Y + t.slots[t.r + i]);
+          if (it.aux)
+            for (int i = tid; i < t.m; i += nt) z[t.slots[i]] = ld(Y + t.slots[i]);
+          __syncthreads();
+          if (t.nE > 0)
+            gemv_rows<1>(t.E, t.ncols, it.lo, it.hi, t.nE, sh, 0,
+                         [&](int c, int, real_t v) { atomicAdd(z + t.eslots[c], -v); });
+          break;
+        }
+        case SW_BQ_A: {  // y_f = x_f - E-tilde z_w over a range of fine rows, the rest copied, into Y
+          const ApQE t = apq[it.op];
+          const int nc = t.ncols;
+          for (int c = tid; c < nc && t.nE > 0; c += nt) sh[c] = ld(z + t.eslots[c]);
+          if (it.aux)
+            for (int i = tid; i < t.m; i += nt)
+              if (i < t.r || i >= t.r + t.nE) Y[t.slots[i]] = ld(z + t.slots[i]);
+          __syncthreads();
+          gemv_t<1>(t.E, nc, it.lo, it.hi, nc, [](int) { return 0; }, sh, nc, red,
+                    [&](int i, int, real_t v) { Y[t.slots[t.r + i]] = ld(z + t.slots[t.r + i]) - v; });
+          break;
+        }
+        case SW_BQ_B: {  // z_p = Q y over a range of output rows (columns of Q^T)
+          const ApQE t = apq[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(Y + t.slots[i]);
+          __syncthreads();
+          gemv_t<1>(t.Qt, m, it.lo, it.hi, m, [](int) { return 0; }, sh, m, red,
+                    [&](int j, int, real_t v) { z[t.slots[j]] = v; });
+          break;
+        }
+        case SW_BS_A: {  // Z_p^{-T} x_p over a range of outputs, into Y
+          const ApScale t = aps[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(z + t.slots[i]);
+          __syncthreads();
+          gemv_t<1>(t.Zinv, m, it.lo, it.hi, m, [](int c) { return c; }, sh, m, red,
+                    [&](int j, int, real_t v) { Y[t.slots[j]] = v; });
+          break;
+        }
+        case SW_BI_A: {  // rows of y = x_s - W_s^T z_w into Y (the diagonal segment skipped)
+          const ApInterior t = api[it.op];
+          const int m = t.m, nc = t.ncols, dc = it.aux;
+          for (int c = tid; c < nc; c += nt) {
+            const int ws = t.wslots[c];
+            sh[c] = ws >= 0 ? ld(z + ws) : (real_t)0;
+          }
+          __syncthreads();
+          gemv_n<1>(t.WT, m, it.lo, it.hi, [&](int) { return dc; }, sh, nc, red,
+                    [&](int r, int, real_t v) { Y[t.slots[r]] = ld(z + t.slots[r]) - v; });
+          const int c1 = dc + m;
+          gemv_n<1>(t.WT + (size_t)c1 * m, m, it.lo, it.hi, [&](int) { return nc - c1; }, sh + c1,
+                    nc, red, [&](int r, int, real_t v) { Y[t.slots[r]] -= v; });
+          break;
+        }
+        case SW_BI_B: {  // z_s = L_s^{-T} y over a range of outputs
+          const ApInterior t = api[it.op];
+          const int m = t.m;
+          for (int i = tid; i < m; i += nt) sh[i] = ld(Y + t.slots[i]);
+          __syncthreads();
+          gemv_t<1>(t.Linv, m, it.lo, it.hi, m, [](int c) { return c; }, sh, m, red,
+                    [&](int j, int, real_t v) { z[t.slots[j]] = v; });
+          break;
+        }
+        default:
+          break;
+      }
+      __syncthreads();  // the shared vectors are refilled by the next item
+    }
+    if (ph + 1 < nph && !sweep_barrier(ctr, abort, (ph + 1) * (int)gridDim.x, limit)) return;
+  }
+}
+
 }  // namespace
 
 // The dynamic shared memory a launch may use beyond the 48 KB default must be
@@ -478,6 +654,39 @@ static ApKernel pick(int nv) {
 template <int NV> struct PickInterior { static constexpr ApKernel k = k_ap_interior<NV>; };
 template <int NV> struct PickScale { static constexpr ApKernel k = k_ap_scale<NV>; };
 template <int NV> struct PickQE { static constexpr ApKernel k = k_ap_qe<NV>; };
+
+int sweep_ctas(int smem_bytes) {
+  if (grant_smem((const void*)k_ap_sweep, smem_bytes) != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ap_sweep, kApThreads, smem_bytes) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per;
+}
+
+cudaError_t launch_ap_sweep(const SwPhase* phases, int nph, const SwItem* items,
+                            const ApInterior* api, const ApScale* aps, const ApQE* apq, real_t* z,
+                            real_t* Y, int* ws, int nctas, int smem_bytes, long long limit,
+                            cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), s);  // the barrier counter
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nctas);
+  cfg.blockDim = dim3(kApThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident, or the launch fails
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_ap_sweep, phases, nph, items, api, aps, apq, z, Y, ws, ws + 1,
+                            limit);
+}
 
 void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,
                         int max_cols, int max_nvec, real_t* z, bool forward, cudaStream_t s) {

@@ -130,12 +130,12 @@ struct Blob {
 enum KernelKind {
   KK_PACK, KK_MERGE, KK_POTRF, KK_TRSM, KK_SCHUR, KK_SCALE_POTRF, KK_SCALE_TRSM, KK_SCALE_COPY,
   KK_RRQR, KK_ECOPY, KK_TRTRI, KK_FORMQ, KK_AP_INTERIOR, KK_AP_SCALE, KK_AP_QE, KK_SPMV, KK_DOT,
-  KK_VEC, KK_RRQR_GRID, KK_SCHUR_TC, KK_COUNT
+  KK_VEC, KK_RRQR_GRID, KK_SCHUR_TC, KK_AP_SWEEP, KK_COUNT
 };
 static const char* const kKindName[KK_COUNT] = {
     "pack", "merge", "potrf", "trsm", "schur", "scale_potrf", "scale_trsm", "scale_copy",
     "rrqr", "e_copy", "trtri", "form_qt", "apply_interior", "apply_scale", "apply_qe", "spmv",
-    "dot", "vector", "rrqr_grid", "schur_tc"};
+    "dot", "vector", "rrqr_grid", "schur_tc", "apply_sweep"};
 
 struct Prof {
   bool on = false;
@@ -455,6 +455,15 @@ struct spand_s {
   int tune_thr[6] = {0, 0, 0, 0, 0, 0};
   int tune_grow[6] = {0, 0, 0, 0, 0, 0};
   bool tuning = false;  // inside spand_tune: RRQR launches split by base bucket
+  // the persistent single-vector apply (k_ap_sweep): its program, scratch
+  // vector and barrier words (factor arena), launch shape and work
+  bool sweep_off = false;  // spand_opts.apply_kernels = 1: the per-phase launches
+  bool sweep_valid = false;
+  void *sweep_phases = nullptr, *sweep_items = nullptr, *sweep_y = nullptr;
+  int* sweep_ws = nullptr;
+  int sweep_nph = 0, sweep_ctas = 0, sweep_smem = 0;
+  double sweep_flops = 0.0, sweep_bytes = 0.0;
+  static constexpr long long kSweepWait = 1LL << 25;  // polls per barrier, a second or so
   int cluster_state[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};  // per precision
   spand::Engine* eng = nullptr;  // multi-RHS apply and PCG of this problem (created on first use)
   spand::FactorGroup fg;      // stage graphs of this problem factored on its own

@@ -201,6 +201,29 @@ int rrqr_gsm_smem_bytes(int m, int cpb, int nseg);
 cudaError_t launch_rrqr_gsm(const RRQRGridTask* t, int ntasks, int nctas, const RRQRSeg* segs,
                             int smem_bytes, cudaStream_t s);
 
+// The persistent single-vector sweep (k_ap_sweep): sub-phases of items, each
+// item one operator (index into the descriptor array of its kind) and a range
+// [lo, hi) of its rows or columns; aux: per kind (SW_FI_B, SW_FQ_B, SW_BQ_A: 1
+// if the item also copies the operator's vector; SW_BI_A: the first column of
+// the diagonal segment of the panel row).
+enum SweepKind {
+  SW_FI_A = 0, SW_FI_B, SW_FS_A, SW_COPY, SW_FQ_A, SW_FQ_B, SW_BQ_A, SW_BQ_B, SW_BS_A, SW_BI_A,
+  SW_BI_B
+};
+struct SwPhase {
+  int kind, item0, nitems, pad;
+};
+struct SwItem {
+  int op, lo, hi, aux;
+};
+// CTAs of one cooperative sweep launch (all resident) for this shared memory; 0 if none.
+int sweep_ctas(int smem_bytes);
+// ws: 2 ints (barrier counter, abort flag); the counter is cleared by the launch.
+cudaError_t launch_ap_sweep(const SwPhase* phases, int nph, const SwItem* items,
+                            const ApInterior* api, const ApScale* aps, const ApQE* apq, real_t* z,
+                            real_t* Y, int* ws, int nctas, int smem_bytes, long long limit,
+                            cudaStream_t s);
+
 // K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
 // over all nitems items (device array); max_nvec: the most vectors of an item.
 void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,

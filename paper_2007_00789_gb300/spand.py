@@ -58,7 +58,7 @@ class _Opts(ctypes.Structure):
                 ("rrqr_kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("plain_launches", ctypes.c_int32), ("rrqr_threads", ctypes.c_int32),
                 ("partition", ctypes.c_int32), ("prescale", ctypes.c_int32),
-                ("schur_simt", ctypes.c_int32)]
+                ("schur_simt", ctypes.c_int32), ("apply_kernels", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -186,7 +186,7 @@ class Spand:
                  skip: int | None = None, maxit: int | None = None, true_res_every: int | None = None,
                  max_restarts: int | None = None, rrqr_kernel: int = 0, precision: int = 0,
                  plain_launches: bool = False, rrqr_threads: int = 0, partition: int = 0,
-                 prescale: bool = False, schur_simt: bool = False):
+                 prescale: bool = False, schur_simt: bool = False, apply_kernels: int = 0):
         """coords None (or partition=1): algebraic nested dissection of A's graph;
         prescale: factor D^{-1/2} A D^{-1/2} and precondition with D^{-1/2} M~ D^{-1/2}."""
         L = load_library()
@@ -206,7 +206,8 @@ class Spand:
                      0 if true_res_every is None else int(true_res_every),
                      -1 if max_restarts is None else int(max_restarts), int(rrqr_kernel),
                      int(precision), 1 if plain_launches else 0, int(rrqr_threads),
-                     int(partition), 1 if prescale else 0, 1 if schur_simt else 0)
+                     int(partition), 1 if prescale else 0, 1 if schur_simt else 0,
+                     int(apply_kernels))
         h = ctypes.c_void_p()
         cptr = None if coords is None else coords.ctypes.data
         cdim = 0 if coords is None else coords.shape[1]
@@ -234,11 +235,14 @@ class Spand:
         _check(self._lib.spand_factor(self._h, _stream_ptr(stream)))
 
     def tune(self, stream=None) -> dict:
-        """spand_tune: the fastest RRQR launch shape per size bucket; leaves the handle factored.
-        Returns {bucket: (threads per CTA, cluster growth)} for the buckets that occurred."""
-        ch = np.zeros(10, dtype=np.int32)
+        """spand_tune: the fastest RRQR launch shape per size bucket and the faster apply form;
+        leaves the handle factored.  Returns {bucket: (threads per CTA, cluster growth)} for the
+        buckets that occurred and {"apply": "persistent" | "per_phase"}."""
+        ch = np.zeros(12, dtype=np.int32)
         _check(self._lib.spand_tune(self._h, _stream_ptr(stream), ch.ctypes.data))
-        return {b + 1: (int(ch[2 * b]), int(ch[2 * b + 1])) for b in range(5) if ch[2 * b]}
+        out = {b + 1: (int(ch[2 * b]), int(ch[2 * b + 1])) for b in range(5) if ch[2 * b]}
+        out["apply"] = "persistent" if ch[10] == 0 else "per_phase"
+        return out
 
     def test_set_qr_wait(self, limit: int = 0, unreachable: bool = False):
         """Testing hook of the multi-CTA RRQR's bounded barrier wait (spand_test_set_qr_wait)."""

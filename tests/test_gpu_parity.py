@@ -301,3 +301,33 @@ def test_refactor_is_deterministic():
     # the factor is bitwise reproducible; the apply accumulates with atomics
     assert np.abs(z1 - z2).max() <= 1e-13 * np.abs(z1).max()
     h.close()
+
+
+@pytest.mark.parametrize("make,ell,scheme,precision", [
+    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 0),
+    (lambda: si.laplacian_2d(64), 6, 2, 0),
+    (lambda: si.diffusion_grid((23, 17, 11), seed=5, lo=-2, hi=2), 7, 0, 0),
+    (lambda: si.diffusion_3d(32, seed=6), 9, 1, 1),
+])
+def test_persistent_apply_equals_per_phase_launches(make, ell, scheme, precision):
+    """The single-vector apply as one persistent launch (the default) and as
+    one launch per phase (apply_kernels = 1) apply the same operators: M r
+    equal up to the order of the sums, and the same PCG iterations."""
+    torch = _torch()
+    from paper_2007_00789_gb300 import spand as S
+    prob = make()
+    a = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=precision)
+    b = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=precision, apply_kernels=1)
+    a.factor()
+    b.factor()
+    r = np.random.default_rng(8).standard_normal(prob.n)
+    za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
+    err = np.abs(za - zb).max() / np.abs(zb).max()
+    assert err <= (1e-12 if precision == 0 else 1e-5), err
+    rhs = torch.from_numpy(si.rhs_normal(prob.n, seed=9)).cuda()
+    xa, xb = torch.zeros_like(rhs), torch.zeros_like(rhs)
+    ita, rela = a.pcg(rhs, xa, 1e-12)
+    itb, _ = b.pcg(rhs, xb, 1e-12)
+    assert abs(ita - itb) <= 1 and rela <= 1e-12
+    a.close()
+    b.close()

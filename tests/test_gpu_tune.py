@@ -29,6 +29,7 @@ def test_tuned_shapes_reproduce_the_factorization(precision):
     choice = h.tune()
     print("tuned shapes per bucket:", choice)
     assert choice, "no interface fell in any cluster bucket"
+    assert choice.pop("apply") in ("persistent", "per_phase")
     for thr, grow in choice.values():
         assert thr in (256, 512) and grow in (1, 2)
     r = np.random.default_rng(2).standard_normal(prob.n)
