@@ -100,9 +100,11 @@ typedef struct {
                              TF32 with a head/tail split of each operand (about FP32 accuracy),
                              the others on the FP32 pipe (the default); 1 = all on the FP32
                              pipe.  FP64 factorizations never use the tensor cores. */
-  int32_t apply_kernels;  /* 0 = a single-vector apply (spand_apply, spand_pcg) is one persistent
-                             cooperative launch that walks every phase of the sweep (the
-                             default); 1 = one launch per phase, as the multi-vector forms. */
+  int32_t apply_kernels;  /* form of the single-vector apply (spand_apply, spand_pcg): 0 =
+                             automatic (the default: spand_tune's timed choice once it has
+                             run, before that the persistent form for n >= 2^21); 1 = one
+                             launch per phase, as the multi-vector forms; 2 = one persistent
+                             cooperative launch that walks every phase of the sweep. */
 } spand_opts;
 
 /* Summary of a factorization (§4 notation). */
@@ -165,9 +167,9 @@ int spand_factor(spand_t h, void* stream);
  * stream, keeps the fastest shape of every bucket, and factors once more with
  * it (graphs captured), leaving the handle factored as spand_factor does.  The
  * handle keeps the choices for later factorizations (also inside a batch).
- * Then it times the two forms of the single-vector apply (spand_opts.
- * apply_kernels: one persistent launch, or one launch per phase) and keeps the
- * faster.  The choices change only the order of some floating-point sums.
+ * Then, unless spand_opts.apply_kernels fixes the form, it times the two forms
+ * of the single-vector apply (one persistent launch, or one launch per phase)
+ * and keeps the faster.  The choices change only the order of some floating-point sums.
  *   choice -- host, may be NULL: 12 int32: the chosen CTA size and cluster
  *             growth of buckets 1..5 (0 where no interface fell in a bucket),
  *             then the apply form (0 persistent, 1 per phase) and a zero.
@@ -277,7 +279,8 @@ int spand_num_clusters(spand_t h, int stage, int32_t* nclusters);
  * on the caller's stream; the elapsed times are accumulated per kernel kind
  * together with the kind's algorithmic work (FLOPs and bytes counted on the
  * host from the task sizes, e.g. m^3/3 per Cholesky, 6 (m-t)(N-t) per QR step).
- * Enabling or disabling clears the accumulated statistics. */
+ * Enabling or disabling clears the accumulated statistics; reading them waits
+ * for the recorded launches to finish (an event synchronisation). */
 typedef struct {
   char name[32];
   int64_t launches;
@@ -287,7 +290,8 @@ typedef struct {
 } spand_kernel_stat;
 
 int spand_set_profiling(spand_t h, int on);
-/* out: host array of cap entries; *count receives the number of kernel kinds. */
+/* out: host array of cap entries; *count receives the number of kernel kinds.
+ * Launches still in flight are waited for and counted. */
 int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count);
 
 /* ---------------------------------------------------------------------------

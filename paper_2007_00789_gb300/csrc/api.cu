@@ -284,9 +284,9 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   h->prescale = opts && opts->prescale == 1;
   if (opts && (opts->schur_simt < 0 || opts->schur_simt > 1)) return fail(SPAND_EINVAL, "schur_simt must be 0 or 1");
   h->schur_simt = opts && opts->schur_simt == 1;
-  if (opts && (opts->apply_kernels < 0 || opts->apply_kernels > 1))
-    return fail(SPAND_EINVAL, "apply_kernels must be 0 or 1");
-  h->sweep_off = opts && opts->apply_kernels == 1;
+  if (opts && (opts->apply_kernels < 0 || opts->apply_kernels > 2))
+    return fail(SPAND_EINVAL, "apply_kernels must be 0, 1 or 2");
+  h->apply_mode = opts ? opts->apply_kernels : 0;
   if (algebraic) h->dim = 0;
   int rc = algebraic ? build_tree_graph(A->rowptr, A->colind, A->n, nlevels, h->tree, err)
                      : build_tree(coords, A->n, dim, nlevels, h->tree, err);
@@ -442,6 +442,7 @@ int spand_tune(spand_t h, void* stream, int32_t* choice) {
       h->tune_grow[b] = best_grow[b];
     }
     h->drop_graphs();
+    if (h->apply_mode == 0) h->sweep_pref = 0;  // build the persistent sweep, to time it
     const int rc = factor_impl(h, s);  // the tuned factorization (graphs captured)
     if (rc != SPAND_OK) {
       h->factored = false;
@@ -455,7 +456,7 @@ int spand_tune(spand_t h, void* stream, int32_t* choice) {
   // the single-vector apply: one persistent launch or one launch per phase,
   // whichever is faster on this problem (timed on the handle's own vectors)
   int apply_choice = h->sweep_valid ? 0 : 1;
-  if (h->sweep_valid) {
+  if (h->apply_mode == 0 && h->sweep_valid) {
     RET(ensure_pcg(h));
     double* r = h->d_r;
     double* z = h->d_z;
@@ -480,7 +481,7 @@ int spand_tune(spand_t h, void* stream, int32_t* choice) {
     RET(rc);
     apply_choice = ms[0] <= ms[1] ? 0 : 1;
     h->sweep_valid = apply_choice == 0;
-    h->sweep_off = apply_choice == 1;  // later factorizations do not build the sweep
+    h->sweep_pref = apply_choice;  // later factorizations build the sweep only if it won
   }
   if (choice) {
     for (int b = 1; b <= 5; ++b) {
@@ -609,6 +610,7 @@ int spand_kernel_stats(spand_t h, spand_kernel_stat* out, int cap, int* count) {
   if (!h || !count) return fail(SPAND_EINVAL, "null argument");
   *count = KK_COUNT;
   if (!out || cap < KK_COUNT) return fail(SPAND_EINVAL, "output too small");
+  h->prof.resolve();
   for (int k = 0; k < KK_COUNT; ++k) out[k] = h->prof.stat[k];
   return SPAND_OK;
 }

@@ -814,6 +814,7 @@ int spand_batch_kernel_stats(spand_batch_t b, spand_kernel_stat* out, int cap, i
   if (!b || !count) return fail(SPAND_EINVAL, "null argument");
   *count = KK_COUNT;
   if (!out || cap < KK_COUNT) return fail(SPAND_EINVAL, "output too small");
+  b->prof.resolve();
   for (int k = 0; k < KK_COUNT; ++k) out[k] = b->prof.stat[k];
   return SPAND_OK;
 }

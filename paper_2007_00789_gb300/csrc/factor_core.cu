@@ -58,6 +58,16 @@ bool debug_plan() {
   return on;
 }
 
+// SPAND_DEBUG_SWEEP=1: every persistent apply sweep records CTA 0's clock per
+// sub-phase and prints, per sub-phase, its kind, items and cycles (stderr).
+bool debug_sweep() {
+  static const bool on = [] {
+    const char* e = getenv("SPAND_DEBUG_SWEEP");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 inline int segcol_of(const std::vector<int>& segs, const std::vector<int>& cols, int d) {
   auto it = std::lower_bound(segs.begin(), segs.end(), d);
   return cols[it - segs.begin()];
@@ -1201,7 +1211,10 @@ constexpr int kSwItem = 16384;
 int build_sweep(Run& R, cudaStream_t s) {
   spand_s* h = R.h;
   h->sweep_valid = false;
-  if (h->sweep_off) return SPAND_OK;
+  const bool want = h->apply_mode == 2 ||
+                    (h->apply_mode == 0 &&
+                     (h->sweep_pref == 0 || (h->sweep_pref < 0 && (int64_t)h->n >= spand_s::kSweepMinN)));
+  if (!want) return SPAND_OK;
   struct Grp {
     int stage, kind, colour;
     std::vector<std::pair<int, int>> ranges;
@@ -1349,6 +1362,8 @@ int build_sweep(Run& R, cudaStream_t s) {
   RET(h->farena.alloc(std::max<size_t>(I.size(), 1) * sizeof(SwItem), &pi));
   RET(h->farena.alloc(std::max<size_t>((size_t)h->n, 1) * sizeof(real_t), &py));
   RET(h->farena.alloc(16, &pw));
+  void* ptr = nullptr;
+  if (debug_sweep()) RET(h->farena.alloc((P.size() + 1) * sizeof(long long), &ptr));
   CK(cudaMemcpyAsync(pp, P.data(), P.size() * sizeof(SwPhase), cudaMemcpyHostToDevice, s));
   if (!I.empty()) CK(cudaMemcpyAsync(pi, I.data(), I.size() * sizeof(SwItem), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(pw, 0, 16, s));
@@ -1357,6 +1372,14 @@ int build_sweep(Run& R, cudaStream_t s) {
   h->sweep_items = pi;
   h->sweep_y = py;
   h->sweep_ws = (int*)pw;
+  h->sweep_trace = (long long*)ptr;
+  h->sweep_trace_kinds.clear();
+  h->sweep_trace_items.clear();
+  if (ptr)
+    for (const SwPhase& p : P) {
+      h->sweep_trace_kinds.push_back(p.kind);
+      h->sweep_trace_items.push_back(p.nitems);
+    }
   h->sweep_nph = (int)P.size();
   h->sweep_ctas = nctas;
   h->sweep_smem = smem;
@@ -1831,9 +1854,22 @@ int apply(spand_s* h, const real_t* r, real_t* z, cudaStream_t s) {
       e = launch_ap_sweep((const SwPhase*)h->sweep_phases, h->sweep_nph,
                           (const SwItem*)h->sweep_items, (const ApInterior*)h->d_api,
                           (const ApScale*)h->d_aps, (const ApQE*)h->d_apq, z, (real_t*)h->sweep_y,
-                          h->sweep_ws, h->sweep_ctas, h->sweep_smem, spand_s::kSweepWait, s);
+                          h->sweep_ws, h->sweep_ctas, h->sweep_smem, spand_s::kSweepWait,
+                          h->sweep_trace, s);
     });
     if (e != cudaSuccess) return fail(SPAND_ECUDA, std::string("apply sweep launch: ") + cudaGetErrorString(e));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (h->sweep_trace && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {
+      std::vector<long long> tr(h->sweep_nph + 1, 0);
+      if (cudaMemcpyAsync(tr.data(), h->sweep_trace, tr.size() * sizeof(long long), cudaMemcpyDeviceToHost, s) ==
+              cudaSuccess &&
+          cudaStreamSynchronize(s) == cudaSuccess)
+        for (int p = 0; p < h->sweep_nph; ++p)
+          fprintf(stderr, "spand sweep: phase %d kind %d items %d cycles %lld\n", p,
+                  h->sweep_trace_kinds[p], h->sweep_trace_items[p],
+                  p + 1 < h->sweep_nph ? tr[p + 1] - tr[p] : -1ll);
+    }
     return SPAND_OK;
   }
   ApSeg seg{h, 0};

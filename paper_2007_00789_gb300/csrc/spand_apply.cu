@@ -459,9 +459,12 @@ __global__ void __launch_bounds__(kApThreads, 2)
     k_ap_sweep(const SwPhase* __restrict__ phases, int nph, const SwItem* __restrict__ items,
                const ApInterior* __restrict__ api, const ApScale* __restrict__ aps,
                const ApQE* __restrict__ apq, real_t* __restrict__ z, real_t* __restrict__ Y,
-               int* ctr, int* abort, long long limit) {
+               int* ctr, int* abort, long long limit, long long* trace) {
   extern __shared__ real_t sh[];
   __shared__ real_t red[2 * kApThreads];
+  // optional clock trace: CTA 0's SM clock at the start and as it leaves each
+  // sub-phase's barrier (when every CTA has finished that sub-phase)
+  if (trace && blockIdx.x == 0 && threadIdx.x == 0) trace[0] = clock64();
   const int tid = threadIdx.x, nt = blockDim.x;
   auto ld = [](const real_t* p) { return __ldcg(p); };
   for (int ph = 0; ph < nph; ++ph) {
@@ -586,6 +589,7 @@ __global__ void __launch_bounds__(kApThreads, 2)
       __syncthreads();  // the shared vectors are refilled by the next item
     }
     if (ph + 1 < nph && !sweep_barrier(ctr, abort, (ph + 1) * (int)gridDim.x, limit)) return;
+    if (trace && blockIdx.x == 0 && threadIdx.x == 0) trace[ph + 1] = clock64();
   }
 }
 
@@ -671,7 +675,7 @@ int sweep_ctas(int smem_bytes) {
 cudaError_t launch_ap_sweep(const SwPhase* phases, int nph, const SwItem* items,
                             const ApInterior* api, const ApScale* aps, const ApQE* apq, real_t* z,
                             real_t* Y, int* ws, int nctas, int smem_bytes, long long limit,
-                            cudaStream_t s) {
+                            long long* trace, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), s);  // the barrier counter
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -685,7 +689,7 @@ cudaError_t launch_ap_sweep(const SwPhase* phases, int nph, const SwItem* items,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_ap_sweep, phases, nph, items, api, aps, apq, z, Y, ws, ws + 1,
-                            limit);
+                            limit, trace);
 }
 
 void launch_ap_interior(const ApItem* items, int nitems, int ntasks, int K, int max_m,

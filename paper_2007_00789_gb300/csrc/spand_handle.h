@@ -191,6 +191,7 @@ struct Prof {
     }();
     for (auto& p : pend) {
       float ms = 0.f;
+      cudaEventSynchronize(p.b);
       cudaEventElapsedTime(&ms, p.a, p.b);
       if (dump)
         fprintf(stderr, "spand launch: %s tag %d ms %.4f flops %.4g bytes %.4g\n", kKindName[p.kind],
@@ -457,10 +458,16 @@ struct spand_s {
   bool tuning = false;  // inside spand_tune: RRQR launches split by base bucket
   // the persistent single-vector apply (k_ap_sweep): its program, scratch
   // vector and barrier words (factor arena), launch shape and work
-  bool sweep_off = false;  // spand_opts.apply_kernels = 1: the per-phase launches
+  int apply_mode = 0;   // spand_opts.apply_kernels: 0 automatic, 1 per phase, 2 persistent
+  int sweep_pref = -1;  // spand_tune's timed choice: 0 persistent, 1 per phase, -1 none yet
   bool sweep_valid = false;
+  // untuned automatic choice: the persistent sweep from this many unknowns up
+  // (below it a sub-phase holds too few items to pay for its grid barrier)
+  static constexpr int64_t kSweepMinN = 1 << 21;
   void *sweep_phases = nullptr, *sweep_items = nullptr, *sweep_y = nullptr;
   int* sweep_ws = nullptr;
+  long long* sweep_trace = nullptr;  // SPAND_DEBUG_SWEEP=1: clock per sub-phase
+  std::vector<int> sweep_trace_kinds, sweep_trace_items;
   int sweep_nph = 0, sweep_ctas = 0, sweep_smem = 0;
   double sweep_flops = 0.0, sweep_bytes = 0.0;
   static constexpr long long kSweepWait = 1LL << 25;  // polls per barrier, a second or so

@@ -184,16 +184,17 @@ __device__ void trsm_blocked(const real_t* __restrict__ L, size_t ldl, int m, re
     for (int i = re + warp; i < m; i += nw) {
       const real_t lv = lnext;
       lnext = lrow(i + nw);
-      real_t s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      // two partial sums: each extra one costs an FP64 add per row on the narrow pipe
+      real_t s0 = 0.0, s1 = 0.0;
       int j = 0;
       for (; j + 3 < w; j += 4) {
         s0 = fma(__shfl_sync(0xffffffffu, lv, j), xs[(rb + j) * kTrsmNC + lane], s0);
         s1 = fma(__shfl_sync(0xffffffffu, lv, j + 1), xs[(rb + j + 1) * kTrsmNC + lane], s1);
-        s2 = fma(__shfl_sync(0xffffffffu, lv, j + 2), xs[(rb + j + 2) * kTrsmNC + lane], s2);
-        s3 = fma(__shfl_sync(0xffffffffu, lv, j + 3), xs[(rb + j + 3) * kTrsmNC + lane], s3);
+        s0 = fma(__shfl_sync(0xffffffffu, lv, j + 2), xs[(rb + j + 2) * kTrsmNC + lane], s0);
+        s1 = fma(__shfl_sync(0xffffffffu, lv, j + 3), xs[(rb + j + 3) * kTrsmNC + lane], s1);
       }
       for (; j < w; ++j) s0 = fma(__shfl_sync(0xffffffffu, lv, j), xs[(rb + j) * kTrsmNC + lane], s0);
-      if (lane < nc) xs[i * kTrsmNC + lane] -= (s0 + s1) + (s2 + s3);
+      if (lane < nc) xs[i * kTrsmNC + lane] -= s0 + s1;
     }
     __syncthreads();
   }
@@ -614,6 +615,34 @@ __global__ void __launch_bounds__(kTcThreads)
 // ---------------------------------------------------------------------------
 constexpr int kQrThreads = 256;
 constexpr int kQrcMaxThreads = 512;  // the cluster RRQR runs 256 or 512 threads per CTA
+// Register budgets of the FP64 on-chip RRQR kernels (compile-time knobs).
+// Under __launch_bounds__(512) the compiler gives the cluster kernel 64
+// registers and spills; a stated cap of 128 compiles to 112 without spills.
+// Measured on the 128^3 diffusion workload (FP64, untuned shapes), cluster
+// kernel per factorization: cap 128 401 ms, cap 72 (64 registers, no spills)
+// 438 ms, the compiler's 64 with spills 416 ms; the multi-CTA kernel under
+// its own 256-thread bound (128 registers) 92 ms, capped at 96 registers 96 ms.
+// SPAND_QR_ACC2: two partial sums in the update's dot products (else four;
+// 401 vs 409 ms).
+#ifndef SPAND_QR_ACC2
+#define SPAND_QR_ACC2 1
+#endif
+#ifndef SPAND_QRC_REGS
+#define SPAND_QRC_REGS 128
+#endif
+#ifndef SPAND_GSM_REGS
+#define SPAND_GSM_REGS 0
+#endif
+#if SPAND_QRC_REGS > 0
+#define kQrcRegCap __maxnreg__(SPAND_QRC_REGS)
+#else
+#define kQrcRegCap __launch_bounds__(kQrcMaxThreads)
+#endif
+#if defined(SPAND_SINGLE) || SPAND_GSM_REGS <= 0
+#define kQrGsmRegCap __launch_bounds__(kQrThreads)
+#else
+#define kQrGsmRegCap __maxnreg__(SPAND_GSM_REGS)
+#endif
 
 struct ArgMax {
   real_t v;
@@ -867,40 +896,43 @@ __device__ __forceinline__ bool qr_grid_barrier(int* ctr, int* abort, int target
 // The merge of the G CTAs' candidates of a step (largest best, ties to the
 // lowest column; second = the largest of the others): thread k < G loads CTA
 // k's slot (all loads in flight at once), the warps reduce with shuffles and
-// thread 0 merges the warps.  Called by every thread of the CTA; the result
-// is returned to every thread.  red_*: shared scratch of kQrThreads / 32.
-__device__ __forceinline__ void grid_merge(const GridSlot* sl, int G, double* red_b, double* red_s,
-                                           int* red_i, double* out_best, double* out_sec,
-                                           int* out_idx) {
-  __shared__ double s_b, s_s;
+// thread 0 merges the warps.  The norms are compared as the bit patterns of
+// the doubles (integers order non-negative doubles as their values; -1, no
+// candidate, sorts below), so the merge issues no FP64 instruction.  Called by
+// every thread of the CTA; the result is returned to every thread.  red_*:
+// shared scratch of kQrThreads / 32.
+__device__ __forceinline__ void grid_merge(const GridSlot* sl, int G, long long* red_b,
+                                           long long* red_s, int* red_i, double* out_best,
+                                           double* out_sec, int* out_idx) {
+  __shared__ long long s_b, s_s;
   __shared__ int s_i;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  double b = -1.0, s2 = -1.0;
+  long long b = -1, s2 = -1;
   int ix = -1;
   for (int k = tid; k < G; k += blockDim.x) {
-    const double kb = __ldcg(&sl[k].best);
-    const double ks = __ldcg(&sl[k].second);
+    const long long kb = __double_as_longlong(__ldcg(&sl[k].best));
+    const long long ks = __double_as_longlong(__ldcg(&sl[k].second));
     const int ki = __ldcg(&sl[k].idx);
     if (ki < 0) continue;
     if (kb > b || (kb == b && (ix < 0 || ki < ix))) {
-      s2 = fmax(fmax(s2, ks), b);
+      s2 = max(max(s2, ks), b);
       b = kb;
       ix = ki;
     } else {
-      s2 = fmax(fmax(s2, ks), kb);
+      s2 = max(max(s2, ks), kb);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, b, o);
-    const double os = __shfl_xor_sync(0xffffffffu, s2, o);
+    const long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+    const long long os = __shfl_xor_sync(0xffffffffu, s2, o);
     const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
     if (oi >= 0 && (ob > b || (ob == b && (ix < 0 || oi < ix)))) {
-      s2 = fmax(fmax(s2, os), b);
+      s2 = max(max(s2, os), b);
       b = ob;
       ix = oi;
     } else {
-      s2 = fmax(fmax(s2, os), oi >= 0 ? ob : -1.0);
+      s2 = max(max(s2, os), oi >= 0 ? ob : -1ll);
     }
   }
   if (lane == 0) {
@@ -910,17 +942,17 @@ __device__ __forceinline__ void grid_merge(const GridSlot* sl, int G, double* re
   }
   __syncthreads();
   if (tid == 0) {
-    double bb = -1.0, ss = -1.0;
+    long long bb = -1, ss = -1;
     int ii = -1;
     for (int w = 0; w < nw; ++w) {
-      const double ob = red_b[w], os = red_s[w];
+      const long long ob = red_b[w], os = red_s[w];
       const int oi = red_i[w];
       if (oi >= 0 && (ob > bb || (ob == bb && (ii < 0 || oi < ii)))) {
-        ss = fmax(fmax(ss, os), bb);
+        ss = max(max(ss, os), bb);
         bb = ob;
         ii = oi;
       } else {
-        ss = fmax(fmax(ss, os), oi >= 0 ? ob : -1.0);
+        ss = max(max(ss, os), oi >= 0 ? ob : -1ll);
       }
     }
     s_b = bb;
@@ -928,8 +960,8 @@ __device__ __forceinline__ void grid_merge(const GridSlot* sl, int G, double* re
     s_i = ii;
   }
   __syncthreads();
-  *out_best = s_b;
-  *out_sec = s_s;
+  *out_best = s_b >= 0 ? __longlong_as_double(s_b) : -1.0;
+  *out_sec = s_s >= 0 ? __longlong_as_double(s_s) : -1.0;
   *out_idx = s_i;
   __syncthreads();  // the scratch and the result may be reused at once
 }
@@ -1086,7 +1118,8 @@ __global__ void __launch_bounds__(kQrThreads)
     // merge the CTAs' candidates
     double best = -1.0, sec = -1.0;
     int bidx = -1;
-    grid_merge(slots + (step & 1) * G, G, s_red, s_sec, s_idx, &best, &sec, &bidx);
+    grid_merge(slots + (step & 1) * G, G, reinterpret_cast<long long*>(s_red),
+               reinterpret_cast<long long*>(s_sec), s_idx, &best, &sec, &bidx);
     if (bidx < 0) break;  // no candidate left (cannot happen for step < min(m, N))
     // the pivot column, in global memory (written by its owner before the barrier)
     int pseg = 0;
@@ -1382,10 +1415,14 @@ __device__ __forceinline__ QrSlot warp_merge(const QrSlot& s) {
 
 // beta, tau and 1/(alpha - beta) of the Householder reflector that maps a
 // column with pivot-row entry alpha and squared norm nsq (pivot row and below)
-// onto beta e_1; called by a whole warp, the result lands in out[0..2].  FP32
-// storage computes them in FP32; FP64 takes the square root once and the two
-// quotients in two lanes of the same instructions (IEEE division: the values
-// are those of separate computations).
+// onto beta e_1; called by a whole warp, the result lands in out[0..2] (out
+// holds kReflScalars entries).  FP32 storage computes them in FP32; FP64 takes
+// the square root once and three quotients in three lanes of the same
+// instructions (IEEE division: the values are those of separate computations):
+// also out[3] = alpha - beta, the pivot-row entry of the unscaled reflector
+// x - beta e_1, and out[4] = tau / (alpha - beta)^2 = 1 / (beta (beta - alpha)),
+// the coefficient of the update with that unscaled reflector.
+constexpr int kReflScalars = 5;
 __device__ __forceinline__ void reflector_scalars(real_t alpha, real_t nsq, int lane, real_t* out) {
   if constexpr (sizeof(real_t) < sizeof(double)) {
     if (lane == 0) {
@@ -1399,20 +1436,24 @@ __device__ __forceinline__ void reflector_scalars(real_t alpha, real_t nsq, int 
       out[0] = beta;
       out[1] = tau;
       out[2] = inv;
+      out[3] = alpha - beta;
+      out[4] = tau * inv * inv;
     }
   } else {
-    if (lane < 2) {
+    if (lane < 3) {
       const double nx = sqrt((double)nsq);
       const double beta = (nx == 0.0) ? (double)alpha : (alpha >= 0.0 ? -nx : nx);
       const double num = lane == 0 ? beta - alpha : 1.0;
-      const double den = lane == 0 ? beta : alpha - beta;
+      const double den = lane == 0 ? beta : lane == 1 ? alpha - beta : beta * (beta - alpha);
       const double q = (nx == 0.0) ? 0.0 : num / den;
       if (lane == 0) {
         out[0] = beta;
         out[1] = q;
-      } else {
+      } else if (lane == 1) {
         out[2] = q;
-        out[3] = alpha - beta;  // the pivot-row entry of the unscaled reflector
+        out[3] = alpha - beta;
+      } else {
+        out[4] = q;
       }
     }
   }
@@ -1460,6 +1501,30 @@ __device__ __forceinline__ int qr_step_flags(bool near, qkey_t bk, qkey_t second
     fl |= 2;
   return fl;
 }
+
+constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
+
+// The downdated trailing norms of the FP64 RRQR kernels (d, its error bound E
+// and the bound B = E + gam (d + E) on |d - exact|, described before
+// qr_update_dd) in few FP64 instructions (each costs the narrow FP64 pipe its
+// full warp width): since d_new <= d_old, one step's growth of E is
+// bounded by E' = c1 E + c2 d_old, c1 = (1 + cst)(1 + 4u), c2 = (cst + 1.01 u)
+// (1 + 4u) (the 1 + 4u factors absorb the rounding of the bound's own
+// arithmetic); with s = d + E, the upper bound d + B = (1 + gam) s and the
+// lower bound d - B = (d - E) - gam s.  The lower bounds' maximum and the
+// membership test compare the bit patterns of the doubles as integers (the
+// order of non-negative doubles; a negative value -- a pivoted column's
+// marker, a negative lower bound -- sorts below every non-negative one).
+struct QrDowndate {
+  double c1, c2, g1, gam;
+  __device__ __forceinline__ QrDowndate(int m) {
+    const double cst = (8.0 * m + 64.0) * kU64;
+    gam = 1.01 * (m + 2) * kU64;
+    c1 = (1.0 + cst) * (1.0 + 4.0 * kU64);
+    c2 = (cst + 1.01 * kU64) * (1.0 + 4.0 * kU64);
+    g1 = (1.0 + gam) * (1.0 + 4.0 * kU64);
+  }
+};
 
 // Two layouts of the on-chip block, one per storage precision.  FP32: column-
 // major in 16-byte vectors (the update is bound by issue and shared-memory
@@ -1662,7 +1727,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   extern __shared__ real_t sm[];
   __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
-  __shared__ real_t s_refl[3];  // FP64: beta, tau, 1/(alpha - beta), formed by warp 0
+  __shared__ real_t s_refl[kReflScalars];  // beta, tau, 1/(alpha - beta), ..., formed by warp 0
   __shared__ double s_nu64;     // FP64 norm of the pivot column (FP32 storage only)
   __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256 or 512
@@ -2027,14 +2092,32 @@ __device__ __forceinline__ void qr_update_one(real_t* a, const real_t* v, int nc
 // they are recomputed exactly (and their d, E reset), and only they become
 // candidates.  The pivot chosen is therefore the one exact recomputation of
 // every norm would choose, with the same tie rule and the same near-tie flags.
-constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
+// (kU64 and QrDowndate, the constants of these bounds, are defined above.)
 
 // One column's part of a step without the norm: the dot product and the
 // update of qr_update_one; the group's first thread (which holds the pivot row)
-// downdates d and grows E.
-__device__ __forceinline__ void qr_update_dd(real_t* a, const real_t* v, int ncl, int step, int m,
-                                             int sl, int tpc, unsigned gmask, real_t tau,
-                                             real_t* d, real_t* eb, double cst) {
+// downdates d, grows E, stores the upper bound d + B in *hb and returns the
+// bit pattern of the lower bound d - B (0 in the other threads).  coef
+// multiplies the unscaled reflector v twice: a -= coef (v^T a) v.
+__device__ __forceinline__ long long qr_update_dd(real_t* a, const real_t* v, int ncl, int step, int m,
+                                                  int sl, int tpc, unsigned gmask, real_t coef,
+                                                  real_t* d, real_t* eb, real_t* hb,
+                                                  const QrDowndate& q) {
+#if SPAND_QR_ACC2
+  // two partial sums, not four: the FMAs queue on the narrow FP64 pipe anyway,
+  // and each extra partial sum costs an FP64 add per column and step
+  real_t d0 = 0, d1 = 0;
+  int i = step + sl;
+#pragma unroll 2
+  for (; i + 3 * tpc < m; i += 4 * tpc) {
+    d0 = fma(v[i], a[(size_t)i * ncl], d0);
+    d1 = fma(v[i + tpc], a[(size_t)(i + tpc) * ncl], d1);
+    d0 = fma(v[i + 2 * tpc], a[(size_t)(i + 2 * tpc) * ncl], d0);
+    d1 = fma(v[i + 3 * tpc], a[(size_t)(i + 3 * tpc) * ncl], d1);
+  }
+  for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
+  real_t dd = d0 + d1;
+#else
   real_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
   int i = step + sl;
 #pragma unroll 2
@@ -2046,8 +2129,9 @@ __device__ __forceinline__ void qr_update_dd(real_t* a, const real_t* v, int ncl
   }
   for (; i < m; i += tpc) d0 = fma(v[i], a[(size_t)i * ncl], d0);
   real_t dd = (d0 + d1) + (d2 + d3);
+#endif
   for (int o = tpc >> 1; o > 0; o >>= 1) dd += __shfl_xor_sync(gmask, dd, o);
-  const real_t f = tau * dd;
+  const real_t f = coef * dd;
   i = step + sl;
   const size_t rs = (size_t)tpc * ncl;
 #pragma unroll 2
@@ -2061,13 +2145,20 @@ __device__ __forceinline__ void qr_update_dd(real_t* a, const real_t* v, int ncl
     p0[3 * rs] = fma(-f, v3, a3);
   }
   for (; i < m; i += tpc) a[(size_t)i * ncl] = fma(-f, v[i], a[(size_t)i * ncl]);
+  long long lk = 0;
   if (sl == 0) {
     const real_t x = a[(size_t)step * ncl];  // written by this thread above
     const real_t dold = *d, eold = *eb;
-    const real_t dn = fmax(fma(-x, x, dold), (real_t)0);  // T >= 0: clamping stays in the bound
+    real_t dn = fma(-x, x, dold);
+    if (__double_as_longlong(dn) < 0) dn = 0.0;  // T >= 0: clamping stays in the bound
+    const real_t en = fma(q.c2, dold, eold * q.c1);
+    const real_t sb = dn + en;
     *d = dn;
-    *eb = eold + cst * (dold + eold) + 1.01 * kU64 * dn;
+    *eb = en;
+    *hb = sb * q.g1;
+    lk = __double_as_longlong(fma(-q.gam, sb, dn - en));
   }
+  return lk;
 }
 
 // One thread per column (or a few, rows split among them): the dot product
@@ -2079,7 +2170,7 @@ __device__ __forceinline__ void qr_update_dd(real_t* a, const real_t* v, int ncl
 // and one cluster barrier.  The owner keeps the pivot column intact until the
 // next step's barrier, when every CTA has read it, and only then writes its R
 // entries.
-__global__ void __launch_bounds__(kQrcMaxThreads)
+__global__ void kQrcRegCap
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int csize) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -2088,7 +2179,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   extern __shared__ real_t sm[];
   __shared__ QrSlot s_in[2][16];  // the cluster's candidates of a step, pushed by every CTA
   __shared__ QrSlot s_warp[kQrcMaxThreads / kWarp];
-  __shared__ real_t s_refl[4];  // beta, tau, 1/(alpha - beta), alpha - beta, formed by warp 0
+  __shared__ real_t s_refl[kReflScalars];  // the reflector's scalars, formed by warp 0
   __shared__ int s_N, s_flags;
   const int nthr = (int)blockDim.x;  // 256 or 512
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr / kWarp;
@@ -2102,12 +2193,13 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
   real_t* v = A + (size_t)m * ncl;                     // m
   real_t* norms = v + m;                               // ncl: d (downdated), -1 once pivoted
   real_t* errb = norms + ncl;                          // ncl: E, the bound on d's error
-  int* pcol = reinterpret_cast<int*>(errb + ncl);      // ncl: column in the panel row
+  real_t* hib = errb + ncl;                            // ncl: d + B, -1 once pivoted
+  int* pcol = reinterpret_cast<int*>(hib + ncl);       // ncl: column in the panel row
   int* segid = pcol + ncl;                             // ncl: segment of the column
-  int* memb = segid + ncl;                             // ncl: columns recomputed this step
-  int* segoff = memb + ncl;                            // nseg + 1
+  int* segoff = segid + ncl;                           // nseg + 1
   __shared__ unsigned long long s_lb[kQrcMaxThreads / kWarp];
-  const double gam = 1.01 * (m + 2) * kU64, cst = (8.0 * m + 64.0) * kU64;
+  const QrDowndate qd(m);
+  const double gam = qd.gam;
   if (tid == 0) {
     int acc = 0;
     for (int g = 0; g < nseg; ++g) {
@@ -2255,7 +2347,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       if (lane == 0) v[step] = s_refl[3];
     }
     __syncthreads();  // s_refl and v[step], written by warp 0; v below it by warps 1..
-    const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2];
+    const real_t beta = s_refl[0], tau = s_refl[1], inv = s_refl[2], coef = s_refl[4];
     const bool own = crank == owner;
     if (own) {  // the stored reflector, scaled: 1 at the pivot row, zero above
       for (int i = tid; i < m; i += nthr)
@@ -2263,6 +2355,7 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       if (tid == 0) {
         t.tau[step] = tau;
         norms[lp] = -1;
+        hib[lp] = -1;
       }
       pend_l = lp;
       pend_step = step;
@@ -2270,37 +2363,29 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
       __syncthreads();  // norms[lp] (the whole CTA skips the pivot column)
     }
     // the update with the unscaled v: tau (v^T a) v = (tau inv^2) (x^T a) x
-    const real_t coef = tau * inv * inv;
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    double lbm = 0.0;  // L: the largest lower bound d - B of the CTA's live columns
+    long long lbk = 0;  // L: the largest lower bound d - B of the CTA's live columns (bits)
     for (int l = grp; l < nloc; l += ngrp) {
-      if (norms[l] < (real_t)0) continue;  // the same l for the whole group
-      qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, coef, norms + l, errb + l, cst);
-      if (sl == 0) {
-        const double d = norms[l], e = errb[l];
-        lbm = fmax(lbm, d - (e + gam * (d + e)));
-      }
+      if (__double_as_longlong(norms[l]) < 0) continue;  // pivoted; the same l for the whole group
+      lbk = max(lbk, qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, coef, norms + l,
+                                  errb + l, hib + l, qd));
     }
     nsteps = step + 1;
-    const unsigned long long lbk = warp_max((unsigned long long)QK::of(lbm));
-    if (lane == 0) s_lb[warp] = lbk;
+    const unsigned long long lbw = warp_max((unsigned long long)lbk);
+    if (lane == 0) s_lb[warp] = lbw;
     __syncthreads();  // every column updated, every warp's bound published
     unsigned long long Lk = 0;
     for (int w = 0; w < nw; ++w) Lk = max(Lk, s_lb[w]);
-    const double Lthr = QK::val((qkey_t)Lk) * (1.0 - 4e-12);
+    // L (1 - 4e-12) or a little less, in integer arithmetic: 36030 steps of
+    // the last bit lower a non-negative double by between 4.0e-12 and 8.0e-12
+    // of its value (an ulp is between 2^-53 and 2^-52 of it)
+    const long long Lthr = Lk > 36030ull ? (long long)Lk - 36030 : 0;
     // the columns that may hold the exact maximum (or a value within 1e-12 of
     // it): warp w tests columns 32 (w + nw j) + lane and recomputes its own
     // members' norms exactly, all lanes on one column; they are the candidates
     for (int c0 = warp * kWarp; c0 < nloc; c0 += nw * kWarp) {
       const int lc = c0 + lane;
-      bool mem = false;
-      if (lc < nloc) {
-        const double d = norms[lc];
-        if (d >= 0.0) {
-          const double e = errb[lc];
-          mem = d + (e + gam * (d + e)) >= Lthr;
-        }
-      }
+      const bool mem = lc < nloc && __double_as_longlong(hib[lc]) >= Lthr;
       unsigned bal = __ballot_sync(0xffffffffu, mem);
       while (bal) {
         const int l = c0 + __ffs(bal) - 1;
@@ -2379,15 +2464,17 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int gsm_ncl(int cpb) { return cpb | 1; }
 
-__global__ void __launch_bounds__(kQrThreads)
+__global__ void kQrGsmRegCap
     k_rrqr_gsm(const RRQRGridTask* __restrict__ tasks, int ntasks, const RRQRSeg* __restrict__ segs) {
   extern __shared__ real_t sm[];
   constexpr int nw = kQrThreads / kWarp;
-  __shared__ double s_bv[nw], s_sv[nw], s_lbg[nw];
+  __shared__ long long s_bv[nw], s_sv[nw];
+  __shared__ unsigned long long s_lbg[nw];
   __shared__ int s_bi[nw];
-  __shared__ double s_best, s_sec, s_nu64;
-  __shared__ int s_ix, s_nm, s_N;
-  __shared__ real_t s_refl[3];
+  __shared__ long long s_best, s_sec;
+  __shared__ double s_nu64;
+  __shared__ int s_ix, s_N;
+  __shared__ real_t s_refl[kReflScalars];
   int lo = 0, hi = ntasks - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -2411,13 +2498,13 @@ __global__ void __launch_bounds__(kQrThreads)
   real_t* norms = v + m;                              // ncl: d (FP64) or the norm (FP32); -1 once pivoted
   real_t* errb = norms + ncl;                         // ncl: FP64 E
   real_t* cand = errb + ncl;                          // ncl: exact norms of the candidates, else -1
-  int* pcol = reinterpret_cast<int*>(cand + ncl);     // ncl
+  real_t* hib = cand + ncl;                           // ncl: FP64 d + B, -1 once pivoted
+  int* pcol = reinterpret_cast<int*>(hib + ncl);      // ncl
   int* segid = pcol + ncl;                            // ncl
-  int* memb = segid + ncl;                            // ncl
-  int* segoff = memb + ncl;                           // nseg + 1
+  int* segoff = segid + ncl;                          // nseg + 1
   constexpr bool kDown = sizeof(real_t) == sizeof(double);
-  const double u64 = 1.1102230246251565e-16;
-  const double gam = 1.01 * (m + 2) * u64, cst = (8.0 * m + 64.0) * u64;
+  const QrDowndate qd(m);
+  const double gam = qd.gam;
   if (tid == 0) {
     int acc = 0;
     for (int g = 0; g < nseg; ++g) {
@@ -2477,33 +2564,35 @@ __global__ void __launch_bounds__(kQrThreads)
   const int maxsteps = min(m, N);
   int r = -1, nsteps = 0, flags = 0, nbar = 0;
   bool ok = true;
-  double nu0sq = 0.0;
+  double nu0sq = 0.0, T1 = 0.0, T2 = 0.0;
   for (int step = 0; step < maxsteps; ++step) {
-    // the CTA's best candidate (ties to the lowest column) and second best
-    double bv = -1.0, sv = -1.0;
+    // the CTA's best candidate (ties to the lowest column) and second best, as
+    // the bit patterns of the norms as doubles (the FP32 norms widen exactly):
+    // integer comparisons, no FP64 instruction; -1 = none
+    long long bv = -1, sv = -1;
     int bi = -1;
-    for (int l = tid; l < nloc; l += kQrThreads) {
-      const double x = (double)cand[l];
-      if (x < 0.0) continue;
-      if (x > bv || (x == bv && g0 + l < bi)) {
-        sv = fmax(sv, bv);
+    for (int l = tid; l < nloc; l += kQrThreads) {  // l rises: an equal key keeps the lower column
+      const long long x = __double_as_longlong((double)cand[l]);
+      if (x < 0) continue;
+      if (x > bv) {
+        sv = max(sv, bv);
         bv = x;
         bi = g0 + l;
       } else {
-        sv = fmax(sv, x);
+        sv = max(sv, x);
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const double os = __shfl_xor_sync(0xffffffffu, sv, o);
+      const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const long long os = __shfl_xor_sync(0xffffffffu, sv, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
-        sv = fmax(fmax(sv, os), bv);
+        sv = max(max(sv, os), bv);
         bv = ov;
         bi = oi;
       } else {
-        sv = fmax(fmax(sv, os), ov);
+        sv = max(max(sv, os), ov);
       }
     }
     if (lane == 0) {
@@ -2513,17 +2602,17 @@ __global__ void __launch_bounds__(kQrThreads)
     }
     __syncthreads();
     if (tid == 0) {
-      double b = s_bv[0], s2 = s_sv[0];
+      long long b = s_bv[0], s2 = s_sv[0];
       int ix = s_bi[0];
       for (int w = 1; w < nw; ++w) {
-        const double ov = s_bv[w];
+        const long long ov = s_bv[w];
         const int oi = s_bi[w];
         if (ov > b || (ov == b && oi >= 0 && (ix < 0 || oi < ix))) {
-          s2 = fmax(fmax(s2, s_sv[w]), b);
+          s2 = max(max(s2, s_sv[w]), b);
           b = ov;
           ix = oi;
         } else {
-          s2 = fmax(fmax(s2, s_sv[w]), ov);
+          s2 = max(max(s2, s_sv[w]), ov);
         }
       }
       s_best = b;
@@ -2540,8 +2629,8 @@ __global__ void __launch_bounds__(kQrThreads)
         for (int i = step + tid; i < m; i += kQrThreads) dst[i] = A[(size_t)i * ncl + (ix - g0)];
       if (tid == 0) {
         GridSlot gs;
-        gs.best = s_best;
-        gs.second = s_sec;
+        gs.best = s_best >= 0 ? __longlong_as_double(s_best) : -1.0;
+        gs.second = s_sec >= 0 ? __longlong_as_double(s_sec) : -1.0;
         gs.idx = ix;
         gs.pad = 0;
         slots[par * G + crank] = gs;
@@ -2580,21 +2669,28 @@ __global__ void __launch_bounds__(kQrThreads)
         __syncthreads();
       }
     }
-    if (sec >= 0.0 && nusq > 0.0 && nusq - sec <= 1e-12 * nusq) flags |= 1;
     if (step == 0) {
       nu0sq = nusq;
       if (nu0sq == 0.0) {
         r = 0;
         break;
       }
+      T1 = thr1 * nu0sq;
+      T2 = thr2 * nu0sq;
     }
-    if (fabs(nusq - thr1 * nu0sq) <= 1e-10 * thr1 * nu0sq) flags |= 2;
-    if (superfine && fabs(nusq - thr2 * nu0sq) <= 1e-10 * thr2 * nu0sq) flags |= 2;
-    if (r < 0 && nusq < thr1 * nu0sq) {
+    // the flags (kept by thread 0 only) and the stop decisions: FP64 work in
+    // one thread, integer comparisons of non-negative doubles in the others
+    if (tid == 0) {
+      if (sec >= 0.0 && nusq > 0.0 && nusq - sec <= 1e-12 * nusq) flags |= 1;
+      if (fabs(nusq - T1) <= 1e-10 * T1) flags |= 2;
+      if (superfine && fabs(nusq - T2) <= 1e-10 * T2) flags |= 2;
+    }
+    const long long nk = __double_as_longlong(nusq);
+    if (r < 0 && nk < __double_as_longlong(T1)) {
       r = step;
       if (!superfine) break;
     }
-    if (superfine && nusq < thr2 * nu0sq) break;
+    if (superfine && nk < __double_as_longlong(T2)) break;
     // warp 0 forms the reflector scalars while the other warps read the pivot
     // column (a long dependent FP64 sequence against an L2 read)
     if (warp == 0) {
@@ -2621,10 +2717,11 @@ __global__ void __launch_bounds__(kQrThreads)
       t.tau[step] = tau;
       norms[lp] = -1;
       cand[lp] = -1;
+      hib[lp] = -1;
     }
-    if (tid == 0) s_nm = 0;
     __syncthreads();
     // apply H_step to the CTA's other live columns
+    long long lbk = 0;  // FP64: the largest lower bound d - B of the CTA's live columns (bits)
     for (int l = grp; l < nloc; l += ngrp) {
       if (norms[l] < (real_t)0) continue;  // the same l for the whole group
       real_t* a = A + l;
@@ -2659,10 +2756,15 @@ __global__ void __launch_bounds__(kQrThreads)
         if (sl == 0) {  // this thread wrote the pivot-row entry
           const double x = a[(size_t)step * ncl];
           const double dold = norms[l], eold = errb[l];
-          const double dn = fmax(fma(-x, x, dold), 0.0);
+          double dn = fma(-x, x, dold);
+          if (__double_as_longlong(dn) < 0) dn = 0.0;  // T >= 0: clamping stays in the bound
+          const double en = fma(qd.c2, dold, eold * qd.c1);
+          const double sb = dn + en;
           norms[l] = dn;
-          errb[l] = eold + cst * (dold + eold) + 1.01 * u64 * dn;
+          errb[l] = en;
+          hib[l] = sb * qd.g1;
           cand[l] = -1;
+          lbk = max(lbk, __double_as_longlong(fma(-qd.gam, sb, dn - en)));
         }
       } else {
         real_t q = q0 + q1;
@@ -2675,43 +2777,36 @@ __global__ void __launch_bounds__(kQrThreads)
     }
     __syncthreads();
     if constexpr (kDown) {
-      double lbm = 0.0;
-      for (int l = tid; l < nloc; l += kQrThreads) {
-        const double dd = norms[l];
-        if (dd < 0.0) continue;
-        const double e = errb[l];
-        lbm = fmax(lbm, dd - (e + gam * (dd + e)));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) lbm = fmax(lbm, __shfl_xor_sync(0xffffffffu, lbm, o));
-      if (lane == 0) s_lbg[warp] = lbm;
+      // the columns that may hold the exact maximum (upper bound d + B at least
+      // L (1 - 4e-12), L the largest lower bound; see the cluster kernel) are
+      // recomputed exactly and become the candidates; integer comparisons
+      const unsigned long long lbw = warp_max((unsigned long long)lbk);
+      if (lane == 0) s_lbg[warp] = lbw;
       __syncthreads();
-      double L = 0.0;
-      for (int w = 0; w < nw; ++w) L = fmax(L, s_lbg[w]);
-      const double Lthr = L * (1.0 - 4e-12);
-      for (int l = tid; l < nloc; l += kQrThreads) {
-        const double dd = norms[l];
-        if (dd < 0.0) continue;
-        const double e = errb[l];
-        if (dd + (e + gam * (dd + e)) >= Lthr) memb[atomicAdd(&s_nm, 1)] = l;
-      }
-      __syncthreads();
-      const int nm = s_nm;
-      for (int q = warp; q < nm; q += nw) {
-        const int l = memb[q];
-        real_t s0 = 0, s1 = 0;
-        int i = step + 1 + lane;
-        for (; i + kWarp < m; i += 2 * kWarp) {
-          const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
-          s0 = fma(x0, x0, s0);
-          s1 = fma(x1, x1, s1);
-        }
-        if (i < m) s0 = fma(A[(size_t)i * ncl + l], A[(size_t)i * ncl + l], s0);
-        const real_t s2 = warp_sum(s0 + s1);
-        if (lane == 0) {
-          norms[l] = s2;
-          errb[l] = gam * s2;
-          cand[l] = s2;
+      unsigned long long Lk = 0;
+      for (int w = 0; w < nw; ++w) Lk = max(Lk, s_lbg[w]);
+      const long long Lthr = Lk > 36030ull ? (long long)Lk - 36030 : 0;  // L (1 - 4e-12) or less
+      for (int c0 = warp * kWarp; c0 < nloc; c0 += nw * kWarp) {
+        const int lc = c0 + lane;
+        const bool mem = lc < nloc && __double_as_longlong((double)hib[lc]) >= Lthr;
+        unsigned bal = __ballot_sync(0xffffffffu, mem);
+        while (bal) {
+          const int l = c0 + __ffs(bal) - 1;
+          bal &= bal - 1;
+          real_t s0 = 0, s1 = 0;
+          int i = step + 1 + lane;
+          for (; i + kWarp < m; i += 2 * kWarp) {
+            const real_t x0 = A[(size_t)i * ncl + l], x1 = A[(size_t)(i + kWarp) * ncl + l];
+            s0 = fma(x0, x0, s0);
+            s1 = fma(x1, x1, s1);
+          }
+          if (i < m) s0 = fma(A[(size_t)i * ncl + l], A[(size_t)i * ncl + l], s0);
+          const real_t s2 = warp_sum(s0 + s1);
+          if (lane == 0) {
+            norms[l] = s2;
+            errb[l] = gam * s2;
+            cand[l] = s2;
+          }
         }
       }
       __syncthreads();
@@ -2850,7 +2945,7 @@ int rrqr_cluster_smem_bytes(int m, int ncols_max, int nseg, int csize) {
   const long b = 16 + e * ldm * (ncl + 1) + e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
 #else
   const long ncl = ((ncols_max + csize - 1) / csize) | 1;
-  const long b = e * m * ncl + e * m + 2 * e * ncl + 12L * ncl + 4L * (nseg + 2) + 16;
+  const long b = e * m * ncl + e * m + 3 * e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
 #endif
   return (int)std::min<long>(b, 1L << 30);
 }
@@ -2924,7 +3019,9 @@ int rrqr_grid_smem_bytes(int max_m, int max_cpb, int max_segs) {
 
 int rrqr_gsm_smem_bytes(int m, int cpb, int nseg) {
   const long ncl = gsm_ncl(cpb), e = (long)sizeof(real_t);
-  const long b = e * m * ncl + e * m + 3 * e * ncl + 12L * ncl + 4L * (nseg + 2) + 16;
+  // the slice, v, then d, E, the candidates' norms and d + B (real_t), the
+  // columns' panel positions and segments (int), the segment offsets
+  const long b = e * m * ncl + e * m + 4 * e * ncl + 8L * ncl + 4L * (nseg + 2) + 16;
   return (int)std::min<long>(b, 1L << 30);
 }
 

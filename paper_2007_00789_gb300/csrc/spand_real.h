@@ -219,10 +219,11 @@ struct SwItem {
 // CTAs of one cooperative sweep launch (all resident) for this shared memory; 0 if none.
 int sweep_ctas(int smem_bytes);
 // ws: 2 ints (barrier counter, abort flag); the counter is cleared by the launch.
+// trace: NULL, or nph clock readings of CTA 0 (debugging: SPAND_DEBUG_SWEEP=1).
 cudaError_t launch_ap_sweep(const SwPhase* phases, int nph, const SwItem* items,
                             const ApInterior* api, const ApScale* aps, const ApQE* apq, real_t* z,
                             real_t* Y, int* ws, int nctas, int smem_bytes, long long limit,
-                            cudaStream_t s);
+                            long long* trace, cudaStream_t s);
 
 // K: CTAs per operator (a thread-block cluster), 1..16; ntasks: operators
 // over all nitems items (device array); max_nvec: the most vectors of an item.

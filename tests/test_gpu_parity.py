@@ -310,18 +310,26 @@ def test_refactor_is_deterministic():
     (lambda: si.diffusion_3d(32, seed=6), 9, 1, 1),
 ])
 def test_persistent_apply_equals_per_phase_launches(make, ell, scheme, precision):
-    """The single-vector apply as one persistent launch (the default) and as
-    one launch per phase (apply_kernels = 1) apply the same operators: M r
-    equal up to the order of the sums, and the same PCG iterations."""
+    """The single-vector apply as one persistent launch (apply_kernels = 2)
+    and as one launch per phase (apply_kernels = 1) apply the same operators:
+    M r equal up to the order of the sums, and the same PCG iterations."""
     torch = _torch()
     from paper_2007_00789_gb300 import spand as S
     prob = make()
-    a = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=precision)
+    a = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=precision, apply_kernels=2)
     b = S.Spand.from_problem(prob, ell, 1e-2, scheme, precision=precision, apply_kernels=1)
     a.factor()
     b.factor()
     r = np.random.default_rng(8).standard_normal(prob.n)
+    for h in (a, b):
+        h.set_profiling(True)
     za, zb = _gpu_apply(a, r), _gpu_apply(b, r)
+    sweeps = []
+    for h in (a, b):
+        ks = {k["name"]: k for k in h.kernel_stats()}
+        sweeps.append(ks.get("apply_sweep", {}).get("launches", 0))
+        h.set_profiling(False)
+    assert sweeps[0] == 1 and sweeps[1] == 0, sweeps  # each handle ran the form it asked for
     err = np.abs(za - zb).max() / np.abs(zb).max()
     assert err <= (1e-12 if precision == 0 else 1e-5), err
     rhs = torch.from_numpy(si.rhs_normal(prob.n, seed=9)).cuda()
