@@ -2166,10 +2166,12 @@ __device__ __forceinline__ long long qr_update_dd(real_t* a, const real_t* v, in
 // in each thread; each thread also keeps the best candidate among its columns
 // for the next step.  The block is stored row-major (row i of the local
 // columns contiguous) so that a warp reads consecutive addresses.  Per step:
-// two block barriers (three for FP64, whose reflector scalars one warp forms)
-// and one cluster barrier.  The owner keeps the pivot column intact until the
-// next step's barrier, when every CTA has read it, and only then writes its R
-// entries.
+// three block barriers (candidates published; v and the reflector scalars,
+// which one warp forms, ready; every column updated) and, for a cluster of
+// several CTAs, one cluster barrier for the candidate exchange (a single CTA
+// merges its warps' candidates in every warp instead).  The owner keeps the
+// pivot column intact until the next step's barrier, when every CTA has read
+// it, and only then writes its R entries.
 __global__ void kQrcRegCap
     k_rrqr_cluster(const RRQRTask* __restrict__ tasks, const RRQRSeg* __restrict__ segs,
                    int csize) {
@@ -2274,17 +2276,23 @@ __global__ void kQrcRegCap
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
-    if (warp == 0) {
-      QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-      if (lane < nw) cta = s_warp[lane];
-      cta = warp_merge(cta);
-      if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
-    }
-    cluster.sync();
     QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-    if (lane < csize) gb = in[lane];
-    gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    if (csize == 1) {
+      // one CTA: every warp merges the warps' candidates itself (no exchange)
+      if (lane < nw) gb = s_warp[lane];
+      gb = warp_merge(gb);
+    } else {
+      QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
+      if (warp == 0) {
+        QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+        if (lane < nw) cta = s_warp[lane];
+        cta = warp_merge(cta);
+        if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
+      }
+      cluster.sync();
+      if (lane < csize) gb = in[lane];
+      gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
+    }
     if (pend_l >= 0) {
       for (int i = pend_step + tid; i < m; i += nthr)
         A[(size_t)i * ncl + pend_l] = (i == pend_step) ? pend_beta : (real_t)0;
@@ -2352,21 +2360,22 @@ __global__ void kQrcRegCap
     if (own) {  // the stored reflector, scaled: 1 at the pivot row, zero above
       for (int i = tid; i < m; i += nthr)
         t.V[i + (size_t)step * m] = i < step ? (real_t)0 : i == step ? (real_t)1 : v[i] * inv;
-      if (tid == 0) {
-        t.tau[step] = tau;
+      if (tid == 0) {  // seen by the other threads after the next barrier; this
+        t.tau[step] = tau;  // step's update skips the pivot column by its index
         norms[lp] = -1;
         hib[lp] = -1;
       }
       pend_l = lp;
       pend_step = step;
       pend_beta = beta;
-      __syncthreads();  // norms[lp] (the whole CTA skips the pivot column)
     }
+    const int lskip = own ? lp : -1;
     // the update with the unscaled v: tau (v^T a) v = (tau inv^2) (x^T a) x
     mine = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
     long long lbk = 0;  // L: the largest lower bound d - B of the CTA's live columns (bits)
     for (int l = grp; l < nloc; l += ngrp) {
-      if (__double_as_longlong(norms[l]) < 0) continue;  // pivoted; the same l for the whole group
+      // pivoted (now or before); the same l for the whole group
+      if (l == lskip || __double_as_longlong(norms[l]) < 0) continue;
       lbk = max(lbk, qr_update_dd(A + l, v, ncl, step, m, sl, tpc, gmask, coef, norms + l,
                                   errb + l, hib + l, qd));
     }
