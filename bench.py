@@ -245,7 +245,7 @@ def run_batch(args, rank, world, local, dist, emit=True):
             return list(ex.map(lambda w: spand.Spand.from_problem(
                 w[0], w[1], args.eps, args.scheme, precision=args.precision,
                 rrqr_kernel=args.rrqr_kernel, plain_launches=plain,
-                rrqr_threads=args.rrqr_threads), work))
+                rrqr_threads=args.rrqr_threads, apply_kernels=args.apply_kernels), work))
 
     hs = analyze_all(args.plain_launches)
     batch = spand.SpandBatch(hs)
@@ -523,6 +523,9 @@ def main():
                     help="no CUDA graphs: every kernel launched on its own (for profilers)")
     ap.add_argument("--rrqr-threads", type=int, default=0, choices=[0, 256, 512],
                     help="threads per CTA of the on-chip RRQR (0: the library's choice)")
+    ap.add_argument("--apply-kernels", type=int, default=0, choices=[0, 1, 2],
+                    help="single-vector apply: 0 the library's choice (tuned, else by size),"
+                         " 1 one launch per phase, 2 one persistent launch")
     ap.add_argument("--rrqr-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="0: on-chip RRQR in clusters of up to 16 CTAs, wider blocks over several"
                          " CTAs with their slices in shared memory where they fit; 1: global-memory"
@@ -568,7 +571,8 @@ def main():
     stream = torch.cuda.current_stream()
     h = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
                                  rrqr_kernel=args.rrqr_kernel, plain_launches=args.plain_launches,
-                                 rrqr_threads=args.rrqr_threads)
+                                 rrqr_threads=args.rrqr_threads,
+                                 apply_kernels=args.apply_kernels)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     measured_peak(args.precision)  # the roofline's denominator, measured before the timed region
@@ -624,7 +628,8 @@ def main():
             he = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=args.precision,
                                           rrqr_kernel=args.rrqr_kernel,
                                           plain_launches=args.plain_launches,
-                                          rrqr_threads=args.rrqr_threads)
+                                          rrqr_threads=args.rrqr_threads,
+                                          apply_kernels=args.apply_kernels)
             he.factor(stream)
             x_host, it_e, rel_e = he.pcg_host(b, tol, stream)
             torch.cuda.synchronize()
@@ -642,7 +647,8 @@ def main():
         hv = spand.Spand.from_problem(prob, ell, args.eps, args.scheme, precision=other,
                                       rrqr_kernel=args.rrqr_kernel,
                                       plain_launches=args.plain_launches,
-                                      rrqr_threads=args.rrqr_threads)
+                                      rrqr_threads=args.rrqr_threads,
+                                      apply_kernels=args.apply_kernels)
         xv = torch.zeros_like(bd)
         for _ in range(args.warmup):
             hv.factor(stream)
@@ -686,6 +692,7 @@ def main():
                     "relres": rel, "mu": info["mu"], "skip": info["skip"],
                     "parallelism": f"replicas x{world}", "cuda_graphs": not args.plain_launches,
                     "rrqr_kernel": args.rrqr_kernel, "rrqr_threads": args.rrqr_threads,
+                    "apply_kernels": args.apply_kernels,
                     "tuned": {str(k): v for k, v in tuned.items()} if tuned else None},
         "clocks": clk.summary(),
         "variant": variant,

@@ -455,7 +455,19 @@ __device__ __forceinline__ bool sweep_barrier(int* ctr, int* abort, int target, 
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(kApThreads, 2)
+// Resident CTAs per SM the sweep is compiled for (registers capped to fit):
+// measured on the 128^3 diffusion problem, one FP64 apply 14.3 / 13.1 / 13.5 ms
+// for 2 / 3 / 4, one FP32 apply 10.0 / 8.1 / 7.5 ms.  (One warp per item for
+// sub-phases of many small items, instead of the whole CTA, measured no faster:
+// 13.8 against 13.2 ms FP64, 7.67 against 7.61 ms FP32.)
+#ifndef SPAND_SWEEP_MINB
+#ifdef SPAND_SINGLE
+#define SPAND_SWEEP_MINB 4
+#else
+#define SPAND_SWEEP_MINB 3
+#endif
+#endif
+__global__ void __launch_bounds__(kApThreads, SPAND_SWEEP_MINB)
     k_ap_sweep(const SwPhase* __restrict__ phases, int nph, const SwItem* __restrict__ items,
                const ApInterior* __restrict__ api, const ApScale* __restrict__ aps,
                const ApQE* __restrict__ apq, real_t* __restrict__ z, real_t* __restrict__ Y,
