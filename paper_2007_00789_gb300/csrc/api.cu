@@ -325,17 +325,20 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   }
   h->pack_split = fsz;
   h->h_pack.assign(A->nnz, -1);
-  for (int i = 0; i < n; ++i)
-    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
-      const int j = A->colind[e];
-      const int a = cl[i], b = cl[j];
-      const auto& rs = S0.rowsegs[a];
-      auto it = std::lower_bound(rs.begin(), rs.end(), b);
-      if (it == rs.end() || *it != b) continue;  // interface row, interior column: kept in the interior's row
-      const int64_t col = segcol[a][it - rs.begin()] + pos[j];
-      const int64_t idx = roff[a] + pos[i] + col * (int64_t)S0.members0[a].size();
-      h->h_pack[e] = S0.interior[a] ? idx : fsz + idx;
-    }
+  constexpr int kRows = 4096;  // rows per parallel chunk (the entries are independent)
+  parallel_for((n + kRows - 1) / kRows, [&](int ch, int) {
+    for (int i = ch * kRows; i < std::min(n, (ch + 1) * kRows); ++i)
+      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+        const int j = A->colind[e];
+        const int a = cl[i], b = cl[j];
+        const auto& rs = S0.rowsegs[a];
+        auto it = std::lower_bound(rs.begin(), rs.end(), b);
+        if (it == rs.end() || *it != b) continue;  // interface row, interior column: kept in the interior's row
+        const int64_t col = segcol[a][it - rs.begin()] + pos[j];
+        const int64_t idx = roff[a] + pos[i] + col * (int64_t)S0.members0[a].size();
+        h->h_pack[e] = S0.interior[a] ? idx : fsz + idx;
+      }
+  });
   h->h_rowptr.assign(A->rowptr, A->rowptr + n + 1);
   h->h_colind.assign(A->colind, A->colind + A->nnz);
   h->h_val.assign(A->val, A->val + A->nnz);

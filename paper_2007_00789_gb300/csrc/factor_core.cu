@@ -68,6 +68,17 @@ bool debug_sweep() {
   return on;
 }
 
+// SPAND_DEBUG_TIME=1: a full factorization prints, per stage, the host time of
+// its planning, of its upload, capture and launch, of the wait for its ranks
+// and of the bookkeeping after them (stderr, milliseconds).
+bool debug_time() {
+  static const bool on = [] {
+    const char* e = getenv("SPAND_DEBUG_TIME");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 inline int segcol_of(const std::vector<int>& segs, const std::vector<int>& cols, int d) {
   auto it = std::lower_bound(segs.begin(), segs.end(), d);
   return cols[it - segs.begin()];
@@ -1717,7 +1728,13 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
   if (capture) G.sg.resize(maxell + 1);
   int64_t launches = 0;
 
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point a) {
+    return std::chrono::duration<double, std::milli>(clk::now() - a).count();
+  };
   for (int k = 0; k <= maxell; ++k) {
+    clk::time_point tk = clk::now();
+    double t_plan = 0, t_launch = 0, t_wait = 0;
     StageWork W;
     std::vector<int> who, ncls;
     std::vector<size_t> ioffs;
@@ -1737,6 +1754,8 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     }
     Blob blob;
     StageBlob O = pack_blob(W, blob);
+    t_plan = ms_since(tk);
+    tk = clk::now();
     char* D = nullptr;
     if (capture) {
       auto& g = G.sg[k];
@@ -1786,11 +1805,15 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       RET(lrc);
     }
     launches += nl;
+    t_launch = ms_since(tk);
+    tk = clk::now();
     if (ioff == 0) continue;
     // ---- read back ranks and the error words (the sync of this stage)
     int* hp = G.h_ints;
     CK(cudaMemcpyAsync(hp, dcnt, ioff * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    t_wait = ms_since(tk);
+    tk = clk::now();
     for (size_t j = 0; j < who.size(); ++j) {
       const int* c = hp + ioffs[j];
       if (c[4 * ncls[j] + 1] != 0) {
@@ -1814,8 +1837,12 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
       if (capture) G.sg[k].expect.insert(G.sg[k].expect.end(), c + ncls[j], c + 3 * ncls[j]);
       RET(finish_stage(runs[who[j]], k, c, P));
     }
+    if (debug_time())
+      fprintf(stderr, "spand time: stage %d plan %.2f launch %.2f wait %.2f finish %.2f ms (%d launches%s)\n",
+              k, t_plan, t_launch, t_wait, ms_since(tk), nl, capture ? ", captured" : "");
   }
   CK(cudaStreamSynchronize(s));
+  clk::time_point tt = clk::now();
   if (P.on) P.resolve();
   for (int i = 0; i < count; ++i) {
     RET(upload_apply_plan(runs[i], s));
@@ -1827,6 +1854,7 @@ int factor_group(spand_s* const* hs, int count, FactorGroup& G, Prof& P, cudaStr
     RET(plan_multi(&seg, 1, hs[i]->self_ma, s));
   }
   CK(cudaGetLastError());
+  if (debug_time()) fprintf(stderr, "spand time: apply plans %.2f ms\n", ms_since(tt));
   G.valid = capture;
   G.layouts.resize(count);
   for (int i = 0; i < count; ++i) {

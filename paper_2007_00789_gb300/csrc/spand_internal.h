@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -62,6 +65,27 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
 int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nlevels, Tree& t,
                      std::string& err);
 int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster);
+
+// fn(i, w) for i in [0, n) on up to 16 host threads; w is the worker index
+// (for per-worker scratch).  The items must be independent.
+template <class F>
+inline void parallel_for(int n, F&& fn) {
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nth = std::max(1, std::min(n, std::min(16, hw)));
+  if (nth <= 1) {
+    for (int i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  std::atomic<int> next(0);
+  auto work = [&](int w) {
+    for (int i; (i = next.fetch_add(1)) < n;) fn(i, w);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& x : th) x.join();
+}
+
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
                  std::vector<StageSym>& st, std::string& err);
 

@@ -32,25 +32,6 @@ namespace spand {
 
 static inline int node_depth(int i) { return 31 - __builtin_clz((unsigned)(i + 1)); }
 
-// fn(i, w) for i in [0, n) on up to 16 host threads; w is the worker index
-// (for per-worker scratch).  The items must be independent.
-template <class F>
-static void parallel_for(int n, F&& fn) {
-  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
-  const int nth = std::max(1, std::min(n, std::min(16, hw)));
-  if (nth <= 1) {
-    for (int i = 0; i < n; ++i) fn(i, 0);
-    return;
-  }
-  std::atomic<int> next(0);
-  auto work = [&](int w) {
-    for (int i; (i = next.fetch_add(1)) < n;) fn(i, w);
-  };
-  std::vector<std::thread> th;
-  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
-  work(0);
-  for (auto& x : th) x.join();
-}
 
 int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err) {
   t.n = n;
@@ -361,21 +342,36 @@ static int cluster_map_graph(const Tree& t, int k, std::vector<int>& cl,
 
 int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
   if (t.algebraic) return cluster_map_graph(t, k, cl, level_of_cluster);
+  // clusters in (node, key) order: the vertices bucketed by node (a counting
+  // sort, vertices ascending within a node), then each node's few vertices
+  // sorted by key
   const int n = t.n;
-  std::vector<std::pair<std::pair<int, uint64_t>, int>> items;
-  items.reserve(n);
+  int nnode = 0;
   for (int v = 0; v < n; ++v)
-    if (t.level_of[v] >= k) items.push_back({{t.node_of[v], vertex_key(t, v, k)}, v});
-  std::sort(items.begin(), items.end());
+    if (t.level_of[v] >= k) nnode = std::max(nnode, t.node_of[v] + 1);
+  std::vector<int> start(nnode + 1, 0);
+  for (int v = 0; v < n; ++v)
+    if (t.level_of[v] >= k) ++start[t.node_of[v] + 1];
+  for (int b = 0; b < nnode; ++b) start[b + 1] += start[b];
+  std::vector<std::pair<uint64_t, int>> items(start[nnode]);
+  {
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int v = 0; v < n; ++v)
+      if (t.level_of[v] >= k) items[fill[t.node_of[v]]++] = {vertex_key(t, v, k), v};
+  }
   cl.assign(n, -1);
   int ncl = -1;
   if (level_of_cluster) level_of_cluster->clear();
-  for (size_t i = 0; i < items.size(); ++i) {
-    if (i == 0 || items[i].first != items[i - 1].first) {
-      ++ncl;
-      if (level_of_cluster) level_of_cluster->push_back(t.level_of[items[i].second]);
+  for (int b = 0; b < nnode; ++b) {
+    const auto first = items.begin() + start[b], last = items.begin() + start[b + 1];
+    std::sort(first, last);
+    for (auto it = first; it != last; ++it) {
+      if (it == first || it->first != (it - 1)->first) {
+        ++ncl;
+        if (level_of_cluster) level_of_cluster->push_back(t.level_of[it->second]);
+      }
+      cl[it->second] = ncl;
     }
-    cl[items[i].second] = ncl;
   }
   return ncl + 1;
 }
@@ -400,9 +396,15 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
   st.assign(ell, StageSym());
   // the cluster maps of all stages depend on the tree only: made in parallel;
   // stage k uses its own map and, for the parents, stage k + 1's
-  std::vector<std::vector<int>> maps(ell);
+  std::vector<std::vector<int>> maps(ell), firsts(ell);
   std::vector<int> nmaps(ell, 0);
-  parallel_for(ell, [&](int k, int) { nmaps[k] = cluster_map(t, k, maps[k], &st[k].level); });
+  parallel_for(ell, [&](int k, int) {
+    nmaps[k] = cluster_map(t, k, maps[k], &st[k].level);
+    // the lowest vertex of every cluster (it names the cluster's parent)
+    firsts[k].assign(nmaps[k], -1);
+    for (int v = n - 1; v >= 0; --v)
+      if (maps[k][v] >= 0) firsts[k][maps[k][v]] = v;
+  });
   for (int k = 0; k < ell; ++k) {
     StageSym& S = st[k];
     S.ncl = nmaps[k];
@@ -421,12 +423,17 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     if (k == 0) {
       S.members0.assign(S.ncl, {});
       for (int v = 0; v < n; ++v) S.members0[cl[v]].push_back(v);
-      for (int i = 0; i < n; ++i)
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-          const int a = cl[i], b = cl[colind[e]];
-          if (a != b) S.adj0[a].push_back(b);
-        }
-      sort_unique(S.adj0);
+      // each cluster's neighbours from its own rows (clusters in parallel)
+      parallel_for(S.ncl, [&](int a, int) {
+        auto& N = S.adj0[a];
+        for (int i : S.members0[a])
+          for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int b = cl[colind[e]];
+            if (a != b) N.push_back(b);
+          }
+        std::sort(N.begin(), N.end());
+        N.erase(std::unique(N.begin(), N.end()), N.end());
+      });
     } else {
       StageSym& P = st[k - 1];
       S.children.assign(S.ncl, {});
@@ -507,15 +514,14 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     S.parent.assign(S.ncl, -1);
     if (k + 1 < ell) {
       const std::vector<int>& cl_next = maps[k + 1];
-      std::vector<int> first(S.ncl, -1);
-      for (int v = 0; v < n; ++v)
-        if (cl[v] >= 0 && first[cl[v]] < 0) first[cl[v]] = v;
+      const std::vector<int>& first = firsts[k];
       for (int p : S.ifaces) S.parent[p] = cl_next[first[p]];
     } else if (!S.ifaces.empty()) {
       err = "interfaces left after the last stage";
       return SPAND_EINVAL;
     }
     std::vector<int>().swap(maps[k]);  // no later stage reads it
+    std::vector<int>().swap(firsts[k]);
   }
   return SPAND_OK;
 }
