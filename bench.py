@@ -168,6 +168,42 @@ def oracle_sample(name="diffusion3d_64", scheme=1, eps=1e-2):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def oracle_batch(indices, eps=1e-2, scheme=1, tol=1e-12):
+    """The CPU oracle's throughput on problems of the batch64 workload: one
+    single-threaded process per problem, as many at a time as the host has
+    cores (and 4 GB of memory each).  Returns (solves/s, processes at a time,
+    wall seconds, the slowest solve's seconds)."""
+    import concurrent.futures as cf
+
+    code = (
+        "import time,sys,json; sys.path.insert(0, %r)\n"
+        "import spand_inputs as si, oracle.spand as OS\n"
+        "prob, ell, b = si.batch_problem(int(sys.argv[1]))\n"
+        "A = prob.to_scipy(); t0 = time.perf_counter()\n"
+        "F, res = OS.solve(A, prob.coords, b, ell, %r, %d, tol=%r)\n"
+        "print(json.dumps({'s': time.perf_counter() - t0, 'iters': res.iters}))\n"
+    ) % (ROOT, eps, scheme, tol)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+    def one(i):
+        out = subprocess.run([sys.executable, "-c", code, str(i)], capture_output=True, text=True,
+                             env=env, timeout=1800)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr[-2000:])
+        return json.loads(out.stdout.strip().splitlines()[-1])
+
+    try:
+        mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError, AttributeError):
+        mem_gb = 16.0
+    par = max(1, min(len(indices), os.cpu_count() or 1, int(mem_gb // 4)))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(par) as ex:
+        res = list(ex.map(one, indices))
+    wall = time.perf_counter() - t0
+    return len(indices) / wall, par, wall, max(o["s"] for o in res)
+
+
 def sample_text(name, o):
     return (f"oracle factor+PCG to 1e-12, measured unscaled on the full {name} problem"
             f" (n={o['n']}, {o['iters']} CG iterations), one core; a lower bound for the"
@@ -741,6 +777,19 @@ def main():
                 "how": "each problem factored and solved through its own handle, one after another"}
         except Exception as exc:
             line["batched"]["fp64_one_at_a_time"] = {"error": str(exc)[:300]}
+        if not args.no_cpu_baseline:
+            try:  # every fourth problem: eight 2D and eight 3D, all sizes of the batch
+                idx = list(range(0, 64, 4)) + list(range(1, 64, 4))
+                sps, par, wall, slow = oracle_batch(idx, args.eps, args.scheme)
+                line["batched"]["cpu_baseline"] = {
+                    "value": sps, "unit": "solves/s", "cores": par, "kind": "oracle",
+                    "sample": f"oracle factor+PCG (FP64) to 1e-12 on {len(idx)} of the 64 problems"
+                              f" (every fourth 2D and every fourth 3D one), one single-threaded"
+                              f" process per problem, {par} at a time: {wall:.1f} s wall,"
+                              f" slowest solve {slow:.1f} s"}
+            except Exception as exc:
+                line["batched"]["cpu_baseline"] = {"value": None, "unit": "solves/s",
+                                                   "kind": "oracle", "sample": f"failed: {exc}"[:300]}
         line["served"] = {"workload": "resident 96^3 diffusion + 6 new 3D problems, 60 requests of"
                                       " 1..32 RHS arriving at 5/s, PCG (FP64) to 1e-10"}
         for prec, tag in ((1, "fp32_factor"), (0, "fp64")):

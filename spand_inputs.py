@@ -224,19 +224,21 @@ def batch_workload(count: int = 64, lo: float = -2.0, hi: float = 2.0):
     cell from seed i, RHS N(0, 1) from seed 1000 + i, depth by the paper's rule.
 
     Returns a list of (problem, nlevels, rhs)."""
+    return [batch_problem(i, count, lo, hi) for i in range(count)]
+
+
+def batch_problem(i: int, count: int = 64, lo: float = -2.0, hi: float = 2.0):
+    """Problem i of batch_workload(count, lo, hi): (problem, nlevels, rhs)."""
     n2 = (count + 1) // 2
     n3 = count // 2
-    out = []
-    for i in range(count):
-        j = i // 2
-        if i % 2 == 0:
-            d = 128 + int(round(384 * j / max(n2 - 1, 1)))
-            prob = diffusion_grid((d, d), seed=i, lo=lo, hi=hi)
-        else:
-            d = 24 + int(round(24 * j / max(n3 - 1, 1)))
-            prob = diffusion_grid((d, d, d), seed=i, lo=lo, hi=hi)
-        out.append((prob, paper_nlevels(prob.n), rhs_normal(prob.n, seed=1000 + i)))
-    return out
+    j = i // 2
+    if i % 2 == 0:
+        d = 128 + int(round(384 * j / max(n2 - 1, 1)))
+        prob = diffusion_grid((d, d), seed=i, lo=lo, hi=hi)
+    else:
+        d = 24 + int(round(24 * j / max(n3 - 1, 1)))
+        prob = diffusion_grid((d, d, d), seed=i, lo=lo, hi=hi)
+    return prob, paper_nlevels(prob.n), rhs_normal(prob.n, seed=1000 + i)
 
 
 def serve_workload(requests: int = 120, rate: float = 20.0, new_problems: int = 12,

@@ -84,6 +84,26 @@ def test_rejects_bad_input():
         S.Spand(A.indptr, A.indices, A.data, prob.coords, 3, 0.1, 1)
 
 
+@pytest.mark.parametrize("make,ell", [
+    (lambda: si.laplacian_grid((2,)), 2),
+    (lambda: si.laplacian_grid((6, 5)), 6),
+    (lambda: si.laplacian_2d(8), 6),
+])
+def test_too_many_levels_rejected_like_the_oracle(make, ell):
+    """More levels than the grid can be cut into leave an empty box in the
+    nested dissection: the library refuses the analysis (EINVAL) where the
+    oracle refuses the partition."""
+    from oracle import spand as OS
+    S = _lib()
+    prob = make()
+    with pytest.raises(ValueError):
+        OS.factor(prob.to_scipy(), prob.coords, ell, 1e-2, 1)
+    with pytest.raises(S.SpandError) as e:
+        S.Spand.from_problem(prob, ell, 1e-2, 1)
+    assert e.value.code == S.SPAND_EINVAL
+    assert "empty nested-dissection box" in str(e.value)
+
+
 def test_factor_before_gpu_is_refused_cleanly():
     """Without a GPU the numeric calls return an error code, never crash."""
     import torch

@@ -16,7 +16,8 @@ Bar (FP64 everywhere):
 Inputs span several tiles (32) and ragged tails: 2D Poisson 64^2 with
 6 levels (clusters of 1..128), 3D diffusion with random coefficients (no
 exact pivot ties), odd grid shapes, eps = 0 (exact Cholesky), one level
-(dense Cholesky only), and skip variants.
+(dense Cholesky only), skip variants, and the degenerate ends: n = 1, eps
+close to 1, separators of a single cell.
 """
 import numpy as np
 import pytest
@@ -88,6 +89,17 @@ CASES = [
     ("diff2d_ragged_sf", lambda: si.diffusion_grid((45, 38), seed=9), 6, 1e-2, 2, 1, False),
     # wide interfaces: on-chip QR in clusters of several CTAs (and the streamed kernel below)
     ("diff3d_32_so", lambda: si.diffusion_3d(32, seed=6), 9, 1e-2, 1, None, False),
+    # degenerate cases: a 1x1 system; eps close to 1 (every interface keeps about one
+    # coarse variable); a line of 200 cells cut 6 times (separators of one cell; a
+    # milder coefficient range than the 3D cases: with 10^U(-3,3) coefficients
+    # this chain has condition number 3.3e8 (1.7e5 with 10^U(-1,1)), and the
+    # rounding of two correct implementations then differs in M r by 2.4e-10,
+    # above the 1e-10 bar)
+    ("n1_one_level", lambda: si.laplacian_grid((1,)), 1, 1e-2, 1, None, False),
+    ("diff3d_12_eps0.9_so", lambda: si.diffusion_3d(12, seed=4), 6, 0.9, 1, None, False),
+    ("diff3d_12_eps0.9_sf", lambda: si.diffusion_3d(12, seed=4), 6, 0.9, 2, None, False),
+    ("line_200_sf", lambda: si.diffusion_grid((200,), seed=1, lo=-1, hi=1), 7, 1e-2, 2, None,
+     False),
 ]
 
 
