@@ -63,12 +63,14 @@ def measured_peak(precision):
             _PEAKS[precision] = (nom, f"nominal (measurement failed: {exc})"[:200])
     return _PEAKS[precision]
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
-# capture of this bench's command (profiles/launches_poisson3d_64_fp64.txt and
-# profiles/launches_poisson3d_64_fp32.txt):
-# (workload, precision, kernel kind) -> bytes per launch.  Only valid for the
-# kernel version that was captured; absent entries report null.
-TRAFFIC_PER_LAUNCH = {("poisson3d_64", 0, "rrqr"): 19.30e6, ("poisson3d_64", 1, "rrqr"): 9.57e6}
+# DRAM bytes (read + write) of the dominant kernel per factorization, from an
+# ncu capture of every launch of that kernel in one factorization of this
+# bench's workload (profiles/dram_k_rrqr_cluster_diffusion3d_128_fp64.txt):
+# (workload, precision, kernel kind) -> bytes per step; the line reports them
+# per launch (divided by the step's launches of the kernel, which the tuned
+# shapes change, the bytes not).  Only valid for the kernel version that was
+# captured; absent entries report null.
+TRAFFIC_PER_STEP = {("diffusion3d_128", 0, "rrqr"): 15.123e9}
 
 WORKLOADS = {
     # name: (factory, ell, rhs, rhs seed)
@@ -711,7 +713,10 @@ def main():
     peak, peak_src = measured_peak(args.precision)
     roof = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, args.precision, dom["name"])),
+            "traffic": (TRAFFIC_PER_STEP[(args.workload, args.precision, dom["name"])]
+                        / (dom["launches"] / args.steps)
+                        if (args.workload, args.precision, dom["name"]) in TRAFFIC_PER_STEP
+                        and dom["launches"] else None),
             "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
             "peak_source": peak_src, "peak_nominal": FP64_NOMINAL_TFLOPS if args.precision == 0
                                                      else FP32_NOMINAL_TFLOPS,
