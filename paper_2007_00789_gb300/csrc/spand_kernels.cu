@@ -1813,20 +1813,20 @@ __global__ void __launch_bounds__(kQrcMaxThreads)
     mine = warp_merge(mine);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
-    if (warp == 0) {
-      QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
-      if (lane < nw) cta = s_warp[lane];
-      cta = warp_merge(cta);
-      if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
-    }
-    QrSlot gb;
-    if (csize == 1) {  // a lone CTA: its own best is the pivot
-      __syncthreads();
-      gb = in[0];
+    QrSlot gb{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+    if (csize == 1) {
+      // a lone CTA: every warp merges the warps' candidates itself (no exchange)
+      if (lane < nw) gb = s_warp[lane];
+      gb = warp_merge(gb);
     } else {
+      QrSlot* in = s_in[step & 1];  // double-buffered: a CTA may push step s+1 while another reads s
+      if (warp == 0) {
+        QrSlot cta{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
+        if (lane < nw) cta = s_warp[lane];
+        cta = warp_merge(cta);
+        if (lane < csize) cluster.map_shared_rank(in, lane)[crank] = cta;
+      }
       cluster.sync();
-      gb = QrSlot{kNoKey, kNoKey, (real_t)0, 0x7fffffff};
       if (lane < csize) gb = in[lane];
       gb = warp_merge(gb);  // every lane of every warp now holds the cluster's best
     }
