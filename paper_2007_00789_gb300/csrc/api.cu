@@ -288,11 +288,24 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     return fail(SPAND_EINVAL, "apply_kernels must be 0, 1 or 2");
   h->apply_mode = opts ? opts->apply_kernels : 0;
   if (algebraic) h->dim = 0;
+  // SPAND_DEBUG_TIME=1: host time of the analysis' parts (stderr, milliseconds)
+  const char* dbg = getenv("SPAND_DEBUG_TIME");
+  const bool timing = dbg && dbg[0] == '1';
+  auto t_prev = std::chrono::steady_clock::now();
+  auto lap = [&](const char* what) {
+    if (!timing) return;
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "spand time: analyze %s %.2f ms\n", what,
+            std::chrono::duration<double, std::milli>(now - t_prev).count());
+    t_prev = now;
+  };
   int rc = algebraic ? build_tree_graph(A->rowptr, A->colind, A->n, nlevels, h->tree, err)
                      : build_tree(coords, A->n, dim, nlevels, h->tree, err);
   if (rc != SPAND_OK) return fail(rc, err);
+  lap("tree");
   rc = build_stages(h->tree, A->rowptr, A->colind, h->skip, h->st, err);
   if (rc != SPAND_OK) return fail(rc, err);
+  lap("stages");
   // stage-0 layout (sizes are the cluster sizes) -> destination of every nonzero
   const StageSym& S0 = h->st[0];
   const int n = A->n;
@@ -339,6 +352,7 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
         h->h_pack[e] = S0.interior[a] ? idx : fsz + idx;
       }
   });
+  lap("pack map");
   h->h_rowptr.assign(A->rowptr, A->rowptr + n + 1);
   h->h_colind.assign(A->colind, A->colind + A->nnz);
   h->h_val.assign(A->val, A->val + A->nnz);
@@ -357,6 +371,7 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
       for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
         h->h_fval[e] = h->h_scale[i] * A->val[e] * h->h_scale[A->colind[e]];
   }
+  lap("copies");
   *out = h.release();
   return SPAND_OK;
 }

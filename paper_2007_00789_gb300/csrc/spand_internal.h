@@ -76,9 +76,13 @@ inline void parallel_for(int n, F&& fn) {
     for (int i = 0; i < n; ++i) fn(i, 0);
     return;
   }
+  // items are drawn in chunks (about 16 per thread), so that many small items
+  // do not serialise on the shared counter
+  const int chunk = std::max(1, n / (nth * 16));
   std::atomic<int> next(0);
   auto work = [&](int w) {
-    for (int i; (i = next.fetch_add(1)) < n;) fn(i, w);
+    for (int i0; (i0 = next.fetch_add(chunk)) < n;)
+      for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
   };
   std::vector<std::thread> th;
   for (int w = 1; w < nth; ++w) th.emplace_back(work, w);

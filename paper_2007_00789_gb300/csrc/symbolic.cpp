@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -32,6 +33,48 @@ namespace spand {
 
 static inline int node_depth(int i) { return 31 - __builtin_clz((unsigned)(i + 1)); }
 
+
+// The floor(d/2)-th of the d distinct values of x[0..cnt) in ascending order
+// (the cut plane of a box).  Grid coordinates take few distinct values, which
+// an open-addressing set collects in one pass; past kDistinct distinct values
+// the values are sorted instead.
+static double distinct_median(const std::vector<double>& x, std::vector<double>& tmp) {
+  constexpr int kDistinct = 2048, kSlots = 4096;  // a power of two, at most half full
+  uint64_t keys[kSlots];
+  bool used[kSlots] = {};
+  int nd = 0;
+  bool small = true;
+  for (double v : x) {
+    if (v == 0.0) v = 0.0;  // -0 and +0 are one value
+    uint64_t b;
+    std::memcpy(&b, &v, sizeof b);
+    uint32_t h = (uint32_t)((b * 0x9E3779B97F4A7C15ull) >> 52);
+    while (used[h] && keys[h] != b) h = (h + 1) & (kSlots - 1);
+    if (!used[h]) {
+      if (nd == kDistinct) {
+        small = false;
+        break;
+      }
+      used[h] = true;
+      keys[h] = b;
+      ++nd;
+    }
+  }
+  tmp.clear();
+  if (small) {
+    for (int h = 0; h < kSlots; ++h)
+      if (used[h]) {
+        double v;
+        std::memcpy(&v, &keys[h], sizeof v);
+        tmp.push_back(v);
+      }
+  } else {
+    tmp.assign(x.begin(), x.end());
+  }
+  std::sort(tmp.begin(), tmp.end());
+  tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+  return tmp[tmp.size() / 2];
+}
 
 int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err) {
   t.n = n;
@@ -50,7 +93,7 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
   // are independent (disjoint vertex slices, their own nodes) and are cut in
   // parallel, each box's children stored at 2i, 2i + 1 as in a serial sweep
   struct Box { int node, b, e; };
-  struct Scratch { std::vector<int> lo, hi; std::vector<double> vals; };
+  struct Scratch { std::vector<int> lo, hi; std::vector<double> vals, tmp; };
   std::vector<Box> frontier{{0, 0, n}}, next;
   std::vector<Scratch> scratch(16);
   std::vector<int> buf, eq;
@@ -76,9 +119,7 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
       const int c = depth % dim;
       vals.clear();
       for (int i = bx.b; i < bx.e; ++i) vals.push_back(coords[(size_t)verts[i] * dim + c]);
-      std::sort(vals.begin(), vals.end());
-      vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
-      const double cut = vals[vals.size() / 2];
+      const double cut = distinct_median(vals, scratch[w].tmp);
       t.cut_dim[bx.node] = c;
       t.cut_val[bx.node] = cut;
       lo.clear();
@@ -383,10 +424,11 @@ static void add_edge(std::vector<std::vector<int>>& adj, int a, int b) {
 }
 
 static void sort_unique(std::vector<std::vector<int>>& adj) {
-  for (auto& v : adj) {
+  parallel_for((int)adj.size(), [&](int i, int) {
+    auto& v = adj[i];
     std::sort(v.begin(), v.end());
     v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
+  });
 }
 
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
@@ -422,6 +464,11 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     S.adj0.assign(S.ncl, {});
     if (k == 0) {
       S.members0.assign(S.ncl, {});
+      {  // counted first, so that each list is allocated once
+        std::vector<int> cnt(S.ncl, 0);
+        for (int v = 0; v < n; ++v) ++cnt[cl[v]];
+        for (int c = 0; c < S.ncl; ++c) S.members0[c].reserve(cnt[c]);
+      }
       for (int v = 0; v < n; ++v) S.members0[cl[v]].push_back(v);
       // each cluster's neighbours from its own rows (clusters in parallel)
       parallel_for(S.ncl, [&](int a, int) {
