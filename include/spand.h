@@ -102,7 +102,8 @@ typedef struct {
                              pipe.  FP64 factorizations never use the tensor cores. */
   int32_t apply_kernels;  /* form of the single-vector apply (spand_apply, spand_pcg): 0 =
                              automatic (the default: spand_tune's timed choice once it has
-                             run, before that the persistent form for n >= 2^21); 1 = one
+                             run, before that the persistent form for FP32 factors with
+                             n >= 2^21, else the per-phase launches); 1 = one
                              launch per phase, as the multi-vector forms; 2 = one persistent
                              cooperative launch that walks every phase of the sweep. */
 } spand_opts;

@@ -1222,9 +1222,12 @@ constexpr int kSwItem = 16384;
 int build_sweep(Run& R, cudaStream_t s) {
   spand_s* h = R.h;
   h->sweep_valid = false;
+  // untuned: the persistent form for FP32 factors from kSweepMinN unknowns up
+  // (FP64: the per-phase launches measured faster at every size)
   const bool want = h->apply_mode == 2 ||
                     (h->apply_mode == 0 &&
-                     (h->sweep_pref == 0 || (h->sweep_pref < 0 && (int64_t)h->n >= spand_s::kSweepMinN)));
+                     (h->sweep_pref == 0 || (h->sweep_pref < 0 && sizeof(real_t) == sizeof(float) &&
+                                             (int64_t)h->n >= spand_s::kSweepMinN)));
   if (!want) return SPAND_OK;
   struct Grp {
     int stage, kind, colour;

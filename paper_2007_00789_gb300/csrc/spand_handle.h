@@ -461,8 +461,9 @@ struct spand_s {
   int apply_mode = 0;   // spand_opts.apply_kernels: 0 automatic, 1 per phase, 2 persistent
   int sweep_pref = -1;  // spand_tune's timed choice: 0 persistent, 1 per phase, -1 none yet
   bool sweep_valid = false;
-  // untuned automatic choice: the persistent sweep from this many unknowns up
-  // (below it a sub-phase holds too few items to pay for its grid barrier)
+  // untuned automatic choice: the persistent sweep for FP32 factors from this
+  // many unknowns up (below it a sub-phase holds too few items to pay for its
+  // grid barrier; FP64 keeps the per-phase launches)
   static constexpr int64_t kSweepMinN = 1 << 21;
   void *sweep_phases = nullptr, *sweep_items = nullptr, *sweep_y = nullptr;
   int* sweep_ws = nullptr;
