@@ -79,6 +79,14 @@ bool debug_time() {
   return on;
 }
 
+// Appends pool[off, off + len) to the pool (a range that lies before its end;
+// the copy indexes the pool after it has grown, so a reallocation is harmless).
+inline void pool_append(std::vector<int>& pool, int64_t off, int len) {
+  const size_t old = pool.size();
+  pool.resize(old + (size_t)len);
+  std::copy(pool.begin() + off, pool.begin() + off + len, pool.begin() + old);
+}
+
 inline int segcol_of(const std::vector<int>& segs, const std::vector<int>& cols, int d) {
   auto it = std::lower_bound(segs.begin(), segs.end(), d);
   return cols[it - segs.begin()];
@@ -406,7 +414,7 @@ int build_stage(Run& R, int k, StageWork& W, int* d_cnt) {
       int m = 0;
       for (int p : S.children[c]) {
         const int live = P.sparsify ? h->ranks[k - 1][p] : Lp.m[p];
-        for (int i = 0; i < live; ++i) pool.push_back(pool[Lp.slot_off[p] + i]);
+        pool_append(pool, Lp.slot_off[p], live);
         m += live;
       }
       Ly.m[c] = m;
@@ -1060,7 +1068,11 @@ int finish_stage(Run& R, int k, const int* hp, Prof& P) {
       a.slots = Ly.slot_off[sidx];
       a.wslots = (int64_t)pool.size();
       for (int d : S.rowsegs[sidx]) {
-        for (int i = 0; i < Ly.m[d]; ++i) pool.push_back(d == sidx ? -1 : pool[Ly.slot_off[d] + i]);
+        if (d == sidx) {
+          pool.insert(pool.end(), (size_t)Ly.m[d], -1);
+        } else {
+          pool_append(pool, Ly.slot_off[d], Ly.m[d]);
+        }
       }
       R.api.push_back(a);
       const double fm = (double)m * (m + 1) / 2 + (double)m * (a.ncols - m);
@@ -1139,7 +1151,7 @@ int finish_stage(Run& R, int k, const int* hp, Prof& P) {
         const int q = rs[i];
         if (q == p) continue;
         const int w = (S.colour[q] < S.colour[p]) ? h->ranks[k][q] : Ly.m[q];
-        for (int j = 0; j < w; ++j) pool.push_back(pool[Ly.slot_off[q] + j]);
+        pool_append(pool, Ly.slot_off[q], w);
         segw.push_back({Ly.segcol[p][i], w});
         ncols += w;
       }
