@@ -298,6 +298,9 @@ bool cluster_ok(spand_s* h, int cs) {
 // most one per SM, holds it in shared memory: the fewest CTAs that do (0 if
 // none).  kQrOnChip marks such tasks (a flag bit beside the testing hook in
 // wait_extra, cleared before the launch).
+#ifndef SPAND_QR_LPT
+#define SPAND_QR_LPT 1
+#endif
 constexpr int kGsmSmem = 220 * 1024;
 constexpr int kQrOnChip = 1 << 20;
 int gsm_need(int m, int ncols, int nseg) {
@@ -754,7 +757,18 @@ StageBlob pack_blob(StageWork& W, Blob& blob) {
   o.id = blob.add(W.ident);
   size_t gi = 0;
   for (auto& kv : W.qr) {
-    const auto& g = kv.second;
+    auto& g = kv.second;
+#if SPAND_QR_LPT
+    // the longest QRs first: the CTAs are handed out in task order as SMs free
+    // up, so the launch ends on short tasks (cost ~ m N min(m, N) of the block)
+    if (g.bucket != 6)
+      std::stable_sort(g.tasks.begin(), g.tasks.end(), [](const RRQRTask& a, const RRQRTask& b) {
+        auto cost = [](const RRQRTask& t) {
+          return (double)t.m * t.ncols_max * std::min(t.m, t.ncols_max);
+        };
+        return cost(a) > cost(b);
+      });
+#endif
     o.qr.push_back(blob.add(g.tasks));
     if (g.bucket == 6) {
       std::vector<RRQRTask> onchip, streamed;
