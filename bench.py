@@ -253,6 +253,19 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist):
+    """The largest value over the ranks of the process group (the job's time is
+    its slowest rank's); the value itself without one.  NCCL reduces a device
+    tensor, gloo a host one."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(args):
     """The config object both arms print for a single-problem workload."""
     return {"workload": args.workload, "scheme": args.scheme, "eps": args.eps, "tol": 1e-12,
@@ -319,10 +332,7 @@ def run_batch(args, rank, world, local, dist, emit=True):
     torch.cuda.synchronize()
     kstats = batch.kernel_stats()
     batch.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     true_rel = max(float(np.linalg.norm(b - p.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b))
                    for (p, _, b), x in zip(work, xs))
     # end to end: analyze + batch factor + batch PCG with the H2D copies of every
@@ -650,10 +660,7 @@ def main():
     torch.cuda.synchronize()
     kstats = h.kernel_stats()
     h.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     info = h.info()
 
     # ---- end to end through the host-buffer path (analyze + factor + PCG, host A/b/x)
