@@ -241,7 +241,12 @@ void split_phase(std::vector<Phase>& phases, std::vector<T>& v, const Phase& ph,
                  const std::vector<int>& cols) {
   std::vector<int> order(ph.end - ph.begin);
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Ks[a] < Ks[b]; });
+  // by cluster size, and within one cluster size the largest operators first
+  // (CTAs are handed out in order as SMs free up: the launch ends on small ones)
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (Ks[a] != Ks[b]) return Ks[a] < Ks[b];
+    return fl[a] > fl[b];
+  });
   std::vector<T> seg(order.size());
   for (size_t i = 0; i < order.size(); ++i) seg[i] = v[ph.begin + order[i]];
   std::copy(seg.begin(), seg.end(), v.begin() + ph.begin);
