@@ -290,9 +290,16 @@ class Spand:
                                            ctypes.byref(rel), _stream_ptr(stream)))
         return int(it.value), float(rel.value)
 
-    def pcg_host(self, b: np.ndarray, tol: float, stream=None):
+    def pcg_host(self, b: np.ndarray, tol: float, stream=None, out: np.ndarray | None = None):
+        """PCG from host buffers; out (optional): the float64 host array that receives
+        x (e.g. a view of pinned memory), else a new one."""
         b = np.ascontiguousarray(b, dtype=np.float64)
-        x = np.empty_like(b)
+        if out is None:
+            x = np.empty_like(b)
+        else:
+            x = out
+            if x.dtype != np.float64 or x.shape != b.shape or not x.flags.c_contiguous:
+                raise ValueError("out must be a contiguous float64 array shaped like b")
         it = ctypes.c_int32()
         rel = ctypes.c_double()
         _check(self._lib.spand_pcg_host(self._h, b.ctypes.data, x.ctypes.data, float(tol),
