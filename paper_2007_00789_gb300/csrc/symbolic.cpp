@@ -417,12 +417,6 @@ int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* le
   return ncl + 1;
 }
 
-static void add_edge(std::vector<std::vector<int>>& adj, int a, int b) {
-  if (a == b) return;
-  adj[a].push_back(b);
-  adj[b].push_back(a);
-}
-
 static void sort_unique(std::vector<std::vector<int>>& adj) {
   parallel_for((int)adj.size(), [&](int i, int) {
     auto& v = adj[i];
@@ -501,16 +495,23 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
           return SPAND_EINVAL;
         }
     // adjacency among interfaces after eliminating the interiors (fill)
+    // (p's interface neighbours, and every other neighbour of each interior next
+    // to p; adj0 is symmetric, so each interface gathers its own list: in parallel)
     S.adj1.assign(S.ncl, {});
-    for (int p : S.ifaces)
-      for (int q : S.adj0[p])
-        if (!S.interior[q]) S.adj1[p].push_back(q);
-    for (int s : S.interiors) {
-      const auto& N = S.adj0[s];
-      for (size_t a = 0; a < N.size(); ++a)
-        for (size_t b = a + 1; b < N.size(); ++b) add_edge(S.adj1, N[a], N[b]);
-    }
-    sort_unique(S.adj1);
+    parallel_for((int)S.ifaces.size(), [&](int i, int) {
+      const int p = S.ifaces[i];
+      auto& N1 = S.adj1[p];
+      for (int q : S.adj0[p]) {
+        if (!S.interior[q]) {
+          N1.push_back(q);
+        } else {
+          for (int r : S.adj0[q])
+            if (r != p) N1.push_back(r);
+        }
+      }
+      std::sort(N1.begin(), N1.end());
+      N1.erase(std::unique(N1.begin(), N1.end()), N1.end());
+    });
     // greedy colouring of the interface graph in id order
     S.colour.assign(S.ncl, -1);
     S.ncolours = 0;
