@@ -310,11 +310,12 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   const StageSym& S0 = h->st[0];
   const int n = A->n;
   std::vector<int> cl(n), pos(n);
-  for (int c = 0; c < S0.ncl; ++c)
+  parallel_for(S0.ncl, [&](int c, int) {
     for (size_t i = 0; i < S0.members0[c].size(); ++i) {
       cl[S0.members0[c][i]] = c;
       pos[S0.members0[c][i]] = (int)i;
     }
+  }, 256);
   std::vector<int64_t> roff(S0.ncl);
   std::vector<std::vector<int>> segcol(S0.ncl);
   int64_t fsz = 0, ssz = 0;
@@ -337,7 +338,7 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
     }
   }
   h->pack_split = fsz;
-  h->h_pack.assign(A->nnz, -1);
+  h->h_pack.resize(A->nnz);  // every entry written below
   constexpr int kRows = 4096;  // rows per parallel chunk (the entries are independent)
   parallel_for((n + kRows - 1) / kRows, [&](int ch, int) {
     for (int i = ch * kRows; i < std::min(n, (ch + 1) * kRows); ++i)
@@ -346,16 +347,22 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
         const int a = cl[i], b = cl[j];
         const auto& rs = S0.rowsegs[a];
         auto it = std::lower_bound(rs.begin(), rs.end(), b);
-        if (it == rs.end() || *it != b) continue;  // interface row, interior column: kept in the interior's row
+        if (it == rs.end() || *it != b) {  // interface row, interior column: kept in the interior's row
+          h->h_pack[e] = -1;
+          continue;
+        }
         const int64_t col = segcol[a][it - rs.begin()] + pos[j];
         const int64_t idx = roff[a] + pos[i] + col * (int64_t)S0.members0[a].size();
         h->h_pack[e] = S0.interior[a] ? idx : fsz + idx;
       }
   });
   lap("pack map");
-  h->h_rowptr.assign(A->rowptr, A->rowptr + n + 1);
-  h->h_colind.assign(A->colind, A->colind + A->nnz);
-  h->h_val.assign(A->val, A->val + A->nnz);
+  h->h_rowptr.resize(n + 1);
+  parallel_copy(h->h_rowptr.data(), A->rowptr, n + 1);
+  h->h_colind.resize(A->nnz);
+  parallel_copy(h->h_colind.data(), A->colind, A->nnz);
+  h->h_val.resize(A->nnz);
+  parallel_copy(h->h_val.data(), A->val, A->nnz);
   if (h->prescale) {
     // S = D^{-1/2}, D = diag(A); the factorization sees S A S
     h->h_scale.assign(n, 0.0);

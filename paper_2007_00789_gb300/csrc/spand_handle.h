@@ -406,8 +406,8 @@ struct spand_s {
   int maxit = 500, true_every = 50, max_restarts = 2;
   spand::Tree tree;
   std::vector<spand::StageSym> st;
-  std::vector<int32_t> h_rowptr, h_colind;
-  std::vector<double> h_val;
+  spand::host_vec<int32_t> h_rowptr, h_colind;
+  spand::host_vec<double> h_val;
   // device copy of A
   int32_t* d_rowptr = nullptr;
   int32_t* d_colind = nullptr;
@@ -420,7 +420,7 @@ struct spand_s {
   double* d_scale = nullptr;
   double* d_fval = nullptr;
   int64_t pack_split = 0;        // interior part / interface part of the stage-0 layout
-  std::vector<int64_t> h_pack;
+  spand::host_vec<int64_t> h_pack;
   // memory
   spand::DevArena farena;
   spand::DevBuf scratch[2];

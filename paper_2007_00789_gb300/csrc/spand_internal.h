@@ -6,9 +6,12 @@
 
 #include <algorithm>
 #include <atomic>
-#include <thread>
 #include <cstdint>
+#include <cstring>
+#include <memory>
 #include <string>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "spand.h"
@@ -19,12 +22,72 @@ namespace spand {
 // Symbolic phase (host): geometric nested dissection and per-stage clusters.
 // ---------------------------------------------------------------------------
 
+// fn(i, w) for i in [0, n) on up to 16 host threads, at least grain items a
+// thread (a loop of few cheap items runs on the calling thread alone); w is
+// the worker index (for per-worker scratch).  The items must be independent.
+template <class F>
+inline void parallel_for(int n, F&& fn, int grain = 1) {
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nth = std::max(1, std::min((n + grain - 1) / std::max(1, grain), std::min(16, hw)));
+  if (nth <= 1) {
+    for (int i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  // items are drawn in chunks (about 16 per thread), so that many small items
+  // do not serialise on the shared counter
+  const int chunk = std::max(1, n / (nth * 16));
+  std::atomic<int> next(0);
+  auto work = [&](int w) {
+    for (int i0; (i0 = next.fetch_add(chunk)) < n;)
+      for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& x : th) x.join();
+}
+
+// Allocator that leaves trivially constructible elements uninitialised on
+// resize, so that a large host array is first touched by the parallel loop
+// that fills it rather than by a serial zero fill.
+template <class T>
+struct uninit_alloc : std::allocator<T> {
+  using value_type = T;
+  template <class U>
+  struct rebind {
+    using other = uninit_alloc<U>;
+  };
+  uninit_alloc() noexcept = default;
+  template <class U>
+  uninit_alloc(const uninit_alloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using host_vec = std::vector<T, uninit_alloc<T>>;
+
+// dst[0..n) = src[0..n), in 1 MiB pieces on the host threads
+template <class T>
+inline void parallel_copy(T* dst, const T* src, int64_t n) {
+  constexpr int64_t kPiece = (int64_t(1) << 20) / sizeof(T);
+  parallel_for((int)((n + kPiece - 1) / kPiece), [&](int c, int) {
+    const int64_t b = c * kPiece, e = std::min(n, b + kPiece);
+    std::memcpy(dst + b, src + b, (size_t)(e - b) * sizeof(T));
+  });
+}
+
 // Nested-dissection tree to depth nlevels-1.  Node i has children 2i+1
 // (coordinate below the cut) and 2i+2 (above); internal nodes are i < nint.
 struct Tree {
   int n = 0, dim = 0, nlevels = 0;
   int algebraic = 0;            // 0: geometric bisection of coordinates; 1: of the graph of A
-  std::vector<double> coords;   // n x dim (geometric)
+  host_vec<double> coords;      // n x dim (geometric)
   std::vector<int> cut_dim;     // per internal node (geometric)
   std::vector<double> cut_val;  // per internal node (geometric)
   std::vector<int> node_of;     // vertex -> separator node or leaf
@@ -65,30 +128,6 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
 int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nlevels, Tree& t,
                      std::string& err);
 int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster);
-
-// fn(i, w) for i in [0, n) on up to 16 host threads; w is the worker index
-// (for per-worker scratch).  The items must be independent.
-template <class F>
-inline void parallel_for(int n, F&& fn) {
-  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
-  const int nth = std::max(1, std::min(n, std::min(16, hw)));
-  if (nth <= 1) {
-    for (int i = 0; i < n; ++i) fn(i, 0);
-    return;
-  }
-  // items are drawn in chunks (about 16 per thread), so that many small items
-  // do not serialise on the shared counter
-  const int chunk = std::max(1, n / (nth * 16));
-  std::atomic<int> next(0);
-  auto work = [&](int w) {
-    for (int i0; (i0 = next.fetch_add(chunk)) < n;)
-      for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
-  };
-  std::vector<std::thread> th;
-  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
-  work(0);
-  for (auto& x : th) x.join();
-}
 
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
                  std::vector<StageSym>& st, std::string& err);

@@ -23,6 +23,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -34,11 +35,10 @@ namespace spand {
 static inline int node_depth(int i) { return 31 - __builtin_clz((unsigned)(i + 1)); }
 
 
-// The floor(d/2)-th of the d distinct values of x[0..cnt) in ascending order
-// (the cut plane of a box).  Grid coordinates take few distinct values, which
-// an open-addressing set collects in one pass; past kDistinct distinct values
-// the values are sorted instead.
-static double distinct_median(const std::vector<double>& x, std::vector<double>& tmp) {
+// The distinct values of x in ascending order, in tmp.  Grid coordinates take
+// few distinct values, which an open-addressing set collects in one pass; past
+// kDistinct distinct values the values are sorted instead.
+static void distinct_values(const std::vector<double>& x, std::vector<double>& tmp) {
   constexpr int kDistinct = 2048, kSlots = 4096;  // a power of two, at most half full
   uint64_t keys[kSlots];
   bool used[kSlots] = {};
@@ -73,6 +73,11 @@ static double distinct_median(const std::vector<double>& x, std::vector<double>&
   }
   std::sort(tmp.begin(), tmp.end());
   tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+}
+
+// The floor(d/2)-th of the d distinct values of x (the cut plane of a box).
+static double distinct_median(const std::vector<double>& x, std::vector<double>& tmp) {
+  distinct_values(x, tmp);
   return tmp[tmp.size() / 2];
 }
 
@@ -80,7 +85,8 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
   t.n = n;
   t.dim = dim;
   t.nlevels = nlevels;
-  t.coords.assign(coords, coords + (size_t)n * dim);
+  t.coords.resize((size_t)n * dim);
+  parallel_copy(t.coords.data(), coords, (int64_t)n * dim);
   const int dmax = nlevels - 1;
   const int nint = (1 << dmax) - 1;
   t.cut_dim.assign(std::max(nint, 1), -1);
@@ -96,14 +102,87 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
   struct Scratch { std::vector<int> lo, hi; std::vector<double> vals, tmp; };
   std::vector<Box> frontier{{0, 0, n}}, next;
   std::vector<Scratch> scratch(16);
-  std::vector<int> buf, eq;
+  const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  std::vector<int> vbuf;
+  std::vector<std::vector<double>> pvals;
+  // A box of the first depths, with fewer boxes than threads, is cut in pieces
+  // on all threads: each piece's distinct values (merged into the box's), each
+  // piece's lower/upper counts, then both children scattered in vertex order
+  // (the serial sweep's order) through vbuf.
+  auto cut_in_pieces = [&](int bi, int depth) {
+    const Box bx = frontier[bi];
+    const int c = depth % dim;
+    const int64_t len = bx.e - bx.b;
+    const int np = (int)std::max<int64_t>(1, std::min<int64_t>(4 * nth, len / 4096));
+    auto piece = [&](int p) { return bx.b + (int)(len * p / np); };
+    pvals.resize(np);
+    parallel_for(np, [&](int p, int w) {
+      std::vector<double>& vals = scratch[w].vals;
+      vals.clear();
+      for (int i = piece(p); i < piece(p + 1); ++i) vals.push_back(coords[(size_t)verts[i] * dim + c]);
+      distinct_values(vals, pvals[p]);
+    });
+    std::vector<double>& all = scratch[0].vals;
+    all.clear();
+    for (int p = 0; p < np; ++p) all.insert(all.end(), pvals[p].begin(), pvals[p].end());
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    const double cut = all[all.size() / 2];
+    t.cut_dim[bx.node] = c;
+    t.cut_val[bx.node] = cut;
+    std::vector<int> nlo(np + 1, 0), nhi(np + 1, 0);
+    parallel_for(np, [&](int p, int) {
+      int a = 0, h = 0;
+      for (int i = piece(p); i < piece(p + 1); ++i) {
+        const int v = verts[i];
+        const double x = coords[(size_t)v * dim + c];
+        if (x < cut) ++a;
+        else if (x > cut) ++h;
+        else {
+          t.node_of[v] = bx.node;
+          t.level_of[v] = dmax - depth;
+        }
+      }
+      nlo[p + 1] = a;
+      nhi[p + 1] = h;
+    });
+    for (int p = 0; p < np; ++p) {
+      nlo[p + 1] += nlo[p];
+      nhi[p + 1] += nhi[p];
+    }
+    const int tlo = nlo[np], thi = nhi[np];
+    vbuf.resize((size_t)tlo + thi);
+    parallel_for(np, [&](int p, int) {
+      int a = nlo[p], h = tlo + nhi[p];
+      for (int i = piece(p); i < piece(p + 1); ++i) {
+        const int v = verts[i];
+        const double x = coords[(size_t)v * dim + c];
+        if (x < cut) vbuf[a++] = v;
+        else if (x > cut) vbuf[h++] = v;
+      }
+    });
+    parallel_copy(verts.data() + bx.b, vbuf.data(), (int64_t)tlo + thi);
+    next[2 * bi] = {2 * bx.node + 1, bx.b, bx.b + tlo};
+    next[2 * bi + 1] = {2 * bx.node + 2, bx.b + tlo, bx.b + tlo + thi};
+  };
   for (int depth = 0; depth <= dmax; ++depth) {
     next.assign(2 * frontier.size(), Box{0, 0, 0});
-    std::atomic<int> empty_node(-1);
-    parallel_for((int)frontier.size(), [&](int bi, int w) {
+    // the first (lowest) empty box of the depth, as a serial sweep meets it
+    std::atomic<int> empty_node(std::numeric_limits<int>::max());
+    auto note_empty = [&](int node) {
+      int cur = empty_node.load();
+      while (node < cur && !empty_node.compare_exchange_weak(cur, node)) {
+      }
+    };
+    if (depth < dmax && (int)frontier.size() < nth) {
+      for (int bi = 0; bi < (int)frontier.size(); ++bi) {
+        if (frontier[bi].e <= frontier[bi].b) note_empty(frontier[bi].node);
+        else cut_in_pieces(bi, depth);
+      }
+    } else parallel_for((int)frontier.size(), [&](int bi, int w) {
       const Box bx = frontier[bi];
       if (bx.e <= bx.b) {
-        empty_node.store(bx.node);
+        note_empty(bx.node);
         return;
       }
       if (depth == dmax) {
@@ -142,14 +221,12 @@ int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::
       next[2 * bi] = {2 * bx.node + 1, bx.b, mid};
       next[2 * bi + 1] = {2 * bx.node + 2, mid, p};
     });
-    if (empty_node.load() >= 0) {
+    if (empty_node.load() != std::numeric_limits<int>::max()) {
       err = "empty nested-dissection box at node " + std::to_string(empty_node.load());
       return SPAND_EINVAL;
     }
     frontier.swap(next);
   }
-  (void)buf;
-  (void)eq;
   return SPAND_OK;
 }
 
@@ -381,48 +458,87 @@ static int cluster_map_graph(const Tree& t, int k, std::vector<int>& cl,
   return ncl + 1;
 }
 
-int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
-  if (t.algebraic) return cluster_map_graph(t, k, cl, level_of_cluster);
-  // clusters in (node, key) order: the vertices bucketed by node (a counting
-  // sort, vertices ascending within a node), then each node's few vertices
-  // sorted by key
+// Geometric clusters of stage k in (node, key) order: the live vertices
+// counting-sorted by node over contiguous vertex pieces (each node's vertices
+// stay ascending), each node's vertices sorted by key, then the clusters
+// numbered node by node.  full: -1 for the vertices eliminated before stage
+// k, else their entries are left as they were.  node_of_cluster and
+// key_of_cluster (optional): every cluster's tree node and key.
+struct KeyedVertex {
+  uint64_t key;
+  int v;
+  bool operator<(const KeyedVertex& o) const { return key != o.key ? key < o.key : v < o.v; }
+};
+static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster,
+                           bool full, std::vector<int>* node_of_cluster = nullptr,
+                           std::vector<uint64_t>* key_of_cluster = nullptr) {
   const int n = t.n;
-  int nnode = 0;
-  for (int v = 0; v < n; ++v)
-    if (t.level_of[v] >= k) nnode = std::max(nnode, t.node_of[v] + 1);
-  std::vector<int> start(nnode + 1, 0);
-  for (int v = 0; v < n; ++v)
-    if (t.level_of[v] >= k) ++start[t.node_of[v] + 1];
-  for (int b = 0; b < nnode; ++b) start[b + 1] += start[b];
-  std::vector<std::pair<uint64_t, int>> items(start[nnode]);
-  {
-    std::vector<int> fill(start.begin(), start.end() - 1);
-    for (int v = 0; v < n; ++v)
-      if (t.level_of[v] >= k) items[fill[t.node_of[v]]++] = {vertex_key(t, v, k), v};
-  }
-  cl.assign(n, -1);
-  int ncl = -1;
-  if (level_of_cluster) level_of_cluster->clear();
+  const int np = std::max(1, std::min(32, n / 65536));
+  auto piece = [&](int p) { return (int)((int64_t)n * p / np); };
+  // for every live vertex of piece p in order: fn(v)
+  auto each = [&](int p, auto&& fn) {
+    for (int v = piece(p); v < piece(p + 1); ++v)
+      if (t.level_of[v] >= k) fn(v);
+  };
+  std::vector<int> pmax(np, 0);
+  parallel_for(np, [&](int p, int) {
+    int mx = 0;
+    each(p, [&](int v) { mx = std::max(mx, t.node_of[v] + 1); });
+    pmax[p] = mx;
+  });
+  const int nnode = *std::max_element(pmax.begin(), pmax.end());
+  // at[b * np + p]: vertices of node b in piece p, then where they go
+  std::vector<int> at((size_t)nnode * np, 0), start(nnode + 1, 0);
+  parallel_for(np, [&](int p, int) { each(p, [&](int v) { ++at[(size_t)t.node_of[v] * np + p]; }); });
+  int total = 0;
   for (int b = 0; b < nnode; ++b) {
-    const auto first = items.begin() + start[b], last = items.begin() + start[b + 1];
-    std::sort(first, last);
-    for (auto it = first; it != last; ++it) {
-      if (it == first || it->first != (it - 1)->first) {
-        ++ncl;
-        if (level_of_cluster) level_of_cluster->push_back(t.level_of[it->second]);
-      }
-      cl[it->second] = ncl;
+    start[b] = total;
+    for (int p = 0; p < np; ++p) {
+      const int c = at[(size_t)b * np + p];
+      at[(size_t)b * np + p] = total;
+      total += c;
     }
   }
-  return ncl + 1;
+  start[nnode] = total;
+  host_vec<KeyedVertex> items(total);
+  parallel_for(np, [&](int p, int) {
+    each(p, [&](int v) { items[at[(size_t)t.node_of[v] * np + p]++] = {vertex_key(t, v, k), v}; });
+  });
+  std::vector<int> ncb(nnode + 1, 0);  // clusters of each node, then their prefix
+  parallel_for(nnode, [&](int b, int) {
+    const auto first = items.begin() + start[b], last = items.begin() + start[b + 1];
+    if (!std::is_sorted(first, last)) std::sort(first, last);  // a leaf's: one key, in vertex order
+    int c = 0;
+    for (auto it = first; it != last; ++it)
+      if (it == first || it->key != (it - 1)->key) ++c;
+    ncb[b + 1] = c;
+  }, 256);
+  for (int b = 0; b < nnode; ++b) ncb[b + 1] += ncb[b];
+  const int ncl = ncb[nnode];
+  if (full) cl.assign(n, -1);
+  else cl.resize(n);
+  if (level_of_cluster) level_of_cluster->assign(ncl, 0);
+  if (node_of_cluster) node_of_cluster->assign(ncl, 0);
+  if (key_of_cluster) key_of_cluster->assign(ncl, 0);
+  parallel_for(nnode, [&](int b, int) {
+    int id = ncb[b] - 1;
+    const auto first = items.begin() + start[b], last = items.begin() + start[b + 1];
+    for (auto it = first; it != last; ++it) {
+      if (it == first || it->key != (it - 1)->key) {
+        ++id;
+        if (level_of_cluster) (*level_of_cluster)[id] = t.level_of[it->v];
+        if (node_of_cluster) (*node_of_cluster)[id] = b;
+        if (key_of_cluster) (*key_of_cluster)[id] = it->key;
+      }
+      cl[it->v] = id;
+    }
+  }, 256);
+  return ncl;
 }
 
-static void sort_unique(std::vector<std::vector<int>>& adj) {
-  parallel_for((int)adj.size(), [&](int i, int) {
-    auto& v = adj[i];
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-  });
+int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
+  if (t.algebraic) return cluster_map_graph(t, k, cl, level_of_cluster);
+  return cluster_map_geo(t, k, cl, level_of_cluster, true);
 }
 
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
@@ -430,17 +546,28 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
   const int ell = t.nlevels;
   const int n = t.n;
   st.assign(ell, StageSym());
-  // the cluster maps of all stages depend on the tree only: made in parallel;
-  // stage k uses its own map and, for the parents, stage k + 1's
+  // algebraic: the cluster maps of all stages depend on the tree only and are
+  // made in parallel; stage k uses its own map and, for the parents, stage
+  // k + 1's.  Geometric: stage 0's map only, with every cluster's tree node and
+  // key; stage k + 1's clusters are stage k's interfaces grouped by node and
+  // by key without its entries of depth nlevels - 2 - k and deeper (the
+  // bisection walk of a vertex at stage k + 1 is a prefix of its walk at
+  // stage k), numbered in (node, key) order as the maps number them.
   std::vector<std::vector<int>> maps(ell), firsts(ell);
   std::vector<int> nmaps(ell, 0);
-  parallel_for(ell, [&](int k, int) {
-    nmaps[k] = cluster_map(t, k, maps[k], &st[k].level);
-    // the lowest vertex of every cluster (it names the cluster's parent)
-    firsts[k].assign(nmaps[k], -1);
-    for (int v = n - 1; v >= 0; --v)
-      if (maps[k][v] >= 0) firsts[k][maps[k][v]] = v;
-  });
+  std::vector<int> cnode;
+  std::vector<uint64_t> ckey;
+  if (t.algebraic) {
+    parallel_for(ell, [&](int k, int) {
+      nmaps[k] = cluster_map(t, k, maps[k], &st[k].level);
+      // the lowest vertex of every cluster (it names the cluster's parent)
+      firsts[k].assign(nmaps[k], -1);
+      for (int v = n - 1; v >= 0; --v)
+        if (maps[k][v] >= 0) firsts[k][maps[k][v]] = v;
+    });
+  } else {
+    nmaps[0] = cluster_map_geo(t, 0, maps[0], &st[0].level, false, &cnode, &ckey);
+  }
   for (int k = 0; k < ell; ++k) {
     StageSym& S = st[k];
     S.ncl = nmaps[k];
@@ -474,19 +601,22 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
           }
         std::sort(N.begin(), N.end());
         N.erase(std::unique(N.begin(), N.end()), N.end());
-      });
+      }, 256);
     } else {
       StageSym& P = st[k - 1];
       S.children.assign(S.ncl, {});
       for (int p : P.ifaces) S.children[P.parent[p]].push_back(p);
-      for (int p : P.ifaces) {
-        const int a = P.parent[p];
-        for (int q : P.adj1[p]) {
-          const int b = P.parent[q];
-          if (a != b) S.adj0[a].push_back(b);
-        }
-      }
-      sort_unique(S.adj0);
+      // a cluster's neighbours: the parents of its children's neighbours
+      parallel_for(S.ncl, [&](int a, int) {
+        auto& N = S.adj0[a];
+        for (int p : S.children[a])
+          for (int q : P.adj1[p]) {
+            const int b = P.parent[q];
+            if (a != b) N.push_back(b);
+          }
+        std::sort(N.begin(), N.end());
+        N.erase(std::unique(N.begin(), N.end()), N.end());
+      }, 256);
     }
     for (int s : S.interiors)
       for (int q : S.adj0[s])
@@ -511,7 +641,7 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
       }
       std::sort(N1.begin(), N1.end());
       N1.erase(std::unique(N1.begin(), N1.end()), N1.end());
-    });
+    }, 256);
     // greedy colouring of the interface graph in id order
     S.colour.assign(S.ncl, -1);
     S.ncolours = 0;
@@ -529,41 +659,99 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     for (int p : S.ifaces) S.by_colour[S.colour[p]].push_back(p);
     // panel-row block lists
     S.rowsegs.assign(S.ncl, {});
-    for (int c = 0; c < S.ncl; ++c) {
+    parallel_for(S.ncl, [&](int c, int) {
       auto& rs = S.rowsegs[c];
       rs = S.interior[c] ? S.adj0[c] : S.adj1[c];
       rs.insert(std::lower_bound(rs.begin(), rs.end(), c), c);
-    }
-    // Schur targets (q >= r) and their contributing interiors
+    }, 256);
+    // Schur targets (q >= r) and their contributing interiors: the (r, s) of
+    // every target row q bucketed by q (sizes counted first, interiors in
+    // parallel), each bucket sorted, then the targets numbered in (q, r) order
     {
-      std::vector<std::pair<int64_t, int>> pairs;
+      std::vector<int64_t> qoff(S.ncl + 1, 0);
       for (int s : S.interiors) {
         const auto& N = S.adj0[s];
-        for (size_t a = 0; a < N.size(); ++a)
-          for (size_t b = 0; b <= a; ++b)
-            pairs.push_back({(int64_t)N[a] * S.ncl + N[b], s});
+        for (size_t a = 0; a < N.size(); ++a) qoff[N[a] + 1] += (int64_t)a + 1;
       }
-      std::sort(pairs.begin(), pairs.end());
-      S.schur_q.clear();
-      S.schur_r.clear();
-      S.schur_ptr.assign(1, 0);
-      S.schur_s.clear();
-      for (size_t i = 0; i < pairs.size(); ++i) {
-        if (i == 0 || pairs[i].first != pairs[i - 1].first) {
-          if (i > 0) S.schur_ptr.push_back((int)S.schur_s.size());
-          S.schur_q.push_back((int)(pairs[i].first / S.ncl));
-          S.schur_r.push_back((int)(pairs[i].first % S.ncl));
+      for (int q = 0; q < S.ncl; ++q) qoff[q + 1] += qoff[q];
+      const int64_t npairs = qoff[S.ncl];
+      std::vector<uint64_t> items((size_t)npairs);  // (r << 32) | s
+      std::unique_ptr<std::atomic<int64_t>[]> fill(new std::atomic<int64_t>[S.ncl]);
+      for (int q = 0; q < S.ncl; ++q) fill[q].store(qoff[q], std::memory_order_relaxed);
+      parallel_for((int)S.interiors.size(), [&](int i, int) {
+        const int s = S.interiors[i];
+        const auto& N = S.adj0[s];
+        for (size_t a = 0; a < N.size(); ++a) {
+          int64_t f = fill[N[a]].fetch_add((int64_t)a + 1, std::memory_order_relaxed);
+          for (size_t b = 0; b <= a; ++b) items[f++] = ((uint64_t)N[b] << 32) | (uint32_t)s;
         }
-        S.schur_s.push_back(pairs[i].second);
-      }
-      if (!pairs.empty()) S.schur_ptr.push_back((int)S.schur_s.size());
+      }, 256);
+      std::vector<int> tq(S.ncl + 1, 0);  // targets of each row q, then their prefix
+      parallel_for(S.ncl, [&](int q, int) {
+        const auto first = items.begin() + qoff[q], last = items.begin() + qoff[q + 1];
+        std::sort(first, last);
+        int cnt = 0;
+        for (auto it = first; it != last; ++it)
+          if (it == first || (*it >> 32) != (*(it - 1) >> 32)) ++cnt;
+        tq[q + 1] = cnt;
+      }, 256);
+      for (int q = 0; q < S.ncl; ++q) tq[q + 1] += tq[q];
+      const int ntarget = tq[S.ncl];
+      S.schur_q.resize(ntarget);
+      S.schur_r.resize(ntarget);
+      S.schur_ptr.resize((size_t)ntarget + 1);
+      S.schur_s.resize((size_t)npairs);
+      parallel_for(S.ncl, [&](int q, int) {
+        int tg = tq[q];
+        for (int64_t i = qoff[q]; i < qoff[q + 1]; ++i) {
+          const int r = (int)(items[i] >> 32);
+          if (i == qoff[q] || r != (int)(items[i - 1] >> 32)) {
+            S.schur_q[tg] = q;
+            S.schur_r[tg] = r;
+            S.schur_ptr[tg] = (int)i;
+            ++tg;
+          }
+          S.schur_s[i] = (int)(uint32_t)items[i];
+        }
+      }, 256);
+      S.schur_ptr[ntarget] = (int)npairs;
     }
     // parents at stage k+1
     S.parent.assign(S.ncl, -1);
-    if (k + 1 < ell) {
+    if (k + 1 < ell && t.algebraic) {
       const std::vector<int>& cl_next = maps[k + 1];
       const std::vector<int>& first = firsts[k];
       for (int p : S.ifaces) S.parent[p] = cl_next[first[p]];
+    } else if (k + 1 < ell) {
+      const int drop = 2 * k + 4;  // key bits of the entries of depth nlevels - 2 - k and deeper
+      const uint64_t keep = drop >= 64 ? 0 : ~((uint64_t(1) << drop) - 1);
+      struct Group {
+        int node;
+        uint64_t key;
+        int p;
+        bool operator<(const Group& o) const {
+          return node != o.node ? node < o.node : (key != o.key ? key < o.key : p < o.p);
+        }
+      };
+      std::vector<Group> g;
+      g.reserve(S.ifaces.size());
+      for (int p : S.ifaces) g.push_back({cnode[p], ckey[p] & keep, p});
+      std::sort(g.begin(), g.end());
+      std::vector<int> node2;
+      std::vector<uint64_t> key2;
+      std::vector<int>& level2 = st[k + 1].level;
+      level2.clear();
+      for (size_t i = 0; i < g.size(); ++i) {
+        if (i == 0 || g[i].node != g[i - 1].node || g[i].key != g[i - 1].key) {
+          node2.push_back(g[i].node);
+          key2.push_back(g[i].key);
+          level2.push_back(S.level[g[i].p]);
+        }
+        S.parent[g[i].p] = (int)node2.size() - 1;
+      }
+      nmaps[k + 1] = (int)node2.size();
+      cnode.swap(node2);
+      ckey.swap(key2);
     } else if (!S.ifaces.empty()) {
       err = "interfaces left after the last stage";
       return SPAND_EINVAL;
