@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libspand.so")
 _F32 = ["-DSPAND_REAL=float", "-DSPAND_NS=f32", "-DSPAND_SINGLE=1"]
 _F64 = ["-DSPAND_REAL=double", "-DSPAND_NS=f64"]
 SOURCES = [
-    ("symbolic.cpp", []), ("api.cu", []), ("spand_pcg.cu", []), ("engine.cu", []), ("probe.cu", []),
+    ("symbolic.cpp", []), ("host_pool.cpp", []), ("api.cu", []), ("spand_pcg.cu", []), ("engine.cu", []), ("probe.cu", []),
     ("factor_core.cu", _F64), ("factor_core.cu", _F32),
     ("spand_kernels.cu", _F64), ("spand_kernels.cu", _F32),
     ("spand_apply.cu", _F64), ("spand_apply.cu", _F32),

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <string>
 #include <thread>
@@ -21,6 +22,11 @@ namespace spand {
 // ---------------------------------------------------------------------------
 // Symbolic phase (host): geometric nested dissection and per-stage clusters.
 // ---------------------------------------------------------------------------
+
+// work(w) for w in [0, nth): w = 0 on the calling thread, the others on the
+// library's kept host threads; false (nothing run) while the threads serve
+// another loop.
+bool host_pool_run(int nth, const std::function<void(int)>& work);
 
 // fn(i, w) for i in [0, n) on up to 16 host threads, at least grain items a
 // thread (a loop of few cheap items runs on the calling thread alone); w is
@@ -37,10 +43,12 @@ inline void parallel_for(int n, F&& fn, int grain = 1) {
   // do not serialise on the shared counter
   const int chunk = std::max(1, n / (nth * 16));
   std::atomic<int> next(0);
-  auto work = [&](int w) {
+  const std::function<void(int)> work = [&](int w) {
     for (int i0; (i0 = next.fetch_add(chunk)) < n;)
       for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
   };
+  if (host_pool_run(nth, work)) return;
+  // the kept threads are busy (a loop inside a loop, or another caller's)
   std::vector<std::thread> th;
   for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
   work(0);
