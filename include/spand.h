@@ -269,7 +269,9 @@ int spand_info(spand_t h, spand_stats* s);
 int spand_ranks(spand_t h, int32_t* out, int64_t cap, int64_t* count);
 
 /* Cluster id of every vertex at stage k (-1 for vertices already
- * eliminated); out is a host array of n int32.  Available after analyze. */
+ * eliminated); out is a host array of n int32.  Available after analyze.
+ * The ids follow the analysis' own stage structure: each vertex's stage-0
+ * cluster, carried through the merges of the stages before k. */
 int spand_cluster_map(spand_t h, int stage, int32_t* out);
 
 /* Number of stages (ell) and of clusters alive at the start of stage k. */

@@ -610,8 +610,16 @@ int spand_ranks(spand_t h, int32_t* out, int64_t cap, int64_t* count) {
 int spand_cluster_map(spand_t h, int stage, int32_t* out) {
   if (!h || !out) return fail(SPAND_EINVAL, "null argument");
   if (stage < 0 || stage >= h->nlevels) return fail(SPAND_EINVAL, "stage out of range");
+  // the stage-0 clusters of the vertices, then each stage's interiors dropped
+  // and its interfaces taken to their parents: the structure the
+  // factorization walks
   std::vector<int> cl;
-  cluster_map(h->tree, stage, cl, nullptr);
+  cluster_map(h->tree, 0, cl, nullptr);
+  for (int k = 0; k < stage; ++k) {
+    const StageSym& S = h->st[k];
+    for (int& c : cl)
+      if (c >= 0) c = S.interior[c] ? -1 : S.parent[c];
+  }
   for (int v = 0; v < h->n; ++v) out[v] = cl[v];
   return SPAND_OK;
 }

@@ -44,6 +44,10 @@ def test_exports_every_declared_symbol():
     (lambda: si.laplacian_grid((9, 7)), 4),
     (lambda: si.laplacian_grid((5,)), 2),
     (lambda: si.laplacian_2d(8), 1),
+    # large enough for the analysis' parallel pieces (bisection of the first
+    # boxes, the stage-0 map over several vertex ranges)
+    (lambda: si.laplacian_3d(52), 10),
+    (lambda: si.laplacian_grid((400, 380)), 12),
 ])
 def test_partition_matches_oracle(make, ell):
     S = _lib()
