@@ -614,7 +614,7 @@ int spand_cluster_map(spand_t h, int stage, int32_t* out) {
   // and its interfaces taken to their parents: the structure the
   // factorization walks
   std::vector<int> cl;
-  cluster_map(h->tree, 0, cl, nullptr);
+  stage0_cluster_map(h->tree, cl);
   for (int k = 0; k < stage; ++k) {
     const StageSym& S = h->st[k];
     for (int& c : cl)

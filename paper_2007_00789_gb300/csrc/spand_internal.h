@@ -131,11 +131,11 @@ struct StageSym {
 };
 
 int build_tree(const double* coords, int n, int dim, int nlevels, Tree& t, std::string& err);
-// Cluster ids of every vertex at stage k (-1 if eliminated); returns #clusters.
 // Algebraic nested dissection of the (symmetric) CSR pattern.
 int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nlevels, Tree& t,
                      std::string& err);
-int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster);
+// Stage-0 cluster of every vertex; returns the number of clusters.
+int stage0_cluster_map(const Tree& t, std::vector<int>& cl);
 
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
                  std::vector<StageSym>& st, std::string& err);

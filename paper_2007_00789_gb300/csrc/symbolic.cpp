@@ -271,14 +271,23 @@ static uint64_t vertex_key(const Tree& t, int v, int k) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// The boxes of one depth are bisected in parallel.  stamp[v] names the box
+// (node + 1) that holds v at the current depth, so a sweep stays inside its
+// box; boxes of other threads only ever hold other stamps, and their writes
+// are relaxed atomics.  dist is written and read only for the box's own
+// vertices.
 struct GraphBisector {
   const int32_t* rowptr;
   const int32_t* colind;
-  std::vector<int> stamp, dist;
+  std::vector<std::atomic<int>>& stamp;
+  std::vector<int>& dist;
   std::vector<int> front, next;
+  std::vector<std::pair<long, int>> ord;
   int cur = 0;
 
-  // distances from root within the vertices stamped `cur` (-1: not reached)
+  bool inside(int u) const { return stamp[u].load(std::memory_order_relaxed) == cur; }
+
+  // distances from root within the box (-1: not reached)
   void bfs(int root) {
     dist[root] = 0;
     front.assign(1, root);
@@ -289,7 +298,7 @@ struct GraphBisector {
       for (int v : front)
         for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
           const int u = colind[e];
-          if (stamp[u] == cur && dist[u] < 0) {
+          if (inside(u) && dist[u] < 0) {
             dist[u] = d;
             next.push_back(u);
           }
@@ -298,11 +307,11 @@ struct GraphBisector {
     }
   }
 
-  void bisect(const std::vector<int>& verts, std::vector<int>& sep, std::vector<int>& lo,
+  void bisect(int box, const std::vector<int>& verts, std::vector<int>& sep, std::vector<int>& lo,
               std::vector<int>& hi) {
-    ++cur;
+    cur = box;
     for (int v : verts) {
-      stamp[v] = cur;
+      stamp[v].store(cur, std::memory_order_relaxed);
       dist[v] = -1;
     }
     bfs(verts[0]);
@@ -315,7 +324,7 @@ struct GraphBisector {
     for (int v : verts) dist[v] = -1;
     bfs(r1);
     const long big = 1L << 40;
-    std::vector<std::pair<long, int>> ord;
+    ord.clear();
     ord.reserve(verts.size());
     for (int v : verts) ord.push_back({dist[v] < 0 ? big : (long)dist[v], v});
     std::nth_element(ord.begin(), ord.begin() + verts.size() / 2, ord.end());
@@ -353,42 +362,64 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
   t.node_of.assign(n, -1);
   t.level_of.assign(n, -1);
   const int dmax = nlevels - 1;
-  GraphBisector gb{rowptr, colind, std::vector<int>(n, 0), std::vector<int>(n, -1), {}, {}, 0};
-  struct Part { int node; std::vector<int> verts; };
+  std::vector<std::atomic<int>> stamp(n);
+  parallel_for(n, [&](int v, int) { stamp[v].store(0, std::memory_order_relaxed); }, 65536);
+  std::vector<int> dist(n, -1);
+  std::vector<GraphBisector> gb;
+  for (int w = 0; w < 16; ++w) gb.push_back(GraphBisector{rowptr, colind, stamp, dist, {}, {}, {}, 0});
+  struct Part {
+    int node;
+    std::vector<int> verts;
+  };
   std::vector<Part> frontier, next;
   frontier.push_back({0, {}});
   frontier[0].verts.resize(n);
   std::iota(frontier[0].verts.begin(), frontier[0].verts.end(), 0);
-  std::vector<int> sep, lo, hi;
+  std::vector<std::vector<int>> seps;
   for (int depth = 0; depth <= dmax; ++depth) {
-    next.clear();
-    for (Part& pt : frontier) {
+    // the first (lowest) empty box of the depth, as a serial sweep meets it
+    for (const Part& pt : frontier)
       if (pt.verts.empty()) {
         err = "empty nested-dissection subdomain at node " + std::to_string(pt.node);
         return SPAND_EINVAL;
       }
-      if (depth == dmax) {
-        for (int v : pt.verts) {
-          t.node_of[v] = pt.node;
+    if (depth == dmax) {
+      parallel_for((int)frontier.size(), [&](int bi, int) {
+        for (int v : frontier[bi].verts) {
+          t.node_of[v] = frontier[bi].node;
           t.level_of[v] = 0;
         }
-        continue;
-      }
-      gb.bisect(pt.verts, sep, lo, hi);
-      for (int v : sep) {
+      });
+      break;
+    }
+    next.assign(2 * frontier.size(), Part{0, {}});
+    seps.resize(frontier.size());
+    parallel_for((int)frontier.size(), [&](int bi, int w) {
+      Part& pt = frontier[bi];
+      gb[w].bisect(pt.node + 1, pt.verts, seps[bi], next[2 * bi].verts, next[2 * bi + 1].verts);
+      for (int v : seps[bi]) {
         t.node_of[v] = pt.node;
         t.level_of[v] = dmax - depth;
       }
-      next.push_back({2 * pt.node + 1, lo});
-      next.push_back({2 * pt.node + 2, hi});
-    }
+      next[2 * bi].node = 2 * pt.node + 1;
+      next[2 * bi + 1].node = 2 * pt.node + 2;
+      std::vector<int>().swap(pt.verts);
+    });
     frontier.swap(next);
   }
-  // reach sets, by increasing level
+  // reach sets, by increasing level (a level's vertices in parallel: they read
+  // the finished sets of lower levels only)
   std::vector<std::vector<int>> R(n);
+  std::vector<int> lstart(dmax + 2, 0), bylevel(n);
+  for (int v = 0; v < n; ++v) ++lstart[t.level_of[v] + 1];
+  for (int l = 0; l <= dmax; ++l) lstart[l + 1] += lstart[l];
+  {
+    std::vector<int> at(lstart.begin(), lstart.end() - 1);
+    for (int v = 0; v < n; ++v) bylevel[at[t.level_of[v]]++] = v;
+  }
   for (int lvl = 1; lvl <= dmax; ++lvl)
-    for (int v = 0; v < n; ++v) {
-      if (t.level_of[v] != lvl) continue;
+    parallel_for(lstart[lvl + 1] - lstart[lvl], [&](int i, int) {
+      const int v = bylevel[lstart[lvl] + i];
       auto& s = R[v];
       for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
         const int u = colind[e];
@@ -397,7 +428,7 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
       }
       std::sort(s.begin(), s.end());
       s.erase(std::unique(s.begin(), s.end()), s.end());
-    }
+    }, 256);
   t.reach_ptr.assign(n + 1, 0);
   t.width = 1;
   for (int v = 0; v < n; ++v) {
@@ -405,57 +436,84 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
     t.width = std::max(t.width, (int)R[v].size());
   }
   t.reach.resize(t.reach_ptr[n]);
-  for (int v = 0; v < n; ++v) std::copy(R[v].begin(), R[v].end(), t.reach.begin() + t.reach_ptr[v]);
+  parallel_for(n, [&](int v, int) { std::copy(R[v].begin(), R[v].end(), t.reach.begin() + t.reach_ptr[v]); },
+               4096);
   return SPAND_OK;
 }
 
 // Stage-k clusters of an algebraic tree: (node, sorted ancestor set padded
 // with -1) in lexicographic order.
-static int cluster_map_graph(const Tree& t, int k, std::vector<int>& cl,
-                             std::vector<int>* level_of_cluster) {
-  const int n = t.n, W = t.width;
-  const int dk = t.nlevels - 1 - k;
-  std::vector<int> live;
-  for (int v = 0; v < n; ++v)
-    if (t.level_of[v] >= k) live.push_back(v);
-  std::vector<int> keys((size_t)live.size() * (W + 1), -1);
-  std::vector<int> tmp;
-  for (size_t i = 0; i < live.size(); ++i) {
-    const int v = live[i];
-    int* row = &keys[i * (W + 1)];
-    row[0] = t.node_of[v];
-    if (t.level_of[v] > k) {
-      tmp.clear();
-      for (int e = t.reach_ptr[v]; e < t.reach_ptr[v + 1]; ++e) tmp.push_back(ancestor_at(t.reach[e], dk));
-      std::sort(tmp.begin(), tmp.end());
-      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-      for (size_t j = 0; j < tmp.size(); ++j) row[1 + j] = tmp[j];
+// Algebraic clusters of stage 0 in (node, key) order, ties by vertex: the
+// vertices bucketed by node over contiguous vertex ranges (each node's
+// vertices stay ascending), each node's vertices sorted by key (a separator
+// vertex's reach, compared as a sequence; leaves have none), then numbered
+// node by node.  node_of_cluster and key_of_cluster (optional): every
+// cluster's node and key.
+static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int>* level_of_cluster,
+                            std::vector<int>* node_of_cluster = nullptr,
+                            std::vector<std::vector<int>>* key_of_cluster = nullptr) {
+  const int n = t.n;
+  const int np = std::max(1, std::min(32, n / 65536));
+  auto piece = [&](int p) { return (int)((int64_t)n * p / np); };
+  int nnode = 0;
+  for (int v = 0; v < n; ++v) nnode = std::max(nnode, t.node_of[v] + 1);
+  std::vector<int> at((size_t)nnode * np, 0), start(nnode + 1, 0);
+  parallel_for(np, [&](int p, int) {
+    for (int v = piece(p); v < piece(p + 1); ++v) ++at[(size_t)t.node_of[v] * np + p];
+  });
+  int total = 0;
+  for (int b = 0; b < nnode; ++b) {
+    start[b] = total;
+    for (int p = 0; p < np; ++p) {
+      const int c = at[(size_t)b * np + p];
+      at[(size_t)b * np + p] = total;
+      total += c;
     }
   }
-  std::vector<int> order(live.size());
-  std::iota(order.begin(), order.end(), 0);
-  auto less = [&](int a, int b) {
-    const int* ra = &keys[(size_t)a * (W + 1)];
-    const int* rb = &keys[(size_t)b * (W + 1)];
-    for (int j = 0; j <= W; ++j)
-      if (ra[j] != rb[j]) return ra[j] < rb[j];
-    return live[a] < live[b];
+  start[nnode] = total;
+  std::vector<int> order(n);
+  parallel_for(np, [&](int p, int) {
+    for (int v = piece(p); v < piece(p + 1); ++v) order[at[(size_t)t.node_of[v] * np + p]++] = v;
+  });
+  const int* R = t.reach.data();
+  const int* Rp = t.reach_ptr.data();
+  auto key_less = [&](int a, int b) {  // keys of two vertices of one node
+    if (t.level_of[a] == 0) return false;  // a leaf's vertices: no keys
+    return std::lexicographical_compare(R + Rp[a], R + Rp[a + 1], R + Rp[b], R + Rp[b + 1]);
   };
-  std::sort(order.begin(), order.end(), less);
+  auto key_eq = [&](int a, int b) {
+    return t.level_of[a] == 0 || std::equal(R + Rp[a], R + Rp[a + 1], R + Rp[b], R + Rp[b + 1]);
+  };
+  std::vector<int> ncb(nnode + 1, 0);  // clusters of each node, then their prefix
+  parallel_for(nnode, [&](int b, int) {
+    const auto first = order.begin() + start[b], last = order.begin() + start[b + 1];
+    std::sort(first, last, [&](int x, int y) { return key_less(x, y) || (!key_less(y, x) && x < y); });
+    int c = 0;
+    for (auto it = first; it != last; ++it)
+      if (it == first || !key_eq(*it, *(it - 1))) ++c;
+    ncb[b + 1] = c;
+  }, 256);
+  for (int b = 0; b < nnode; ++b) ncb[b + 1] += ncb[b];
+  const int ncl = ncb[nnode];
   cl.assign(n, -1);
-  int ncl = -1;
-  if (level_of_cluster) level_of_cluster->clear();
-  for (size_t i = 0; i < order.size(); ++i) {
-    const int a = order[i];
-    const bool same = i > 0 && std::equal(&keys[(size_t)a * (W + 1)], &keys[(size_t)a * (W + 1)] + W + 1,
-                                          &keys[(size_t)order[i - 1] * (W + 1)]);
-    if (!same) {
-      ++ncl;
-      if (level_of_cluster) level_of_cluster->push_back(t.level_of[live[a]]);
+  if (level_of_cluster) level_of_cluster->assign(ncl, 0);
+  if (node_of_cluster) node_of_cluster->assign(ncl, 0);
+  if (key_of_cluster) key_of_cluster->assign(ncl, {});
+  parallel_for(nnode, [&](int b, int) {
+    int id = ncb[b] - 1;
+    const auto first = order.begin() + start[b], last = order.begin() + start[b + 1];
+    for (auto it = first; it != last; ++it) {
+      const int v = *it;
+      if (it == first || !key_eq(v, *(it - 1))) {
+        ++id;
+        if (level_of_cluster) (*level_of_cluster)[id] = t.level_of[v];
+        if (node_of_cluster) (*node_of_cluster)[id] = b;
+        if (key_of_cluster && t.level_of[v] > 0) (*key_of_cluster)[id].assign(R + Rp[v], R + Rp[v + 1]);
+      }
+      cl[v] = id;
     }
-    cl[live[a]] = ncl;
-  }
-  return ncl + 1;
+  }, 256);
+  return ncl;
 }
 
 // Geometric clusters of stage k in (node, key) order: the live vertices
@@ -536,9 +594,9 @@ static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vect
   return ncl;
 }
 
-int cluster_map(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster) {
-  if (t.algebraic) return cluster_map_graph(t, k, cl, level_of_cluster);
-  return cluster_map_geo(t, k, cl, level_of_cluster, true);
+int stage0_cluster_map(const Tree& t, std::vector<int>& cl) {
+  if (t.algebraic) return stage0_map_graph(t, cl, nullptr);
+  return cluster_map_geo(t, 0, cl, nullptr, true);
 }
 
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
@@ -546,28 +604,21 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
   const int ell = t.nlevels;
   const int n = t.n;
   st.assign(ell, StageSym());
-  // algebraic: the cluster maps of all stages depend on the tree only and are
-  // made in parallel; stage k uses its own map and, for the parents, stage
-  // k + 1's.  Geometric: stage 0's map only, with every cluster's tree node and
-  // key; stage k + 1's clusters are stage k's interfaces grouped by node and
-  // by key without its entries of depth nlevels - 2 - k and deeper (the
-  // bisection walk of a vertex at stage k + 1 is a prefix of its walk at
-  // stage k), numbered in (node, key) order as the maps number them.
-  std::vector<std::vector<int>> maps(ell), firsts(ell);
+  // Only stage 0 maps vertices to clusters, and records every cluster's tree
+  // node and key.  Stage k + 1's clusters are stage k's interfaces grouped by
+  // node and by their key at stage k + 1, numbered in (node, key) order as a
+  // per-vertex map would number them.  Geometric: the key without its entries
+  // of depth nlevels - 2 - k and deeper (a vertex's bisection walk at stage
+  // k + 1 is a prefix of its walk at stage k).  Algebraic: the parents of the
+  // key's nodes (the depth-d ancestors of the reach are the parents of its
+  // depth-(d + 1) ones), empty for the level-(k + 1) separators.
+  std::vector<std::vector<int>> maps(ell);
   std::vector<int> nmaps(ell, 0);
   std::vector<int> cnode;
-  std::vector<uint64_t> ckey;
-  if (t.algebraic) {
-    parallel_for(ell, [&](int k, int) {
-      nmaps[k] = cluster_map(t, k, maps[k], &st[k].level);
-      // the lowest vertex of every cluster (it names the cluster's parent)
-      firsts[k].assign(nmaps[k], -1);
-      for (int v = n - 1; v >= 0; --v)
-        if (maps[k][v] >= 0) firsts[k][maps[k][v]] = v;
-    });
-  } else {
-    nmaps[0] = cluster_map_geo(t, 0, maps[0], &st[0].level, false, &cnode, &ckey);
-  }
+  std::vector<uint64_t> ckey;            // geometric keys
+  std::vector<std::vector<int>> gkey;    // algebraic keys
+  if (t.algebraic) nmaps[0] = stage0_map_graph(t, maps[0], &st[0].level, &cnode, &gkey);
+  else nmaps[0] = cluster_map_geo(t, 0, maps[0], &st[0].level, false, &cnode, &ckey);
   for (int k = 0; k < ell; ++k) {
     StageSym& S = st[k];
     S.ncl = nmaps[k];
@@ -719,9 +770,39 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     // parents at stage k+1
     S.parent.assign(S.ncl, -1);
     if (k + 1 < ell && t.algebraic) {
-      const std::vector<int>& cl_next = maps[k + 1];
-      const std::vector<int>& first = firsts[k];
-      for (int p : S.ifaces) S.parent[p] = cl_next[first[p]];
+      const int ni = (int)S.ifaces.size();
+      std::vector<std::vector<int>> key2(ni);
+      parallel_for(ni, [&](int i, int) {
+        const int p = S.ifaces[i];
+        if (S.level[p] == k + 1) return;  // separators eliminated at stage k + 1: no key
+        auto& kk = key2[i];
+        for (int a : gkey[p]) kk.push_back((a - 1) / 2);  // parents stay ascending
+        kk.erase(std::unique(kk.begin(), kk.end()), kk.end());
+      }, 256);
+      std::vector<int> ord(ni);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+        const int nx = cnode[S.ifaces[x]], ny = cnode[S.ifaces[y]];
+        if (nx != ny) return nx < ny;
+        if (key2[x] != key2[y]) return key2[x] < key2[y];
+        return x < y;
+      });
+      std::vector<int> node2;
+      std::vector<std::vector<int>> gkey2;
+      std::vector<int>& level2 = st[k + 1].level;
+      level2.clear();
+      for (int i = 0; i < ni; ++i) {
+        const int x = ord[i], p = S.ifaces[x];
+        if (i == 0 || cnode[p] != node2.back() || key2[x] != gkey2.back()) {
+          node2.push_back(cnode[p]);
+          gkey2.push_back(std::move(key2[x]));
+          level2.push_back(S.level[p]);
+        }
+        S.parent[p] = (int)node2.size() - 1;
+      }
+      nmaps[k + 1] = (int)node2.size();
+      cnode.swap(node2);
+      gkey.swap(gkey2);
     } else if (k + 1 < ell) {
       const int drop = 2 * k + 4;  // key bits of the entries of depth nlevels - 2 - k and deeper
       const uint64_t keep = drop >= 64 ? 0 : ~((uint64_t(1) << drop) - 1);
@@ -757,7 +838,6 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
       return SPAND_EINVAL;
     }
     std::vector<int>().swap(maps[k]);  // no later stage reads it
-    std::vector<int>().swap(firsts[k]);
   }
   return SPAND_OK;
 }

@@ -143,6 +143,8 @@ def test_batch_arguments_checked_without_gpu():
     (lambda: si.laplacian_2d(20), 5, 1),
     (lambda: si.laplacian_grid((9, 7, 6)), 5, 2),
     (lambda: si.diffusion_grid((30, 11), seed=2), 6, 3),
+    # large enough for the parallel pieces of the analysis (n = 140,608)
+    (lambda: si.laplacian_3d(52), 8, 4),
 ])
 def test_algebraic_partition_matches_oracle(make, ell, seed):
     """Without coordinates the library partitions A's graph; cluster maps equal the oracle's."""
