@@ -172,3 +172,45 @@ def test_prescale_rejects_nonpositive_diagonal():
     with pytest.raises(S.SpandError) as e:
         S.Spand(p.rowptr, p.colind, val, p.coords, 3, 1e-2, 1, prescale=True)
     assert e.value.code == S.SPAND_ENOTSPD
+
+
+def test_concurrent_analyses_match_sequential():
+    """Analyses on several host threads at once (the library's kept worker
+    threads serve one loop at a time; the others run on threads of their own)
+    give the same partition as one at a time."""
+    import threading
+    S = _lib()
+    probs = [(si.laplacian_3d(40), 9), (si.laplacian_grid((300, 280)), 11),
+             (si.diffusion_grid((36, 30, 28), seed=3), 9), (si.laplacian_3d(24), 7)]
+    # the algebraic partition as well: no coordinates
+    probs.append((si.laplacian_3d(30), 7))
+
+    def maps(prob, ell, algebraic):
+        coords = None if algebraic else prob.coords
+        h = S.Spand(prob.rowptr, prob.colind, prob.val, coords, ell, 0.1, 1)
+        out = [h.cluster_map(k) for k in range(ell)]
+        h.close()
+        return out
+
+    jobs = [(p, ell, i == len(probs) - 1) for i, (p, ell) in enumerate(probs)]
+    want = [maps(*j) for j in jobs]
+    got = [None] * len(jobs)
+    errors = []
+
+    def run(i):
+        try:
+            for _ in range(2):
+                got[i] = maps(*jobs[i])
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(len(jobs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for w, g in zip(want, got):
+        assert len(w) == len(g)
+        for a, b in zip(w, g):
+            assert np.array_equal(a, b)
