@@ -8,8 +8,10 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <exception>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <utility>
@@ -43,16 +45,28 @@ inline void parallel_for(int n, F&& fn, int grain = 1) {
   // do not serialise on the shared counter
   const int chunk = std::max(1, n / (nth * 16));
   std::atomic<int> next(0);
+  // an exception (a failed allocation) stops the loop and is rethrown on the
+  // calling thread once every thread has left it
+  std::exception_ptr error;
+  std::mutex error_m;
   const std::function<void(int)> work = [&](int w) {
-    for (int i0; (i0 = next.fetch_add(chunk)) < n;)
-      for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
+    try {
+      for (int i0; (i0 = next.fetch_add(chunk)) < n;)
+        for (int i = i0; i < std::min(n, i0 + chunk); ++i) fn(i, w);
+    } catch (...) {
+      std::lock_guard<std::mutex> g(error_m);
+      if (!error) error = std::current_exception();
+      next.store(n);
+    }
   };
-  if (host_pool_run(nth, work)) return;
-  // the kept threads are busy (a loop inside a loop, or another caller's)
-  std::vector<std::thread> th;
-  for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
-  work(0);
-  for (auto& x : th) x.join();
+  if (!host_pool_run(nth, work)) {
+    // the kept threads are busy (a loop inside a loop, or another caller's)
+    std::vector<std::thread> th;
+    for (int w = 1; w < nth; ++w) th.emplace_back(work, w);
+    work(0);
+    for (auto& x : th) x.join();
+  }
+  if (error) std::rethrow_exception(error);
 }
 
 // Allocator that leaves trivially constructible elements uninitialised on
