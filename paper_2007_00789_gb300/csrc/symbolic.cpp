@@ -453,10 +453,11 @@ static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int
                             std::vector<int>* node_of_cluster = nullptr,
                             std::vector<std::vector<int>>* key_of_cluster = nullptr) {
   const int n = t.n;
-  const int np = std::max(1, std::min(32, n / 65536));
-  auto piece = [&](int p) { return (int)((int64_t)n * p / np); };
   int nnode = 0;
   for (int v = 0; v < n; ++v) nnode = std::max(nnode, t.node_of[v] + 1);
+  // vertex ranges of the counting sort (counts: nodes x ranges, within 8M entries)
+  const int np = std::max(1, std::min({32, n / 65536, (1 << 23) / std::max(1, nnode)}));
+  auto piece = [&](int p) { return (int)((int64_t)n * p / np); };
   std::vector<int> at((size_t)nnode * np, 0), start(nnode + 1, 0);
   parallel_for(np, [&](int p, int) {
     for (int v = piece(p); v < piece(p + 1); ++v) ++at[(size_t)t.node_of[v] * np + p];
@@ -531,20 +532,24 @@ static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vect
                            bool full, std::vector<int>* node_of_cluster = nullptr,
                            std::vector<uint64_t>* key_of_cluster = nullptr) {
   const int n = t.n;
-  const int np = std::max(1, std::min(32, n / 65536));
+  const int np0 = std::max(1, std::min(32, n / 65536));
+  std::vector<int> pmax(np0, 0);
+  parallel_for(np0, [&](int p, int) {
+    int mx = 0;
+    for (int v = (int)((int64_t)n * p / np0); v < (int)((int64_t)n * (p + 1) / np0); ++v)
+      if (t.level_of[v] >= k) mx = std::max(mx, t.node_of[v] + 1);
+    pmax[p] = mx;
+  });
+  const int nnode = *std::max_element(pmax.begin(), pmax.end());
+  // vertex ranges of the counting sort: fewer for many nodes, so that the
+  // counts (nodes x ranges) stay within 8M entries
+  const int np = std::max(1, std::min(np0, (1 << 23) / std::max(1, nnode)));
   auto piece = [&](int p) { return (int)((int64_t)n * p / np); };
   // for every live vertex of piece p in order: fn(v)
   auto each = [&](int p, auto&& fn) {
     for (int v = piece(p); v < piece(p + 1); ++v)
       if (t.level_of[v] >= k) fn(v);
   };
-  std::vector<int> pmax(np, 0);
-  parallel_for(np, [&](int p, int) {
-    int mx = 0;
-    each(p, [&](int v) { mx = std::max(mx, t.node_of[v] + 1); });
-    pmax[p] = mx;
-  });
-  const int nnode = *std::max_element(pmax.begin(), pmax.end());
   // at[b * np + p]: vertices of node b in piece p, then where they go
   std::vector<int> at((size_t)nnode * np, 0), start(nnode + 1, 0);
   parallel_for(np, [&](int p, int) { each(p, [&](int v) { ++at[(size_t)t.node_of[v] * np + p]; }); });
