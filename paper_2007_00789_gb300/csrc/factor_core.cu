@@ -135,11 +135,6 @@ double copy_bytes(const std::vector<CopyTask>& v) {
   for (auto& t : v) b += 16.0 * t.rows * t.cols;
   return b;
 }
-double potrf_flops(const std::vector<PotrfTask>& v) {
-  double f = 0.0;
-  for (auto& t : v) f += (double)t.m * t.m * t.m / 3.0;
-  return f;
-}
 double potrf_bytes(const std::vector<PotrfTask>& v) {
   double b = 0.0;
   for (auto& t : v) b += 16.0 * t.m * t.m;
