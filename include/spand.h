@@ -132,7 +132,9 @@ typedef struct {
 /* Symbolic analysis (the multilevel spaND partitioning of §3, built
  * geometrically from grid coordinates).  Host-only: A is copied into the
  * handle and uploaded to the device by the first call that needs it
- * (spand_factor or spand_matvec), so analyze works without a GPU.
+ * (spand_factor or spand_matvec), so analyze works without a GPU.  Runs on up
+ * to 16 host threads, which the library keeps (idle) between calls; analyses
+ * may run concurrently on different handles.
  *   A       -- the matrix (host arrays, see spand_csr).
  *   coords  -- host, n x dim row-major coordinates of the unknowns (grid
  *              coordinates; only their order along each axis matters).
