@@ -447,11 +447,12 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
 // vertices bucketed by node over contiguous vertex ranges (each node's
 // vertices stay ascending), each node's vertices sorted by key (a separator
 // vertex's reach, compared as a sequence; leaves have none), then numbered
-// node by node.  node_of_cluster and key_of_cluster (optional): every
-// cluster's node and key.
+// node by node.  node_of_cluster, key_of_cluster and members (optional):
+// every cluster's node, key and vertices (ascending).
 static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int>* level_of_cluster,
                             std::vector<int>* node_of_cluster = nullptr,
-                            std::vector<std::vector<int>>* key_of_cluster = nullptr) {
+                            std::vector<std::vector<int>>* key_of_cluster = nullptr,
+                            std::vector<std::vector<int>>* members = nullptr) {
   const int n = t.n;
   int nnode = 0;
   for (int v = 0; v < n; ++v) nnode = std::max(nnode, t.node_of[v] + 1);
@@ -500,6 +501,7 @@ static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int
   if (level_of_cluster) level_of_cluster->assign(ncl, 0);
   if (node_of_cluster) node_of_cluster->assign(ncl, 0);
   if (key_of_cluster) key_of_cluster->assign(ncl, {});
+  if (members) members->assign(ncl, {});
   parallel_for(nnode, [&](int b, int) {
     int id = ncb[b] - 1;
     const auto first = order.begin() + start[b], last = order.begin() + start[b + 1];
@@ -512,6 +514,7 @@ static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int
         if (key_of_cluster && t.level_of[v] > 0) (*key_of_cluster)[id].assign(R + Rp[v], R + Rp[v + 1]);
       }
       cl[v] = id;
+      if (members) (*members)[id].push_back(v);
     }
   }, 256);
   return ncl;
@@ -521,8 +524,9 @@ static int stage0_map_graph(const Tree& t, std::vector<int>& cl, std::vector<int
 // counting-sorted by node over contiguous vertex pieces (each node's vertices
 // stay ascending), each node's vertices sorted by key, then the clusters
 // numbered node by node.  full: -1 for the vertices eliminated before stage
-// k, else their entries are left as they were.  node_of_cluster and
-// key_of_cluster (optional): every cluster's tree node and key.
+// k, else their entries are left as they were.  node_of_cluster,
+// key_of_cluster and members (optional): every cluster's tree node, key and
+// vertices (ascending).
 struct KeyedVertex {
   uint64_t key;
   int v;
@@ -530,7 +534,8 @@ struct KeyedVertex {
 };
 static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vector<int>* level_of_cluster,
                            bool full, std::vector<int>* node_of_cluster = nullptr,
-                           std::vector<uint64_t>* key_of_cluster = nullptr) {
+                           std::vector<uint64_t>* key_of_cluster = nullptr,
+                           std::vector<std::vector<int>>* members = nullptr) {
   const int n = t.n;
   const int np0 = std::max(1, std::min(32, n / 65536));
   std::vector<int> pmax(np0, 0);
@@ -583,6 +588,7 @@ static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vect
   if (level_of_cluster) level_of_cluster->assign(ncl, 0);
   if (node_of_cluster) node_of_cluster->assign(ncl, 0);
   if (key_of_cluster) key_of_cluster->assign(ncl, 0);
+  if (members) members->assign(ncl, {});
   parallel_for(nnode, [&](int b, int) {
     int id = ncb[b] - 1;
     const auto first = items.begin() + start[b], last = items.begin() + start[b + 1];
@@ -594,6 +600,7 @@ static int cluster_map_geo(const Tree& t, int k, std::vector<int>& cl, std::vect
         if (key_of_cluster) (*key_of_cluster)[id] = it->key;
       }
       cl[it->v] = id;
+      if (members) (*members)[id].push_back(it->v);
     }
   }, 256);
   return ncl;
@@ -607,10 +614,9 @@ int stage0_cluster_map(const Tree& t, std::vector<int>& cl) {
 int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, int skip,
                  std::vector<StageSym>& st, std::string& err) {
   const int ell = t.nlevels;
-  const int n = t.n;
   st.assign(ell, StageSym());
   // Only stage 0 maps vertices to clusters, and records every cluster's tree
-  // node and key.  Stage k + 1's clusters are stage k's interfaces grouped by
+  // node, key and vertices.  Stage k + 1's clusters are stage k's interfaces grouped by
   // node and by their key at stage k + 1, numbered in (node, key) order as a
   // per-vertex map would number them.  Geometric: the key without its entries
   // of depth nlevels - 2 - k and deeper (a vertex's bisection walk at stage
@@ -622,8 +628,8 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
   std::vector<int> cnode;
   std::vector<uint64_t> ckey;            // geometric keys
   std::vector<std::vector<int>> gkey;    // algebraic keys
-  if (t.algebraic) nmaps[0] = stage0_map_graph(t, maps[0], &st[0].level, &cnode, &gkey);
-  else nmaps[0] = cluster_map_geo(t, 0, maps[0], &st[0].level, false, &cnode, &ckey);
+  if (t.algebraic) nmaps[0] = stage0_map_graph(t, maps[0], &st[0].level, &cnode, &gkey, &st[0].members0);
+  else nmaps[0] = cluster_map_geo(t, 0, maps[0], &st[0].level, false, &cnode, &ckey, &st[0].members0);
   for (int k = 0; k < ell; ++k) {
     StageSym& S = st[k];
     S.ncl = nmaps[k];
@@ -640,13 +646,7 @@ int build_stages(const Tree& t, const int32_t* rowptr, const int32_t* colind, in
     S.sparsify = (k >= skip) && (k < ell - 1);
     S.adj0.assign(S.ncl, {});
     if (k == 0) {
-      S.members0.assign(S.ncl, {});
-      {  // counted first, so that each list is allocated once
-        std::vector<int> cnt(S.ncl, 0);
-        for (int v = 0; v < n; ++v) ++cnt[cl[v]];
-        for (int c = 0; c < S.ncl; ++c) S.members0[c].reserve(cnt[c]);
-      }
-      for (int v = 0; v < n; ++v) S.members0[cl[v]].push_back(v);
+      // S.members0: from the stage-0 map
       // each cluster's neighbours from its own rows (clusters in parallel)
       parallel_for(S.ncl, [&](int a, int) {
         auto& N = S.adj0[a];
