@@ -174,35 +174,64 @@ int pcg_impl(spand_s* h, const double* b, double* x, double tol, int32_t* iters,
   return rc;
 }
 
+// The first defect of row i's entries: 0 none, 1 a column out of range, 2
+// columns not strictly ascending, 3 no diagonal entry.
+int row_defect(const spand_csr* A, int i) {
+  bool diag = false;
+  for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+    const int j = A->colind[e];
+    if (j < 0 || j >= A->n) return 1;
+    if (e > A->rowptr[i] && A->colind[e - 1] >= j) return 2;
+    if (j == i) diag = true;
+  }
+  return diag ? 0 : 3;
+}
+
+// Checks the CSR and reports its first defect in row order, as a sweep over
+// the rows would meet it; the rows are checked in parallel.
 int validate_csr(const spand_csr* A, std::string& err) {
   if (!A || !A->rowptr || !A->colind || !A->val) return (err = "null CSR array", SPAND_EINVAL);
   const int n = A->n;
   if (n < 1) return (err = "n must be >= 1", SPAND_EINVAL);
   if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return (err = "rowptr inconsistent with nnz", SPAND_EINVAL);
-  std::vector<int32_t> cnt(n, 0);
-  for (int i = 0; i < n; ++i) {
-    if (A->rowptr[i + 1] < A->rowptr[i]) return (err = "rowptr not monotone", SPAND_EINVAL);
-    bool diag = false;
-    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
-      const int j = A->colind[e];
-      if (j < 0 || j >= n) return (err = "column index out of range", SPAND_EINVAL);
-      if (e > A->rowptr[i] && A->colind[e - 1] >= j) return (err = "columns not strictly ascending", SPAND_EINVAL);
-      if (j == i) diag = true;
-      ++cnt[j];
-    }
-    if (!diag) return (err = "missing diagonal entry in row " + std::to_string(i), SPAND_EINVAL);
-  }
-  // pattern symmetry: every (i, j) has (j, i)
-  for (int i = 0; i < n; ++i) {
-    if (cnt[i] != A->rowptr[i + 1] - A->rowptr[i]) return (err = "pattern is not symmetric", SPAND_EINVAL);
-  }
+  // the first row whose extent is not within [rowptr[i], nnz] (its entries are not read)
+  int bad_ptr = n;
   for (int i = 0; i < n; ++i)
+    if (A->rowptr[i + 1] < A->rowptr[i] || A->rowptr[i + 1] > A->nnz) {
+      bad_ptr = i;
+      break;
+    }
+  std::atomic<int> bad_row(bad_ptr);
+  parallel_for(bad_ptr, [&](int i, int) {
+    if (row_defect(A, i)) {
+      int cur = bad_row.load();
+      while (i < cur && !bad_row.compare_exchange_weak(cur, i)) {
+      }
+    }
+  }, 4096);
+  const int r = bad_row.load();
+  if (r < bad_ptr) {
+    const int d = row_defect(A, r);
+    err = d == 1 ? std::string("column index out of range")
+        : d == 2 ? std::string("columns not strictly ascending")
+                 : "missing diagonal entry in row " + std::to_string(r);
+    return SPAND_EINVAL;
+  }
+  if (bad_ptr < n) return (err = "rowptr not monotone", SPAND_EINVAL);
+  // pattern symmetry: every (i, j) has (j, i) (columns are ascending and in range now)
+  std::atomic<bool> asym(false);
+  parallel_for(n, [&](int i, int) {
     for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
       const int j = A->colind[e];
       const int32_t* b = A->colind + A->rowptr[j];
       const int32_t* en = A->colind + A->rowptr[j + 1];
-      if (!std::binary_search(b, en, i)) return (err = "pattern is not symmetric", SPAND_EINVAL);
+      if (!std::binary_search(b, en, i)) {
+        asym.store(true, std::memory_order_relaxed);
+        return;
+      }
     }
+  }, 4096);
+  if (asym.load()) return (err = "pattern is not symmetric", SPAND_EINVAL);
   return SPAND_OK;
 }
 

@@ -214,3 +214,50 @@ def test_concurrent_analyses_match_sequential():
         assert len(w) == len(g)
         for a, b in zip(w, g):
             assert np.array_equal(a, b)
+
+
+def test_csr_defects_reported_in_row_order():
+    """The CSR check reports the first defect in row order (rows are checked in
+    parallel), and never reads entries past a row pointer beyond nnz."""
+    S = _lib()
+    prob = si.laplacian_3d(24)  # n = 13824: several parallel chunks of rows
+    rp, ci, val = prob.rowptr.copy(), prob.colind.copy(), prob.val.copy()
+
+    def err(rp_, ci_, val_=None):
+        with pytest.raises(S.SpandError) as e:
+            S.Spand(rp_, ci_, val if val_ is None else val_, prob.coords, 5, 0.1, 1)
+        assert e.value.code == S.SPAND_EINVAL
+        return str(e.value)
+
+    def without_entry(row, col):
+        e = rp[row] + int(np.nonzero(ci[rp[row]:rp[row + 1]] == col)[0][0])
+        rp2 = rp.copy()
+        rp2[row + 1:] -= 1
+        return rp2, np.delete(ci, e), np.delete(val, e)
+
+    # missing diagonal late and early: the early row is named
+    r2, c2, v2 = without_entry(9000, 9000)
+    assert "missing diagonal entry in row 9000" in err(r2, c2, v2)
+    r2, c2, v2 = without_entry(9000, 9000)
+    c2[rp[20] + 1], c2[rp[20] + 2] = c2[rp[20] + 2], c2[rp[20] + 1]  # row 20 unsorted
+    assert "columns not strictly ascending" in err(r2, c2, v2)
+    c3 = ci.copy()
+    c3[rp[5000 + 1] - 1] = prob.n  # out of range in row 5000
+    assert "column index out of range" in err(rp, c3)
+    # a row pointer past nnz, then a decrease: reported, not read
+    r4 = rp.copy()
+    r4[100] = len(ci) + 1000
+    assert "rowptr not monotone" in err(r4, ci)
+    # entry defects in rows before a bad row pointer come first
+    r5 = r4.copy()
+    c5 = ci.copy()
+    c5[rp[10]], c5[rp[10] + 1] = c5[rp[10] + 1], c5[rp[10]]
+    assert "columns not strictly ascending" in err(r5, c5)
+    # an entry without its mirror
+    A = prob.to_scipy().tolil()
+    A[12000, 3] = -0.5
+    A = A.tocsr()
+    A.sort_indices()
+    with pytest.raises(S.SpandError) as e:
+        S.Spand(A.indptr, A.indices, A.data, prob.coords, 5, 0.1, 1)
+    assert "pattern is not symmetric" in str(e.value)
