@@ -393,19 +393,29 @@ int analyze_impl(const spand_csr* A, const double* coords, int dim, int nlevels,
   h->h_val.resize(A->nnz);
   parallel_copy(h->h_val.data(), A->val, A->nnz);
   if (h->prescale) {
-    // S = D^{-1/2}, D = diag(A); the factorization sees S A S
-    h->h_scale.assign(n, 0.0);
-    for (int i = 0; i < n; ++i)
-      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
-        if (A->colind[e] == i) {
-          if (!(A->val[e] > 0.0))
-            return fail(SPAND_ENOTSPD, "non-positive diagonal entry in row " + std::to_string(i));
-          h->h_scale[i] = 1.0 / std::sqrt(A->val[e]);
+    // S = D^{-1/2}, D = diag(A); the factorization sees S A S (rows in
+    // parallel; the first non-positive pivot in row order is reported)
+    h->h_scale.resize(n);
+    std::atomic<int> bad(n);
+    parallel_for(n, [&](int i, int) {
+      const int32_t* c = A->colind + A->rowptr[i];
+      const int64_t e = A->rowptr[i] + (std::lower_bound(c, A->colind + A->rowptr[i + 1], i) - c);
+      if (!(A->val[e] > 0.0)) {  // the diagonal is present (checked above)
+        int cur = bad.load();
+        while (i < cur && !bad.compare_exchange_weak(cur, i)) {
         }
+        h->h_scale[i] = 0.0;
+        return;
+      }
+      h->h_scale[i] = 1.0 / std::sqrt(A->val[e]);
+    }, 4096);
+    if (bad.load() < n)
+      return fail(SPAND_ENOTSPD, "non-positive diagonal entry in row " + std::to_string(bad.load()));
     h->h_fval.resize(A->nnz);
-    for (int i = 0; i < n; ++i)
+    parallel_for(n, [&](int i, int) {
       for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
         h->h_fval[e] = h->h_scale[i] * A->val[e] * h->h_scale[A->colind[e]];
+    }, 4096);
   }
   lap("copies");
   *out = h.release();

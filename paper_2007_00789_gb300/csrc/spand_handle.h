@@ -416,7 +416,7 @@ struct spand_s {
   // diagonal prescaling: the factorization is of D^{-1/2} A D^{-1/2} (values
   // d_fval) and the apply is D^{-1/2} M~ D^{-1/2}; without it d_fval = d_val
   bool prescale = false;
-  std::vector<double> h_scale, h_fval;
+  spand::host_vec<double> h_scale, h_fval;
   double* d_scale = nullptr;
   double* d_fval = nullptr;
   int64_t pack_split = 0;        // interior part / interface part of the stage-0 layout
