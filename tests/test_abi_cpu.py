@@ -261,3 +261,39 @@ def test_csr_defects_reported_in_row_order():
     with pytest.raises(S.SpandError) as e:
         S.Spand(A.indptr, A.indices, A.data, prob.coords, 5, 0.1, 1)
     assert "pattern is not symmetric" in str(e.value)
+
+
+def test_analysis_in_a_forked_child():
+    """A child forked after the library's host threads exist (which it does not
+    inherit) still analyses: it starts host threads of its own."""
+    import signal
+    import time
+    import warnings
+    S = _lib()
+    prob = si.laplacian_3d(40)  # large enough for parallel loops
+    h = S.Spand.from_problem(prob, 9, 0.1, 1)
+    want = h.cluster_map(3)
+    h.close()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", DeprecationWarning)  # fork of a threaded process
+        pid = os.fork()
+    if pid == 0:
+        code = 1
+        try:
+            signal.alarm(60)
+            hc = S.Spand.from_problem(prob, 9, 0.1, 1)
+            code = 0 if np.array_equal(hc.cluster_map(3), want) else 1
+            hc.close()
+        finally:
+            os._exit(code)
+    deadline = time.time() + 90
+    while True:
+        done, status = os.waitpid(pid, os.WNOHANG)
+        if done:
+            break
+        if time.time() > deadline:
+            os.kill(pid, signal.SIGKILL)
+            os.waitpid(pid, 0)
+            pytest.fail("the forked child's analysis did not finish")
+        time.sleep(0.05)
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
