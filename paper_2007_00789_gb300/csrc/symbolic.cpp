@@ -280,29 +280,58 @@ struct GraphBisector {
   const int32_t* rowptr;
   const int32_t* colind;
   std::vector<std::atomic<int>>& stamp;
-  std::vector<int>& dist;
-  std::vector<int> front, next;
-  std::vector<std::pair<long, int>> ord;
+  std::vector<std::atomic<int>>& dist;
+  std::vector<int> front, next, hist;
+  std::vector<std::vector<int>> found;  // per range of a wide level
+  int reach_d = 0;                      // the largest distance of the last sweep
   int cur = 0;
+  bool wide = false;  // the only box in work: its wide levels run on all threads
 
   bool inside(int u) const { return stamp[u].load(std::memory_order_relaxed) == cur; }
+  int dist_of(int v) const { return dist[v].load(std::memory_order_relaxed); }
 
-  // distances from root within the box (-1: not reached)
+  // distances from root within the box (-1: not reached).  A wide level is
+  // expanded in ranges on all threads, each vertex claimed by the one thread
+  // whose exchange finds it unreached; the distances equal the serial ones
+  // (only the order of the next level differs).
   void bfs(int root) {
-    dist[root] = 0;
+    constexpr size_t kWide = 8192;  // level size from which it is expanded in parallel
+    dist[root].store(0, std::memory_order_relaxed);
     front.assign(1, root);
+    reach_d = 0;
     int d = 0;
     while (!front.empty()) {
       next.clear();
       ++d;
-      for (int v : front)
-        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
-          const int u = colind[e];
-          if (inside(u) && dist[u] < 0) {
-            dist[u] = d;
-            next.push_back(u);
+      if (!wide || front.size() < kWide) {
+        for (int v : front)
+          for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            const int u = colind[e];
+            if (inside(u) && dist_of(u) < 0) {
+              dist[u].store(d, std::memory_order_relaxed);
+              next.push_back(u);
+            }
           }
-        }
+      } else {
+        const int nr = (int)std::min<size_t>(64, front.size() / 1024);
+        found.resize(nr);
+        parallel_for(nr, [&](int r, int) {
+          std::vector<int>& mine = found[r];
+          mine.clear();
+          const size_t b = front.size() * r / nr, en = front.size() * (r + 1) / nr;
+          for (size_t i = b; i < en; ++i) {
+            const int v = front[i];
+            for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+              const int u = colind[e];
+              if (!inside(u) || dist_of(u) >= 0) continue;
+              int unreached = -1;
+              if (dist[u].compare_exchange_strong(unreached, d, std::memory_order_relaxed)) mine.push_back(u);
+            }
+          }
+        });
+        for (const auto& f : found) next.insert(next.end(), f.begin(), f.end());
+      }
+      if (!next.empty()) reach_d = d;
       front.swap(next);
     }
   }
@@ -312,28 +341,35 @@ struct GraphBisector {
     cur = box;
     for (int v : verts) {
       stamp[v].store(cur, std::memory_order_relaxed);
-      dist[v] = -1;
+      dist[v].store(-1, std::memory_order_relaxed);
     }
     bfs(verts[0]);
     int far = -1, r1 = -1;
     for (int v : verts)
-      if (dist[v] > far) {
-        far = dist[v];
+      if (dist_of(v) > far) {
+        far = dist_of(v);
         r1 = v;
       }
-    for (int v : verts) dist[v] = -1;
+    for (int v : verts) dist[v].store(-1, std::memory_order_relaxed);
     bfs(r1);
+    // the median key: the (|V|/2)-th smallest distance, unreached vertices
+    // last (counted per distance: the keys are levels of the sweep)
     const long big = 1L << 40;
-    ord.clear();
-    ord.reserve(verts.size());
-    for (int v : verts) ord.push_back({dist[v] < 0 ? big : (long)dist[v], v});
-    std::nth_element(ord.begin(), ord.begin() + verts.size() / 2, ord.end());
-    const long med = ord[verts.size() / 2].first;
+    hist.assign(reach_d + 2, 0);
+    for (int v : verts) ++hist[dist_of(v) < 0 ? reach_d + 1 : dist_of(v)];
+    long med = big;
+    for (int k = 0, below = 0; k <= reach_d; ++k) {
+      below += hist[k];
+      if (below > (int)verts.size() / 2) {
+        med = k;
+        break;
+      }
+    }
     sep.clear();
     lo.clear();
     hi.clear();
     for (int v : verts) {
-      const long key = dist[v] < 0 ? big : (long)dist[v];
+      const long key = dist_of(v) < 0 ? big : (long)dist_of(v);
       if (med == big) {
         (key < big ? lo : hi).push_back(v);
       } else if (key == med) {
@@ -364,9 +400,10 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
   const int dmax = nlevels - 1;
   std::vector<std::atomic<int>> stamp(n);
   parallel_for(n, [&](int v, int) { stamp[v].store(0, std::memory_order_relaxed); }, 65536);
-  std::vector<int> dist(n, -1);
+  std::vector<std::atomic<int>> dist(n);
   std::vector<GraphBisector> gb;
-  for (int w = 0; w < 16; ++w) gb.push_back(GraphBisector{rowptr, colind, stamp, dist, {}, {}, {}, 0});
+  for (int w = 0; w < 16; ++w) gb.push_back(GraphBisector{rowptr, colind, stamp, dist, {}, {}, {}, {}, 0, false});
+  const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
   struct Part {
     int node;
     std::vector<int> verts;
@@ -394,7 +431,7 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
     }
     next.assign(2 * frontier.size(), Part{0, {}});
     seps.resize(frontier.size());
-    parallel_for((int)frontier.size(), [&](int bi, int w) {
+    auto cut = [&](int bi, int w) {
       Part& pt = frontier[bi];
       gb[w].bisect(pt.node + 1, pt.verts, seps[bi], next[2 * bi].verts, next[2 * bi + 1].verts);
       for (int v : seps[bi]) {
@@ -404,7 +441,16 @@ int build_tree_graph(const int32_t* rowptr, const int32_t* colind, int n, int nl
       next[2 * bi].node = 2 * pt.node + 1;
       next[2 * bi + 1].node = 2 * pt.node + 2;
       std::vector<int>().swap(pt.verts);
-    });
+    };
+    // fewer boxes than threads (the first depths): one box at a time, its
+    // wide sweep levels on all threads; else the boxes in parallel
+    const bool few = frontier.size() <= 2 && nth > 2;
+    gb[0].wide = few;
+    if (few) {
+      for (int bi = 0; bi < (int)frontier.size(); ++bi) cut(bi, 0);
+    } else {
+      parallel_for((int)frontier.size(), cut);
+    }
     frontier.swap(next);
   }
   // reach sets, by increasing level (a level's vertices in parallel: they read

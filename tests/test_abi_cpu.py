@@ -297,3 +297,31 @@ def test_analysis_in_a_forked_child():
             pytest.fail("the forked child's analysis did not finish")
         time.sleep(0.05)
     assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+
+
+@pytest.mark.parametrize("comps,ell,seed", [
+    ([(8, 8), (8, 8)], 3, 0),             # the first sweep reaches exactly half: empty separator
+    ([(5, 4), (9, 7)], 3, 3),
+    ([(4, 4), (4, 4), (6, 6)], 3, 4),
+    ([(10,), (10,), (10,), (10,)], 3, 5),
+    ([(7, 7), (7, 7)], 4, 6),
+])
+def test_algebraic_partition_of_disconnected_graphs(comps, ell, seed):
+    """Graphs of several components (unreached vertices in the breadth-first
+    sweeps, medians among them): the library's partition equals the oracle's."""
+    import scipy.sparse as sp
+    from paper_2007_00789_gb300 import spand as S
+    A = sp.block_diag([si.laplacian_grid(c).to_scipy() for c in comps]).tocsr()
+    n = A.shape[0]
+    perm = np.random.default_rng(seed).permutation(n)
+    A = A[perm][:, perm].tocsr()
+    A.sort_indices()
+    tree = P.graph_nested_dissection(A.indptr, A.indices, ell)
+    h = S.Spand(A.indptr, A.indices, A.data, None, ell, 1e-2, 1)
+    for k in range(ell):
+        sc = P.stage_clusters(tree, k)
+        want = np.full(n, -1)
+        for ci, key in enumerate(sc.keys):
+            want[sc.members[key]] = ci
+        assert np.array_equal(h.cluster_map(k), want), k
+    h.close()
